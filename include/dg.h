@@ -1,0 +1,202 @@
+/*
+ * dg.h -- C ABI of the GB300 tree-based dGSEM library (arXiv 2404.16648, hot path).
+ *
+ * The library advances the perturbation form of the compressible Euler equations
+ * (rho', rho u, rho theta' about a hydrostatic background; Sec. 2.1, Eq. "eulervector") with a
+ * nodal strong-form discontinuous Galerkin spectral element method on LGL nodes (Sec. 2.2),
+ * on a 2:1-balanced forest of quad/oct-trees of axis-aligned boxes (Sec. 3.1), with Rusanov
+ * fluxes (Sec. 2.2), mortars on hanging faces and conservative L2 solution transfer on
+ * refinement/coarsening (Sec. 3.3), and explicit SSP-RK3 time stepping with one uniform dt
+ * (Sec. 3.1: no subcycling).
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a dg_status; DG_OK is 0.  No call throws or aborts; on failure
+ *    dg_last_error(mesh) returns a human-readable detail string owned by the mesh.
+ *  - Coordinates: a 2D mesh is the vertical x-z plane (axis 0 = x, axis 1 = z); a 3D mesh
+ *    is x, y, z.  The last axis is vertical; gravity acts along -z.
+ *  - Prognostic variables, in order: rho', U_0 .. U_{d-1} (momentum), Theta' (= (rho theta)').
+ *    nv = d + 2.
+ *  - State layout ("SoA"): q[v][e][n], v < nv, e < dg_num_elements(), n < (N+1)^d with node
+ *    n = i_0 + (N+1) i_1 + (N+1)^2 i_2 (axis 0 fastest), elements in the current leaf order
+ *    (roots lexicographic with x fastest, Morton order inside each root).  The element type
+ *    is double for DG_FP64 and float for DG_FP32_PERT.
+ *  - Device pointers passed in are caller-owned and must hold the full state; host pointers
+ *    likewise.  The library owns every buffer it allocates and frees it in dg_mesh_destroy.
+ *  - Calls on one mesh are not thread-safe; distinct meshes may be used from distinct threads.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = 1,          /* invalid argument (null pointer, size, range, layout) */
+  DG_ERR_CUDA = 2,         /* a CUDA runtime call failed; detail in dg_last_error */
+  DG_ERR_OOM = 3,          /* device or host allocation failed */
+  DG_ERR_STATE = 4,        /* non-finite value detected in the state */
+  DG_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
+  DG_ERR_UNSUPPORTED = 6   /* combination not compiled in (dimension, degree, precision) */
+} dg_status;
+
+enum { DG_FP64 = 0, DG_FP32_PERT = 1 };   /* dg_mesh_desc.precision */
+enum { DG_HOST = 0, DG_DEVICE = 1 };      /* where a state pointer lives */
+enum { DG_CRIT_THETA = 0, DG_CRIT_FLAGS = 1 };  /* dg_adapt_params.criterion */
+
+#define DG_NUM_INTEGRALS 5
+#define DG_MAX_N 8
+#define DG_MAX_LEVEL 12
+
+/* Mesh description.  Defaults for the physics are theta0 = 300 K, p0 = 1e5 Pa, g = 9.81,
+ * R = 287, cp = 1004.5 (the paper gives none; Sec. 4.3 gives theta0 = 300 K). */
+typedef struct {
+  int32_t dim;          /* 2 (x-z) or 3 */
+  int32_t N;            /* polynomial degree, 1..DG_MAX_N; (N+1)^d LGL nodes per element */
+  int32_t base[3];      /* root cells per axis (forest of trees, Sec. 3.1); base[2] unused in 2D */
+  double length[3];     /* box extents in metres; the box is [0, length[a]] per axis */
+  int32_t max_level;    /* deepest refinement level, 0..DG_MAX_LEVEL */
+  int32_t precision;    /* DG_FP64 or DG_FP32_PERT (FP32 state and flux arithmetic; FP64 for
+                           the background, the pressure perturbation and the integrals) */
+  double theta0, p0, g, R, cp;
+  double nu;            /* artificial viscosity (m^2/s); only 0 is supported */
+} dg_mesh_desc;
+
+/* Cosine-bell potential-temperature bubble (Sec. 4.2 Eq. cosine-bell, Sec. 4.3):
+ * theta' = amp (1 + cos(pi r)) for r <= 1, r = |(x - center) / radius| per axis, plus an
+ * optional random Fourier-feature field sigma sqrt(2/K) sum_k cos(k_k . x + phase_k).
+ * The state is set to Theta' = 0, U = 0, rho' = -rho_bar theta' / (theta0 + theta'), which
+ * keeps the pressure hydrostatic.  rff_k is [n_rff][3] (host), rff_phase [n_rff] (host). */
+typedef struct {
+  double center[3];
+  double radius[3];
+  double amp;
+  int32_t n_rff;
+  double rff_sigma;
+  const double* rff_k;
+  const double* rff_phase;
+} dg_bubble_desc;
+
+/* Regrid parameters (Sec. 3.2.1: regrid every T steps with a buffer of B cells; Sec. 3.1).
+ * criterion DG_CRIT_THETA tags a leaf when max over its nodes of |theta'| > threshold;
+ * DG_CRIT_FLAGS uses flags[e] != 0 (host array, one byte per current leaf).  A tagged leaf
+ * below max_level is refined together with its B-hop face neighbourhood; refinement is closed
+ * under the 2:1 rule; a family of 2^d leaf siblings is coarsened when none of them is tagged,
+ * within the buffer or refined, and no face neighbour would end finer than the siblings. */
+typedef struct {
+  double threshold;
+  int32_t buffer;       /* B, face-adjacency hops */
+  int32_t max_level;    /* -1: use the mesh's max_level */
+  int32_t criterion;
+  const uint8_t* flags;
+} dg_adapt_params;
+
+typedef struct {
+  int64_t elements_before;
+  int64_t elements_after;
+  int64_t refined;      /* leaves that were split */
+  int64_t coarsened;    /* families that were merged */
+} dg_adapt_report;
+
+typedef struct dg_mesh dg_mesh;
+
+/* Creates a uniform level-0 forest of base[0] x base[1] (x base[2]) roots with a zero state
+ * (the hydrostatic atmosphere at rest).  `stream` is a cudaStream_t (NULL: legacy default
+ * stream) used by every later call on this mesh.  On success *out owns all device memory. */
+dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out);
+
+/* Frees everything; NULL is allowed. */
+void dg_mesh_destroy(dg_mesh* mesh);
+
+int64_t dg_num_elements(const dg_mesh* mesh);
+int64_t dg_num_nodes(const dg_mesh* mesh);       /* elements x (N+1)^d */
+
+/* Leaves in the current order as rows of 5 int32: root index, level, c_0, c_1, c_2 (integer
+ * coordinates at the leaf's level; c_2 = 0 in 2D).  `cap` is the number of int32 in `out`. */
+dg_status dg_get_leaves(const dg_mesh* mesh, int32_t* out, size_t cap);
+
+/* Face lists in the canonical order (Sec. 3.3 mortars).  Counts are always written.  When the
+ * matching array is non-NULL and its capacity (in rows) suffices it is filled:
+ *   conforming rows (3 int32): low element, high element, axis;
+ *   mortar rows (3 + 4 int32): coarse element, axis, side (0 low, 1 high), fine elements in
+ *     Morton order over the tangential axes (unused slots -1);
+ *   boundary rows (3 int32): element, axis, side. */
+dg_status dg_get_faces(const dg_mesh* mesh, int64_t counts[3], int32_t* conforming, size_t cap_c,
+                       int32_t* mortars, size_t cap_m, int32_t* boundary, size_t cap_b);
+
+/* Copies a state in (out) in the layout above; where = DG_HOST or DG_DEVICE.  Synchronous. */
+dg_status dg_set_state(dg_mesh* mesh, const void* q, int where);
+dg_status dg_get_state(dg_mesh* mesh, void* q, int where);
+
+/* Evaluates the initial condition analytically at the current nodes (FP64 on the device). */
+dg_status dg_set_bubble(dg_mesh* mesh, const dg_bubble_desc* bubble);
+
+/* dq/dt of the strong-form dGSEM (Sec. 2.2) for the caller's device state q (same layout and
+ * type as the mesh state), written to the caller's device buffer dqdt.  Pure: the mesh state is
+ * untouched.  Asynchronous on `stream` (NULL: the mesh stream). */
+dg_status dg_rhs(dg_mesh* mesh, const void* q, void* dqdt, void* stream);
+
+/* nsteps SSP-RK3 steps of size dt on the mesh state (Shu-Osher form), asynchronous on
+ * `stream` (NULL: the mesh stream).  Three fused stage launches per step. */
+dg_status dg_step(dg_mesh* mesh, double dt, int32_t nsteps, void* stream);
+
+/* One regrid pass with conservative transfer of the state (Sec. 3.3).  Synchronous: the
+ * criterion is evaluated on the device, the tree work runs on the host, the transfer on the
+ * device.  Element order and count change; state pointers obtained earlier stay valid only as
+ * copies.  `report` may be NULL. */
+dg_status dg_adapt(dg_mesh* mesh, const dg_adapt_params* params, dg_adapt_report* report);
+
+/* Per-element refinement indicator max_n |theta'| (FP64), written to host `out` (E doubles). */
+dg_status dg_indicator(dg_mesh* mesh, double* out, size_t cap);
+
+/* Domain integrals with weights w_i w_j (w_k) |J|, accumulated in FP64 with compensated
+ * (Neumaier) sums and a fixed reduction order: out = {mass, total energy
+ * (p cv/R + |U|^2/(2 rho) + rho g z), kinetic energy, volume, perturbation mass int rho'}.
+ * Synchronous; DG_ERR_STATE if a non-finite value was met (out is still written). */
+dg_status dg_integrals(dg_mesh* mesh, double out[DG_NUM_INTEGRALS]);
+
+/* Kernel timing: when enabled, the fused stage launches of dg_step are bracketed by CUDA
+ * events on the mesh stream; dg_stage_timing returns the summed milliseconds and launch count
+ * since the last reset (synchronises the stream). */
+dg_status dg_enable_timing(dg_mesh* mesh, int32_t enable);
+dg_status dg_stage_timing(dg_mesh* mesh, double* total_ms, int64_t* launches, int32_t reset);
+
+/* ---- Host-only forest (no CUDA call): the same tree code dg_adapt runs, exposed so the
+ * integer work (leaf order, 2:1 balance, face and mortar lists, transfer map) can be checked
+ * on machines without a GPU.  Sec. 3.1 (forest of trees, active leaves), Sec. 3.2.1 (T, B),
+ * Sec. 4.3 (2:1 balance). */
+typedef struct dg_forest dg_forest;
+
+/* Uniform level-0 forest of base[0] x base[1] (x base[2]) roots. */
+dg_status dg_forest_create(int32_t dim, const int32_t base[3], int32_t max_level, dg_forest** out);
+void dg_forest_destroy(dg_forest* forest);
+int64_t dg_forest_size(const dg_forest* forest);
+/* Leaves as in dg_get_leaves. */
+dg_status dg_forest_leaves(const dg_forest* forest, int32_t* out, size_t cap);
+/* Face lists as in dg_get_faces. */
+dg_status dg_forest_faces(const dg_forest* forest, int64_t counts[3], int32_t* conforming,
+                          size_t cap_c, int32_t* mortars, size_t cap_m, int32_t* boundary,
+                          size_t cap_b);
+/* One regrid pass with the rules of dg_adapt_params on explicit flags (one byte per leaf).
+ * When `transfer` is non-NULL and cap >= 9 x (new leaf count) it receives one row of 9 int32
+ * per new leaf: kind (0 keep, 1 child, 2 parent), then keep: old leaf; child: parent, child
+ * index; parent: the 2^d old children in child-index order (unused slots -1).  Returns the
+ * new leaf count through *new_size. */
+dg_status dg_forest_regrid(dg_forest* forest, const uint8_t* flags, int32_t buffer,
+                           int32_t max_level, int32_t* transfer, size_t cap, int64_t* new_size);
+
+/* Detail of the last error on this mesh (never NULL). */
+const char* dg_last_error(const dg_mesh* mesh);
+
+/* Library version string. */
+const char* dg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

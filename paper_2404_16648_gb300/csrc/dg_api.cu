@@ -1,0 +1,456 @@
+// C ABI of the GB300 dGSEM library (declared in include/dg.h).
+//
+// A dg_mesh owns: the host forest (tree.hpp), the 1D operators (basis.hpp), and device buffers
+// for three state copies (q^n and two RK stage states), the per-element integer tables, the
+// FP64 background, the mortar flux buffer, and the integral reduction scratch.  Regrids
+// rebuild the tables and transfer q^n; the stage states are reallocated with it.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "basis.hpp"
+#include "dg_launch.hpp"
+#include "tree.hpp"
+
+struct dg_mesh {
+  dg_mesh_desc desc{};
+  int D = 2, N = 1, n1 = 2, NP = 4, NV = 4, NSUB = 2, NF = 2;
+  int prec = 0;
+  size_t tsize = 8;
+  cudaStream_t stream = nullptr;
+  dgl::Forest forest;
+  dgl::Basis1D basis;
+  dgk::PhysC ph{};
+  double root_h[3] = {1, 1, 1};
+  int64_t E = 0, G = 0, cap = 0;
+  std::vector<int32_t> conf, mort, bnd;
+  // device buffers
+  void* q[3] = {nullptr, nullptr, nullptr};
+  int32_t* d_elem = nullptr;
+  int32_t* d_conn = nullptr;
+  int32_t* d_groups = nullptr;
+  double* d_bg = nullptr;
+  void* d_mbuf = nullptr;
+  void* d_ops = nullptr;       // precision T
+  double* d_opsd = nullptr;    // FP64: D, P0, P1, C0, C1, w, x
+  double* d_partial = nullptr;
+  double* d_out = nullptr;
+  int* d_bad = nullptr;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  std::string err;
+};
+
+namespace {
+
+dg_status fail(dg_mesh* m, dg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (m) m->err = buf;
+  return st;
+}
+
+#define CU(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      return fail(m, e_ == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,     \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                   \
+  } while (0)
+
+void dfree(void* p) { if (p) cudaFree(p); }
+
+int64_t plane(const dg_mesh* m) { return m->E * m->NP; }
+
+dg_status upload_ops(dg_mesh* m) {
+  const int nn = m->n1 * m->n1;
+  std::vector<double> od;
+  od.insert(od.end(), m->basis.D.begin(), m->basis.D.end());
+  od.insert(od.end(), m->basis.P[0].begin(), m->basis.P[0].end());
+  od.insert(od.end(), m->basis.P[1].begin(), m->basis.P[1].end());
+  od.insert(od.end(), m->basis.C[0].begin(), m->basis.C[0].end());
+  od.insert(od.end(), m->basis.C[1].begin(), m->basis.C[1].end());
+  od.insert(od.end(), m->basis.w.begin(), m->basis.w.end());
+  od.insert(od.end(), m->basis.x.begin(), m->basis.x.end());
+  (void)nn;
+  CU(cudaMalloc(&m->d_opsd, od.size() * sizeof(double)));
+  CU(cudaMemcpy(m->d_opsd, od.data(), od.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CU(cudaMalloc(&m->d_ops, od.size() * m->tsize));
+  if (m->prec == DG_FP64) {
+    CU(cudaMemcpy(m->d_ops, od.data(), od.size() * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> of(od.begin(), od.end());
+    CU(cudaMemcpy(m->d_ops, of.data(), of.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  return DG_OK;
+}
+
+const double* d_w(const dg_mesh* m) { return m->d_opsd + 5 * m->n1 * m->n1; }
+const double* d_x(const dg_mesh* m) { return m->d_opsd + 5 * m->n1 * m->n1 + m->n1; }
+
+// (Re)builds the device tables for the current forest; state buffers sized for E elements.
+dg_status rebuild_topology(dg_mesh* m) {
+  m->E = m->forest.size();
+  m->forest.face_lists(&m->conf, &m->mort, &m->bnd);
+  m->G = (int64_t)(m->mort.size() / 7);
+  std::vector<int32_t> conn;
+  m->forest.connectivity(m->mort, &conn);
+  // every index a kernel will follow must be in range before anything is uploaded
+  const int nf = 2 * m->D;
+  for (int64_t r = 0; r < m->E * nf; ++r) {
+    const int32_t* c = conn.data() + r * 5;
+    bool ok = true;
+    switch (c[0]) {
+      case dgl::FACE_WALL: break;
+      case dgl::FACE_CONF: ok = c[1] >= 0 && c[1] < m->E; break;
+      case dgl::FACE_FINE: ok = c[1] >= 0 && c[1] < m->E && c[2] >= 0 && c[2] < m->G && c[3] >= 0 && c[3] < m->NSUB; break;
+      case dgl::FACE_COARSE: ok = c[1] >= 0 && c[1] < m->G; break;
+      default: ok = false;
+    }
+    if (!ok) return fail(m, DG_ERR_STATE, "inconsistent connectivity at element %lld face %d",
+                         (long long)(r / nf), (int)(r % nf));
+  }
+  for (int64_t g = 0; g < m->G; ++g)
+    for (int k = 0; k < 3 + m->NSUB; ++k) {
+      const int32_t v = m->mort[g * 7 + k];
+      const bool ok = k == 0 || k >= 3 ? (v >= 0 && v < m->E) : (v >= 0 && v < (k == 1 ? m->D : 2));
+      if (!ok) return fail(m, DG_ERR_STATE, "inconsistent mortar group %lld", (long long)g);
+    }
+  std::vector<int32_t> elem((size_t)m->E * 4);
+  const auto& L = m->forest.leaves();
+  for (int64_t e = 0; e < m->E; ++e) {
+    elem[e * 4] = L[e].level;
+    for (int a = 0; a < 3; ++a) elem[e * 4 + 1 + a] = L[e].c[a];
+  }
+  dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
+  m->d_elem = nullptr; m->d_conn = nullptr; m->d_groups = nullptr; m->d_bg = nullptr; m->d_mbuf = nullptr;
+  CU(cudaMalloc(&m->d_elem, elem.size() * sizeof(int32_t)));
+  CU(cudaMemcpy(m->d_elem, elem.data(), elem.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CU(cudaMalloc(&m->d_conn, conn.size() * sizeof(int32_t)));
+  CU(cudaMemcpy(m->d_conn, conn.data(), conn.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (m->G > 0) {
+    CU(cudaMalloc(&m->d_groups, m->mort.size() * sizeof(int32_t)));
+    CU(cudaMemcpy(m->d_groups, m->mort.data(), m->mort.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CU(cudaMalloc(&m->d_mbuf, (size_t)m->G * (1 + m->NSUB) * m->NV * m->NF * m->tsize));
+  }
+  CU(cudaMalloc(&m->d_bg, (size_t)m->E * m->n1 * 4 * sizeof(double)));
+  CU(dgk::launch_background((int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), m->root_h[m->D - 1],
+                            m->ph, m->d_bg, m->stream));
+  return DG_OK;
+}
+
+dg_status alloc_states(dg_mesh* m, void* q[3]) {
+  const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
+  for (int i = 0; i < 3; ++i) {
+    q[i] = nullptr;
+    CU(cudaMalloc(&q[i], bytes > 0 ? bytes : 16));
+  }
+  return DG_OK;
+}
+
+dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* qn, void* out, int mode,
+                          double dt, double ca, double cb, cudaStream_t s) {
+  if (m->G > 0) {
+    dgk::MortarArgs M{qs, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, m->d_ops, m->ph};
+    bool ok = m->prec == DG_FP64
+                  ? (m->D == 2 ? dgk::launch_mortar_f64_2d(m->N, M, s) : dgk::launch_mortar_f64_3d(m->N, M, s))
+                  : (m->D == 2 ? dgk::launch_mortar_f32_2d(m->N, M, s) : dgk::launch_mortar_f32_3d(m->N, M, s));
+    if (!ok) return fail(m, DG_ERR_UNSUPPORTED, "mortar kernel for N=%d not compiled", m->N);
+    CU(cudaGetLastError());
+  }
+  dgk::StageArgs A{};
+  A.qs = qs; A.qn = qn; A.out = out; A.mbuf = m->d_mbuf; A.plane = plane(m); A.E = (int32_t)m->E;
+  A.elem = m->d_elem; A.conn = m->d_conn; A.bg = m->d_bg; A.ops = m->d_ops;
+  for (int a = 0; a < 3; ++a) A.root_h[a] = m->root_h[a];
+  A.dt = dt; A.ca = ca; A.cb = cb; A.mode = mode; A.ph = m->ph;
+  const bool timed = m->timing && mode == 1;
+  if (timed) {
+    while (m->ev.size() < m->ev_used + 2) {
+      cudaEvent_t e;
+      CU(cudaEventCreate(&e));
+      m->ev.push_back(e);
+    }
+    CU(cudaEventRecord(m->ev[m->ev_used], s));
+  }
+  bool ok = m->prec == DG_FP64
+                ? (m->D == 2 ? dgk::launch_stage_f64_2d(m->N, A, s) : dgk::launch_stage_f64_3d(m->N, A, s))
+                : (m->D == 2 ? dgk::launch_stage_f32_2d(m->N, A, s) : dgk::launch_stage_f32_3d(m->N, A, s));
+  if (!ok) return fail(m, DG_ERR_UNSUPPORTED, "stage kernel for N=%d not compiled", m->N);
+  CU(cudaGetLastError());
+  if (timed) {
+    CU(cudaEventRecord(m->ev[m->ev_used + 1], s));
+    m->ev_used += 2;
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dg_version(void) { return "gb300-dgsem 0.1 (sm_103a)"; }
+
+const char* dg_last_error(const dg_mesh* m) { return m ? m->err.c_str() : "null mesh"; }
+
+dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) {
+  dg_mesh* m = nullptr;
+  if (!desc || !out) return DG_ERR_ARG;
+  *out = nullptr;
+  if (desc->dim != 2 && desc->dim != 3) return DG_ERR_ARG;
+  if (desc->N < 1 || desc->N > DG_MAX_N) return DG_ERR_ARG;
+  if (desc->max_level < 0 || desc->max_level > DG_MAX_LEVEL) return DG_ERR_ARG;
+  if (desc->precision != DG_FP64 && desc->precision != DG_FP32_PERT) return DG_ERR_ARG;
+  if (desc->nu != 0.0) return DG_ERR_UNSUPPORTED;
+  for (int a = 0; a < desc->dim; ++a) {
+    if (desc->base[a] < 1 || !(desc->length[a] > 0.0)) return DG_ERR_ARG;
+    if (((int64_t)desc->base[a] << desc->max_level) >= (1 << 19)) return DG_ERR_ARG;
+  }
+  if (!(desc->p0 > 0.0) || !(desc->R > 0.0) || !(desc->cp > desc->R) || !(desc->theta0 > 0.0))
+    return DG_ERR_ARG;
+  m = new (std::nothrow) dg_mesh();
+  if (!m) return DG_ERR_OOM;
+  m->desc = *desc;
+  m->D = desc->dim; m->N = desc->N; m->n1 = m->N + 1;
+  m->NP = m->D == 3 ? m->n1 * m->n1 * m->n1 : m->n1 * m->n1;
+  m->NF = m->D == 3 ? m->n1 * m->n1 : m->n1;
+  m->NV = m->D + 2; m->NSUB = 1 << (m->D - 1);
+  m->prec = desc->precision;
+  m->tsize = m->prec == DG_FP64 ? sizeof(double) : sizeof(float);
+  m->stream = (cudaStream_t)stream;
+  m->ph.theta0 = desc->theta0; m->ph.p0 = desc->p0; m->ph.g = desc->g; m->ph.R = desc->R;
+  m->ph.cp = desc->cp; m->ph.cv = desc->cp - desc->R; m->ph.gamma = desc->cp / (desc->cp - desc->R);
+  int base[3] = {desc->base[0], desc->base[1], desc->dim == 3 ? desc->base[2] : 1};
+  for (int a = 0; a < 3; ++a) m->root_h[a] = a < m->D ? desc->length[a] / base[a] : 1.0;
+  m->forest = dgl::Forest(m->D, base, desc->max_level);
+  m->basis = dgl::make_basis(m->N);
+  dg_status st = upload_ops(m);
+  if (st == DG_OK) st = rebuild_topology(m);
+  if (st == DG_OK) st = alloc_states(m, m->q);
+  if (st == DG_OK) {
+    if (cudaMalloc(&m->d_partial, dgk::integrals_scratch_doubles() * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&m->d_out, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&m->d_bad, sizeof(int)) != cudaSuccess)
+      st = fail(m, DG_ERR_OOM, "scratch allocation failed");
+  }
+  if (st == DG_OK) {
+    if (cudaMemsetAsync(m->q[0], 0, (size_t)m->NV * plane(m) * m->tsize, m->stream) != cudaSuccess ||
+        cudaStreamSynchronize(m->stream) != cudaSuccess)
+      st = fail(m, DG_ERR_CUDA, "initialisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  if (st != DG_OK) { dg_mesh_destroy(m); return st; }
+  *out = m;
+  return DG_OK;
+}
+
+void dg_mesh_destroy(dg_mesh* m) {
+  if (!m) return;
+  if (m->stream) cudaStreamSynchronize(m->stream); else cudaDeviceSynchronize();
+  for (int i = 0; i < 3; ++i) dfree(m->q[i]);
+  dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
+  dfree(m->d_ops); dfree(m->d_opsd); dfree(m->d_partial); dfree(m->d_out); dfree(m->d_bad);
+  for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  delete m;
+}
+
+int64_t dg_num_elements(const dg_mesh* m) { return m ? m->E : 0; }
+int64_t dg_num_nodes(const dg_mesh* m) { return m ? m->E * m->NP : 0; }
+
+dg_status dg_get_leaves(const dg_mesh* mc, int32_t* out, size_t cap) {
+  dg_mesh* m = const_cast<dg_mesh*>(mc);
+  if (!m || !out) return DG_ERR_ARG;
+  if (cap < (size_t)m->E * 5) return fail(m, DG_ERR_ARG, "leaf buffer too small");
+  const auto& L = m->forest.leaves();
+  for (int64_t e = 0; e < m->E; ++e) {
+    out[e * 5] = m->forest.root_index(L[e]);
+    out[e * 5 + 1] = L[e].level;
+    for (int a = 0; a < 3; ++a) out[e * 5 + 2 + a] = L[e].c[a];
+  }
+  return DG_OK;
+}
+
+dg_status dg_get_faces(const dg_mesh* mc, int64_t counts[3], int32_t* conforming, size_t cap_c,
+                       int32_t* mortars, size_t cap_m, int32_t* boundary, size_t cap_b) {
+  dg_mesh* m = const_cast<dg_mesh*>(mc);
+  if (!m || !counts) return DG_ERR_ARG;
+  counts[0] = (int64_t)m->conf.size() / 3;
+  counts[1] = (int64_t)m->mort.size() / 7;
+  counts[2] = (int64_t)m->bnd.size() / 3;
+  if (conforming && cap_c >= (size_t)counts[0]) std::memcpy(conforming, m->conf.data(), m->conf.size() * 4);
+  if (mortars && cap_m >= (size_t)counts[1]) std::memcpy(mortars, m->mort.data(), m->mort.size() * 4);
+  if (boundary && cap_b >= (size_t)counts[2]) std::memcpy(boundary, m->bnd.data(), m->bnd.size() * 4);
+  return DG_OK;
+}
+
+dg_status dg_set_state(dg_mesh* m, const void* q, int where) {
+  if (!m || !q || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
+  const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
+  CU(cudaMemcpyAsync(m->q[0], q, bytes, where == DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, m->stream));
+  CU(cudaStreamSynchronize(m->stream));
+  return DG_OK;
+}
+
+dg_status dg_get_state(dg_mesh* m, void* q, int where) {
+  if (!m || !q || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
+  const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
+  CU(cudaMemcpyAsync(q, m->q[0], bytes, where == DG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, m->stream));
+  CU(cudaStreamSynchronize(m->stream));
+  return DG_OK;
+}
+
+dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) {
+  if (!m || !b) return fail(m, DG_ERR_ARG, "bad argument");
+  for (int a = 0; a < m->D; ++a)
+    if (!(b->radius[a] > 0.0)) return fail(m, DG_ERR_ARG, "bubble radius must be positive");
+  if (b->n_rff < 0 || (b->n_rff > 0 && (!b->rff_k || !b->rff_phase)))
+    return fail(m, DG_ERR_ARG, "bad random-feature arguments");
+  double* dk = nullptr;
+  double* dp = nullptr;
+  if (b->n_rff > 0) {
+    CU(cudaMalloc(&dk, (size_t)b->n_rff * 3 * sizeof(double)));
+    CU(cudaMalloc(&dp, (size_t)b->n_rff * sizeof(double)));
+    CU(cudaMemcpy(dk, b->rff_k, (size_t)b->n_rff * 3 * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dp, b->rff_phase, (size_t)b->n_rff * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  const double scale = b->n_rff > 0 ? b->rff_sigma * std::sqrt(2.0 / b->n_rff) : 0.0;
+  cudaError_t e = dgk::launch_bubble(m->prec, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), m->root_h,
+                                     m->d_bg, b->center, b->radius, b->amp, b->n_rff, scale, dk, dp,
+                                     m->ph.theta0, m->q[0], plane(m), m->stream);
+  cudaError_t e2 = cudaStreamSynchronize(m->stream);
+  dfree(dk); dfree(dp);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(m, DG_ERR_CUDA, "bubble kernel failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  return DG_OK;
+}
+
+dg_status dg_rhs(dg_mesh* m, const void* q, void* dqdt, void* stream) {
+  if (!m || !q || !dqdt) return fail(m, DG_ERR_ARG, "bad argument");
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  return launch_rhs_pass(m, q, nullptr, dqdt, 0, 0.0, 0.0, 1.0, s);
+}
+
+dg_status dg_step(dg_mesh* m, double dt, int32_t nsteps, void* stream) {
+  if (!m || nsteps < 0 || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  for (int32_t it = 0; it < nsteps; ++it) {
+    // Shu-Osher SSP-RK3: q1 = q + dt L(q); q2 = 3/4 q + 1/4 (q1 + dt L(q1));
+    // q^{n+1} = 1/3 q + 2/3 (q2 + dt L(q2)), the last one written over q^n
+    dg_status st = launch_rhs_pass(m, m->q[0], m->q[0], m->q[1], 1, dt, 0.0, 1.0, s);
+    if (st == DG_OK) st = launch_rhs_pass(m, m->q[1], m->q[0], m->q[2], 1, dt, 0.75, 0.25, s);
+    if (st == DG_OK) st = launch_rhs_pass(m, m->q[2], m->q[0], m->q[0], 1, dt, 1.0 / 3.0, 2.0 / 3.0, s);
+    if (st != DG_OK) return st;
+  }
+  return DG_OK;
+}
+
+dg_status dg_indicator(dg_mesh* m, double* out, size_t cap) {
+  if (!m || !out || cap < (size_t)m->E) return fail(m, DG_ERR_ARG, "bad argument");
+  double* d = nullptr;
+  CU(cudaMalloc(&d, (size_t)(m->E > 0 ? m->E : 1) * sizeof(double)));
+  cudaError_t e = dgk::launch_indicator(m->prec, (int32_t)m->E, m->n1, m->D, m->d_bg, m->q[0], plane(m),
+                                        m->ph.theta0, d, m->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)m->E * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "indicator failed: %s", cudaGetErrorString(e));
+  return DG_OK;
+}
+
+dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
+  if (!m || !p) return fail(m, DG_ERR_ARG, "bad argument");
+  if (p->buffer < 0) return fail(m, DG_ERR_ARG, "buffer must be >= 0");
+  const int maxl = p->max_level < 0 ? m->desc.max_level : p->max_level;
+  if (maxl > m->desc.max_level) return fail(m, DG_ERR_ARG, "max_level above the mesh limit");
+  std::vector<uint8_t> tag((size_t)m->E, 0);
+  if (p->criterion == DG_CRIT_FLAGS) {
+    if (!p->flags) return fail(m, DG_ERR_ARG, "flags missing");
+    for (int64_t e = 0; e < m->E; ++e) tag[e] = p->flags[e] ? 1 : 0;
+  } else if (p->criterion == DG_CRIT_THETA) {
+    std::vector<double> ind((size_t)m->E);
+    dg_status st = dg_indicator(m, ind.data(), ind.size());
+    if (st != DG_OK) return st;
+    for (int64_t e = 0; e < m->E; ++e) tag[e] = ind[e] > p->threshold ? 1 : 0;
+  } else {
+    return fail(m, DG_ERR_ARG, "unknown criterion");
+  }
+  dgl::Forest nf;
+  std::vector<dgl::TransferEntry> tmap;
+  int64_t nref = 0, ncoarse = 0;
+  std::string why;
+  if (!m->forest.regrid(tag, p->buffer, maxl, &nf, &tmap, &nref, &ncoarse, &why))
+    return fail(m, DG_ERR_STATE, "regrid failed: %s", why.c_str());
+  const int64_t E_old = m->E;
+  const int64_t plane_old = plane(m);
+  std::vector<int32_t> tm(tmap.size() * 9);
+  for (size_t i = 0; i < tmap.size(); ++i) {
+    tm[i * 9] = tmap[i].kind;
+    for (int k = 0; k < 8; ++k) tm[i * 9 + 1 + k] = tmap[i].src[k];
+  }
+  int32_t* d_tm = nullptr;
+  CU(cudaMalloc(&d_tm, tm.size() * sizeof(int32_t) + 4));
+  CU(cudaMemcpy(d_tm, tm.data(), tm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  m->forest = std::move(nf);
+  void* oldq[3] = {m->q[0], m->q[1], m->q[2]};
+  dg_status st = rebuild_topology(m);
+  void* newq[3] = {nullptr, nullptr, nullptr};
+  if (st == DG_OK) st = alloc_states(m, newq);
+  if (st == DG_OK) {
+    cudaError_t e = dgk::launch_transfer(m->prec, (int32_t)m->E, m->n1, m->D, d_tm, m->d_opsd, oldq[0],
+                                         plane_old, newq[0], plane(m), m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) st = fail(m, DG_ERR_CUDA, "transfer failed: %s", cudaGetErrorString(e));
+  }
+  cudaFree(d_tm);
+  if (st != DG_OK) return st;
+  for (int i = 0; i < 3; ++i) { dfree(oldq[i]); m->q[i] = newq[i]; }
+  if (rep) {
+    rep->elements_before = E_old;
+    rep->elements_after = m->E;
+    rep->refined = nref;
+    rep->coarsened = ncoarse;
+  }
+  return DG_OK;
+}
+
+dg_status dg_integrals(dg_mesh* m, double out[DG_NUM_INTEGRALS]) {
+  if (!m || !out) return fail(m, DG_ERR_ARG, "bad argument");
+  CU(cudaMemsetAsync(m->d_bad, 0, sizeof(int), m->stream));
+  CU(dgk::launch_integrals(m->prec, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), d_w(m), m->root_h,
+                           m->d_bg, m->q[0], plane(m), m->ph, m->d_partial, m->d_bad, m->d_out, m->stream));
+  int bad = 0;
+  CU(cudaMemcpyAsync(out, m->d_out, DG_NUM_INTEGRALS * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  CU(cudaMemcpyAsync(&bad, m->d_bad, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  CU(cudaStreamSynchronize(m->stream));
+  if (bad) return fail(m, DG_ERR_STATE, "non-finite value in the state");
+  return DG_OK;
+}
+
+dg_status dg_enable_timing(dg_mesh* m, int32_t enable) {
+  if (!m) return DG_ERR_ARG;
+  m->timing = enable != 0;
+  return DG_OK;
+}
+
+dg_status dg_stage_timing(dg_mesh* m, double* total_ms, int64_t* launches, int32_t reset) {
+  if (!m || !total_ms || !launches) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->ev_used > 0) CU(cudaEventSynchronize(m->ev[m->ev_used - 1]));
+  double sum = 0.0;
+  for (size_t i = 0; i + 1 < m->ev_used; i += 2) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, m->ev[i], m->ev[i + 1]));
+    sum += ms;
+  }
+  *total_ms = sum;
+  *launches = (int64_t)(m->ev_used / 2);
+  if (reset) m->ev_used = 0;
+  return DG_OK;
+}
+
+}  // extern "C"

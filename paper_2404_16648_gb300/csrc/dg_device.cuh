@@ -1,0 +1,364 @@
+// Device kernels of the GB300 tree-based dGSEM hot path (sm_103a).
+//
+// Per SSP-RK3 stage two launches:
+//  * mortar_kernel: one CTA per hanging face (Sec. 3.3 mortar method).  Projects the coarse
+//    trace onto the 2^(d-1) mortars (P = M^{-1} S, exact interpolation), solves the Rusanov
+//    problem on every mortar node against the fine traces (the fine face is the mortar:
+//    identity projection), stores F* for the fine sides and the back-projection
+//    sum_m s M^{-1} S^T F*_m (s = 1/2 per tangential axis) for the coarse side.
+//  * stage_kernel: one thread per LGL node, EPB elements per CTA.  Volume term of the strong
+//    form (Sec. 2.2): flux at the node, D applied along each axis through shared memory
+//    (sum factorisation), buoyancy source; face terms: Rusanov on conforming faces and walls
+//    (mirror state), precomputed mortar fluxes on hanging faces, lifted with 2/(h w_0); then the
+//    Shu-Osher stage combination, written in place of the caller's output.
+//
+// Face fluxes use explicitly rounded arithmetic (__dadd_rn etc.), so the two elements that
+// share a conforming face compute bit-identical F* and the scheme conserves mass and Theta
+// to the rounding of the update itself.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dgk {
+
+struct PhysC {
+  double theta0, p0, g, R, cp, cv, gamma;
+};
+
+enum { FACE_WALL = 0, FACE_CONF = 1, FACE_FINE = 2, FACE_COARSE = 3 };
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
+
+// Pressure perturbation P(Theta_bar + Theta') - P(Theta_bar) in FP64 through the exact identity
+// P_bar * ((1 + Theta'/Theta_bar)^gamma - 1) = P_bar * expm1(gamma * log1p(Theta'/Theta_bar)),
+// free of the cancellation between two ~1e5 Pa values (EOS of Sec. 2.1).
+__device__ __forceinline__ double pressure_pert(double tp, double Tb, double pb, double gamma) {
+  return __dmul_rn(pb, expm1(__dmul_rn(gamma, log1p(__ddiv_rn(tp, Tb)))));
+}
+
+// Component `a` of the Euler flux (Sec. 2.1, Eq. "eulervector") at one node, perturbation form:
+// rho': U_a;  U_b: U_b u_a + P' delta_ab;  Theta': (Theta_bar + Theta') u_a.
+// Optionally the wave speed |u_a| + c with c = sqrt(gamma P / rho) of the total state.
+// `ppd` is pressure_pert of this state (computed once per node by the caller).
+template <class T, int D>
+__device__ __forceinline__ void flux_axis(const T* q, double rb, double Tb, double pb,
+                                          double ppd, int a, const PhysC& ph, T* F, T* speed) {
+  const T rho = add_rn((T)rb, q[0]);
+  const T ua = div_rn(q[1 + a], rho);
+  const T pp = (T)ppd;
+  F[0] = q[1 + a];
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    T f = mul_rn(q[1 + b], ua);
+    if (b == a) f = add_rn(f, pp);
+    F[1 + b] = f;
+  }
+  F[D + 1] = mul_rn(add_rn((T)Tb, q[D + 1]), ua);
+  if (speed) {
+    const T P = (T)__dadd_rn(pb, ppd);
+    const T c = sqrt_rn(div_rn(mul_rn((T)ph.gamma, P), rho));
+    *speed = add_rn(ua < (T)0 ? -ua : ua, c);
+  }
+}
+
+// Rusanov flux along +axis a (Sec. 2.2): F* = (F(qm) + F(qp))/2 - lambda/2 (qp - qm),
+// lambda = max(|u_a| + c) over both sides.  qm is the low side, qp the high side.
+template <class T, int D>
+__device__ __forceinline__ void rusanov(const T* qm, double rbm, double Tbm, double pbm, double ppm,
+                                        const T* qp, double rbp, double Tbp, double pbp, double ppp,
+                                        int a, const PhysC& ph, T* Fs) {
+  constexpr int NV = D + 2;
+  T Fm[NV], Fp[NV], sm, sp;
+  flux_axis<T, D>(qm, rbm, Tbm, pbm, ppm, a, ph, Fm, &sm);
+  flux_axis<T, D>(qp, rbp, Tbp, pbp, ppp, a, ph, Fp, &sp);
+  const T hl = mul_rn((T)0.5, sm > sp ? sm : sp);
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    Fs[v] = sub_rn(mul_rn((T)0.5, add_rn(Fm[v], Fp[v])), mul_rn(hl, sub_rn(qp[v], qm[v])));
+}
+
+struct StageArgs {
+  const void* qs;        // stage input state (T), planes of `plane` entries per variable
+  const void* qn;        // q^n for the Shu-Osher combination (T)
+  void* out;             // output (T): dq/dt (mode 0) or the next stage state (mode 1)
+  const void* mbuf;      // mortar fluxes [G][1 + 2^(d-1)][NV][NF] (T)
+  int64_t plane;         // entries per variable plane (elements x nodes)
+  int32_t E;
+  const int32_t* elem;   // [E][4]: level, c0, c1, c2
+  const int32_t* conn;   // [E][2d][5] (see tree.cpp)
+  const double* bg;      // [E][N+1][4]: rho_bar, Theta_bar, p_bar, 1/Theta_bar at the z-nodes
+  const void* ops;       // (T) D, P0, P1, C0, C1 (n1 x n1 each), w (n1)
+  double root_h[3];
+  double dt, ca, cb;
+  int32_t mode;
+  PhysC ph;
+};
+
+struct MortarArgs {
+  const void* qs;
+  void* mbuf;
+  int64_t plane;
+  int32_t G;
+  const int32_t* groups; // [G][7]: coarse element, axis, side, fine elements (Morton order)
+  const double* bg;
+  const void* ops;
+  PhysC ph;
+};
+
+template <int D, int N>
+__device__ __forceinline__ int face_node(int a, int side, int t) {
+  // element node index of tangential position t on face (a, side); tangential axes ascending,
+  // the lower one fastest
+  constexpr int n1 = N + 1;
+  int idx[3] = {0, 0, 0};
+  idx[a] = side ? N : 0;
+  int r = t;
+#pragma unroll
+  for (int b = 0; b < D; ++b)
+    if (b != a) { idx[b] = r % n1; r /= n1; }
+  return idx[0] + n1 * (idx[1] + n1 * idx[2]);
+}
+
+template <class T, int D, int N, int EPB>
+__global__ void __launch_bounds__(EPB * ipow(N + 1, D))
+stage_kernel(const StageArgs A) {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  constexpr int NSUB = 1 << (D - 1);
+  __shared__ T sD[n1 * n1];
+  __shared__ T sF[EPB][NV][NP];
+  const int tid = threadIdx.x;
+  const T* ops = (const T*)A.ops;
+  for (int i = tid; i < n1 * n1; i += blockDim.x) sD[i] = ops[i];
+  const T w0 = ops[5 * n1 * n1];
+  const int le = tid / NP, n = tid - le * NP;
+  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const bool valid = e < A.E;
+  int idx[3];
+  idx[0] = n % n1;
+  idx[1] = (n / n1) % n1;
+  idx[2] = (D == 3) ? n / (n1 * n1) : 0;
+  const T* qs = (const T*)A.qs;
+  T q[NV], acc[NV], inv2h[D];
+  double rb = 1.0, Tb = 1.0, pb = 1.0, pp = 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { q[v] = (T)0; acc[v] = (T)0; }
+#pragma unroll
+  for (int a = 0; a < D; ++a) inv2h[a] = (T)0;
+  if (valid) {
+    const size_t base = (size_t)e * NP + n;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = qs[(size_t)v * A.plane + base];
+    const int level = A.elem[e * 4];
+#pragma unroll
+    for (int a = 0; a < D; ++a) inv2h[a] = (T)(2.0 / ldexp(A.root_h[a], -level));
+    const double* b = A.bg + ((size_t)e * n1 + idx[D - 1]) * 4;
+    rb = b[0]; Tb = b[1]; pb = b[2];
+    pp = pressure_pert((double)q[D + 1], Tb, pb, A.ph.gamma);
+    acc[D] = -(q[0] * (T)A.ph.g);   // buoyancy -rho' g on the vertical momentum
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    T F[NV];
+    flux_axis<T, D>(q, rb, Tb, pb, pp, a, A.ph, F, nullptr);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sF[le][v][n] = F[v];
+    __syncthreads();
+    if (valid) {
+      const int stride = ipow(n1, a) ;
+      const int ia = idx[a];
+      const int b0 = n - ia * stride;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T s = (T)0;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) s = fma(sD[ia * n1 + m], sF[le][v][b0 + m * stride], s);
+        acc[v] -= inv2h[a] * s;
+      }
+    }
+    __syncthreads();
+  }
+  if (!valid) return;
+  const T* mbuf = (const T*)A.mbuf;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (idx[a] != (s ? N : 0)) continue;
+      const int32_t* c = A.conn + ((size_t)e * 2 * D + 2 * a + s) * 5;
+      const int kind = c[0];
+      int t = 0, mul = 1;
+#pragma unroll
+      for (int b = 0; b < D; ++b)
+        if (b != a) { t += idx[b] * mul; mul *= n1; }
+      T Fs[NV];
+      if (kind == FACE_WALL) {
+        T gq[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) gq[v] = q[v];
+        gq[1 + a] = -q[1 + a];
+        if (s) rusanov<T, D>(q, rb, Tb, pb, pp, gq, rb, Tb, pb, pp, a, A.ph, Fs);
+        else   rusanov<T, D>(gq, rb, Tb, pb, pp, q, rb, Tb, pb, pp, a, A.ph, Fs);
+      } else if (kind == FACE_CONF) {
+        // the neighbour's matching node: same tangential indices, opposite face; its z (hence
+        // its background) is bit-identical to this node's
+        const int64_t nb = c[1];
+        const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
+        const int nn = n + ((s ? 0 : N) - idx[a]) * stride_a;
+        T qo[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) qo[v] = qs[(size_t)v * A.plane + (size_t)nb * NP + nn];
+        const double ppo = pressure_pert((double)qo[D + 1], Tb, pb, A.ph.gamma);
+        if (s) rusanov<T, D>(q, rb, Tb, pb, pp, qo, rb, Tb, pb, ppo, a, A.ph, Fs);
+        else   rusanov<T, D>(qo, rb, Tb, pb, ppo, q, rb, Tb, pb, pp, a, A.ph, Fs);
+      } else {
+        const int64_t g = (kind == FACE_FINE) ? c[2] : c[1];
+        const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
+        const T* src = mbuf + (((size_t)g * (1 + NSUB) + slot) * NV) * NF + t;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fs[v] = src[(size_t)v * NF];
+      }
+      T Fo[NV];
+      flux_axis<T, D>(q, rb, Tb, pb, pp, a, A.ph, Fo, nullptr);
+      const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += coef * (Fs[v] - Fo[v]);
+    }
+  }
+  T* out = (T*)A.out;
+  const size_t base = (size_t)e * NP + n;
+  if (A.mode == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[(size_t)v * A.plane + base] = acc[v];
+  } else if (A.ca == 0.0) {
+    const T dt = (T)A.dt;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[(size_t)v * A.plane + base] = q[v] + dt * acc[v];
+  } else {
+    const T dt = (T)A.dt, ca = (T)A.ca, cb = (T)A.cb;
+    const T* qn = (const T*)A.qn;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const size_t k = (size_t)v * A.plane + base;
+      out[k] = ca * qn[k] + cb * (q[v] + dt * acc[v]);
+    }
+  }
+}
+
+// One CTA per mortar group; NSUB * NF threads: thread (m, t) owns mortar node t of mortar m.
+template <class T, int D, int N>
+__global__ void __launch_bounds__((1 << (D - 1)) * ipow(N + 1, D - 1))
+mortar_kernel(const MortarArgs A) {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  constexpr int NSUB = 1 << (D - 1);
+  __shared__ T sP[2][n1 * n1], sC[2][n1 * n1];
+  __shared__ T sQc[NV][NF];
+  __shared__ T sT[NSUB][NV][NF];
+  __shared__ T sM[NSUB][NV][NF];
+  const int tid = threadIdx.x;
+  const T* ops = (const T*)A.ops;
+  for (int i = tid; i < n1 * n1; i += blockDim.x) {
+    sP[0][i] = ops[1 * n1 * n1 + i];
+    sP[1][i] = ops[2 * n1 * n1 + i];
+    sC[0][i] = ops[3 * n1 * n1 + i];
+    sC[1][i] = ops[4 * n1 * n1 + i];
+  }
+  const int g = blockIdx.x;
+  const int32_t* row = A.groups + (size_t)g * 7;
+  const int64_t ec = row[0];
+  const int a = row[1], side = row[2];
+  const int m = tid / NF, t = tid - m * NF;
+  const T* qs = (const T*)A.qs;
+  for (int i = tid; i < NV * NF; i += blockDim.x) {
+    const int v = i / NF, tt = i - v * NF;
+    sQc[v][tt] = qs[(size_t)v * A.plane + (size_t)ec * NP + face_node<D, N>(a, side, tt)];
+  }
+  __syncthreads();
+  // sub-face bits of mortar m over the tangential axes (lower axis first)
+  const int b0 = m & 1, b1 = (m >> 1) & 1;
+  const int t0 = t % n1, t1 = t / n1;
+  // coarse trace -> mortar m, first tangential axis
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T s = (T)0;
+#pragma unroll
+    for (int j = 0; j < n1; ++j) s = fma(sP[b0][t0 * n1 + j], sQc[v][j + n1 * t1], s);
+    sT[m][v][t] = s;
+  }
+  __syncthreads();
+  if (D == 3) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T s = (T)0;
+#pragma unroll
+      for (int j = 0; j < n1; ++j) s = fma(sP[b1][t1 * n1 + j], sT[m][v][t0 + n1 * j], s);
+      sM[m][v][t] = s;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sM[m][v][t] = sT[m][v][t];
+  }
+  __syncthreads();
+  // Rusanov on mortar node (m, t); the fine face is the mortar (identity projection)
+  const int64_t ef = row[3 + m];
+  const int nf = face_node<D, N>(a, 1 - side, t);
+  T qf[NV], qc[NV], Fs[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    qf[v] = qs[(size_t)v * A.plane + (size_t)ef * NP + nf];
+    qc[v] = sM[m][v][t];
+  }
+  const int kf = (D == 3) ? nf / (n1 * n1) : nf / n1;
+  const double* b = A.bg + ((size_t)ef * n1 + kf) * 4;
+  const double ppf = pressure_pert((double)qf[D + 1], b[1], b[2], A.ph.gamma);
+  const double ppc = pressure_pert((double)qc[D + 1], b[1], b[2], A.ph.gamma);
+  if (side) rusanov<T, D>(qc, b[0], b[1], b[2], ppc, qf, b[0], b[1], b[2], ppf, a, A.ph, Fs);
+  else      rusanov<T, D>(qf, b[0], b[1], b[2], ppf, qc, b[0], b[1], b[2], ppc, a, A.ph, Fs);
+  T* mb = (T*)A.mbuf + ((size_t)g * (1 + NSUB) * NV) * NF;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    mb[((size_t)(1 + m) * NV + v) * NF + t] = Fs[v];
+    sM[m][v][t] = Fs[v];
+  }
+  __syncthreads();
+  // back to the coarse face: sum_m (C_b1 x C_b0) F*_m
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    T s = (T)0;
+#pragma unroll
+    for (int j = 0; j < n1; ++j) s = fma(sC[b0][t0 * n1 + j], sM[m][v][j + n1 * t1], s);
+    sT[m][v][t] = s;
+  }
+  __syncthreads();
+  if (m == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T acc = (T)0;
+      for (int mm = 0; mm < NSUB; ++mm) {
+        if (D == 3) {
+          const int c1 = (mm >> 1) & 1;
+          T s = (T)0;
+#pragma unroll
+          for (int j = 0; j < n1; ++j) s = fma(sC[c1][t1 * n1 + j], sT[mm][v][t0 + n1 * j], s);
+          acc += s;
+        } else {
+          acc += sT[mm][v][t];
+        }
+      }
+      mb[(size_t)v * NF + t] = acc;
+    }
+  }
+}
+
+}  // namespace dgk

@@ -1,0 +1,40 @@
+// Internal launch interface between the C ABI (dg_api.cu) and the kernel translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dg_device.cuh"
+
+namespace dgk {
+
+constexpr int NUM_INTEGRALS = 5;
+
+// Fused RK stage (or pure RHS) and mortar launches; return false when (D, N) is not compiled.
+bool launch_stage_f64_2d(int N, const StageArgs& A, cudaStream_t s);
+bool launch_stage_f64_3d(int N, const StageArgs& A, cudaStream_t s);
+bool launch_stage_f32_2d(int N, const StageArgs& A, cudaStream_t s);
+bool launch_stage_f32_3d(int N, const StageArgs& A, cudaStream_t s);
+bool launch_mortar_f64_2d(int N, const MortarArgs& A, cudaStream_t s);
+bool launch_mortar_f64_3d(int N, const MortarArgs& A, cudaStream_t s);
+bool launch_mortar_f32_2d(int N, const MortarArgs& A, cudaStream_t s);
+bool launch_mortar_f32_3d(int N, const MortarArgs& A, cudaStream_t s);
+
+cudaError_t launch_background(int32_t E, int n1, int D, const int32_t* elem, const double* xi,
+                              double root_hz, const PhysC& ph, double* bg, cudaStream_t s);
+cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* elem,
+                          const double* xi, const double* root_h, const double* bg,
+                          const double* center, const double* radius, double amp, int n_rff,
+                          double rff_scale, const double* rff_k, const double* rff_phase,
+                          double theta0, void* q, int64_t plane, cudaStream_t s);
+cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
+                             int64_t plane, double theta0, double* out, cudaStream_t s);
+size_t integrals_scratch_doubles();
+cudaError_t launch_integrals(int prec, int32_t E, int n1, int D, const int32_t* elem,
+                             const double* xi, const double* w, const double* root_h,
+                             const double* bg, const void* q, int64_t plane, const PhysC& ph,
+                             double* partial, int* bad, double* out, cudaStream_t s);
+cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, const int32_t* tmap,
+                            const double* ops, const void* qold, int64_t plane_old, void* qnew,
+                            int64_t plane_new, cudaStream_t s);
+
+}  // namespace dgk

@@ -1,0 +1,11 @@
+// Stage and mortar kernels, float state, 3D.
+#include "stage_inst.cuh"
+
+namespace dgk {
+bool launch_stage_f32_3d(int N, const StageArgs& A, cudaStream_t s) {
+  return stage_dispatch<float, 3>(N, A, s);
+}
+bool launch_mortar_f32_3d(int N, const MortarArgs& A, cudaStream_t s) {
+  return mortar_dispatch<float, 3>(N, A, s);
+}
+}  // namespace dgk

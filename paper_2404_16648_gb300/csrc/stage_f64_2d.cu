@@ -1,0 +1,11 @@
+// Stage and mortar kernels, double state, 2D.
+#include "stage_inst.cuh"
+
+namespace dgk {
+bool launch_stage_f64_2d(int N, const StageArgs& A, cudaStream_t s) {
+  return stage_dispatch<double, 2>(N, A, s);
+}
+bool launch_mortar_f64_2d(int N, const MortarArgs& A, cudaStream_t s) {
+  return mortar_dispatch<double, 2>(N, A, s);
+}
+}  // namespace dgk

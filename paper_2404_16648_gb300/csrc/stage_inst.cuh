@@ -1,0 +1,52 @@
+// Instantiates the stage and mortar kernels of one (precision, dimension) for N = 1..8.
+// Included by stage_<prec>_<dim>.cu with DG_T and DG_D defined.
+#include "dg_launch.hpp"
+
+namespace dgk {
+namespace {
+
+template <class T, int D, int N>
+void run_stage(const StageArgs& A, cudaStream_t s) {
+  constexpr int NP = ipow(N + 1, D);
+  constexpr int EPB = NP >= 128 ? 1 : 256 / NP;
+  const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
+  if (blocks) stage_kernel<T, D, N, EPB><<<blocks, EPB * NP, 0, s>>>(A);
+}
+
+template <class T, int D, int N>
+void run_mortar(const MortarArgs& A, cudaStream_t s) {
+  if (A.G) mortar_kernel<T, D, N><<<A.G, (1 << (D - 1)) * ipow(N + 1, D - 1), 0, s>>>(A);
+}
+
+template <class T, int D>
+bool stage_dispatch(int N, const StageArgs& A, cudaStream_t s) {
+  switch (N) {
+    case 1: run_stage<T, D, 1>(A, s); return true;
+    case 2: run_stage<T, D, 2>(A, s); return true;
+    case 3: run_stage<T, D, 3>(A, s); return true;
+    case 4: run_stage<T, D, 4>(A, s); return true;
+    case 5: run_stage<T, D, 5>(A, s); return true;
+    case 6: run_stage<T, D, 6>(A, s); return true;
+    case 7: run_stage<T, D, 7>(A, s); return true;
+    case 8: run_stage<T, D, 8>(A, s); return true;
+    default: return false;
+  }
+}
+
+template <class T, int D>
+bool mortar_dispatch(int N, const MortarArgs& A, cudaStream_t s) {
+  switch (N) {
+    case 1: run_mortar<T, D, 1>(A, s); return true;
+    case 2: run_mortar<T, D, 2>(A, s); return true;
+    case 3: run_mortar<T, D, 3>(A, s); return true;
+    case 4: run_mortar<T, D, 4>(A, s); return true;
+    case 5: run_mortar<T, D, 5>(A, s); return true;
+    case 6: run_mortar<T, D, 6>(A, s); return true;
+    case 7: run_mortar<T, D, 7>(A, s); return true;
+    case 8: run_mortar<T, D, 8>(A, s); return true;
+    default: return false;
+  }
+}
+
+}  // namespace
+}  // namespace dgk

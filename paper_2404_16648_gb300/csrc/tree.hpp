@@ -1,0 +1,82 @@
+// Host forest of quad/oct-trees for the GB300 dGSEM library.
+//
+// Sec. 3.1 of arXiv 2404.16648: every base cell is the root of a tree ("forest of trees") and
+// only active leaves are stored.  Sec. 3.2.1: regrid every T steps with a buffer of B cells.
+// Sec. 4.3: 2:1 balance across all levels.  Sec. 3.3: conforming faces and hanging faces with
+// 2^(d-1) mortars.  The integer work runs on the host; its outputs (leaf order, face kinds,
+// neighbour indices, transfer map) are uploaded to the device as flat int32 arrays.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+namespace dgl {
+
+struct Leaf {
+  int32_t level;
+  int32_t c[3];   // integer coordinates at `level` (c[2] = 0 in 2D)
+};
+
+// Face kinds of an element face, as seen from that element.
+enum FaceKind : int32_t {
+  FACE_WALL = 0,     // domain boundary (no-flux wall)
+  FACE_CONF = 1,     // same-level neighbour nb[0]
+  FACE_FINE = 2,     // this element is the fine side; nb[0] is the coarse neighbour
+  FACE_COARSE = 3    // this element is the coarse side; nb[0..2^(d-1)-1] are the fine ones
+};
+
+struct FaceInfo {
+  int32_t kind;
+  int32_t nb[4];
+};
+
+// Transfer map entry for one new leaf.
+enum TransferKind : int32_t { XFER_KEEP = 0, XFER_CHILD = 1, XFER_PARENT = 2 };
+struct TransferEntry {
+  int32_t kind;
+  int32_t src[8];   // KEEP: src[0]; CHILD: src[0] parent, src[1] child index; PARENT: 2^d kids
+};
+
+class Forest {
+ public:
+  Forest() = default;
+  Forest(int dim, const int base[3], int max_level);   // uniform level-0 forest
+
+  int dim() const { return dim_; }
+  int max_level() const { return max_level_; }
+  const int* base() const { return base_; }
+  int64_t size() const { return (int64_t)leaves_.size(); }
+  const std::vector<Leaf>& leaves() const { return leaves_; }
+  int32_t root_index(const Leaf& l) const;
+
+  // -1 if (level, c) is not a leaf.
+  int32_t find(int level, const int32_t c[3]) const;
+  FaceInfo classify(int32_t e, int axis, int side) const;
+
+  // One regrid pass.  Returns false (with `err`) if the forest is not 2:1 balanced.
+  bool regrid(const std::vector<uint8_t>& tag, int B, int max_level, Forest* out,
+              std::vector<TransferEntry>* tmap, int64_t* n_refined, int64_t* n_coarsened,
+              std::string* err) const;
+
+  // Canonical face lists (see dg.h, dg_get_faces).
+  void face_lists(std::vector<int32_t>* conf, std::vector<int32_t>* mort,
+                  std::vector<int32_t>* bnd) const;
+
+  // Per element, per face f = 2*axis + side, 5 int32 (see tree.cpp); `mort` from face_lists.
+  void connectivity(const std::vector<int32_t>& mort, std::vector<int32_t>* conn) const;
+
+ private:
+  void set_leaves(std::vector<Leaf> leaves);
+  static uint64_t key(int level, const int32_t c[3]);
+  int32_t extent(int level, int axis) const { return base_[axis] << level; }
+  void neighbours(int32_t e, std::vector<int32_t>* out) const;
+
+  int dim_ = 0;
+  int base_[3] = {1, 1, 1};
+  int max_level_ = 0;
+  std::vector<Leaf> leaves_;
+  std::unordered_map<uint64_t, int32_t> index_;
+};
+
+}  // namespace dgl

@@ -1,0 +1,360 @@
+"""Thin ctypes binding of the C ABI in ``include/dg.h`` (argument marshalling only).
+
+Every step of the hot path runs in the CUDA kernels of ``libdg.so``; this module only converts
+Python/NumPy/PyTorch arguments to the C structs and pointers.  There is no CPU fallback: if
+the library is missing, importing or constructing a :class:`Mesh` raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdg.so")
+
+DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_STATE, DG_ERR_TIMEOUT, DG_ERR_UNSUPPORTED = range(7)
+DG_FP64, DG_FP32_PERT = 0, 1
+DG_HOST, DG_DEVICE = 0, 1
+DG_CRIT_THETA, DG_CRIT_FLAGS = 0, 1
+NUM_INTEGRALS = 5
+STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 4: "DG_ERR_STATE",
+                5: "DG_ERR_TIMEOUT", 6: "DG_ERR_UNSUPPORTED"}
+
+# every symbol include/dg.h declares
+EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_nodes", "dg_get_leaves",
+            "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_bubble", "dg_rhs", "dg_step",
+            "dg_adapt", "dg_indicator", "dg_integrals", "dg_enable_timing", "dg_stage_timing",
+            "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
+            "dg_forest_faces", "dg_forest_regrid", "dg_last_error", "dg_version"]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("N", ctypes.c_int32), ("base", ctypes.c_int32 * 3),
+                ("length", ctypes.c_double * 3), ("max_level", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("theta0", ctypes.c_double), ("p0", ctypes.c_double),
+                ("g", ctypes.c_double), ("R", ctypes.c_double), ("cp", ctypes.c_double),
+                ("nu", ctypes.c_double)]
+
+
+class BubbleDesc(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_double * 3), ("radius", ctypes.c_double * 3),
+                ("amp", ctypes.c_double), ("n_rff", ctypes.c_int32), ("rff_sigma", ctypes.c_double),
+                ("rff_k", ctypes.POINTER(ctypes.c_double)),
+                ("rff_phase", ctypes.POINTER(ctypes.c_double))]
+
+
+class AdaptParams(ctypes.Structure):
+    _fields_ = [("threshold", ctypes.c_double), ("buffer", ctypes.c_int32),
+                ("max_level", ctypes.c_int32), ("criterion", ctypes.c_int32),
+                ("flags", ctypes.POINTER(ctypes.c_uint8))]
+
+
+class AdaptReport(ctypes.Structure):
+    _fields_ = [("elements_before", ctypes.c_int64), ("elements_after", ctypes.c_int64),
+                ("refined", ctypes.c_int64), ("coarsened", ctypes.c_int64)]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path=None):
+    """Loads libdg.so (raises OSError if it was not built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError("libdg.so not built at %s; run __graft_entry__.build()" % p)
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, sz, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double
+    sigs = {
+        "dg_mesh_create": (i32, [ctypes.POINTER(MeshDesc), vp, ctypes.POINTER(vp)]),
+        "dg_mesh_destroy": (None, [vp]),
+        "dg_num_elements": (i64, [vp]),
+        "dg_num_nodes": (i64, [vp]),
+        "dg_get_leaves": (i32, [vp, ctypes.POINTER(ctypes.c_int32), sz]),
+        "dg_get_faces": (i32, [vp, ctypes.POINTER(ctypes.c_int64), vp, sz, vp, sz, vp, sz]),
+        "dg_set_state": (i32, [vp, vp, ctypes.c_int]),
+        "dg_get_state": (i32, [vp, vp, ctypes.c_int]),
+        "dg_set_bubble": (i32, [vp, ctypes.POINTER(BubbleDesc)]),
+        "dg_rhs": (i32, [vp, vp, vp, vp]),
+        "dg_step": (i32, [vp, dbl, i32, vp]),
+        "dg_adapt": (i32, [vp, ctypes.POINTER(AdaptParams), ctypes.POINTER(AdaptReport)]),
+        "dg_indicator": (i32, [vp, ctypes.POINTER(ctypes.c_double), sz]),
+        "dg_integrals": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "dg_enable_timing": (i32, [vp, i32]),
+        "dg_stage_timing": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]),
+        "dg_forest_create": (i32, [i32, ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(vp)]),
+        "dg_forest_destroy": (None, [vp]),
+        "dg_forest_size": (i64, [vp]),
+        "dg_forest_leaves": (i32, [vp, ctypes.POINTER(ctypes.c_int32), sz]),
+        "dg_forest_faces": (i32, [vp, ctypes.POINTER(ctypes.c_int64), vp, sz, vp, sz, vp, sz]),
+        "dg_forest_regrid": (i32, [vp, ctypes.POINTER(ctypes.c_uint8), i32, i32, vp, sz,
+                                   ctypes.POINTER(ctypes.c_int64)]),
+        "dg_last_error": (ctypes.c_char_p, [vp]),
+        "dg_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(x):
+    """(address, where) of a NumPy array (host) or a torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, DG_HOST
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr(), (DG_DEVICE if x.is_cuda else DG_HOST)
+
+
+class Mesh:
+    """A forest-of-trees dGSEM mesh with its state on the GPU (one dg_mesh handle)."""
+
+    def __init__(self, dim, N, base, length, max_level=0, precision="fp64", theta0=300.0,
+                 p0=1.0e5, g=9.81, R=287.0, cp=1004.5, nu=0.0, stream=None):
+        self.lib = load_library()
+        d = MeshDesc()
+        d.dim, d.N = dim, N
+        for a in range(3):
+            d.base[a] = int(base[a]) if a < len(base) else 1
+            d.length[a] = float(length[a]) if a < len(length) else 1.0
+        d.max_level = max_level
+        d.precision = DG_FP64 if precision == "fp64" else DG_FP32_PERT
+        d.theta0, d.p0, d.g, d.R, d.cp, d.nu = theta0, p0, g, R, cp, nu
+        self.desc = d
+        self.dim, self.N, self.nv = dim, N, dim + 2
+        self.np_ = (N + 1) ** dim
+        self.precision = precision
+        self.np_dtype = np.float64 if precision == "fp64" else np.float32
+        h = ctypes.c_void_p()
+        self._stream = stream
+        st = self.lib.dg_mesh_create(ctypes.byref(d), self._stream_ptr(stream), ctypes.byref(h))
+        if st != DG_OK:
+            raise DGError(st, "dg_mesh_create failed")
+        self.h = h
+
+    # ------------------------------------------------------------------ plumbing
+    def _stream_ptr(self, stream):
+        if stream is None:
+            return None
+        return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+    def _check(self, st):
+        if st != DG_OK:
+            raise DGError(st, self.lib.dg_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.dg_mesh_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ queries
+    @property
+    def num_elements(self):
+        return int(self.lib.dg_num_elements(self.h))
+
+    @property
+    def num_nodes(self):
+        return int(self.lib.dg_num_nodes(self.h))
+
+    @property
+    def state_shape(self):
+        return (self.nv, self.num_elements, self.np_)
+
+    def leaves(self):
+        E = self.num_elements
+        out = np.zeros((E, 5), dtype=np.int32)
+        self._check(self.lib.dg_get_leaves(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), out.size))
+        return out
+
+    def faces(self):
+        counts = (ctypes.c_int64 * 3)()
+        self._check(self.lib.dg_get_faces(self.h, counts, None, 0, None, 0, None, 0))
+        c = np.zeros((counts[0], 3), np.int32)
+        m = np.zeros((counts[1], 7), np.int32)
+        b = np.zeros((counts[2], 3), np.int32)
+        self._check(self.lib.dg_get_faces(self.h, counts, c.ctypes.data, counts[0], m.ctypes.data,
+                                          counts[1], b.ctypes.data, counts[2]))
+        return c, m, b
+
+    # ------------------------------------------------------------------ state
+    def set_state(self, q):
+        if tuple(q.shape) != self.state_shape:
+            raise ValueError("state shape %s != %s" % (tuple(q.shape), self.state_shape))
+        if isinstance(q, np.ndarray) and q.dtype != self.np_dtype:
+            raise ValueError("state dtype must be %s" % self.np_dtype)
+        p, where = _ptr(q)
+        self._check(self.lib.dg_set_state(self.h, ctypes.c_void_p(p), where))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.state_shape, dtype=self.np_dtype)
+        p, where = _ptr(out)
+        self._check(self.lib.dg_get_state(self.h, ctypes.c_void_p(p), where))
+        return out
+
+    def set_bubble(self, center, radius, amp, rff=None):
+        b = BubbleDesc()
+        for a in range(3):
+            b.center[a] = float(center[a]) if a < len(center) else 0.0
+            b.radius[a] = float(radius[a]) if a < len(radius) else 1.0
+        b.amp = amp
+        keep = []
+        if rff is not None:
+            sigma, kvec, phase = rff
+            k3 = np.zeros((len(phase), 3))
+            k3[:, :kvec.shape[1]] = kvec
+            k3 = np.ascontiguousarray(k3, dtype=np.float64)
+            ph = np.ascontiguousarray(phase, dtype=np.float64)
+            keep = [k3, ph]
+            b.n_rff = len(ph)
+            b.rff_sigma = sigma
+            b.rff_k = k3.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            b.rff_phase = ph.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        self._check(self.lib.dg_set_bubble(self.h, ctypes.byref(b)))
+        del keep
+
+    # ------------------------------------------------------------------ hot path
+    def rhs(self, q, out=None, stream=None):
+        """dq/dt for a device tensor q (shape state_shape) into a device tensor."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(q)
+        if not (q.is_cuda and out.is_cuda):
+            raise ValueError("dg_rhs takes device tensors")
+        self._check(self.lib.dg_rhs(self.h, ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                    self._stream_ptr(stream)))
+        return out
+
+    def step(self, dt, nsteps=1, stream=None):
+        self._check(self.lib.dg_step(self.h, float(dt), int(nsteps), self._stream_ptr(stream)))
+
+    def adapt(self, threshold=0.0, buffer=2, max_level=-1, flags=None):
+        p = AdaptParams()
+        p.threshold, p.buffer, p.max_level = threshold, buffer, max_level
+        keep = None
+        if flags is not None:
+            keep = np.ascontiguousarray(flags, dtype=np.uint8)
+            if keep.size != self.num_elements:
+                raise ValueError("one flag per element")
+            p.criterion = DG_CRIT_FLAGS
+            p.flags = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        else:
+            p.criterion = DG_CRIT_THETA
+        r = AdaptReport()
+        self._check(self.lib.dg_adapt(self.h, ctypes.byref(p), ctypes.byref(r)))
+        return {"before": r.elements_before, "after": r.elements_after, "refined": r.refined,
+                "coarsened": r.coarsened}
+
+    def indicator(self):
+        out = np.zeros(self.num_elements)
+        self._check(self.lib.dg_indicator(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size))
+        return out
+
+    def integrals(self, check=True):
+        out = (ctypes.c_double * NUM_INTEGRALS)()
+        st = self.lib.dg_integrals(self.h, out)
+        if check:
+            self._check(st)
+        return np.array(list(out))
+
+    def enable_timing(self, on=True):
+        self._check(self.lib.dg_enable_timing(self.h, 1 if on else 0))
+
+    def stage_timing(self, reset=True):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self.lib.dg_stage_timing(self.h, ctypes.byref(ms), ctypes.byref(n), 1 if reset else 0))
+        return ms.value, n.value
+
+
+class Forest:
+    """Host-only handle on the library's forest (no GPU needed)."""
+
+    def __init__(self, dim, base, max_level):
+        self.lib = load_library()
+        b = (ctypes.c_int32 * 3)(*[int(base[a]) if a < len(base) else 1 for a in range(3)])
+        h = ctypes.c_void_p()
+        st = self.lib.dg_forest_create(dim, b, max_level, ctypes.byref(h))
+        if st != DG_OK:
+            raise DGError(st, "dg_forest_create failed")
+        self.h = h
+        self.dim = dim
+
+    def __len__(self):
+        return int(self.lib.dg_forest_size(self.h))
+
+    def leaves(self):
+        out = np.zeros((len(self), 5), dtype=np.int32)
+        st = self.lib.dg_forest_leaves(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), out.size)
+        if st != DG_OK:
+            raise DGError(st, "dg_forest_leaves failed")
+        return out
+
+    def faces(self):
+        counts = (ctypes.c_int64 * 3)()
+        self.lib.dg_forest_faces(self.h, counts, None, 0, None, 0, None, 0)
+        c = np.zeros((counts[0], 3), np.int32)
+        m = np.zeros((counts[1], 7), np.int32)
+        b = np.zeros((counts[2], 3), np.int32)
+        st = self.lib.dg_forest_faces(self.h, counts, c.ctypes.data, counts[0], m.ctypes.data,
+                                      counts[1], b.ctypes.data, counts[2])
+        if st != DG_OK:
+            raise DGError(st, "dg_forest_faces failed")
+        return c, m, b
+
+    def regrid(self, flags, buffer, max_level=-1):
+        fl = np.ascontiguousarray(flags, dtype=np.uint8)
+        if fl.size != len(self):
+            raise ValueError("one flag per leaf")
+        cap = 9 * (len(self) << self.dim)
+        tr = np.zeros(cap, dtype=np.int32)
+        n = ctypes.c_int64()
+        st = self.lib.dg_forest_regrid(self.h, fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), buffer,
+                                       max_level, tr.ctypes.data, cap, ctypes.byref(n))
+        if st != DG_OK:
+            raise DGError(st, "dg_forest_regrid failed")
+        return tr[:9 * n.value].reshape(n.value, 9)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.dg_forest_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def adapt_initial(mesh, bubble, threshold, buffer):
+    """Adapts mesh.max_level times on the analytic bubble, re-evaluated after each pass."""
+    for _ in range(mesh.desc.max_level):
+        mesh.set_bubble(**bubble)
+        mesh.adapt(threshold=threshold, buffer=buffer)
+    mesh.set_bubble(**bubble)

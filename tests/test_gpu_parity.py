@@ -1,0 +1,199 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 RHS within 1e-12 of max|rhs| per variable (the relative-per-RHS target);
+FP64 steps, transfers and integrals within 1e-12 / 1e-13 relative; the FP32 perturbation path
+within the bound stated in each test (FP32 rounding of the state and fluxes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import dg as odg, forest as ofo, physics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2404_16648_gb300 import build as b
+    b.build()
+    import paper_2404_16648_gb300 as p
+    return p
+
+
+def _pair(pkg, dim, N, base, length, max_level=2, flags_rounds=(), precision="fp64", B=1):
+    """Library mesh and oracle mesh built independently with the same explicit flags."""
+    lm = pkg.Mesh(dim, N, base, length, max_level=max_level, precision=precision)
+    of = ofo.Forest(base, max_level)
+    for p, seed in flags_rounds:
+        flags = workloads.random_flags(len(of), p, seed)
+        lm.adapt(flags=flags, buffer=B)
+        of, _ = of.regrid(flags.astype(bool), B)
+    om = odg.Mesh(of, N, length)
+    lv = lm.leaves()
+    assert lv.shape[0] == om.E
+    np.testing.assert_array_equal(lv[:, 1], [l for l, _ in of.leaves])
+    return lm, om
+
+
+def _rel_err(got, want):
+    errs = []
+    for v in range(want.shape[0]):
+        scale = np.abs(want[v]).max()
+        errs.append(np.abs(got[v] - want[v]).max() / (scale if scale > 0 else 1.0))
+    return max(errs)
+
+
+def _gpu_rhs(lm, q):
+    import torch
+    qt = torch.from_numpy(q).cuda()
+    out = lm.rhs(qt)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+MESHES = [
+    (2, 4, (10, 10), (1000.0, 1000.0), ()),
+    (2, 4, (4, 3), (1200.0, 900.0), ((0.3, 1), (0.3, 2))),
+    (2, 7, (3, 3), (3000.0, 3000.0), ((0.3, 3),)),
+    (3, 3, (2, 2, 2), (2000.0, 2000.0, 2000.0), ((0.3, 4), (0.2, 5))),
+    (3, 7, (2, 2, 2), (2000.0, 2000.0, 2000.0), ((0.3, 6),)),
+    (2, 1, (3, 2), (300.0, 200.0), ((0.5, 7),)),
+    (3, 8, (1, 2, 1), (1000.0, 2000.0, 1000.0), ((0.5, 8),)),
+]
+
+
+@pytest.mark.parametrize("dim,N,base,length,rounds", MESHES)
+def test_rhs_parity_fp64(pkg, dim, N, base, length, rounds):
+    lm, om = _pair(pkg, dim, N, base, length, flags_rounds=rounds)
+    q = workloads.random_state(om.nv, om.E, om.np_, seed=N + 10 * dim)
+    got = _gpu_rhs(lm, q)
+    want = odg.rhs(om, q)
+    assert _rel_err(got, want) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rest_state_exactly_zero(pkg, precision):
+    lm, om = _pair(pkg, 3, 4, (2, 2, 2), (2000.0,) * 3, flags_rounds=((0.3, 9),), precision=precision)
+    import torch
+    q = torch.zeros(lm.state_shape, dtype=torch.float64 if precision == "fp64" else torch.float32,
+                    device="cuda")
+    out = lm.rhs(q)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0
+
+
+@pytest.mark.parametrize("dim,N,base,length,rounds", MESHES[:5])
+def test_rhs_parity_fp32_perturbation(pkg, dim, N, base, length, rounds):
+    # FP32 state and flux arithmetic, FP64 background and pressure perturbation.  Bound: the
+    # oracle evaluated on the FP32-rounded input, error <= 2e-5 of max|rhs| per variable.
+    lm, om = _pair(pkg, dim, N, base, length, flags_rounds=rounds, precision="fp32")
+    q32 = workloads.random_state(om.nv, om.E, om.np_, seed=N + 10 * dim, dtype=np.float32)
+    got = _gpu_rhs(lm, q32).astype(np.float64)
+    want = odg.rhs(om, q32.astype(np.float64))
+    assert _rel_err(got, want) <= 2e-5
+
+
+def test_bubble_initial_state_and_indicator(pkg):
+    cfg = workloads.RTB_2D
+    lm, om = _pair(pkg, 2, cfg["N"], cfg["base"], cfg["length"], max_level=0)
+    lm.set_bubble(**cfg["bubble"])
+    got = lm.get_state()
+    b = cfg["bubble"]
+    want = odg.state_from_theta(om, odg.bubble_theta(om, b["center"], b["radius"], b["amp"]))
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-15 * np.abs(want).max() + 1e-300)
+    np.testing.assert_allclose(lm.indicator(), odg.indicator(om, want), rtol=0, atol=1e-12)
+
+
+def test_step_parity_rising_bubble(pkg):
+    cfg = workloads.RTB_2D
+    lm, om = _pair(pkg, 2, cfg["N"], cfg["base"], cfg["length"], max_level=0)
+    lm.set_bubble(**cfg["bubble"])
+    q0 = lm.get_state()
+    nsteps = 10
+    lm.step(cfg["dt"], nsteps)
+    got = lm.get_state()
+    want = odg.step(om, q0, cfg["dt"], nsteps)
+    # compare the tendency-carrying part: state change over the steps
+    assert _rel_err(got - q0, want - q0) <= 1e-11
+
+
+def test_step_parity_hanging_3d(pkg):
+    lm, om = _pair(pkg, 3, 3, (2, 2, 2), (2000.0,) * 3, flags_rounds=((0.3, 11),))
+    q0 = workloads.random_state(om.nv, om.E, om.np_, seed=11, rho_scale=1e-4, u_scale=0.1,
+                                theta_scale=0.01)
+    lm.set_state(q0)
+    lm.step(0.002, 3)
+    got = lm.get_state()
+    want = odg.step(om, q0, 0.002, 3)
+    assert _rel_err(got - q0, want - q0) <= 1e-11
+
+
+@pytest.mark.parametrize("dim,N,base", [(2, 4, (3, 3)), (3, 3, (2, 2, 2))])
+def test_adapt_transfer_parity(pkg, dim, N, base):
+    length = tuple(1000.0 for _ in base)
+    lm, om = _pair(pkg, dim, N, base, length, flags_rounds=((0.4, 12),))
+    q = workloads.random_state(om.nv, om.E, om.np_, seed=13)
+    lm.set_state(q)
+    flags = workloads.random_flags(om.E, 0.3, 14)
+    flags[: om.E // 2] = 0
+    rep = lm.adapt(flags=flags, buffer=0)
+    of2, tmap = om.forest.regrid(flags.astype(bool), 0)
+    om2 = odg.Mesh(of2, N, length)
+    assert rep["after"] == om2.E
+    np.testing.assert_array_equal(lm.leaves()[:, 1], [l for l, _ in of2.leaves])
+    want = odg.transfer(q, om, om2, tmap)
+    got = lm.get_state()
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * np.abs(q).max())
+
+
+def test_integrals_parity(pkg):
+    lm, om = _pair(pkg, 3, 4, (2, 2, 3), (2000.0, 2000.0, 3000.0), flags_rounds=((0.3, 15),))
+    q = workloads.random_state(om.nv, om.E, om.np_, seed=16)
+    lm.set_state(q)
+    got = lm.integrals()
+    want = odg.integrals(om, q)
+    np.testing.assert_allclose(got[[0, 1, 3]], want[[0, 1, 3]], rtol=1e-14)
+    np.testing.assert_allclose(got[[2, 4]], want[[2, 4]], rtol=1e-12)
+
+
+def test_mass_conserved_through_steps_and_adapts(pkg):
+    # total mass conserved to 1e-13 relative over a run with regrids (FP64)
+    cfg = workloads.RTB_2D
+    lm = pkg.Mesh(2, 4, (5, 5), (1000.0, 1000.0), max_level=2)
+    bub = dict(center=(500.0, 350.0), radius=(250.0, 250.0), amp=0.25)
+    pkg.adapt_initial(lm, bub, threshold=0.05, buffer=1)
+    m0 = lm.integrals()
+    for _ in range(4):
+        lm.step(cfg["dt"], 5)
+        lm.adapt(threshold=0.05, buffer=1)
+    m1 = lm.integrals()
+    assert abs(m1[0] - m0[0]) <= 1e-13 * m0[0]
+    assert abs(m1[4] - m0[4]) <= 1e-13 * m0[0]
+
+
+def test_full_size_octree_sampled_parity(pkg):
+    """The benchmark's 3D octree workload at full size (16^3 roots, N = 7, two levels), GPU
+    RHS on every element against the oracle on a seeded sample of elements."""
+    cfg = workloads.BUBBLE_3D
+    b = cfg["bubble"]
+    lm = pkg.Mesh(3, cfg["N"], cfg["base"], cfg["length"], max_level=cfg["max_level"])
+    pkg.adapt_initial(lm, b, cfg["threshold"], cfg["buffer"])
+    om = odg.adapt_initial(ofo.Forest(cfg["base"], cfg["max_level"]), cfg["N"], cfg["length"],
+                           lambda m: odg.bubble_theta(m, b["center"], b["radius"], b["amp"]),
+                           cfg["threshold"], cfg["buffer"])
+    np.testing.assert_array_equal(lm.leaves()[:, 1:5][:, 0], [l for l, _ in om.forest.leaves])
+    assert om.E > 8000 and len(om.forest.face_lists()[1]) > 0
+    q = workloads.random_state(om.nv, om.E, om.np_, seed=21, rho_scale=1e-3, u_scale=1.0,
+                               theta_scale=0.2)
+    got = _gpu_rhs(lm, q)
+    sample = workloads.sample_elements(om.E, 48, seed=22)
+    _, mort, _ = om.forest.face_lists()
+    coarse = sorted({m[0] for m in mort})[:8]
+    sample = np.unique(np.concatenate([sample, coarse]))
+    want = odg.rhs(om, q, elems=sample)
+    assert _rel_err(got[:, sample], want[:, sample]) <= 1e-12
