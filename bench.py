@@ -1,0 +1,324 @@
+"""Benchmark: DOF-stage updates/s of the tree-based dGSEM hot path on one GB300.
+
+A step is one SSP-RK3 step (three fused RHS+stage launches plus the mortar launches) on the 3D
+octree warm-bubble workload (16^3 roots, N = 7, two extra levels where |theta'| > 0.05 K,
+dt = 0.005 s), with the regrid (indicator, host tree, conservative transfer) every 20 steps
+inside the timed region.  DOF-stage updates = nodes per variable x 3 stages per step.
+
+The main line is the FP32-perturbation path; the FP64 path is measured in the same run and
+reported under "fp64".  With --impl reference the oracle (plain NumPy FP64) is timed on the
+host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "DOF-stage updates/s"
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index) \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/dg_clocks_%d.csv" % os.getpid()
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + CLOCK_QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _barrier_max(t, world):
+    if world == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    x = torch.tensor([t], dtype=torch.float64, device="cuda")
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def build_mesh(pkg, cfg, precision):
+    m = pkg.Mesh(cfg["dim"], cfg["N"], cfg["base"], cfg["length"], max_level=cfg["max_level"],
+                 precision=precision)
+    pkg.adapt_initial(m, cfg["bubble"], cfg["threshold"], cfg["buffer"])
+    return m
+
+
+def stage_bytes(E, NP, NV, b, n1, D):
+    """Algorithmic HBM bytes of the three stage launches of one RK3 step: stage 1 reads q^n and
+    writes q^1; stages 2 and 3 read q^s and q^n and write the next state; every launch reads
+    the per-element tables (FP64 background column, level/coordinates, face connectivity)."""
+    nodes = E * NP
+    per_elem = n1 * 4 * 8 + 16 + 2 * D * 5 * 4
+    return nodes * NV * b * (2 + 3 + 3) + 3 * E * per_elem
+
+
+def stage_flops(E, NP, NV, n1, D):
+    """Algorithmic flops of the three stage launches of one RK3 step: the sum-factorised
+    derivative (2 NV D (N+1) per node), the D flux evaluations (D (D + 6) per node) and the
+    stage combination (4 NV per node); transcendental functions and face terms not counted."""
+    per_node = 2 * NV * D * n1 + D * (D + 6) + 4 * NV
+    return 3 * E * NP * per_node
+
+
+def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, world=1):
+    import torch
+    m = build_mesh(pkg, cfg, precision)
+    dt = cfg["dt"]
+    D, N = cfg["dim"], cfg["N"]
+    n1, NP, NV = N + 1, (N + 1) ** D, D + 2
+    b = 8 if precision == "fp64" else 4
+    for i in range(warmup):
+        m.step(dt, 1)
+    torch.cuda.synchronize()
+    m.integrals()
+    m.enable_timing(True)
+    m.stage_timing(reset=True)
+    _barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    dof_stage = 0
+    alg_bytes = 0
+    alg_flops = 0
+    launches = 0
+    ev0.record()
+    for i in range(steps):
+        E = m.num_elements
+        m.step(dt, 1)
+        dof_stage += 3 * E * NP
+        alg_bytes += stage_bytes(E, NP, NV, b, n1, D)
+        alg_flops += stage_flops(E, NP, NV, n1, D)
+        launches += 3 * (1 + (m.num_mortars > 0))   # stage (+ mortar) launches per step
+        if regrid_every and (i + 1) % regrid_every == 0:
+            m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
+            launches += 3   # indicator, transfer, background
+    ev1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    ms = _barrier_max(ms, world)
+    stage_ms, stage_launches = m.stage_timing(reset=True)
+    m.enable_timing(False)
+    integ = m.integrals()
+    out = dict(ms=ms, dof_stage=dof_stage, stage_ms=stage_ms, stage_launches=stage_launches,
+               alg_bytes=alg_bytes, alg_flops=alg_flops, launches=launches, clocks=clocks,
+               elements=m.num_elements, nodes=m.num_nodes, integrals=integ.tolist(),
+               state_bytes=NV * m.num_nodes * b, mortars=m.num_mortars)
+    return m, out
+
+
+def run_e2e(pkg, m, cfg, steps, regrid_every):
+    """Same metric through the public API with host buffers: each step copies the state in from
+    pinned host memory, advances one step and copies the state and the integrals back."""
+    import torch
+    dt = cfg["dt"]
+    dtype = torch.float64 if m.precision == "fp64" else torch.float32
+    host = torch.empty(m.state_shape, dtype=dtype).pin_memory()
+    m.get_state(host)
+    torch.cuda.synchronize()
+    h2d = d2h = 0
+    dof = 0
+    t0 = time.perf_counter()
+    for i in range(steps):
+        if tuple(host.shape) != m.state_shape:
+            host = torch.empty(m.state_shape, dtype=dtype).pin_memory()
+            m.get_state(host)
+            d2h += host.numel() * host.element_size()
+        m.set_state(host)
+        h2d += host.numel() * host.element_size()
+        m.step(dt, 1)
+        dof += 3 * m.num_nodes
+        m.get_state(host)
+        m.integrals()
+        d2h += host.numel() * host.element_size() + 5 * 8
+        if regrid_every and (i + 1) % regrid_every == 0:
+            m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    return dict(value=dof / sec, unit=METRIC, h2d_bytes_per_step=h2d // steps,
+                d2h_bytes_per_step=d2h // steps)
+
+
+def oracle_sample(cfg, n_elem=1024, reps=1, warmup=0):
+    """Times the oracle on a bounded sample: per repetition, three RHS evaluations (one RK3
+    step's worth) restricted to a contiguous block of elements of the adapted mesh."""
+    from oracle import dg as odg, forest as ofo
+    b = cfg["bubble"]
+    om = odg.adapt_initial(ofo.Forest(cfg["base"], cfg["max_level"]), cfg["N"], cfg["length"],
+                           lambda mm: odg.bubble_theta(mm, b["center"], b["radius"], b["amp"]),
+                           cfg["threshold"], cfg["buffer"])
+    q = odg.state_from_theta(om, odg.bubble_theta(om, b["center"], b["radius"], b["amp"]))
+    start = max(0, om.E // 2 - n_elem // 2)
+    elems = np.arange(start, min(om.E, start + n_elem))
+    for _ in range(warmup):
+        odg.rhs(om, q, elems=elems)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for _s in range(3):
+            odg.rhs(om, q, elems=elems)
+    sec = time.perf_counter() - t0
+    units = reps * 3 * len(elems) * om.np_
+    return units / sec, len(elems), om.E, sec
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=workloads.BUBBLE_3D["name"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    cfg = workloads.CONFIGS[args.config]
+    world, rank, local = _dist()
+    regrid_every = cfg.get("regrid_every")
+    config = {"workload": cfg["name"], "dim": cfg["dim"], "N": cfg["N"], "base": list(cfg["base"]),
+              "max_level": cfg["max_level"], "dt": cfg["dt"], "regrid_every": regrid_every,
+              "buffer": cfg["buffer"], "l2": "inputs larger than L2 (state > 129 MB)",
+              "parallelism": "replicas" if world > 1 else "single"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        rate, nel, E, sec = oracle_sample(cfg, n_elem=256, reps=max(1, args.steps),
+                                          warmup=args.warmup)
+        line = {"metric": METRIC, "value": rate, "unit": METRIC, "impl": "reference",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * sec / max(1, args.steps), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config,
+                "cpu_baseline": {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+                                 "sample": "3 RHS evaluations per step on %d of %d elements" % (nel, E)},
+                "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import paper_2404_16648_gb300 as pkg
+    pkg.load_library()
+    peaks, peak_kind = _peaks()
+    sampler = ClockSampler(local)
+    m32, r32 = run_path(pkg, cfg, "fp32", args.steps, args.warmup, regrid_every, sampler, world)
+    e2e = run_e2e(pkg, m32, cfg, max(4, min(args.steps, 20)), regrid_every)
+    m32.close()
+    r64 = None
+    if not args.no_fp64:
+        m64, r64 = run_path(pkg, cfg, "fp64", args.steps, args.warmup, regrid_every, None, world)
+        m64.close()
+    value = world * r32["dof_stage"] / (r32["ms"] / 1e3)
+    achieved = r32["alg_bytes"] / (r32["stage_ms"] / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config,
+            "precision_path": "FP32 state/flux arithmetic; FP64 background, p' and integrals",
+            "elements": r32["elements"], "nodes_per_variable": r32["nodes"],
+            "gpu_launches": r32["launches"], "mortar_groups": r32["mortars"],
+            "roofline": {"bound": "hbm", "kernel": "stage_kernel", "achieved": achieved,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                         "traffic": None, "stage_ms_per_launch": r32["stage_ms"] / max(1, r32["stage_launches"])},
+            "clocks": r32["clocks"], "e2e": e2e}
+    if r64 is not None:
+        v64 = world * r64["dof_stage"] / (r64["ms"] / 1e3)
+        fp64_peak = 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 * 4 / 1e12
+        ach64 = r64["alg_flops"] / (r64["stage_ms"] / 1e3) / 1e12
+        line["fp64"] = {"value": v64, "ms_per_step": r64["ms"] / args.steps, "dtype": "f64",
+                        "roofline": {"bound": "alu", "kernel": "stage_kernel", "achieved": ach64,
+                                     "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach64 / fp64_peak,
+                                     "peak_kind": "derived: 152 SMs x max SM clock x 4 FP64 flop/clk"},
+                        "integrals": r64["integrals"]}
+        line["fp32_over_fp64"] = value / v64
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, nel, E, sec = oracle_sample(cfg, n_elem=1024, reps=1)
+        line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+                                "sample": "3 RHS evaluations on %d of %d elements (%.1f s)" % (nel, E, sec)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -182,6 +182,12 @@ class Mesh:
         return int(self.lib.dg_num_nodes(self.h))
 
     @property
+    def num_mortars(self):
+        counts = (ctypes.c_int64 * 3)()
+        self._check(self.lib.dg_get_faces(self.h, counts, None, 0, None, 0, None, 0))
+        return int(counts[1])
+
+    @property
     def state_shape(self):
         return (self.nv, self.num_elements, self.np_)
 
