@@ -4,6 +4,7 @@
 // for three state copies (q^n and two RK stage states), the per-element integer tables, the
 // FP64 background, the mortar flux buffer, and the integral reduction scratch.  Regrids
 // rebuild the tables and transfer q^n; the stage states are reallocated with it.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -33,7 +34,10 @@ struct dg_mesh {
   int32_t* d_conn = nullptr;
   int32_t* d_groups = nullptr;
   double* d_bg = nullptr;
+  float* d_bgf = nullptr;      // FP32 copy of the background (FP32 path)
   void* d_mbuf = nullptr;
+  void* d_ppscratch = nullptr; // P' plane of a caller's state in dg_rhs
+  bool pp_valid = false;       // P' plane of q[0] matches q[0]
   void* d_ops = nullptr;       // precision T
   double* d_opsd = nullptr;    // FP64: D, P0, P1, C0, C1, w, x
   double* d_partial = nullptr;
@@ -131,7 +135,9 @@ dg_status rebuild_topology(dg_mesh* m) {
     for (int a = 0; a < 3; ++a) elem[e * 4 + 1 + a] = L[e].c[a];
   }
   dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
+  dfree(m->d_bgf); dfree(m->d_ppscratch);
   m->d_elem = nullptr; m->d_conn = nullptr; m->d_groups = nullptr; m->d_bg = nullptr; m->d_mbuf = nullptr;
+  m->d_bgf = nullptr; m->d_ppscratch = nullptr;
   CU(cudaMalloc(&m->d_elem, elem.size() * sizeof(int32_t)));
   CU(cudaMemcpy(m->d_elem, elem.data(), elem.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CU(cudaMalloc(&m->d_conn, conn.size() * sizeof(int32_t)));
@@ -142,13 +148,17 @@ dg_status rebuild_topology(dg_mesh* m) {
     CU(cudaMalloc(&m->d_mbuf, (size_t)m->G * (1 + m->NSUB) * m->NV * m->NF * m->tsize));
   }
   CU(cudaMalloc(&m->d_bg, (size_t)m->E * m->n1 * 4 * sizeof(double)));
+  if (m->prec == DG_FP32_PERT) CU(cudaMalloc(&m->d_bgf, (size_t)m->E * m->n1 * 4 * sizeof(float)));
+  CU(cudaMalloc(&m->d_ppscratch, (size_t)(m->E > 0 ? plane(m) : 1) * m->tsize));
   CU(dgk::launch_background((int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), m->root_h[m->D - 1],
-                            m->ph, m->d_bg, m->stream));
+                            m->ph, m->d_bg, m->d_bgf, m->stream));
+  m->pp_valid = false;
   return DG_OK;
 }
 
+// Each state buffer holds the NV variable planes followed by the P' plane of that state.
 dg_status alloc_states(dg_mesh* m, void* q[3]) {
-  const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
+  const size_t bytes = (size_t)(m->NV + 1) * plane(m) * m->tsize;
   for (int i = 0; i < 3; ++i) {
     q[i] = nullptr;
     CU(cudaMalloc(&q[i], bytes > 0 ? bytes : 16));
@@ -156,10 +166,19 @@ dg_status alloc_states(dg_mesh* m, void* q[3]) {
   return DG_OK;
 }
 
-dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* qn, void* out, int mode,
-                          double dt, double ca, double cb, cudaStream_t s) {
+void* pp_plane(const dg_mesh* m, void* q) {
+  return (char*)q + (size_t)m->NV * plane(m) * m->tsize;
+}
+
+const void* bgt(const dg_mesh* m) {
+  return m->prec == DG_FP64 ? (const void*)m->d_bg : (const void*)m->d_bgf;
+}
+
+dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const void* qn, void* out,
+                          void* pp_out, int mode, double dt, double ca, double cb, cudaStream_t s) {
   if (m->G > 0) {
-    dgk::MortarArgs M{qs, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, m->d_ops, m->ph};
+    dgk::MortarArgs M{qs, pp_in, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, bgt(m),
+                      m->d_ops, m->ph};
     bool ok = m->prec == DG_FP64
                   ? (m->D == 2 ? dgk::launch_mortar_f64_2d(m->N, M, s) : dgk::launch_mortar_f64_3d(m->N, M, s))
                   : (m->D == 2 ? dgk::launch_mortar_f32_2d(m->N, M, s) : dgk::launch_mortar_f32_3d(m->N, M, s));
@@ -167,9 +186,15 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* qn, void* out,
     CU(cudaGetLastError());
   }
   dgk::StageArgs A{};
-  A.qs = qs; A.qn = qn; A.out = out; A.mbuf = m->d_mbuf; A.plane = plane(m); A.E = (int32_t)m->E;
-  A.elem = m->d_elem; A.conn = m->d_conn; A.bg = m->d_bg; A.ops = m->d_ops;
-  for (int a = 0; a < 3; ++a) A.root_h[a] = m->root_h[a];
+  A.qs = qs; A.pp_in = pp_in; A.qn = qn; A.out = out; A.pp_out = pp_out; A.mbuf = m->d_mbuf;
+  A.plane = plane(m); A.E = (int32_t)m->E;
+  A.elem = m->d_elem; A.conn = m->d_conn; A.bg = m->d_bg; A.bgt = bgt(m); A.ops = m->d_ops;
+  for (int l = 0; l < dgk::kMaxLevels; ++l)
+    for (int a = 0; a < 3; ++a) {
+      // 2/h = (2/h_root) 2^level: power-of-two scaling is exact
+      A.inv2hd[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+      A.inv2hf[l][a] = (float)A.inv2hd[l][a];
+    }
   A.dt = dt; A.ca = ca; A.cb = cb; A.mode = mode; A.ph = m->ph;
   const bool timed = m->timing && mode == 1;
   if (timed) {
@@ -227,6 +252,14 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   m->stream = (cudaStream_t)stream;
   m->ph.theta0 = desc->theta0; m->ph.p0 = desc->p0; m->ph.g = desc->g; m->ph.R = desc->R;
   m->ph.cp = desc->cp; m->ph.cv = desc->cp - desc->R; m->ph.gamma = desc->cp / (desc->cp - desc->R);
+  {
+    // binom(gamma, k) = prod_{j<k} (gamma - j) / k! for the P' series
+    double c = 1.0;
+    for (int k = 1; k <= dgk::kSeries; ++k) {
+      c = c * (m->ph.gamma - (k - 1)) / k;
+      m->ph.binom[k - 1] = c;
+    }
+  }
   int base[3] = {desc->base[0], desc->base[1], desc->dim == 3 ? desc->base[2] : 1};
   for (int a = 0; a < 3; ++a) m->root_h[a] = a < m->D ? desc->length[a] / base[a] : 1.0;
   m->forest = dgl::Forest(m->D, base, desc->max_level);
@@ -255,6 +288,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   if (m->stream) cudaStreamSynchronize(m->stream); else cudaDeviceSynchronize();
   for (int i = 0; i < 3; ++i) dfree(m->q[i]);
   dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
+  dfree(m->d_bgf); dfree(m->d_ppscratch);
   dfree(m->d_ops); dfree(m->d_opsd); dfree(m->d_partial); dfree(m->d_out); dfree(m->d_bad);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   delete m;
@@ -292,6 +326,7 @@ dg_status dg_get_faces(const dg_mesh* mc, int64_t counts[3], int32_t* conforming
 dg_status dg_set_state(dg_mesh* m, const void* q, int where) {
   if (!m || !q || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
   const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
+  m->pp_valid = false;
   CU(cudaMemcpyAsync(m->q[0], q, bytes, where == DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, m->stream));
   CU(cudaStreamSynchronize(m->stream));
   return DG_OK;
@@ -320,6 +355,7 @@ dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) {
     CU(cudaMemcpy(dp, b->rff_phase, (size_t)b->n_rff * sizeof(double), cudaMemcpyHostToDevice));
   }
   const double scale = b->n_rff > 0 ? b->rff_sigma * std::sqrt(2.0 / b->n_rff) : 0.0;
+  m->pp_valid = false;
   cudaError_t e = dgk::launch_bubble(m->prec, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), m->root_h,
                                      m->d_bg, b->center, b->radius, b->amp, b->n_rff, scale, dk, dp,
                                      m->ph.theta0, m->q[0], plane(m), m->stream);
@@ -333,20 +369,31 @@ dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) {
 dg_status dg_rhs(dg_mesh* m, const void* q, void* dqdt, void* stream) {
   if (!m || !q || !dqdt) return fail(m, DG_ERR_ARG, "bad argument");
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
-  return launch_rhs_pass(m, q, nullptr, dqdt, 0, 0.0, 0.0, 1.0, s);
+  const void* theta = (const char*)q + (size_t)(m->NV - 1) * plane(m) * m->tsize;
+  CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->ph, m->d_ppscratch, s));
+  return launch_rhs_pass(m, q, m->d_ppscratch, nullptr, dqdt, nullptr, 0, 0.0, 0.0, 1.0, s);
 }
 
 dg_status dg_step(dg_mesh* m, double dt, int32_t nsteps, void* stream) {
   if (!m || nsteps < 0 || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  void* p0 = pp_plane(m, m->q[0]);
+  void* p1 = pp_plane(m, m->q[1]);
+  void* p2 = pp_plane(m, m->q[2]);
+  if (!m->pp_valid && nsteps > 0) {
+    const void* theta = (const char*)m->q[0] + (size_t)(m->NV - 1) * plane(m) * m->tsize;
+    CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->ph, p0, s));
+  }
   for (int32_t it = 0; it < nsteps; ++it) {
     // Shu-Osher SSP-RK3: q1 = q + dt L(q); q2 = 3/4 q + 1/4 (q1 + dt L(q1));
-    // q^{n+1} = 1/3 q + 2/3 (q2 + dt L(q2)), the last one written over q^n
-    dg_status st = launch_rhs_pass(m, m->q[0], m->q[0], m->q[1], 1, dt, 0.0, 1.0, s);
-    if (st == DG_OK) st = launch_rhs_pass(m, m->q[1], m->q[0], m->q[2], 1, dt, 0.75, 0.25, s);
-    if (st == DG_OK) st = launch_rhs_pass(m, m->q[2], m->q[0], m->q[0], 1, dt, 1.0 / 3.0, 2.0 / 3.0, s);
+    // q^{n+1} = 1/3 q + 2/3 (q2 + dt L(q2)), the last one written over q^n (each thread reads
+    // q^n only at its own node, and the stage reads P' of q2, not of q^n)
+    dg_status st = launch_rhs_pass(m, m->q[0], p0, m->q[0], m->q[1], p1, 1, dt, 0.0, 1.0, s);
+    if (st == DG_OK) st = launch_rhs_pass(m, m->q[1], p1, m->q[0], m->q[2], p2, 1, dt, 0.75, 0.25, s);
+    if (st == DG_OK) st = launch_rhs_pass(m, m->q[2], p2, m->q[0], m->q[0], p0, 1, dt, 1.0 / 3.0, 2.0 / 3.0, s);
     if (st != DG_OK) return st;
   }
+  if (nsteps > 0) m->pp_valid = true;
   return DG_OK;
 }
 
@@ -410,6 +457,7 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   cudaFree(d_tm);
   if (st != DG_OK) return st;
   for (int i = 0; i < 3; ++i) { dfree(oldq[i]); m->q[i] = newq[i]; }
+  m->pp_valid = false;
   if (rep) {
     rep->elements_before = E_old;
     rep->elements_after = m->E;

@@ -10,7 +10,9 @@
 //    form (Sec. 2.2): flux at the node, D applied along each axis through shared memory
 //    (sum factorisation), buoyancy source; face terms: Rusanov on conforming faces and walls
 //    (mirror state), precomputed mortar fluxes on hanging faces, lifted with 2/(h w_0); then the
-//    Shu-Osher stage combination, written in place of the caller's output.
+//    Shu-Osher stage combination.  The epilogue also evaluates the pressure perturbation P' of
+//    the new state in FP64 and stores it as an extra plane, so that the next stage reads P' of
+//    its own node and of its face neighbours instead of recomputing it.
 //
 // Face fluxes use explicitly rounded arithmetic (__dadd_rn etc.), so the two elements that
 // share a conforming face compute bit-identical F* and the scheme conserves mass and Theta
@@ -21,8 +23,12 @@
 
 namespace dgk {
 
+constexpr int kMaxLevels = 13;   // DG_MAX_LEVEL + 1
+constexpr int kSeries = 11;      // binomial-series terms kept for the FP64 pressure perturbation
+
 struct PhysC {
   double theta0, p0, g, R, cp, cv, gamma;
+  double binom[kSeries];         // binom(gamma, k) for k = 1..kSeries
 };
 
 enum { FACE_WALL = 0, FACE_CONF = 1, FACE_FINE = 2, FACE_COARSE = 3 };
@@ -40,23 +46,43 @@ __device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, 
 __device__ __forceinline__ double sqrt_rn(double a) { return __dsqrt_rn(a); }
 __device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
 
-// Pressure perturbation P(Theta_bar + Theta') - P(Theta_bar) in FP64 through the exact identity
-// P_bar * ((1 + Theta'/Theta_bar)^gamma - 1) = P_bar * expm1(gamma * log1p(Theta'/Theta_bar)),
-// free of the cancellation between two ~1e5 Pa values (EOS of Sec. 2.1).
-__device__ __forceinline__ double pressure_pert(double tp, double Tb, double pb, double gamma) {
-  return __dmul_rn(pb, expm1(__dmul_rn(gamma, log1p(__ddiv_rn(tp, Tb)))));
+// Pressure perturbation P(Theta_bar + Theta') - P(Theta_bar) of the EOS of Sec. 2.1, in FP64,
+// through the exact identity P' = P_bar ((1 + x)^gamma - 1), x = Theta' / Theta_bar, which has
+// no cancellation between two ~1e5 Pa values.  For |x| <= 2^-5 the binomial series
+// sum_{k=1..K} binom(gamma, k) x^k is summed by Horner's rule: K = 11 keeps the truncation below
+// 1e-19 relative (FP64 path, integrals), K = 5 below 2e-9 relative, far under the FP32
+// rounding of the result (FP32 path).  Larger |x| take expm1(gamma log1p(x)).
+template <int K>
+__device__ __forceinline__ double pressure_pert(double tp, double invTb, double pb,
+                                                const PhysC& ph) {
+  const double x = tp * invTb;
+  if (fabs(x) <= 0.03125) {
+    double p = ph.binom[K - 1];
+#pragma unroll
+    for (int k = K - 2; k >= 0; --k) p = fma(p, x, ph.binom[k]);
+    return __dmul_rn(pb, __dmul_rn(p, x));
+  }
+  return __dmul_rn(pb, expm1(__dmul_rn(ph.gamma, log1p(x))));
 }
+
+template <class T> struct SeriesTerms { static constexpr int K = kSeries; };
+template <> struct SeriesTerms<float> { static constexpr int K = 5; };
+
+// Background and pressure at one node, in the flux arithmetic type T.
+template <class T>
+struct NodeBg {
+  T rb, Tb, pb;
+};
 
 // Component `a` of the Euler flux (Sec. 2.1, Eq. "eulervector") at one node, perturbation form:
 // rho': U_a;  U_b: U_b u_a + P' delta_ab;  Theta': (Theta_bar + Theta') u_a.
-// Optionally the wave speed |u_a| + c with c = sqrt(gamma P / rho) of the total state.
-// `ppd` is pressure_pert of this state (computed once per node by the caller).
+// Optionally the wave speed |u_a| + c with c = sqrt(gamma P / rho) of the total state
+// (P = P_bar + P', rho = rho_bar + rho').
 template <class T, int D>
-__device__ __forceinline__ void flux_axis(const T* q, double rb, double Tb, double pb,
-                                          double ppd, int a, const PhysC& ph, T* F, T* speed) {
-  const T rho = add_rn((T)rb, q[0]);
+__device__ __forceinline__ void flux_axis(const T* q, const NodeBg<T>& bg, T pp, int a,
+                                          const PhysC& ph, T* F, T* speed) {
+  const T rho = add_rn(bg.rb, q[0]);
   const T ua = div_rn(q[1 + a], rho);
-  const T pp = (T)ppd;
   F[0] = q[1 + a];
 #pragma unroll
   for (int b = 0; b < D; ++b) {
@@ -64,9 +90,9 @@ __device__ __forceinline__ void flux_axis(const T* q, double rb, double Tb, doub
     if (b == a) f = add_rn(f, pp);
     F[1 + b] = f;
   }
-  F[D + 1] = mul_rn(add_rn((T)Tb, q[D + 1]), ua);
+  F[D + 1] = mul_rn(add_rn(bg.Tb, q[D + 1]), ua);
   if (speed) {
-    const T P = (T)__dadd_rn(pb, ppd);
+    const T P = add_rn(bg.pb, pp);
     const T c = sqrt_rn(div_rn(mul_rn((T)ph.gamma, P), rho));
     *speed = add_rn(ua < (T)0 ? -ua : ua, c);
   }
@@ -75,13 +101,13 @@ __device__ __forceinline__ void flux_axis(const T* q, double rb, double Tb, doub
 // Rusanov flux along +axis a (Sec. 2.2): F* = (F(qm) + F(qp))/2 - lambda/2 (qp - qm),
 // lambda = max(|u_a| + c) over both sides.  qm is the low side, qp the high side.
 template <class T, int D>
-__device__ __forceinline__ void rusanov(const T* qm, double rbm, double Tbm, double pbm, double ppm,
-                                        const T* qp, double rbp, double Tbp, double pbp, double ppp,
-                                        int a, const PhysC& ph, T* Fs) {
+__device__ __forceinline__ void rusanov(const T* qm, const NodeBg<T>& bgm, T ppm, const T* qp,
+                                        const NodeBg<T>& bgp, T ppp, int a, const PhysC& ph,
+                                        T* Fs) {
   constexpr int NV = D + 2;
   T Fm[NV], Fp[NV], sm, sp;
-  flux_axis<T, D>(qm, rbm, Tbm, pbm, ppm, a, ph, Fm, &sm);
-  flux_axis<T, D>(qp, rbp, Tbp, pbp, ppp, a, ph, Fp, &sp);
+  flux_axis<T, D>(qm, bgm, ppm, a, ph, Fm, &sm);
+  flux_axis<T, D>(qp, bgp, ppp, a, ph, Fp, &sp);
   const T hl = mul_rn((T)0.5, sm > sp ? sm : sp);
 #pragma unroll
   for (int v = 0; v < NV; ++v)
@@ -89,17 +115,21 @@ __device__ __forceinline__ void rusanov(const T* qm, double rbm, double Tbm, dou
 }
 
 struct StageArgs {
-  const void* qs;        // stage input state (T), planes of `plane` entries per variable
+  const void* qs;        // stage input state (T), NV planes of `plane` entries
+  const void* pp_in;     // P' of qs (T), one plane
   const void* qn;        // q^n for the Shu-Osher combination (T)
   void* out;             // output (T): dq/dt (mode 0) or the next stage state (mode 1)
+  void* pp_out;          // mode 1: P' of the output state (T), one plane
   const void* mbuf;      // mortar fluxes [G][1 + 2^(d-1)][NV][NF] (T)
   int64_t plane;         // entries per variable plane (elements x nodes)
   int32_t E;
   const int32_t* elem;   // [E][4]: level, c0, c1, c2
   const int32_t* conn;   // [E][2d][5] (see tree.cpp)
-  const double* bg;      // [E][N+1][4]: rho_bar, Theta_bar, p_bar, 1/Theta_bar at the z-nodes
+  const double* bg;      // [E][N+1][4]: rho_bar, Theta_bar, p_bar, 1/Theta_bar (FP64)
+  const void* bgt;       // [E][N+1][4]: the same in T (the FP64 array itself when T = double)
   const void* ops;       // (T) D, P0, P1, C0, C1 (n1 x n1 each), w (n1)
-  double root_h[3];
+  float inv2hf[kMaxLevels][3];    // 2/h per level and axis
+  double inv2hd[kMaxLevels][3];
   double dt, ca, cb;
   int32_t mode;
   PhysC ph;
@@ -107,14 +137,24 @@ struct StageArgs {
 
 struct MortarArgs {
   const void* qs;
+  const void* pp_in;
   void* mbuf;
   int64_t plane;
   int32_t G;
   const int32_t* groups; // [G][7]: coarse element, axis, side, fine elements (Morton order)
   const double* bg;
+  const void* bgt;
   const void* ops;
   PhysC ph;
 };
+
+template <class T> __device__ __forceinline__ T inv2h_of(const StageArgs& A, int level, int a);
+template <> __device__ __forceinline__ float inv2h_of<float>(const StageArgs& A, int level, int a) {
+  return A.inv2hf[level][a];
+}
+template <> __device__ __forceinline__ double inv2h_of<double>(const StageArgs& A, int level, int a) {
+  return A.inv2hd[level][a];
+}
 
 template <int D, int N>
 __device__ __forceinline__ int face_node(int a, int side, int t) {
@@ -149,8 +189,10 @@ stage_kernel(const StageArgs A) {
   idx[1] = (n / n1) % n1;
   idx[2] = (D == 3) ? n / (n1 * n1) : 0;
   const T* qs = (const T*)A.qs;
+  const T* ppin = (const T*)A.pp_in;
   T q[NV], acc[NV], inv2h[D];
-  double rb = 1.0, Tb = 1.0, pb = 1.0, pp = 0.0;
+  T pp = (T)0;
+  NodeBg<T> bg{(T)1, (T)1, (T)1};
 #pragma unroll
   for (int v = 0; v < NV; ++v) { q[v] = (T)0; acc[v] = (T)0; }
 #pragma unroll
@@ -159,24 +201,24 @@ stage_kernel(const StageArgs A) {
     const size_t base = (size_t)e * NP + n;
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = qs[(size_t)v * A.plane + base];
+    pp = ppin[base];
     const int level = A.elem[e * 4];
 #pragma unroll
-    for (int a = 0; a < D; ++a) inv2h[a] = (T)(2.0 / ldexp(A.root_h[a], -level));
-    const double* b = A.bg + ((size_t)e * n1 + idx[D - 1]) * 4;
-    rb = b[0]; Tb = b[1]; pb = b[2];
-    pp = pressure_pert((double)q[D + 1], Tb, pb, A.ph.gamma);
+    for (int a = 0; a < D; ++a) inv2h[a] = inv2h_of<T>(A, level, a);
+    const T* b = (const T*)A.bgt + ((size_t)e * n1 + idx[D - 1]) * 4;
+    bg.rb = b[0]; bg.Tb = b[1]; bg.pb = b[2];
     acc[D] = -(q[0] * (T)A.ph.g);   // buoyancy -rho' g on the vertical momentum
   }
   __syncthreads();
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T F[NV];
-    flux_axis<T, D>(q, rb, Tb, pb, pp, a, A.ph, F, nullptr);
+    flux_axis<T, D>(q, bg, pp, a, A.ph, F, nullptr);
 #pragma unroll
     for (int v = 0; v < NV; ++v) sF[le][v][n] = F[v];
     __syncthreads();
     if (valid) {
-      const int stride = ipow(n1, a) ;
+      const int stride = ipow(n1, a);
       const int ia = idx[a];
       const int b0 = n - ia * stride;
 #pragma unroll
@@ -208,20 +250,20 @@ stage_kernel(const StageArgs A) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) gq[v] = q[v];
         gq[1 + a] = -q[1 + a];
-        if (s) rusanov<T, D>(q, rb, Tb, pb, pp, gq, rb, Tb, pb, pp, a, A.ph, Fs);
-        else   rusanov<T, D>(gq, rb, Tb, pb, pp, q, rb, Tb, pb, pp, a, A.ph, Fs);
+        if (s) rusanov<T, D>(q, bg, pp, gq, bg, pp, a, A.ph, Fs);
+        else   rusanov<T, D>(gq, bg, pp, q, bg, pp, a, A.ph, Fs);
       } else if (kind == FACE_CONF) {
         // the neighbour's matching node: same tangential indices, opposite face; its z (hence
         // its background) is bit-identical to this node's
         const int64_t nb = c[1];
         const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
-        const int nn = n + ((s ? 0 : N) - idx[a]) * stride_a;
+        const size_t no = (size_t)nb * NP + n + ((s ? 0 : N) - idx[a]) * stride_a;
         T qo[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) qo[v] = qs[(size_t)v * A.plane + (size_t)nb * NP + nn];
-        const double ppo = pressure_pert((double)qo[D + 1], Tb, pb, A.ph.gamma);
-        if (s) rusanov<T, D>(q, rb, Tb, pb, pp, qo, rb, Tb, pb, ppo, a, A.ph, Fs);
-        else   rusanov<T, D>(qo, rb, Tb, pb, ppo, q, rb, Tb, pb, pp, a, A.ph, Fs);
+        for (int v = 0; v < NV; ++v) qo[v] = qs[(size_t)v * A.plane + no];
+        const T ppo = ppin[no];
+        if (s) rusanov<T, D>(q, bg, pp, qo, bg, ppo, a, A.ph, Fs);
+        else   rusanov<T, D>(qo, bg, ppo, q, bg, pp, a, A.ph, Fs);
       } else {
         const int64_t g = (kind == FACE_FINE) ? c[2] : c[1];
         const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
@@ -230,7 +272,7 @@ stage_kernel(const StageArgs A) {
         for (int v = 0; v < NV; ++v) Fs[v] = src[(size_t)v * NF];
       }
       T Fo[NV];
-      flux_axis<T, D>(q, rb, Tb, pb, pp, a, A.ph, Fo, nullptr);
+      flux_axis<T, D>(q, bg, pp, a, A.ph, Fo, nullptr);
       const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += coef * (Fs[v] - Fo[v]);
@@ -241,19 +283,38 @@ stage_kernel(const StageArgs A) {
   if (A.mode == 0) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) out[(size_t)v * A.plane + base] = acc[v];
-  } else if (A.ca == 0.0) {
-    const T dt = (T)A.dt;
+    return;
+  }
+  T qnew[NV];
+  const T dt = (T)A.dt;
+  if (A.ca == 0.0) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) out[(size_t)v * A.plane + base] = q[v] + dt * acc[v];
+    for (int v = 0; v < NV; ++v) qnew[v] = q[v] + dt * acc[v];
   } else {
-    const T dt = (T)A.dt, ca = (T)A.ca, cb = (T)A.cb;
+    const T ca = (T)A.ca, cb = (T)A.cb;
     const T* qn = (const T*)A.qn;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const size_t k = (size_t)v * A.plane + base;
-      out[k] = ca * qn[k] + cb * (q[v] + dt * acc[v]);
-    }
+    for (int v = 0; v < NV; ++v) qnew[v] = ca * qn[(size_t)v * A.plane + base] + cb * (q[v] + dt * acc[v]);
   }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) out[(size_t)v * A.plane + base] = qnew[v];
+  const double* bd = A.bg + ((size_t)e * n1 + idx[D - 1]) * 4;
+  ((T*)A.pp_out)[base] =
+      (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
+}
+
+// P' of every node of a state (FP64 evaluation, stored in T): used when a state enters from
+// outside the time loop (set_state, initial condition, transfer, dg_rhs input).
+template <class T>
+__global__ void pprime_kernel(int64_t total, int NP, int n1, int D, const T* theta_plane,
+                              const double* bg, PhysC ph, T* pp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int64_t e = i / NP;
+  const int n = (int)(i - e * NP);
+  const int k = D == 3 ? n / (n1 * n1) : n / n1;
+  const double* b = bg + (e * n1 + k) * 4;
+  pp[i] = (T)pressure_pert<SeriesTerms<T>::K>((double)theta_plane[i], b[3], b[2], ph);
 }
 
 // One CTA per mortar group; NSUB * NF threads: thread (m, t) owns mortar node t of mortar m.
@@ -310,7 +371,8 @@ mortar_kernel(const MortarArgs A) {
     for (int v = 0; v < NV; ++v) sM[m][v][t] = sT[m][v][t];
   }
   __syncthreads();
-  // Rusanov on mortar node (m, t); the fine face is the mortar (identity projection)
+  // Rusanov on mortar node (m, t); the fine face is the mortar (identity projection), and the
+  // projected coarse state takes the fine side's background (the mortar points' heights)
   const int64_t ef = row[3 + m];
   const int nf = face_node<D, N>(a, 1 - side, t);
   T qf[NV], qc[NV], Fs[NV];
@@ -320,11 +382,13 @@ mortar_kernel(const MortarArgs A) {
     qc[v] = sM[m][v][t];
   }
   const int kf = (D == 3) ? nf / (n1 * n1) : nf / n1;
-  const double* b = A.bg + ((size_t)ef * n1 + kf) * 4;
-  const double ppf = pressure_pert((double)qf[D + 1], b[1], b[2], A.ph.gamma);
-  const double ppc = pressure_pert((double)qc[D + 1], b[1], b[2], A.ph.gamma);
-  if (side) rusanov<T, D>(qc, b[0], b[1], b[2], ppc, qf, b[0], b[1], b[2], ppf, a, A.ph, Fs);
-  else      rusanov<T, D>(qf, b[0], b[1], b[2], ppf, qc, b[0], b[1], b[2], ppc, a, A.ph, Fs);
+  const double* bd = A.bg + ((size_t)ef * n1 + kf) * 4;
+  const T* bt = (const T*)A.bgt + ((size_t)ef * n1 + kf) * 4;
+  const NodeBg<T> bgf{bt[0], bt[1], bt[2]};
+  const T ppf = ((const T*)A.pp_in)[(size_t)ef * NP + nf];
+  const T ppc = (T)pressure_pert<SeriesTerms<T>::K>((double)qc[D + 1], bd[3], bd[2], A.ph);
+  if (side) rusanov<T, D>(qc, bgf, ppc, qf, bgf, ppf, a, A.ph, Fs);
+  else      rusanov<T, D>(qf, bgf, ppf, qc, bgf, ppc, a, A.ph, Fs);
   T* mb = (T*)A.mbuf + ((size_t)g * (1 + NSUB) * NV) * NF;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {

@@ -20,7 +20,10 @@ bool launch_mortar_f32_2d(int N, const MortarArgs& A, cudaStream_t s);
 bool launch_mortar_f32_3d(int N, const MortarArgs& A, cudaStream_t s);
 
 cudaError_t launch_background(int32_t E, int n1, int D, const int32_t* elem, const double* xi,
-                              double root_hz, const PhysC& ph, double* bg, cudaStream_t s);
+                              double root_hz, const PhysC& ph, double* bg, float* bgf,
+                              cudaStream_t s);
+cudaError_t launch_pprime(int prec, int32_t E, int n1, int D, const void* theta_plane,
+                          const double* bg, const PhysC& ph, void* pp, cudaStream_t s);
 cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* elem,
                           const double* xi, const double* root_h, const double* bg,
                           const double* center, const double* radius, double amp, int n_rff,

@@ -17,7 +17,8 @@ __device__ __forceinline__ double node_coord(int c, double xi, double h) {
 // pi = 1 - g z / (cp theta0), rho_bar = p0 pi^(cv/R) / (R theta0), Theta_bar = rho_bar theta0,
 // p_bar := P(Theta_bar) = p0 (R Theta_bar / p0)^gamma so that a fluid at rest has P' = 0.
 __global__ void background_kernel(int32_t E, int n1, int D, const int32_t* elem,
-                                  const double* xi, double root_hz, PhysC ph, double* bg) {
+                                  const double* xi, double root_hz, PhysC ph, double* bg,
+                                  float* bgf) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)E * n1) return;
   const int64_t e = i / n1;
@@ -31,6 +32,10 @@ __global__ void background_kernel(int32_t E, int n1, int D, const int32_t* elem,
   const double pb = ph.p0 * pow(ph.R * Tb / ph.p0, ph.gamma);
   double* o = bg + i * 4;
   o[0] = rb; o[1] = Tb; o[2] = pb; o[3] = 1.0 / Tb;
+  if (bgf) {
+    float* f = bgf + i * 4;
+    f[0] = (float)rb; f[1] = (float)Tb; f[2] = (float)pb; f[3] = (float)(1.0 / Tb);
+  }
 }
 
 template <class T>
@@ -145,7 +150,7 @@ integrals_partial(int32_t E, int n1, int D, const int32_t* elem, const double* x
     }
     const double ke = 0.5 * u2 / rho;
     const double tp = (double)q[(int64_t)(D + 1) * plane + i];
-    const double pp = b[2] * expm1(ph.gamma * log1p(tp / b[1]));
+    const double pp = pressure_pert<kSeries>(tp, b[3], b[2], ph);
     const double p = b[2] + pp;
     const double en = p * ph.cv / ph.R + ke + rho * ph.g * z;
     if (!isfinite(rho) || !isfinite(en)) nonfinite = 1;
@@ -247,10 +252,24 @@ __global__ void transfer_kernel(int32_t Enew, int n1, int D, const int32_t* tmap
 }  // namespace
 
 cudaError_t launch_background(int32_t E, int n1, int D, const int32_t* elem, const double* xi,
-                              double root_hz, const PhysC& ph, double* bg, cudaStream_t s) {
+                              double root_hz, const PhysC& ph, double* bg, float* bgf,
+                              cudaStream_t s) {
   const int64_t n = (int64_t)E * n1;
   if (n == 0) return cudaSuccess;
-  background_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, n1, D, elem, xi, root_hz, ph, bg);
+  background_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, n1, D, elem, xi, root_hz, ph, bg, bgf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pprime(int prec, int32_t E, int n1, int D, const void* theta_plane,
+                          const double* bg, const PhysC& ph, void* pp, cudaStream_t s) {
+  const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
+  const int64_t n = (int64_t)E * NP;
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (prec == 0)
+    pprime_kernel<double><<<blocks, 256, 0, s>>>(n, NP, n1, D, (const double*)theta_plane, bg, ph, (double*)pp);
+  else
+    pprime_kernel<float><<<blocks, 256, 0, s>>>(n, NP, n1, D, (const float*)theta_plane, bg, ph, (float*)pp);
   return cudaGetLastError();
 }
 

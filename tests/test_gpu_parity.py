@@ -197,3 +197,17 @@ def test_full_size_octree_sampled_parity(pkg):
     sample = np.unique(np.concatenate([sample, coarse]))
     want = odg.rhs(om, q, elems=sample)
     assert _rel_err(got[:, sample], want[:, sample]) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_rhs_parity_large_theta_uses_fallback_branch(pkg, precision, tol):
+    # |Theta'| ~ 20 makes |Theta'/Theta_bar| exceed 2^-5 at many nodes, so the pressure
+    # perturbation takes the expm1/log1p branch there and the series elsewhere
+    lm, om = _pair(pkg, 3, 3, (2, 2, 2), (2000.0,) * 3, flags_rounds=((0.3, 31),), precision=precision)
+    dt = np.float64 if precision == "fp64" else np.float32
+    q = workloads.random_state(om.nv, om.E, om.np_, seed=32, theta_scale=20.0, dtype=dt)
+    rb, Tb, pb = om.bg
+    assert np.mean(np.abs(q[-1] / Tb) > 2 ** -5) > 0.2
+    got = _gpu_rhs(lm, q).astype(np.float64)
+    want = odg.rhs(om, q.astype(np.float64))
+    assert _rel_err(got, want) <= tol
