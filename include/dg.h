@@ -159,6 +159,12 @@ dg_status dg_indicator(dg_mesh* mesh, double* out, size_t cap);
  * Synchronous; DG_ERR_STATE if a non-finite value was met (out is still written). */
 dg_status dg_integrals(dg_mesh* mesh, double out[DG_NUM_INTEGRALS]);
 
+/* Tuning options.  DG_OPT_STAGE_KERNEL selects the fused stage kernel's thread layout:
+ * 0 = one thread per vertical node column (default), 1 = one thread per node.  Both compute
+ * the same operator; the option exists for tuning and cross-checking. */
+enum { DG_OPT_STAGE_KERNEL = 1 };
+dg_status dg_set_option(dg_mesh* mesh, int32_t option, int64_t value);
+
 /* Kernel timing: when enabled, the fused stage launches of dg_step are bracketed by CUDA
  * events on the mesh stream; dg_stage_timing returns the summed milliseconds and launch count
  * since the last reset (synchronises the stream). */

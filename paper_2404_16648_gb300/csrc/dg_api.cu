@@ -8,6 +8,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -38,6 +40,7 @@ struct dg_mesh {
   void* d_mbuf = nullptr;
   void* d_ppscratch = nullptr; // P' plane of a caller's state in dg_rhs
   bool pp_valid = false;       // P' plane of q[0] matches q[0]
+  int variant = 0;             // stage kernel layout (DG_OPT_STAGE_KERNEL)
   void* d_ops = nullptr;       // precision T
   double* d_opsd = nullptr;    // FP64: D, P0, P1, C0, C1, w, x
   double* d_partial = nullptr;
@@ -195,7 +198,7 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
       A.inv2hd[l][a] = std::ldexp(2.0 / m->root_h[a], l);
       A.inv2hf[l][a] = (float)A.inv2hd[l][a];
     }
-  A.dt = dt; A.ca = ca; A.cb = cb; A.mode = mode; A.ph = m->ph;
+  A.dt = dt; A.ca = ca; A.cb = cb; A.mode = mode; A.variant = m->variant; A.ph = m->ph;
   const bool timed = m->timing && mode == 1;
   if (timed) {
     while (m->ev.size() < m->ev_used + 2) {
@@ -217,9 +220,41 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
   return DG_OK;
 }
 
+// Uploads the derivative matrices of every degree to the constant memory of each kernel unit,
+// once per device.
+dg_status init_device_tables(dg_mesh* m) {
+  static std::mutex mu;
+  static std::set<int> done;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(dev)) return DG_OK;
+  std::vector<double> all;
+  for (int N = 1; N <= DG_MAX_N; ++N) {
+    dgl::Basis1D b = dgl::make_basis(N);
+    all.insert(all.end(), b.D.begin(), b.D.end());
+  }
+  CU(dgk::init_stage_f64_2d(all.data()));
+  CU(dgk::init_stage_f64_3d(all.data()));
+  CU(dgk::init_stage_f32_2d(all.data()));
+  CU(dgk::init_stage_f32_3d(all.data()));
+  done.insert(dev);
+  return DG_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+dg_status dg_set_option(dg_mesh* m, int32_t option, int64_t value) {
+  if (!m) return DG_ERR_ARG;
+  if (option == DG_OPT_STAGE_KERNEL) {
+    if (value != 0 && value != 1) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0 or 1");
+    m->variant = (int)value;
+    return DG_OK;
+  }
+  return fail(m, DG_ERR_ARG, "unknown option %d", option);
+}
 
 const char* dg_version(void) { return "gb300-dgsem 0.1 (sm_103a)"; }
 
@@ -264,7 +299,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   for (int a = 0; a < 3; ++a) m->root_h[a] = a < m->D ? desc->length[a] / base[a] : 1.0;
   m->forest = dgl::Forest(m->D, base, desc->max_level);
   m->basis = dgl::make_basis(m->N);
-  dg_status st = upload_ops(m);
+  dg_status st = init_device_tables(m);
+  if (st == DG_OK) st = upload_ops(m);
   if (st == DG_OK) st = rebuild_topology(m);
   if (st == DG_OK) st = alloc_states(m, m->q);
   if (st == DG_OK) {

@@ -132,6 +132,7 @@ struct StageArgs {
   double inv2hd[kMaxLevels][3];
   double dt, ca, cb;
   int32_t mode;
+  int32_t variant;       // 0: column-mapped kernel (default), 1: node-per-thread kernel
   PhysC ph;
 };
 

@@ -18,6 +18,12 @@ bool launch_mortar_f64_2d(int N, const MortarArgs& A, cudaStream_t s);
 bool launch_mortar_f64_3d(int N, const MortarArgs& A, cudaStream_t s);
 bool launch_mortar_f32_2d(int N, const MortarArgs& A, cudaStream_t s);
 bool launch_mortar_f32_3d(int N, const MortarArgs& A, cudaStream_t s);
+// Upload the derivative matrices of every degree (concatenated, N = 1..8) to each unit's
+// constant memory; called once before the first stage launch.
+cudaError_t init_stage_f64_2d(const double* dtab_all);
+cudaError_t init_stage_f64_3d(const double* dtab_all);
+cudaError_t init_stage_f32_2d(const double* dtab_all);
+cudaError_t init_stage_f32_3d(const double* dtab_all);
 
 cudaError_t launch_background(int32_t E, int n1, int D, const int32_t* elem, const double* xi,
                               double root_hz, const PhysC& ph, double* bg, float* bgf,

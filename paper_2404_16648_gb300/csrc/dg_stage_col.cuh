@@ -1,0 +1,309 @@
+// Column-mapped fused stage kernel (the default stage kernel).
+//
+// Same operator as stage_kernel in dg_device.cuh (strong-form volume term, Rusanov face terms,
+// precomputed mortar fluxes, Shu-Osher combination, FP64 P' epilogue), with a thread layout
+// that cuts shared-memory traffic and divergence:
+//  * one thread per vertical line (column) of an element: (i, j) in 3D, i in 2D; the thread
+//    keeps the N+1 nodes of its column in registers, so the vertical derivative needs no shared
+//    memory and reads D from constant memory (uniform across the warp);
+//  * the horizontal derivatives go through shared memory, one tile per axis holding the flux
+//    of all nodes; along x the D-row is contiguous and read with vector loads;
+//  * face terms are evaluated face-node-major: on a horizontal-normal face, thread t takes
+//    face node t (all lanes busy, no divergence) and leaves its lift in shared memory for the
+//    column that owns the node; the bottom and top faces belong to every column.
+// The arithmetic of each flux and Rusanov evaluation is the same explicitly rounded code as in
+// dg_device.cuh, so both elements of a conforming face still compute bit-identical F*.
+#pragma once
+#include "dg_device.cuh"
+
+namespace dgk {
+
+// Offsets of the degree-N blocks in the constant D tables (N = 1..8).
+__host__ __device__ constexpr int dtab_offset(int N) {
+  return N <= 1 ? 0 : dtab_offset(N - 1) + N * N;
+}
+constexpr int kDTabSize = dtab_offset(9);   // sum_{N=1..8} (N+1)^2
+
+// Collocation derivative matrices of every degree, per translation unit (static); filled by
+// upload_dtab() of the same unit before its first launch.
+static __constant__ float c_dtab_f[kDTabSize];
+static __constant__ double c_dtab_d[kDTabSize];
+
+static inline cudaError_t upload_dtab(const double* all) {
+  float f[kDTabSize];
+  for (int i = 0; i < kDTabSize; ++i) f[i] = (float)all[i];
+  cudaError_t e = cudaMemcpyToSymbol(c_dtab_f, f, sizeof(f));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_dtab_d, all, sizeof(double) * kDTabSize);
+}
+
+template <class T> __device__ __forceinline__ T dtab(int i);
+template <> __device__ __forceinline__ float dtab<float>(int i) { return c_dtab_f[i]; }
+template <> __device__ __forceinline__ double dtab<double>(int i) { return c_dtab_d[i]; }
+
+// Dynamic shared memory of the column kernel per CTA (bytes).
+template <class T, int D, int N, int EPB>
+__host__ __device__ constexpr size_t col_smem_bytes() {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NV = D + 2, NT = D - 1;
+  constexpr int QT = (n1 + 1) * ((D == 3) ? n1 : 1) * n1;
+  return sizeof(T) * ((size_t)EPB * NT * NV * NP + (size_t)EPB * (NV + 1) * QT +
+                      (size_t)EPB * n1 * 3 + (size_t)n1 * n1);
+}
+
+template <class T, int D, int N, int EPB>
+__global__ void __launch_bounds__(EPB * ipow(N + 1, D - 1))
+stage_kernel_col(const StageArgs A) {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  constexpr int NSUB = 1 << (D - 1);
+  constexpr int NT = D - 1;                 // horizontal (tangential-to-z) axes
+  constexpr int P1 = n1 + 1;                // padded row of the state tile
+  constexpr int JS = (D == 3) ? n1 : 1;
+  constexpr int QT = P1 * JS * n1;          // padded state tile per variable
+  constexpr bool VEC = (sizeof(T) == 4) && (n1 % 4 == 0);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // horizontal fluxes (reused for the face lifts), state and P' tile, background, D
+  T (*sFh)[NT][NV][NP] = reinterpret_cast<T (*)[NT][NV][NP]>(smem_raw);
+  T (*sQ)[NV + 1][QT] = reinterpret_cast<T (*)[NV + 1][QT]>(smem_raw + sizeof(T) * EPB * NT * NV * NP);
+  T (*sBg)[n1][3] = reinterpret_cast<T (*)[n1][3]>(smem_raw + sizeof(T) * (EPB * NT * NV * NP + EPB * (NV + 1) * QT));
+  T* sDh = reinterpret_cast<T*>(smem_raw + sizeof(T) * (EPB * NT * NV * NP + EPB * (NV + 1) * QT + EPB * n1 * 3));
+  const int tid = threadIdx.x;
+  const int le = tid / NF, t = tid - le * NF;
+  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const bool valid = e < A.E;
+  const int ci = t % n1, cj = (D == 3) ? t / n1 : 0;
+  const T* ops = (const T*)A.ops;
+  for (int x = tid; x < n1 * n1; x += blockDim.x) sDh[x] = ops[x];
+  const T w0 = ops[5 * n1 * n1];
+  const T* qs = (const T*)A.qs;
+  const T* ppin = (const T*)A.pp_in;
+  const T g = (T)A.ph.g;
+  T acc[NV][n1];
+  T inv2h[D];
+  int level = 0;
+  if (valid) {
+    level = A.elem[e * 4];
+    if (t < n1) {
+      const T* b = (const T*)A.bgt + ((size_t)e * n1 + t) * 4;
+      sBg[le][t][0] = b[0]; sBg[le][t][1] = b[1]; sBg[le][t][2] = b[2];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) inv2h[a] = valid ? inv2h_of<T>(A, level, a) : (T)0;
+  __syncthreads();
+  // ---- load the column, fluxes: horizontal ones to shared memory, vertical one kept here
+  T Fz[NV][n1];
+#pragma unroll
+  for (int k = 0; k < n1; ++k) {
+    const int n = t + NF * k;
+    T q[NV];
+    T pp = (T)0;
+    NodeBg<T> bg{(T)1, (T)1, (T)1};
+    if (valid) {
+      const size_t base = (size_t)e * NP + n;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) q[v] = qs[(size_t)v * A.plane + base];
+      pp = ppin[base];
+      bg = NodeBg<T>{sBg[le][k][0], sBg[le][k][1], sBg[le][k][2]};
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) q[v] = (T)0;
+    }
+    const int qi = ci + P1 * (cj + JS * k);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sQ[le][v][qi] = q[v];
+    sQ[le][NV][qi] = pp;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v][k] = (T)0;
+    acc[D][k] = -(q[0] * g);               // buoyancy -rho' g on the vertical momentum
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      T F[NV];
+      flux_axis<T, D>(q, bg, pp, a, A.ph, F, nullptr);
+      if (a < NT) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sFh[le][a][v][n] = F[v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fz[v][k] = F[v];
+      }
+    }
+  }
+  // ---- vertical derivative from registers, D from constant memory
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int k = 0; k < n1; ++k) {
+      T s = (T)0;
+#pragma unroll
+      for (int m = 0; m < n1; ++m) s = fma(dtab<T>(dtab_offset(N) + k * n1 + m), Fz[v][m], s);
+      acc[v][k] -= inv2h[D - 1] * s;
+    }
+  __syncthreads();
+  // ---- horizontal derivatives through shared memory
+  if (valid) {
+    T Di[n1];
+#pragma unroll
+    for (int m = 0; m < n1; ++m) Di[m] = sDh[ci * n1 + m];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int k = 0; k < n1; ++k) {
+        const T* row = &sFh[le][0][v][NF * k + n1 * cj];
+        T s = (T)0;
+        if constexpr (VEC) {
+#pragma unroll
+          for (int m = 0; m < n1; m += 4) {
+            const float4 f = *reinterpret_cast<const float4*>(row + m);
+            s = fma(Di[m], (T)f.x, s);
+            s = fma(Di[m + 1], (T)f.y, s);
+            s = fma(Di[m + 2], (T)f.z, s);
+            s = fma(Di[m + 3], (T)f.w, s);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < n1; ++m) s = fma(Di[m], row[m], s);
+        }
+        acc[v][k] -= inv2h[0] * s;
+      }
+    if (D == 3) {
+      T Dj[n1];
+#pragma unroll
+      for (int m = 0; m < n1; ++m) Dj[m] = sDh[cj * n1 + m];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int k = 0; k < n1; ++k) {
+          const T* col = &sFh[le][NT - 1][v][NF * k + ci];
+          T s = (T)0;
+#pragma unroll
+          for (int m = 0; m < n1; ++m) s = fma(Dj[m], col[n1 * m], s);
+          acc[v][k] -= inv2h[1] * s;
+        }
+    }
+  }
+  __syncthreads();
+  // ---- face terms
+  const T* mbuf = (const T*)A.mbuf;
+  T (*sLift)[NV][NF] = reinterpret_cast<T (*)[NV][NF]>(&sFh[le][0][0][0]);   // [2*NT][NV][NF]
+  auto face_flux = [&](int a, int s, int fn, const T* qo_own, T pp_own, const NodeBg<T>& bg,
+                       int own_node, T* Fs) {
+    const int32_t* c = A.conn + ((size_t)e * 2 * D + 2 * a + s) * 5;
+    const int kind = c[0];
+    if (kind == FACE_WALL) {
+      T gq[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) gq[v] = qo_own[v];
+      gq[1 + a] = -qo_own[1 + a];
+      if (s) rusanov<T, D>(qo_own, bg, pp_own, gq, bg, pp_own, a, A.ph, Fs);
+      else   rusanov<T, D>(gq, bg, pp_own, qo_own, bg, pp_own, a, A.ph, Fs);
+    } else if (kind == FACE_CONF) {
+      const int64_t nb = c[1];
+      const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
+      const size_t no = (size_t)nb * NP + own_node + (s ? -N : N) * stride_a;
+      T qo[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qo[v] = qs[(size_t)v * A.plane + no];
+      const T ppo = ppin[no];
+      if (s) rusanov<T, D>(qo_own, bg, pp_own, qo, bg, ppo, a, A.ph, Fs);
+      else   rusanov<T, D>(qo, bg, ppo, qo_own, bg, pp_own, a, A.ph, Fs);
+    } else {
+      const int64_t gg = (kind == FACE_FINE) ? c[2] : c[1];
+      const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
+      const T* src = mbuf + (((size_t)gg * (1 + NSUB) + slot) * NV) * NF + fn;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fs[v] = src[(size_t)v * NF];
+    }
+  };
+  if (valid) {
+    // horizontal-normal faces: thread t takes face node t
+#pragma unroll
+    for (int a = 0; a < NT; ++a) {
+      // tangential coordinates of face node t: the other horizontal axis (3D) fastest, then k
+      const int u = (D == 3) ? t % n1 : 0;
+      const int k = (D == 3) ? t / n1 : t;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        int ii, jj;
+        if (a == 0) { ii = s ? N : 0; jj = u; } else { ii = u; jj = s ? N : 0; }
+        const int qi = ii + P1 * (jj + JS * k);
+        T qo_own[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) qo_own[v] = sQ[le][v][qi];
+        const T pp_own = sQ[le][NV][qi];
+        const NodeBg<T> bg{sBg[le][k][0], sBg[le][k][1], sBg[le][k][2]};
+        const int own_node = ii + n1 * jj + NF * k;
+        T Fs[NV], Fo[NV];
+        face_flux(a, s, t, qo_own, pp_own, bg, own_node, Fs);
+        flux_axis<T, D>(qo_own, bg, pp_own, a, A.ph, Fo, nullptr);
+        const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sLift[2 * a + s][v][t] = coef * (Fs[v] - Fo[v]);
+      }
+    }
+    // bottom and top faces: every column owns one node on each
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int k = s ? N : 0;
+      const int qi = ci + P1 * (cj + JS * k);
+      T qo_own[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qo_own[v] = sQ[le][v][qi];
+      const T pp_own = sQ[le][NV][qi];
+      const NodeBg<T> bg{sBg[le][k][0], sBg[le][k][1], sBg[le][k][2]};
+      T Fs[NV], Fo[NV];
+      face_flux(D - 1, s, t, qo_own, pp_own, bg, t + NF * k, Fs);
+      flux_axis<T, D>(qo_own, bg, pp_own, D - 1, A.ph, Fo, nullptr);
+      const T coef = s ? -(inv2h[D - 1] / w0) : inv2h[D - 1] / w0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v][k] += coef * (Fs[v] - Fo[v]);
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  // lifts of the horizontal-normal faces into the owning columns
+#pragma unroll
+  for (int a = 0; a < NT; ++a) {
+    const int own = (a == 0) ? ci : cj;
+    const int u = (a == 0) ? cj : ci;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (own != (s ? N : 0)) continue;
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int k = 0; k < n1; ++k) acc[v][k] += sLift[2 * a + s][v][(D == 3 ? u : 0) + (D == 3 ? n1 : 1) * k];
+    }
+  }
+  // ---- output
+  T* out = (T*)A.out;
+  if (A.mode == 0) {
+#pragma unroll
+    for (int k = 0; k < n1; ++k) {
+      const size_t base = (size_t)e * NP + t + NF * k;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) out[(size_t)v * A.plane + base] = acc[v][k];
+    }
+    return;
+  }
+  const T dt = (T)A.dt, ca = (T)A.ca, cb = (T)A.cb;
+  const bool first = A.ca == 0.0;
+  const T* qn = (const T*)A.qn;
+  T* ppo = (T*)A.pp_out;
+#pragma unroll
+  for (int k = 0; k < n1; ++k) {
+    const size_t base = (size_t)e * NP + t + NF * k;
+    const int qi = ci + P1 * (cj + JS * k);
+    T qnew[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T qsv = sQ[le][v][qi];
+      qnew[v] = first ? qsv + dt * acc[v][k]
+                      : ca * qn[(size_t)v * A.plane + base] + cb * (qsv + dt * acc[v][k]);
+      out[(size_t)v * A.plane + base] = qnew[v];
+    }
+    const double* bd = A.bg + ((size_t)e * n1 + k) * 4;
+    ppo[base] = (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
+  }
+}
+
+}  // namespace dgk

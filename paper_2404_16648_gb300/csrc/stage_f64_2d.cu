@@ -8,4 +8,5 @@ bool launch_stage_f64_2d(int N, const StageArgs& A, cudaStream_t s) {
 bool launch_mortar_f64_2d(int N, const MortarArgs& A, cudaStream_t s) {
   return mortar_dispatch<double, 2>(N, A, s);
 }
+cudaError_t init_stage_f64_2d(const double* dtab_all) { return upload_dtab(dtab_all); }
 }  // namespace dgk

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 
 # every symbol include/dg.h declares
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_nodes", "dg_get_leaves",
             "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_bubble", "dg_rhs", "dg_step",
-            "dg_adapt", "dg_indicator", "dg_integrals", "dg_enable_timing", "dg_stage_timing",
+            "dg_adapt", "dg_indicator", "dg_integrals", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
             "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_last_error", "dg_version"]
 
@@ -88,6 +88,7 @@ def load_library(path=None):
         "dg_adapt": (i32, [vp, ctypes.POINTER(AdaptParams), ctypes.POINTER(AdaptReport)]),
         "dg_indicator": (i32, [vp, ctypes.POINTER(ctypes.c_double), sz]),
         "dg_integrals": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "dg_set_option": (i32, [vp, i32, i64]),
         "dg_enable_timing": (i32, [vp, i32]),
         "dg_stage_timing": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]),
         "dg_forest_create": (i32, [i32, ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(vp)]),
@@ -287,6 +288,10 @@ class Mesh:
         if check:
             self._check(st)
         return np.array(list(out))
+
+    def set_stage_kernel(self, layout):
+        """0: one thread per vertical node column (default); 1: one thread per node."""
+        self._check(self.lib.dg_set_option(self.h, 1, int(layout)))
 
     def enable_timing(self, on=True):
         self._check(self.lib.dg_enable_timing(self.h, 1 if on else 0))

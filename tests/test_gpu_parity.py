@@ -67,9 +67,11 @@ MESHES = [
 ]
 
 
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("dim,N,base,length,rounds", MESHES)
-def test_rhs_parity_fp64(pkg, dim, N, base, length, rounds):
+def test_rhs_parity_fp64(pkg, dim, N, base, length, rounds, layout):
     lm, om = _pair(pkg, dim, N, base, length, flags_rounds=rounds)
+    lm.set_stage_kernel(layout)
     q = workloads.random_state(om.nv, om.E, om.np_, seed=N + 10 * dim)
     got = _gpu_rhs(lm, q)
     want = odg.rhs(om, q)
@@ -87,11 +89,13 @@ def test_rest_state_exactly_zero(pkg, precision):
     assert torch.count_nonzero(out).item() == 0
 
 
-@pytest.mark.parametrize("dim,N,base,length,rounds", MESHES[:5])
-def test_rhs_parity_fp32_perturbation(pkg, dim, N, base, length, rounds):
+@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("dim,N,base,length,rounds", MESHES)
+def test_rhs_parity_fp32_perturbation(pkg, dim, N, base, length, rounds, layout):
     # FP32 state and flux arithmetic, FP64 background and pressure perturbation.  Bound: the
     # oracle evaluated on the FP32-rounded input, error <= 2e-5 of max|rhs| per variable.
     lm, om = _pair(pkg, dim, N, base, length, flags_rounds=rounds, precision="fp32")
+    lm.set_stage_kernel(layout)
     q32 = workloads.random_state(om.nv, om.E, om.np_, seed=N + 10 * dim, dtype=np.float32)
     got = _gpu_rhs(lm, q32).astype(np.float64)
     want = odg.rhs(om, q32.astype(np.float64))
@@ -122,8 +126,10 @@ def test_step_parity_rising_bubble(pkg):
     assert _rel_err(got - q0, want - q0) <= 1e-11
 
 
-def test_step_parity_hanging_3d(pkg):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_step_parity_hanging_3d(pkg, layout):
     lm, om = _pair(pkg, 3, 3, (2, 2, 2), (2000.0,) * 3, flags_rounds=((0.3, 11),))
+    lm.set_stage_kernel(layout)
     q0 = workloads.random_state(om.nv, om.E, om.np_, seed=11, rho_scale=1e-4, u_scale=0.1,
                                 theta_scale=0.01)
     lm.set_state(q0)
