@@ -171,6 +171,29 @@ dg_status dg_set_option(dg_mesh* mesh, int32_t option, int64_t value);
 dg_status dg_enable_timing(dg_mesh* mesh, int32_t enable);
 dg_status dg_stage_timing(dg_mesh* mesh, double* total_ms, int64_t* launches, int32_t reset);
 
+/* Allocation-free variant of dg_integrals.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code running while a stream is
+ * captured into a CUDA graph (cudaMalloc cannot be captured), hosts whose device memory is
+ * owned by an external pool, or real-time loops that must stay out of the allocator.  It needs
+ * no dg_mesh: everything comes from the caller, and nothing is allocated (no cudaMalloc,
+ * cudaFree or allocating library call).
+ *   desc          the mesh description (dim, N, base, length, precision, constants);
+ *   elem          device array [num_elements][4] int32: level, c0, c1, c2 of every leaf, in the
+ *                 state's element order (columns 1..4 of dg_get_leaves rows);
+ *   q             device state in the dg_set_state layout and the desc precision;
+ *   out           device array of DG_NUM_INTEGRALS + 1 doubles: the five integrals of
+ *                 dg_integrals, then 1.0 if a non-finite value was met, else 0.0.
+ * Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream): synchronise before
+ * reading `out`.  The reduction scratch is a fixed file-scope device array (about 160 KB, held
+ * by every GPU that loads the library until the process exits); states above 67,108,864 nodes
+ * (elements x (N+1)^d) are rejected with DG_ERR_ARG.  All calls share that array and it keeps
+ * the last call's contents (each call rewrites what it reads); calls that overlap on the GPU
+ * (other streams, unordered host threads) race.  The first call on each device looks up the
+ * array's device address with that device current; make that first call before any stream
+ * capture begins. */
+dg_status dg_integrals_noalloc(const dg_mesh_desc* desc, const int32_t* elem, int64_t num_elements,
+                               const void* q, double* out, void* stream);
+
 /* ---- Host-only forest (no CUDA call): the same tree code dg_adapt runs, exposed so the
  * integer work (leaf order, 2:1 balance, face and mortar lists, transfer map) can be checked
  * on machines without a GPU.  Sec. 3.1 (forest of trees, active leaves), Sec. 3.2.1 (T, B),

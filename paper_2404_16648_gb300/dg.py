@@ -25,7 +25,8 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_bubble", "dg_rhs", "dg_step",
             "dg_adapt", "dg_indicator", "dg_integrals", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
             "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
-            "dg_forest_faces", "dg_forest_regrid", "dg_last_error", "dg_version"]
+            "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_last_error",
+            "dg_version"]
 
 
 class MeshDesc(ctypes.Structure):
@@ -98,6 +99,7 @@ def load_library(path=None):
         "dg_forest_faces": (i32, [vp, ctypes.POINTER(ctypes.c_int64), vp, sz, vp, sz, vp, sz]),
         "dg_forest_regrid": (i32, [vp, ctypes.POINTER(ctypes.c_uint8), i32, i32, vp, sz,
                                    ctypes.POINTER(ctypes.c_int64)]),
+        "dg_integrals_noalloc": (i32, [ctypes.POINTER(MeshDesc), vp, i64, vp, vp, vp]),
         "dg_last_error": (ctypes.c_char_p, [vp]),
         "dg_version": (ctypes.c_char_p, []),
     }
