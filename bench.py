@@ -108,9 +108,14 @@ def _barrier(world):
         dist.barrier()
 
 
+STAGE_KERNEL = None   # None: library default; 0 column layout; 1 node-per-thread layout
+
+
 def build_mesh(pkg, cfg, precision):
     m = pkg.Mesh(cfg["dim"], cfg["N"], cfg["base"], cfg["length"], max_level=cfg["max_level"],
                  precision=precision)
+    if STAGE_KERNEL is not None:
+        m.set_stage_kernel(STAGE_KERNEL)
     pkg.adapt_initial(m, cfg["bubble"], cfg["threshold"], cfg["buffer"])
     return m
 
@@ -244,7 +249,11 @@ def main():
     ap.add_argument("--config", default=workloads.BUBBLE_3D["name"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1],
+                    help="stage kernel layout: 0 column, 1 node-per-thread (default: library's)")
     args = ap.parse_args()
+    global STAGE_KERNEL
+    STAGE_KERNEL = args.stage_kernel
     cfg = workloads.CONFIGS[args.config]
     world, rank, local = _dist()
     regrid_every = cfg.get("regrid_every")
@@ -292,6 +301,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config,
             "precision_path": "FP32 state/flux arithmetic; FP64 background, p' and integrals",
+            "stage_kernel": {None: "default", 0: "column", 1: "node"}[STAGE_KERNEL],
             "elements": r32["elements"], "nodes_per_variable": r32["nodes"],
             "gpu_launches": r32["launches"], "mortar_groups": r32["mortars"],
             "roofline": {"bound": "hbm", "kernel": "stage_kernel", "achieved": achieved,

@@ -106,6 +106,9 @@ const double* d_x(const dg_mesh* m) { return m->d_opsd + 5 * m->n1 * m->n1 + m->
 // (Re)builds the device tables for the current forest; state buffers sized for E elements.
 dg_status rebuild_topology(dg_mesh* m) {
   m->E = m->forest.size();
+  if ((int64_t)(m->NV + 1) * m->E * m->NP >= ((int64_t)1 << 31))
+    return fail(m, DG_ERR_UNSUPPORTED, "mesh too large for 32-bit state offsets (%lld elements)",
+                (long long)m->E);
   m->forest.face_lists(&m->conf, &m->mort, &m->bnd);
   m->G = (int64_t)(m->mort.size() / 7);
   std::vector<int32_t> conn;
@@ -181,7 +184,7 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
                           void* pp_out, int mode, double dt, double ca, double cb, cudaStream_t s) {
   if (m->G > 0) {
     dgk::MortarArgs M{qs, pp_in, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, bgt(m),
-                      m->d_ops, m->ph};
+                      m->d_ops, (float)m->ph.gamma, m->ph};
     bool ok = m->prec == DG_FP64
                   ? (m->D == 2 ? dgk::launch_mortar_f64_2d(m->N, M, s) : dgk::launch_mortar_f64_3d(m->N, M, s))
                   : (m->D == 2 ? dgk::launch_mortar_f32_2d(m->N, M, s) : dgk::launch_mortar_f32_3d(m->N, M, s));
@@ -199,6 +202,8 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
       A.inv2hf[l][a] = (float)A.inv2hd[l][a];
     }
   A.dt = dt; A.ca = ca; A.cb = cb; A.mode = mode; A.variant = m->variant; A.ph = m->ph;
+  A.plane32 = (int32_t)plane(m);
+  A.gammaf = (float)m->ph.gamma; A.gf = (float)m->ph.g;
   const bool timed = m->timing && mode == 1;
   if (timed) {
     while (m->ev.size() < m->ev_used + 2) {

@@ -74,15 +74,32 @@ struct NodeBg {
   T rb, Tb, pb;
 };
 
-// Component `a` of the Euler flux (Sec. 2.1, Eq. "eulervector") at one node, perturbation form:
-// rho': U_a;  U_b: U_b u_a + P' delta_ab;  Theta': (Theta_bar + Theta') u_a.
-// Optionally the wave speed |u_a| + c with c = sqrt(gamma P / rho) of the total state
-// (P = P_bar + P', rho = rho_bar + rho').
+// Reciprocal and square root used by the fluxes.  Deterministic (the same inputs give the same
+// bits wherever they are evaluated), so the two elements of a face agree bit for bit.  FP64:
+// correctly rounded.  FP32: the hardware approximations (about 1 ulp), far below the FP32 path's
+// stated error bound.
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double sqrt_fast(double x) { return __dsqrt_rn(x); }
+__device__ __forceinline__ float sqrt_fast(float x) { return __fmul_rn(x, rsqrtf(x)); }
+
+// Quantities of one node's state that every flux component needs, computed once.
+template <class T>
+struct NodeDer {
+  T rinv;    // 1 / (rho_bar + rho')
+  T Theta;   // Theta_bar + Theta'
+};
+
 template <class T, int D>
-__device__ __forceinline__ void flux_axis(const T* q, const NodeBg<T>& bg, T pp, int a,
-                                          const PhysC& ph, T* F, T* speed) {
-  const T rho = add_rn(bg.rb, q[0]);
-  const T ua = div_rn(q[1 + a], rho);
+__device__ __forceinline__ NodeDer<T> node_der(const T* q, const NodeBg<T>& bg) {
+  return NodeDer<T>{recip(add_rn(bg.rb, q[0])), add_rn(bg.Tb, q[D + 1])};
+}
+
+// Component `a` of the Euler flux (Sec. 2.1, Eq. "eulervector") at one node, perturbation form:
+// rho': U_a;  U_b: U_b u_a + P' delta_ab;  Theta': (Theta_bar + Theta') u_a, with u_a = U_a / rho.
+template <class T, int D>
+__device__ __forceinline__ void flux_axis(const T* q, const NodeDer<T>& nd, T pp, int a, T* F) {
+  const T ua = mul_rn(q[1 + a], nd.rinv);
   F[0] = q[1 + a];
 #pragma unroll
   for (int b = 0; b < D; ++b) {
@@ -90,28 +107,37 @@ __device__ __forceinline__ void flux_axis(const T* q, const NodeBg<T>& bg, T pp,
     if (b == a) f = add_rn(f, pp);
     F[1 + b] = f;
   }
-  F[D + 1] = mul_rn(add_rn(bg.Tb, q[D + 1]), ua);
-  if (speed) {
-    const T P = add_rn(bg.pb, pp);
-    const T c = sqrt_rn(div_rn(mul_rn((T)ph.gamma, P), rho));
-    *speed = add_rn(ua < (T)0 ? -ua : ua, c);
-  }
+  F[D + 1] = mul_rn(nd.Theta, ua);
+}
+
+// Wave speed |u_a| + c, c = sqrt(gamma P / rho) of the total state (P = P_bar + P').
+template <class T>
+__device__ __forceinline__ T wave_speed(const T* q, const NodeDer<T>& nd, const NodeBg<T>& bg, T pp,
+                                        int a, T gamma) {
+  const T ua = mul_rn(q[1 + a], nd.rinv);
+  const T c = sqrt_fast(mul_rn(mul_rn(gamma, add_rn(bg.pb, pp)), nd.rinv));
+  return add_rn(ua < (T)0 ? -ua : ua, c);
 }
 
 // Rusanov flux along +axis a (Sec. 2.2): F* = (F(qm) + F(qp))/2 - lambda/2 (qp - qm),
-// lambda = max(|u_a| + c) over both sides.  qm is the low side, qp the high side.
+// lambda = max(|u_a| + c) over both sides; qm is the low side, qp the high side, with their
+// fluxes Fm, Fp and wave speeds sm, sp already evaluated.
 template <class T, int D>
-__device__ __forceinline__ void rusanov(const T* qm, const NodeBg<T>& bgm, T ppm, const T* qp,
-                                        const NodeBg<T>& bgp, T ppp, int a, const PhysC& ph,
-                                        T* Fs) {
+__device__ __forceinline__ void rusanov(const T* qm, const T* Fm, T sm, const T* qp, const T* Fp,
+                                        T sp, T* Fs) {
   constexpr int NV = D + 2;
-  T Fm[NV], Fp[NV], sm, sp;
-  flux_axis<T, D>(qm, bgm, ppm, a, ph, Fm, &sm);
-  flux_axis<T, D>(qp, bgp, ppp, a, ph, Fp, &sp);
   const T hl = mul_rn((T)0.5, sm > sp ? sm : sp);
 #pragma unroll
   for (int v = 0; v < NV; ++v)
     Fs[v] = sub_rn(mul_rn((T)0.5, add_rn(Fm[v], Fp[v])), mul_rn(hl, sub_rn(qp[v], qm[v])));
+}
+
+// Flux and wave speed of a face state in one call.
+template <class T, int D>
+__device__ __forceinline__ T face_side(const T* q, const NodeBg<T>& bg, T pp, int a, T gamma, T* F) {
+  const NodeDer<T> nd = node_der<T, D>(q, bg);
+  flux_axis<T, D>(q, nd, pp, a, F);
+  return wave_speed<T>(q, nd, bg, pp, a, gamma);
 }
 
 struct StageArgs {
@@ -133,6 +159,8 @@ struct StageArgs {
   double dt, ca, cb;
   int32_t mode;
   int32_t variant;       // 0: column-mapped kernel (default), 1: node-per-thread kernel
+  int32_t plane32;       // `plane` as int32 (the host guarantees (NV+1) * plane < 2^31)
+  float gammaf, gf;      // gamma and g in FP32
   PhysC ph;
 };
 
@@ -146,8 +174,13 @@ struct MortarArgs {
   const double* bg;
   const void* bgt;
   const void* ops;
+  float gammaf;
   PhysC ph;
 };
+
+template <class T> __device__ __forceinline__ T gamma_of(const PhysC& ph, float gf) {
+  return sizeof(T) == 4 ? (T)gf : (T)ph.gamma;
+}
 
 template <class T> __device__ __forceinline__ T inv2h_of(const StageArgs& A, int level, int a);
 template <> __device__ __forceinline__ float inv2h_of<float>(const StageArgs& A, int level, int a) {
@@ -182,6 +215,7 @@ stage_kernel(const StageArgs A) {
   const T* ops = (const T*)A.ops;
   for (int i = tid; i < n1 * n1; i += blockDim.x) sD[i] = ops[i];
   const T w0 = ops[5 * n1 * n1];
+  const T gamma = gamma_of<T>(A.ph, A.gammaf);
   const int le = tid / NP, n = tid - le * NP;
   const int64_t e = (int64_t)blockIdx.x * EPB + le;
   const bool valid = e < A.E;
@@ -189,8 +223,9 @@ stage_kernel(const StageArgs A) {
   idx[0] = n % n1;
   idx[1] = (n / n1) % n1;
   idx[2] = (D == 3) ? n / (n1 * n1) : 0;
-  const T* qs = (const T*)A.qs;
-  const T* ppin = (const T*)A.pp_in;
+  const int P = A.plane32;
+  const T* qe = (const T*)A.qs + (valid ? e : 0) * NP;
+  const T* ppe = (const T*)A.pp_in + (valid ? e : 0) * NP;
   T q[NV], acc[NV], inv2h[D];
   T pp = (T)0;
   NodeBg<T> bg{(T)1, (T)1, (T)1};
@@ -199,10 +234,9 @@ stage_kernel(const StageArgs A) {
 #pragma unroll
   for (int a = 0; a < D; ++a) inv2h[a] = (T)0;
   if (valid) {
-    const size_t base = (size_t)e * NP + n;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) q[v] = qs[(size_t)v * A.plane + base];
-    pp = ppin[base];
+    for (int v = 0; v < NV; ++v) q[v] = qe[v * P + n];
+    pp = ppe[n];
     const int level = A.elem[e * 4];
 #pragma unroll
     for (int a = 0; a < D; ++a) inv2h[a] = inv2h_of<T>(A, level, a);
@@ -210,11 +244,12 @@ stage_kernel(const StageArgs A) {
     bg.rb = b[0]; bg.Tb = b[1]; bg.pb = b[2];
     acc[D] = -(q[0] * (T)A.ph.g);   // buoyancy -rho' g on the vertical momentum
   }
+  const NodeDer<T> nd = node_der<T, D>(q, bg);
   __syncthreads();
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T F[NV];
-    flux_axis<T, D>(q, bg, pp, a, A.ph, F, nullptr);
+    flux_axis<T, D>(q, nd, pp, a, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) sF[le][v][n] = F[v];
     __syncthreads();
@@ -245,26 +280,31 @@ stage_kernel(const StageArgs A) {
 #pragma unroll
       for (int b = 0; b < D; ++b)
         if (b != a) { t += idx[b] * mul; mul *= n1; }
-      T Fs[NV];
-      if (kind == FACE_WALL) {
-        T gq[NV];
+      T Fo[NV], Fs[NV];
+      flux_axis<T, D>(q, nd, pp, a, Fo);
+      if (kind == FACE_WALL || kind == FACE_CONF) {
+        const T so = wave_speed<T>(q, nd, bg, pp, a, gamma);
+        T qo[NV], Fn[NV], sn;
+        if (kind == FACE_WALL) {
+          // mirror state: same Theta, rho and P', normal momentum negated
 #pragma unroll
-        for (int v = 0; v < NV; ++v) gq[v] = q[v];
-        gq[1 + a] = -q[1 + a];
-        if (s) rusanov<T, D>(q, bg, pp, gq, bg, pp, a, A.ph, Fs);
-        else   rusanov<T, D>(gq, bg, pp, q, bg, pp, a, A.ph, Fs);
-      } else if (kind == FACE_CONF) {
-        // the neighbour's matching node: same tangential indices, opposite face; its z (hence
-        // its background) is bit-identical to this node's
-        const int64_t nb = c[1];
-        const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
-        const size_t no = (size_t)nb * NP + n + ((s ? 0 : N) - idx[a]) * stride_a;
-        T qo[NV];
+          for (int v = 0; v < NV; ++v) qo[v] = q[v];
+          qo[1 + a] = -q[1 + a];
+          flux_axis<T, D>(qo, nd, pp, a, Fn);
+          sn = so;
+        } else {
+          // the neighbour's matching node: same tangential indices, opposite face; its z (hence
+          // its background) is bit-identical to this node's
+          const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
+          const int no = n + ((s ? 0 : N) - idx[a]) * stride_a;
+          const T* qb = (const T*)A.qs + (int64_t)c[1] * NP;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) qo[v] = qs[(size_t)v * A.plane + no];
-        const T ppo = ppin[no];
-        if (s) rusanov<T, D>(q, bg, pp, qo, bg, ppo, a, A.ph, Fs);
-        else   rusanov<T, D>(qo, bg, ppo, q, bg, pp, a, A.ph, Fs);
+          for (int v = 0; v < NV; ++v) qo[v] = qb[v * P + no];
+          const T ppo = ((const T*)A.pp_in)[(int64_t)c[1] * NP + no];
+          sn = face_side<T, D>(qo, bg, ppo, a, gamma, Fn);
+        }
+        if (s) rusanov<T, D>(q, Fo, so, qo, Fn, sn, Fs);
+        else   rusanov<T, D>(qo, Fn, sn, q, Fo, so, Fs);
       } else {
         const int64_t g = (kind == FACE_FINE) ? c[2] : c[1];
         const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
@@ -272,18 +312,15 @@ stage_kernel(const StageArgs A) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) Fs[v] = src[(size_t)v * NF];
       }
-      T Fo[NV];
-      flux_axis<T, D>(q, bg, pp, a, A.ph, Fo, nullptr);
       const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += coef * (Fs[v] - Fo[v]);
     }
   }
-  T* out = (T*)A.out;
-  const size_t base = (size_t)e * NP + n;
+  T* oute = (T*)A.out + e * NP;
   if (A.mode == 0) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) out[(size_t)v * A.plane + base] = acc[v];
+    for (int v = 0; v < NV; ++v) oute[v * P + n] = acc[v];
     return;
   }
   T qnew[NV];
@@ -293,14 +330,14 @@ stage_kernel(const StageArgs A) {
     for (int v = 0; v < NV; ++v) qnew[v] = q[v] + dt * acc[v];
   } else {
     const T ca = (T)A.ca, cb = (T)A.cb;
-    const T* qn = (const T*)A.qn;
+    const T* qne = (const T*)A.qn + e * NP;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) qnew[v] = ca * qn[(size_t)v * A.plane + base] + cb * (q[v] + dt * acc[v]);
+    for (int v = 0; v < NV; ++v) qnew[v] = ca * qne[v * P + n] + cb * (q[v] + dt * acc[v]);
   }
 #pragma unroll
-  for (int v = 0; v < NV; ++v) out[(size_t)v * A.plane + base] = qnew[v];
+  for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];
   const double* bd = A.bg + ((size_t)e * n1 + idx[D - 1]) * 4;
-  ((T*)A.pp_out)[base] =
+  ((T*)A.pp_out)[e * NP + n] =
       (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
 }
 
@@ -388,8 +425,12 @@ mortar_kernel(const MortarArgs A) {
   const NodeBg<T> bgf{bt[0], bt[1], bt[2]};
   const T ppf = ((const T*)A.pp_in)[(size_t)ef * NP + nf];
   const T ppc = (T)pressure_pert<SeriesTerms<T>::K>((double)qc[D + 1], bd[3], bd[2], A.ph);
-  if (side) rusanov<T, D>(qc, bgf, ppc, qf, bgf, ppf, a, A.ph, Fs);
-  else      rusanov<T, D>(qf, bgf, ppf, qc, bgf, ppc, a, A.ph, Fs);
+  const T gamma = gamma_of<T>(A.ph, A.gammaf);
+  T Ff[NV], Fc[NV];
+  const T sf = face_side<T, D>(qf, bgf, ppf, a, gamma, Ff);
+  const T sc = face_side<T, D>(qc, bgf, ppc, a, gamma, Fc);
+  if (side) rusanov<T, D>(qc, Fc, sc, qf, Ff, sf, Fs);
+  else      rusanov<T, D>(qf, Ff, sf, qc, Fc, sc, Fs);
   T* mb = (T*)A.mbuf + ((size_t)g * (1 + NSUB) * NV) * NF;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {

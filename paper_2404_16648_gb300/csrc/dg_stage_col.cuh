@@ -55,13 +55,14 @@ __global__ void __launch_bounds__(EPB * ipow(N + 1, D - 1))
 stage_kernel_col(const StageArgs A) {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
   constexpr int NSUB = 1 << (D - 1);
-  constexpr int NT = D - 1;                 // horizontal (tangential-to-z) axes
+  constexpr int NT = D - 1;                 // horizontal axes
   constexpr int P1 = n1 + 1;                // padded row of the state tile
   constexpr int JS = (D == 3) ? n1 : 1;
   constexpr int QT = P1 * JS * n1;          // padded state tile per variable
   constexpr bool VEC = (sizeof(T) == 4) && (n1 % 4 == 0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // horizontal fluxes (reused for the face lifts), state and P' tile, background, D
+  // horizontal fluxes: tile 0 in node order (x lines contiguous), tile 1 (3D) transposed so that
+  // y lines are contiguous; reused for the face lifts.  Then the state and P' tile, background, D.
   T (*sFh)[NT][NV][NP] = reinterpret_cast<T (*)[NT][NV][NP]>(smem_raw);
   T (*sQ)[NV + 1][QT] = reinterpret_cast<T (*)[NV + 1][QT]>(smem_raw + sizeof(T) * EPB * NT * NV * NP);
   T (*sBg)[n1][3] = reinterpret_cast<T (*)[n1][3]>(smem_raw + sizeof(T) * (EPB * NT * NV * NP + EPB * (NV + 1) * QT));
@@ -74,9 +75,11 @@ stage_kernel_col(const StageArgs A) {
   const T* ops = (const T*)A.ops;
   for (int x = tid; x < n1 * n1; x += blockDim.x) sDh[x] = ops[x];
   const T w0 = ops[5 * n1 * n1];
-  const T* qs = (const T*)A.qs;
-  const T* ppin = (const T*)A.pp_in;
-  const T g = (T)A.ph.g;
+  const T gamma = gamma_of<T>(A.ph, A.gammaf);
+  const T g = sizeof(T) == 4 ? (T)A.gf : (T)A.ph.g;
+  const int P = A.plane32;
+  const T* qe = (const T*)A.qs + (valid ? e : 0) * NP;
+  const T* ppe = (const T*)A.pp_in + (valid ? e : 0) * NP;
   T acc[NV][n1];
   T inv2h[D];
   int level = 0;
@@ -90,7 +93,7 @@ stage_kernel_col(const StageArgs A) {
 #pragma unroll
   for (int a = 0; a < D; ++a) inv2h[a] = valid ? inv2h_of<T>(A, level, a) : (T)0;
   __syncthreads();
-  // ---- load the column, fluxes: horizontal ones to shared memory, vertical one kept here
+  // ---- load the column; horizontal fluxes to shared memory, the vertical one kept here
   T Fz[NV][n1];
 #pragma unroll
   for (int k = 0; k < n1; ++k) {
@@ -99,10 +102,9 @@ stage_kernel_col(const StageArgs A) {
     T pp = (T)0;
     NodeBg<T> bg{(T)1, (T)1, (T)1};
     if (valid) {
-      const size_t base = (size_t)e * NP + n;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) q[v] = qs[(size_t)v * A.plane + base];
-      pp = ppin[base];
+      for (int v = 0; v < NV; ++v) q[v] = qe[v * P + n];
+      pp = ppe[n];
       bg = NodeBg<T>{sBg[le][k][0], sBg[le][k][1], sBg[le][k][2]};
     } else {
 #pragma unroll
@@ -115,18 +117,19 @@ stage_kernel_col(const StageArgs A) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v][k] = (T)0;
     acc[D][k] = -(q[0] * g);               // buoyancy -rho' g on the vertical momentum
+    const NodeDer<T> nd = node_der<T, D>(q, bg);
+    T F[NV];
+    flux_axis<T, D>(q, nd, pp, 0, F);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      T F[NV];
-      flux_axis<T, D>(q, bg, pp, a, A.ph, F, nullptr);
-      if (a < NT) {
+    for (int v = 0; v < NV; ++v) sFh[le][0][v][n] = F[v];
+    if (D == 3) {
+      flux_axis<T, D>(q, nd, pp, 1, F);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) sFh[le][a][v][n] = F[v];
-      } else {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Fz[v][k] = F[v];
-      }
+      for (int v = 0; v < NV; ++v) sFh[le][NT - 1][v][NF * k + n1 * ci + cj] = F[v];
     }
+    flux_axis<T, D>(q, nd, pp, D - 1, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fz[v][k] = F[v];
   }
   // ---- vertical derivative from registers, D from constant memory
 #pragma unroll
@@ -139,73 +142,79 @@ stage_kernel_col(const StageArgs A) {
       acc[v][k] -= inv2h[D - 1] * s;
     }
   __syncthreads();
-  // ---- horizontal derivatives through shared memory
-  if (valid) {
-    T Di[n1];
+  // ---- horizontal derivatives through shared memory (contiguous lines, vector loads)
+  auto line_dot = [&](const T* row, const T* Dr) {
+    T s = (T)0;
+    if constexpr (VEC) {
 #pragma unroll
-    for (int m = 0; m < n1; ++m) Di[m] = sDh[ci * n1 + m];
+      for (int m = 0; m < n1; m += 4) {
+        const float4 f = *reinterpret_cast<const float4*>(row + m);
+        s = fma(Dr[m], (T)f.x, s);
+        s = fma(Dr[m + 1], (T)f.y, s);
+        s = fma(Dr[m + 2], (T)f.z, s);
+        s = fma(Dr[m + 3], (T)f.w, s);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < n1; ++m) s = fma(Dr[m], row[m], s);
+    }
+    return s;
+  };
+  if (valid) {
+    T Dr[n1];
+#pragma unroll
+    for (int m = 0; m < n1; ++m) Dr[m] = sDh[ci * n1 + m];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int k = 0; k < n1; ++k) {
-        const T* row = &sFh[le][0][v][NF * k + n1 * cj];
-        T s = (T)0;
-        if constexpr (VEC) {
-#pragma unroll
-          for (int m = 0; m < n1; m += 4) {
-            const float4 f = *reinterpret_cast<const float4*>(row + m);
-            s = fma(Di[m], (T)f.x, s);
-            s = fma(Di[m + 1], (T)f.y, s);
-            s = fma(Di[m + 2], (T)f.z, s);
-            s = fma(Di[m + 3], (T)f.w, s);
-          }
-        } else {
-#pragma unroll
-          for (int m = 0; m < n1; ++m) s = fma(Di[m], row[m], s);
-        }
-        acc[v][k] -= inv2h[0] * s;
-      }
+      for (int k = 0; k < n1; ++k)
+        acc[v][k] -= inv2h[0] * line_dot(&sFh[le][0][v][NF * k + n1 * cj], Dr);
     if (D == 3) {
-      T Dj[n1];
 #pragma unroll
-      for (int m = 0; m < n1; ++m) Dj[m] = sDh[cj * n1 + m];
+      for (int m = 0; m < n1; ++m) Dr[m] = sDh[cj * n1 + m];
 #pragma unroll
       for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int k = 0; k < n1; ++k) {
-          const T* col = &sFh[le][NT - 1][v][NF * k + ci];
-          T s = (T)0;
-#pragma unroll
-          for (int m = 0; m < n1; ++m) s = fma(Dj[m], col[n1 * m], s);
-          acc[v][k] -= inv2h[1] * s;
-        }
+        for (int k = 0; k < n1; ++k)
+          acc[v][k] -= inv2h[1] * line_dot(&sFh[le][NT - 1][v][NF * k + n1 * ci], Dr);
     }
   }
   __syncthreads();
   // ---- face terms
   const T* mbuf = (const T*)A.mbuf;
   T (*sLift)[NV][NF] = reinterpret_cast<T (*)[NV][NF]>(&sFh[le][0][0][0]);   // [2*NT][NV][NF]
-  auto face_flux = [&](int a, int s, int fn, const T* qo_own, T pp_own, const NodeBg<T>& bg,
-                       int own_node, T* Fs) {
+  // lift contribution coef (F* - F_own) of face (a, s) at face node fn, own node own_node
+  auto face_lift = [&](int a, int s, int fn, int own_qi, int k, int own_node, T* L) {
     const int32_t* c = A.conn + ((size_t)e * 2 * D + 2 * a + s) * 5;
     const int kind = c[0];
-    if (kind == FACE_WALL) {
-      T gq[NV];
+    T q[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) gq[v] = qo_own[v];
-      gq[1 + a] = -qo_own[1 + a];
-      if (s) rusanov<T, D>(qo_own, bg, pp_own, gq, bg, pp_own, a, A.ph, Fs);
-      else   rusanov<T, D>(gq, bg, pp_own, qo_own, bg, pp_own, a, A.ph, Fs);
-    } else if (kind == FACE_CONF) {
-      const int64_t nb = c[1];
-      const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
-      const size_t no = (size_t)nb * NP + own_node + (s ? -N : N) * stride_a;
-      T qo[NV];
+    for (int v = 0; v < NV; ++v) q[v] = sQ[le][v][own_qi];
+    const T pp = sQ[le][NV][own_qi];
+    const NodeBg<T> bg{sBg[le][k][0], sBg[le][k][1], sBg[le][k][2]};
+    const NodeDer<T> nd = node_der<T, D>(q, bg);
+    T Fo[NV], Fs[NV];
+    flux_axis<T, D>(q, nd, pp, a, Fo);
+    if (kind == FACE_WALL || kind == FACE_CONF) {
+      const T so = wave_speed<T>(q, nd, bg, pp, a, gamma);
+      T qo[NV], Fn[NV], sn;
+      if (kind == FACE_WALL) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) qo[v] = qs[(size_t)v * A.plane + no];
-      const T ppo = ppin[no];
-      if (s) rusanov<T, D>(qo_own, bg, pp_own, qo, bg, ppo, a, A.ph, Fs);
-      else   rusanov<T, D>(qo, bg, ppo, qo_own, bg, pp_own, a, A.ph, Fs);
+        for (int v = 0; v < NV; ++v) qo[v] = q[v];
+        qo[1 + a] = -q[1 + a];
+        flux_axis<T, D>(qo, nd, pp, a, Fn);
+        sn = so;
+      } else {
+        const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
+        const int no = own_node + (s ? -N : N) * stride_a;
+        const T* qb = (const T*)A.qs + (int64_t)c[1] * NP;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) qo[v] = qb[v * P + no];
+        const T ppo = ((const T*)A.pp_in)[(int64_t)c[1] * NP + no];
+        sn = face_side<T, D>(qo, bg, ppo, a, gamma, Fn);
+      }
+      if (s) rusanov<T, D>(q, Fo, so, qo, Fn, sn, Fs);
+      else   rusanov<T, D>(qo, Fn, sn, q, Fo, so, Fs);
     } else {
       const int64_t gg = (kind == FACE_FINE) ? c[2] : c[1];
       const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
@@ -213,49 +222,34 @@ stage_kernel_col(const StageArgs A) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Fs[v] = src[(size_t)v * NF];
     }
+    const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) L[v] = coef * (Fs[v] - Fo[v]);
   };
   if (valid) {
-    // horizontal-normal faces: thread t takes face node t
+    // horizontal-normal faces: thread t takes face node t (the other horizontal axis fastest)
 #pragma unroll
     for (int a = 0; a < NT; ++a) {
-      // tangential coordinates of face node t: the other horizontal axis (3D) fastest, then k
       const int u = (D == 3) ? t % n1 : 0;
       const int k = (D == 3) ? t / n1 : t;
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         int ii, jj;
         if (a == 0) { ii = s ? N : 0; jj = u; } else { ii = u; jj = s ? N : 0; }
-        const int qi = ii + P1 * (jj + JS * k);
-        T qo_own[NV];
+        T L[NV];
+        face_lift(a, s, t, ii + P1 * (jj + JS * k), k, ii + n1 * jj + NF * k, L);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) qo_own[v] = sQ[le][v][qi];
-        const T pp_own = sQ[le][NV][qi];
-        const NodeBg<T> bg{sBg[le][k][0], sBg[le][k][1], sBg[le][k][2]};
-        const int own_node = ii + n1 * jj + NF * k;
-        T Fs[NV], Fo[NV];
-        face_flux(a, s, t, qo_own, pp_own, bg, own_node, Fs);
-        flux_axis<T, D>(qo_own, bg, pp_own, a, A.ph, Fo, nullptr);
-        const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) sLift[2 * a + s][v][t] = coef * (Fs[v] - Fo[v]);
+        for (int v = 0; v < NV; ++v) sLift[2 * a + s][v][t] = L[v];
       }
     }
     // bottom and top faces: every column owns one node on each
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const int k = s ? N : 0;
-      const int qi = ci + P1 * (cj + JS * k);
-      T qo_own[NV];
+      T L[NV];
+      face_lift(D - 1, s, t, ci + P1 * (cj + JS * k), k, t + NF * k, L);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) qo_own[v] = sQ[le][v][qi];
-      const T pp_own = sQ[le][NV][qi];
-      const NodeBg<T> bg{sBg[le][k][0], sBg[le][k][1], sBg[le][k][2]};
-      T Fs[NV], Fo[NV];
-      face_flux(D - 1, s, t, qo_own, pp_own, bg, t + NF * k, Fs);
-      flux_axis<T, D>(qo_own, bg, pp_own, D - 1, A.ph, Fo, nullptr);
-      const T coef = s ? -(inv2h[D - 1] / w0) : inv2h[D - 1] / w0;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v][k] += coef * (Fs[v] - Fo[v]);
+      for (int v = 0; v < NV; ++v) acc[v][k] += L[v];
     }
   }
   __syncthreads();
@@ -275,34 +269,31 @@ stage_kernel_col(const StageArgs A) {
     }
   }
   // ---- output
-  T* out = (T*)A.out;
+  T* oute = (T*)A.out + e * NP;
   if (A.mode == 0) {
 #pragma unroll
-    for (int k = 0; k < n1; ++k) {
-      const size_t base = (size_t)e * NP + t + NF * k;
+    for (int k = 0; k < n1; ++k)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) out[(size_t)v * A.plane + base] = acc[v][k];
-    }
+      for (int v = 0; v < NV; ++v) oute[v * P + t + NF * k] = acc[v][k];
     return;
   }
   const T dt = (T)A.dt, ca = (T)A.ca, cb = (T)A.cb;
   const bool first = A.ca == 0.0;
-  const T* qn = (const T*)A.qn;
-  T* ppo = (T*)A.pp_out;
+  const T* qne = (const T*)A.qn + e * NP;
+  T* ppo = (T*)A.pp_out + e * NP;
 #pragma unroll
   for (int k = 0; k < n1; ++k) {
-    const size_t base = (size_t)e * NP + t + NF * k;
+    const int n = t + NF * k;
     const int qi = ci + P1 * (cj + JS * k);
     T qnew[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const T qsv = sQ[le][v][qi];
-      qnew[v] = first ? qsv + dt * acc[v][k]
-                      : ca * qn[(size_t)v * A.plane + base] + cb * (qsv + dt * acc[v][k]);
-      out[(size_t)v * A.plane + base] = qnew[v];
+      qnew[v] = first ? qsv + dt * acc[v][k] : ca * qne[v * P + n] + cb * (qsv + dt * acc[v][k]);
+      oute[v * P + n] = qnew[v];
     }
     const double* bd = A.bg + ((size_t)e * n1 + k) * 4;
-    ppo[base] = (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
+    ppo[n] = (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
   }
 }
 
