@@ -249,8 +249,9 @@ def main():
     ap.add_argument("--config", default=workloads.BUBBLE_3D["name"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1],
-                    help="stage kernel layout: 0 column, 1 node-per-thread (default: library's)")
+    ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2],
+                    help="stage kernel layout: 0 column, 1 node-per-thread, 2 column with "
+                         "asynchronous staging (default: the library's)")
     args = ap.parse_args()
     global STAGE_KERNEL
     STAGE_KERNEL = args.stage_kernel
@@ -301,7 +302,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config,
             "precision_path": "FP32 state/flux arithmetic; FP64 background, p' and integrals",
-            "stage_kernel": {None: "default", 0: "column", 1: "node"}[STAGE_KERNEL],
+            "stage_kernel": {None: "default", 0: "column", 1: "node", 2: "column-async"}[STAGE_KERNEL],
             "elements": r32["elements"], "nodes_per_variable": r32["nodes"],
             "gpu_launches": r32["launches"], "mortar_groups": r32["mortars"],
             "roofline": {"bound": "hbm", "kernel": "stage_kernel", "achieved": achieved,

@@ -254,7 +254,7 @@ extern "C" {
 dg_status dg_set_option(dg_mesh* m, int32_t option, int64_t value) {
   if (!m) return DG_ERR_ARG;
   if (option == DG_OPT_STAGE_KERNEL) {
-    if (value != 0 && value != 1) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0 or 1");
+    if (value < 0 || value > 2) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0, 1 or 2");
     m->variant = (int)value;
     return DG_OK;
   }

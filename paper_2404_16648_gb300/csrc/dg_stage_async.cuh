@@ -1,0 +1,322 @@
+// Column-mapped fused stage kernel with asynchronous staging (layout 2).
+//
+// Same operator and thread layout as stage_kernel_col (one thread per vertical node column),
+// but every global read of the CTA is issued up front as cp.async copies into shared memory:
+// the element's state and P' planes (contiguous, 16-byte chunks), its background column, the
+// neighbour traces of its conforming faces and the mortar fluxes of its hanging faces.  The
+// q^n tile of the Shu-Osher combination is requested as soon as the derivative tiles are free
+// and lands while the face terms are computed.  The computation then runs from shared memory,
+// so a CTA waits on memory twice instead of once per dependent load chain, and the resident CTAs
+// of an SM overlap one another's copies with their arithmetic.
+#pragma once
+#include "dg_stage_col.cuh"
+
+namespace dgk {
+
+__device__ __forceinline__ void cp_async_bytes(void* smem, const void* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Copies `count` elements of T from a global run to shared memory with the threads
+// [tid0, tid0 + nthr) of the CTA; 16-byte copies when both ends allow it.
+template <class T>
+__device__ __forceinline__ void stage_run(T* dst, const T* src, int count, int lane, int nthr) {
+  constexpr int per16 = 16 / sizeof(T);
+  const bool aligned = ((((uintptr_t)dst) | ((uintptr_t)src)) & 15) == 0 && (count % per16) == 0;
+  if (aligned) {
+    for (int c = lane; c < count / per16; c += nthr) cp_async_bytes(dst + c * per16, src + c * per16, 16);
+  } else {
+    for (int c = lane; c < count; c += nthr) cp_async_bytes(dst + c, src + c, (int)sizeof(T));
+  }
+}
+
+// Shared memory of the asynchronous kernel per CTA (bytes), per element:
+//   region A  max(horizontal flux tiles, lifts + q^n tile)
+//   sQ        (NV + 1) x NP     state and P'
+//   sNb       2d x (NV + 1) x NF  neighbour traces / mortar fluxes per face
+//   sBg       n1 x 4            background column (T)
+// plus the derivative matrix once.
+template <class T, int D, int N>
+__host__ __device__ constexpr int async_region_a() {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2, NT = D - 1;
+  constexpr int tiles = NT * NV * NP;
+  constexpr int lifts_qn = 2 * NT * NV * NF + NV * NP;
+  return ((tiles > lifts_qn ? tiles : lifts_qn) + 3) / 4 * 4;
+}
+template <class T, int D, int N>
+__host__ __device__ constexpr int async_elem_words() {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  return async_region_a<T, D, N>() + ((NV + 1) * NP + 3) / 4 * 4 + (2 * D * (NV + 1) * NF + 3) / 4 * 4 + n1 * 4;
+}
+template <class T, int D, int N, int EPB>
+__host__ __device__ constexpr size_t async_smem_bytes() {
+  return sizeof(T) * ((size_t)EPB * async_elem_words<T, D, N>() + (size_t)(N + 1) * (N + 1));
+}
+
+template <class T, int D, int N, int EPB>
+__global__ void __launch_bounds__(EPB * ipow(N + 1, D - 1))
+stage_kernel_async(const StageArgs A) {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  constexpr int NSUB = 1 << (D - 1);
+  constexpr int NT = D - 1;
+  constexpr int RA = async_region_a<T, D, N>();
+  constexpr int RQ = ((NV + 1) * NP + 3) / 4 * 4;
+  constexpr int RN = (2 * D * (NV + 1) * NF + 3) / 4 * 4;
+  constexpr int EW = async_elem_words<T, D, N>();
+  constexpr bool VEC = (sizeof(T) == 4) && (n1 % 4 == 0);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
+  const int le = tid / NF, t = tid - le * NF;
+  T* base = reinterpret_cast<T*>(smem_raw) + le * EW;
+  T* sA = base;                       // flux tiles; later lifts [2NT][NV][NF] then q^n [NV][NP]
+  T* sQ = base + RA;                  // [NV + 1][NP]
+  T* sNb = base + RA + RQ;            // [2D][NV + 1][NF]
+  T* sBg = base + RA + RQ + RN;       // [n1][4]
+  T* sDh = reinterpret_cast<T*>(smem_raw) + EPB * EW;
+  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const bool valid = e < A.E;
+  const int ci = t % n1, cj = (D == 3) ? t / n1 : 0;
+  const int P = A.plane32;
+  const T* qe = (const T*)A.qs + (valid ? e : 0) * NP;
+  // ---- stage 1: own state, P', background column (contiguous runs)
+  if (valid) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) stage_run<T>(sQ + v * NP, qe + v * P, NP, t, NF);
+    stage_run<T>(sQ + NV * NP, (const T*)A.pp_in + e * NP, NP, t, NF);
+    stage_run<T>(sBg, (const T*)A.bgt + e * n1 * 4, n1 * 4, t, NF);
+  }
+  const T* ops = (const T*)A.ops;
+  for (int x = tid; x < n1 * n1; x += blockDim.x) sDh[x] = ops[x];
+  // ---- neighbour traces of conforming faces, mortar fluxes of hanging faces
+  int kinds[2 * D];
+  if (valid) {
+#pragma unroll
+    for (int f = 0; f < 2 * D; ++f) {
+      const int32_t* c = A.conn + ((size_t)e * 2 * D + f) * 5;
+      const int kind = c[0];
+      kinds[f] = kind;
+      const int a = f >> 1, s = f & 1;
+      T* dst = sNb + f * (NV + 1) * NF;
+      if (kind == FACE_CONF) {
+        const int no = face_node<D, N>(a, 1 - s, t);
+        const T* qb = (const T*)A.qs + (int64_t)c[1] * NP;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) cp_async_bytes(dst + v * NF + t, qb + v * P + no, (int)sizeof(T));
+        cp_async_bytes(dst + NV * NF + t, (const T*)A.pp_in + (int64_t)c[1] * NP + no, (int)sizeof(T));
+      } else if (kind == FACE_FINE || kind == FACE_COARSE) {
+        const int64_t gg = (kind == FACE_FINE) ? c[2] : c[1];
+        const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
+        const T* src = (const T*)A.mbuf + (((size_t)gg * (1 + NSUB) + slot) * NV) * NF;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) cp_async_bytes(dst + v * NF + t, src + v * NF + t, (int)sizeof(T));
+      }
+    }
+  }
+  cp_async_commit();
+  const T w0 = ops[5 * n1 * n1];
+  const T gamma = gamma_of<T>(A.ph, A.gammaf);
+  const T g = sizeof(T) == 4 ? (T)A.gf : (T)A.ph.g;
+  T inv2h[D];
+  const int level = valid ? A.elem[e * 4] : 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) inv2h[a] = valid ? inv2h_of<T>(A, level, a) : (T)0;
+  cp_async_wait_all();
+  __syncthreads();
+  // ---- column fluxes; horizontal ones to the tiles, the vertical one kept in registers
+  T acc[NV][n1];
+  T Fz[NV][n1];
+#pragma unroll
+  for (int k = 0; k < n1; ++k) {
+    const int n = t + NF * k;
+    T q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = valid ? sQ[v * NP + n] : (T)0;
+    const T pp = valid ? sQ[NV * NP + n] : (T)0;
+    const NodeBg<T> bg = valid ? NodeBg<T>{sBg[k * 4], sBg[k * 4 + 1], sBg[k * 4 + 2]}
+                               : NodeBg<T>{(T)1, (T)1, (T)1};
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v][k] = (T)0;
+    acc[D][k] = -(q[0] * g);               // buoyancy -rho' g on the vertical momentum
+    const NodeDer<T> nd = node_der<T, D>(q, bg);
+    T F[NV];
+    flux_axis<T, D>(q, nd, pp, 0, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) sA[v * NP + n] = F[v];
+    if (D == 3) {
+      flux_axis<T, D>(q, nd, pp, 1, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sA[(NV + v) * NP + NF * k + n1 * ci + cj] = F[v];
+    }
+    flux_axis<T, D>(q, nd, pp, D - 1, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fz[v][k] = F[v];
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int k = 0; k < n1; ++k) {
+      T s = (T)0;
+#pragma unroll
+      for (int m = 0; m < n1; ++m) s = fma(dtab<T>(dtab_offset(N) + k * n1 + m), Fz[v][m], s);
+      acc[v][k] -= inv2h[D - 1] * s;
+    }
+  __syncthreads();
+  auto line_dot = [&](const T* row, const T* Dr) {
+    T s = (T)0;
+    if constexpr (VEC) {
+#pragma unroll
+      for (int m = 0; m < n1; m += 4) {
+        const float4 f = *reinterpret_cast<const float4*>(row + m);
+        s = fma(Dr[m], (T)f.x, s);
+        s = fma(Dr[m + 1], (T)f.y, s);
+        s = fma(Dr[m + 2], (T)f.z, s);
+        s = fma(Dr[m + 3], (T)f.w, s);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < n1; ++m) s = fma(Dr[m], row[m], s);
+    }
+    return s;
+  };
+  if (valid) {
+    T Dr[n1];
+#pragma unroll
+    for (int m = 0; m < n1; ++m) Dr[m] = sDh[ci * n1 + m];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int k = 0; k < n1; ++k) acc[v][k] -= inv2h[0] * line_dot(&sA[v * NP + NF * k + n1 * cj], Dr);
+    if (D == 3) {
+#pragma unroll
+      for (int m = 0; m < n1; ++m) Dr[m] = sDh[cj * n1 + m];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+          acc[v][k] -= inv2h[1] * line_dot(&sA[(NV + v) * NP + NF * k + n1 * ci], Dr);
+    }
+  }
+  __syncthreads();
+  // ---- the tiles are free: request the q^n tile behind the lifts
+  T* sLift = sA;                           // [2NT][NV][NF]
+  T* sQn = sA + 2 * NT * NV * NF;          // [NV][NP]
+  const bool first = A.ca == 0.0;
+  if (valid && A.mode == 1 && !first) {
+    const T* qne = (const T*)A.qn + e * NP;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) stage_run<T>(sQn + v * NP, qne + v * P, NP, t, NF);
+  }
+  cp_async_commit();
+  // ---- face terms, all operands in shared memory
+  auto face_lift = [&](int a, int s, int fn, int own_node, int k, T* L) {
+    const int f = 2 * a + s;
+    const int kind = kinds[f];
+    T q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = sQ[v * NP + own_node];
+    const T pp = sQ[NV * NP + own_node];
+    const NodeBg<T> bg{sBg[k * 4], sBg[k * 4 + 1], sBg[k * 4 + 2]};
+    const NodeDer<T> nd = node_der<T, D>(q, bg);
+    const T* nb = sNb + f * (NV + 1) * NF;
+    T Fo[NV], Fs[NV];
+    flux_axis<T, D>(q, nd, pp, a, Fo);
+    if (kind == FACE_WALL || kind == FACE_CONF) {
+      const T so = wave_speed<T>(q, nd, bg, pp, a, gamma);
+      T qo[NV], Fn[NV], sn;
+      if (kind == FACE_WALL) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) qo[v] = q[v];
+        qo[1 + a] = -q[1 + a];
+        flux_axis<T, D>(qo, nd, pp, a, Fn);
+        sn = so;
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) qo[v] = nb[v * NF + fn];
+        sn = face_side<T, D>(qo, bg, nb[NV * NF + fn], a, gamma, Fn);
+      }
+      if (s) rusanov<T, D>(q, Fo, so, qo, Fn, sn, Fs);
+      else   rusanov<T, D>(qo, Fn, sn, q, Fo, so, Fs);
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fs[v] = nb[v * NF + fn];
+    }
+    const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) L[v] = coef * (Fs[v] - Fo[v]);
+  };
+  if (valid) {
+#pragma unroll
+    for (int a = 0; a < NT; ++a) {
+      const int u = (D == 3) ? t % n1 : 0;
+      const int k = (D == 3) ? t / n1 : t;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        int ii, jj;
+        if (a == 0) { ii = s ? N : 0; jj = u; } else { ii = u; jj = s ? N : 0; }
+        T L[NV];
+        face_lift(a, s, t, ii + n1 * jj + NF * k, k, L);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) sLift[((2 * a + s) * NV + v) * NF + t] = L[v];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int k = s ? N : 0;
+      T L[NV];
+      face_lift(D - 1, s, t, t + NF * k, k, L);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v][k] += L[v];
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (!valid) return;
+#pragma unroll
+  for (int a = 0; a < NT; ++a) {
+    const int own = (a == 0) ? ci : cj;
+    const int u = (a == 0) ? cj : ci;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (own != (s ? N : 0)) continue;
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int k = 0; k < n1; ++k)
+          acc[v][k] += sLift[((2 * a + s) * NV + v) * NF + (D == 3 ? u : 0) + (D == 3 ? n1 : 1) * k];
+    }
+  }
+  // ---- output
+  T* oute = (T*)A.out + e * NP;
+  if (A.mode == 0) {
+#pragma unroll
+    for (int k = 0; k < n1; ++k)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) oute[v * P + t + NF * k] = acc[v][k];
+    return;
+  }
+  const T dt = (T)A.dt, ca = (T)A.ca, cb = (T)A.cb;
+  T* ppo = (T*)A.pp_out + e * NP;
+#pragma unroll
+  for (int k = 0; k < n1; ++k) {
+    const int n = t + NF * k;
+    T qnew[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T qsv = sQ[v * NP + n];
+      qnew[v] = first ? qsv + dt * acc[v][k] : ca * sQn[v * NP + n] + cb * (qsv + dt * acc[v][k]);
+      oute[v * P + n] = qnew[v];
+    }
+    const double* bd = A.bg + ((size_t)e * n1 + k) * 4;
+    ppo[n] = (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
+  }
+}
+
+}  // namespace dgk

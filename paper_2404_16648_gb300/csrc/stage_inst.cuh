@@ -1,7 +1,7 @@
 // Instantiates the stage and mortar kernels of one (precision, dimension) for N = 1..8.
 // Included by stage_<prec>_<dim>.cu with DG_T and DG_D defined.
 #include "dg_launch.hpp"
-#include "dg_stage_col.cuh"
+#include "dg_stage_async.cuh"
 
 namespace dgk {
 namespace {
@@ -32,8 +32,26 @@ cudaError_t run_stage_col(const StageArgs& A, cudaStream_t s) {
 }
 
 template <class T, int D, int N>
+cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
+  constexpr int NF = ipow(N + 1, D - 1);
+  constexpr int EPB = NF >= 64 ? 1 : (128 / NF > 0 ? 128 / NF : 1);
+  constexpr size_t smem = async_smem_bytes<T, D, N, EPB>();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel_async<T, D, N, EPB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
+  if (blocks) stage_kernel_async<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
+  return cudaSuccess;
+}
+
+template <class T, int D, int N>
 void run_stage(const StageArgs& A, cudaStream_t s) {
   if (A.variant == 1) run_stage_node<T, D, N>(A, s);
+  else if (A.variant == 2) run_stage_async<T, D, N>(A, s);
   else run_stage_col<T, D, N>(A, s);
 }
 
