@@ -50,8 +50,8 @@ __device__ __forceinline__ float sqrt_rn(float a) { return __fsqrt_rn(a); }
 // through the exact identity P' = P_bar ((1 + x)^gamma - 1), x = Theta' / Theta_bar, which has
 // no cancellation between two ~1e5 Pa values.  For |x| <= 2^-5 the binomial series
 // sum_{k=1..K} binom(gamma, k) x^k is summed by Horner's rule: K = 11 keeps the truncation below
-// 1e-19 relative (FP64 path, integrals), K = 5 below 2e-9 relative, far under the FP32
-// rounding of the result (FP32 path).  Larger |x| take expm1(gamma log1p(x)).
+// 1e-19 relative (FP64 path, integrals), K = 4 below 8e-9 relative, under the FP32 rounding of
+// the result (FP32 path).  Larger |x| take expm1(gamma log1p(x)).
 template <int K>
 __device__ __forceinline__ double pressure_pert(double tp, double invTb, double pb,
                                                 const PhysC& ph) {
@@ -66,7 +66,7 @@ __device__ __forceinline__ double pressure_pert(double tp, double invTb, double 
 }
 
 template <class T> struct SeriesTerms { static constexpr int K = kSeries; };
-template <> struct SeriesTerms<float> { static constexpr int K = 5; };
+template <> struct SeriesTerms<float> { static constexpr int K = 4; };
 
 // Background and pressure at one node, in the flux arithmetic type T.
 template <class T>

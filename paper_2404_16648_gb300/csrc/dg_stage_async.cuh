@@ -4,10 +4,11 @@
 // but every global read of the CTA is issued up front as cp.async copies into shared memory:
 // the element's state and P' planes (contiguous, 16-byte chunks), its background column, the
 // neighbour traces of its conforming faces and the mortar fluxes of its hanging faces.  The
-// q^n tile of the Shu-Osher combination is requested as soon as the derivative tiles are free
-// and lands while the face terms are computed.  The computation then runs from shared memory,
-// so a CTA waits on memory twice instead of once per dependent load chain, and the resident CTAs
-// of an SM overlap one another's copies with their arithmetic.
+// column's q^n values (Shu-Osher combination) are loaded into registers before the face terms
+// and consumed at the end.  The computation runs from shared memory, so a CTA waits on memory
+// once instead of once per dependent load chain, and the resident CTAs of an SM overlap one
+// another's copies with their arithmetic.  One horizontal flux tile serves both horizontal
+// axes (the y fluxes are recomputed from the staged state), which keeps the CTA at 32 KB.
 #pragma once
 #include "dg_stage_col.cuh"
 
@@ -39,7 +40,7 @@ __device__ __forceinline__ void stage_run(T* dst, const T* src, int count, int l
 }
 
 // Shared memory of the asynchronous kernel per CTA (bytes), per element:
-//   region A  max(horizontal flux tiles, lifts + q^n tile)
+//   region A  max(one horizontal flux tile, face lifts)
 //   sQ        (NV + 1) x NP     state and P'
 //   sNb       2d x (NV + 1) x NF  neighbour traces / mortar fluxes per face
 //   sBg       n1 x 4            background column (T)
@@ -47,9 +48,9 @@ __device__ __forceinline__ void stage_run(T* dst, const T* src, int count, int l
 template <class T, int D, int N>
 __host__ __device__ constexpr int async_region_a() {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2, NT = D - 1;
-  constexpr int tiles = NT * NV * NP;
-  constexpr int lifts_qn = 2 * NT * NV * NF + NV * NP;
-  return ((tiles > lifts_qn ? tiles : lifts_qn) + 3) / 4 * 4;
+  constexpr int tile = NV * NP;
+  constexpr int lifts = 2 * NT * NV * NF;
+  return ((tile > lifts ? tile : lifts) + 3) / 4 * 4;
 }
 template <class T, int D, int N>
 __host__ __device__ constexpr int async_elem_words() {
@@ -76,7 +77,7 @@ stage_kernel_async(const StageArgs A) {
   const int tid = threadIdx.x;
   const int le = tid / NF, t = tid - le * NF;
   T* base = reinterpret_cast<T*>(smem_raw) + le * EW;
-  T* sA = base;                       // flux tiles; later lifts [2NT][NV][NF] then q^n [NV][NP]
+  T* sA = base;                       // one horizontal flux tile; later the lifts [2NT][NV][NF]
   T* sQ = base + RA;                  // [NV + 1][NP]
   T* sNb = base + RA + RQ;            // [2D][NV + 1][NF]
   T* sBg = base + RA + RQ + RN;       // [n1][4]
@@ -150,11 +151,6 @@ stage_kernel_async(const StageArgs A) {
     flux_axis<T, D>(q, nd, pp, 0, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) sA[v * NP + n] = F[v];
-    if (D == 3) {
-      flux_axis<T, D>(q, nd, pp, 1, F);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sA[(NV + v) * NP + NF * k + n1 * ci + cj] = F[v];
-    }
     flux_axis<T, D>(q, nd, pp, D - 1, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) Fz[v][k] = F[v];
@@ -194,27 +190,49 @@ stage_kernel_async(const StageArgs A) {
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int k = 0; k < n1; ++k) acc[v][k] -= inv2h[0] * line_dot(&sA[v * NP + NF * k + n1 * cj], Dr);
-    if (D == 3) {
+  }
+  if (D == 3) {
+    // y fluxes recomputed from the staged state into the same tile, transposed so that the
+    // y lines are contiguous
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < n1; ++k) {
+      const int n = t + NF * k;
+      T q[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) q[v] = valid ? sQ[v * NP + n] : (T)0;
+      const T pp = valid ? sQ[NV * NP + n] : (T)0;
+      const NodeBg<T> bg = valid ? NodeBg<T>{sBg[k * 4], sBg[k * 4 + 1], sBg[k * 4 + 2]}
+                                 : NodeBg<T>{(T)1, (T)1, (T)1};
+      T F[NV];
+      flux_axis<T, D>(q, node_der<T, D>(q, bg), pp, 1, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sA[v * NP + NF * k + n1 * ci + cj] = F[v];
+    }
+    __syncthreads();
+    if (valid) {
+      T Dr[n1];
 #pragma unroll
       for (int m = 0; m < n1; ++m) Dr[m] = sDh[cj * n1 + m];
 #pragma unroll
       for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int k = 0; k < n1; ++k)
-          acc[v][k] -= inv2h[1] * line_dot(&sA[(NV + v) * NP + NF * k + n1 * ci], Dr);
+          acc[v][k] -= inv2h[1] * line_dot(&sA[v * NP + NF * k + n1 * ci], Dr);
     }
   }
   __syncthreads();
-  // ---- the tiles are free: request the q^n tile behind the lifts
+  // ---- the tile is free for the lifts; q^n of this column is requested now and used last
   T* sLift = sA;                           // [2NT][NV][NF]
-  T* sQn = sA + 2 * NT * NV * NF;          // [NV][NP]
   const bool first = A.ca == 0.0;
+  T qn_col[NV][n1];
   if (valid && A.mode == 1 && !first) {
     const T* qne = (const T*)A.qn + e * NP;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) stage_run<T>(sQn + v * NP, qne + v * P, NP, t, NF);
+    for (int k = 0; k < n1; ++k)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qn_col[v][k] = qne[v * P + t + NF * k];
   }
-  cp_async_commit();
   // ---- face terms, all operands in shared memory
   auto face_lift = [&](int a, int s, int fn, int own_node, int k, T* L) {
     const int f = 2 * a + s;
@@ -276,7 +294,6 @@ stage_kernel_async(const StageArgs A) {
       for (int v = 0; v < NV; ++v) acc[v][k] += L[v];
     }
   }
-  cp_async_wait_all();
   __syncthreads();
   if (!valid) return;
 #pragma unroll
@@ -311,7 +328,7 @@ stage_kernel_async(const StageArgs A) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       const T qsv = sQ[v * NP + n];
-      qnew[v] = first ? qsv + dt * acc[v][k] : ca * sQn[v * NP + n] + cb * (qsv + dt * acc[v][k]);
+      qnew[v] = first ? qsv + dt * acc[v][k] : ca * qn_col[v][k] + cb * (qsv + dt * acc[v][k]);
       oute[v * P + n] = qnew[v];
     }
     const double* bd = A.bg + ((size_t)e * n1 + k) * 4;
