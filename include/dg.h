@@ -160,8 +160,8 @@ dg_status dg_indicator(dg_mesh* mesh, double* out, size_t cap);
 dg_status dg_integrals(dg_mesh* mesh, double out[DG_NUM_INTEGRALS]);
 
 /* Tuning options.  DG_OPT_STAGE_KERNEL selects the fused stage kernel's thread layout:
- * 0 = one thread per vertical node column (default), 1 = one thread per node, 2 = one thread
- * per column with all operands staged into shared memory by asynchronous copies.  All compute
+ * 0 = one thread per vertical node column, 1 = one thread per node, 2 = one thread per column
+ * with all operands staged into shared memory by asynchronous copies (default).  All compute
  * the same operator; the option exists for tuning and cross-checking. */
 enum { DG_OPT_STAGE_KERNEL = 1 };
 dg_status dg_set_option(dg_mesh* mesh, int32_t option, int64_t value);

@@ -40,7 +40,7 @@ struct dg_mesh {
   void* d_mbuf = nullptr;
   void* d_ppscratch = nullptr; // P' plane of a caller's state in dg_rhs
   bool pp_valid = false;       // P' plane of q[0] matches q[0]
-  int variant = 0;             // stage kernel layout (DG_OPT_STAGE_KERNEL)
+  int variant = 2;             // stage kernel layout (DG_OPT_STAGE_KERNEL)
   void* d_ops = nullptr;       // precision T
   double* d_opsd = nullptr;    // FP64: D, P0, P1, C0, C1, w, x
   double* d_partial = nullptr;

@@ -158,7 +158,7 @@ struct StageArgs {
   double inv2hd[kMaxLevels][3];
   double dt, ca, cb;
   int32_t mode;
-  int32_t variant;       // 0: column-mapped kernel (default), 1: node-per-thread kernel
+  int32_t variant;       // 0: column kernel, 1: node-per-thread kernel, 2: column kernel with async staging
   int32_t plane32;       // `plane` as int32 (the host guarantees (NV+1) * plane < 2^31)
   float gammaf, gf;      // gamma and g in FP32
   PhysC ph;

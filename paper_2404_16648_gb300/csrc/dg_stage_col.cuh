@@ -1,4 +1,4 @@
-// Column-mapped fused stage kernel (the default stage kernel).
+// Column-mapped fused stage kernel (layout 0).
 //
 // Same operator as stage_kernel in dg_device.cuh (strong-form volume term, Rusanov face terms,
 // precomputed mortar fluxes, Shu-Osher combination, FP64 P' epilogue), with a thread layout

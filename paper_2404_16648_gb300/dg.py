@@ -292,8 +292,8 @@ class Mesh:
         return np.array(list(out))
 
     def set_stage_kernel(self, layout):
-        """0: one thread per vertical node column (default); 1: one thread per node;
-        2: column layout with asynchronous staging of every operand in shared memory."""
+        """0: one thread per vertical node column; 1: one thread per node; 2 (default): column
+        layout with asynchronous staging of every operand in shared memory."""
         self._check(self.lib.dg_set_option(self.h, 1, int(layout)))
 
     def enable_timing(self, on=True):
