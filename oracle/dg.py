@@ -332,7 +332,7 @@ def state_from_theta(mesh, th):
     """Hydrostatic-pressure initial state for a theta' field: Theta' = 0, U = 0,
     rho' = -rho_bar theta' / (theta0 + theta') (reading O-4 of the initial balance)."""
     rb, _, _ = mesh.bg
-    q = np.zeros((mesh.nv, mesh.E, mesh.np_))
+    q = np.zeros((mesh.nv, mesh.E, mesh.np_), dtype=np.result_type(th, np.float64))
     q[0] = -rb * th / (mesh.K.theta0 + th)
     return q
 

@@ -119,6 +119,23 @@ def source(q, K):
     return S
 
 
+def abs_cs(x):
+    """|x|; on complex input (complex-step differentiation) sign(Re x) x with sign(0) = 0, the
+    derivative a central finite difference sees at 0.  Same values as np.abs on real input."""
+    x = np.asarray(x)
+    if np.iscomplexobj(x):
+        r = x.real
+        return np.where(r > 0, x, np.where(r < 0, -x, r + 0j))
+    return np.abs(x)
+
+
+def max_cs(a, b):
+    """max(a, b); on complex input chosen by the real part, ties to a (the low side)."""
+    if np.iscomplexobj(a) or np.iscomplexobj(b):
+        return np.where(np.real(a) >= np.real(b), a, b)
+    return np.maximum(a, b)
+
+
 def rusanov(qm, qp, bgm, bgp, K, axis):
     """Rusanov flux along +axis between the low-side state qm and high-side state qp.
 
@@ -130,8 +147,8 @@ def rusanov(qm, qp, bgm, bgp, K, axis):
     Fp = flux(qp, bgp, K, axis)
     rm, um, _, _, Pm = primitives(qm, bgm, K)
     rp, up, _, _, Pp = primitives(qp, bgp, K)
-    lam = np.maximum(np.abs(um[axis]) + sound_speed(Pm, rm, K),
-                     np.abs(up[axis]) + sound_speed(Pp, rp, K))
+    lam = max_cs(abs_cs(um[axis]) + sound_speed(Pm, rm, K),
+                 abs_cs(up[axis]) + sound_speed(Pp, rp, K))
     Fs = 0.5 * (Fm + Fp) - 0.5 * lam * (qp - qm)
     return Fs, Fm, Fp
 
