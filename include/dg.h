@@ -135,6 +135,10 @@ dg_status dg_get_state(dg_mesh* mesh, void* q, int where);
 /* Evaluates the initial condition analytically at the current nodes (FP64 on the device). */
 dg_status dg_set_bubble(dg_mesh* mesh, const dg_bubble_desc* bubble);
 
+/* The same analytic theta' as dg_set_bubble, written to the caller's device array
+ * theta[elements x (N+1)^d] (FP64) instead of setting the state. */
+dg_status dg_bubble_theta(dg_mesh* mesh, const dg_bubble_desc* bubble, double* theta);
+
 /* dq/dt of the strong-form dGSEM (Sec. 2.2) for the caller's device state q (same layout and
  * type as the mesh state), written to the caller's device buffer dqdt.  Pure: the mesh state is
  * untouched.  Asynchronous on `stream` (NULL: the mesh stream). */
@@ -158,6 +162,38 @@ dg_status dg_indicator(dg_mesh* mesh, double* out, size_t cap);
  * (p cv/R + |U|^2/(2 rho) + rho g z), kinetic energy, volume, perturbation mass int rho'}.
  * Synchronous; DG_ERR_STATE if a non-finite value was met (out is still written). */
 dg_status dg_integrals(dg_mesh* mesh, double out[DG_NUM_INTEGRALS]);
+
+/* ---- Adjoint (FP64 meshes; DG_ERR_UNSUPPORTED otherwise).  Hand-written discrete
+ * vector-Jacobian products of the operator above, for sensitivities of forecast diagnostics to
+ * the initial theta' field.  All pointers are caller-owned device buffers in the state layout;
+ * asynchronous on `stream` (NULL: the mesh stream).  Non-smooth parts use the derivative of the
+ * active branch: max(s-, s+) of the Rusanov speed gives its gradient to the low side on ties,
+ * and |u| has derivative sign(u) with sign(0) = 0. */
+
+/* out = J(q)^T lam, J = d dg_rhs(q) / dq. */
+dg_status dg_rhs_vjp(dg_mesh* mesh, const void* q, const void* lam, void* out, void* stream);
+
+/* nsteps SSP-RK3 steps from the caller's state q_in to q_out (any precision; may alias), using
+ * the mesh's workspace; the mesh state is untouched. */
+dg_status dg_step_state(dg_mesh* mesh, const void* q_in, void* q_out, double dt, int32_t nsteps,
+                        void* stream);
+
+/* lam_in = (d step(q_in) / d q_in)^T lam_out for one SSP-RK3 step of size dt; the stage states
+ * are recomputed from q_in.  lam_in must not alias lam_out. */
+dg_status dg_step_vjp(dg_mesh* mesh, const void* q_in, double dt, const void* lam_out,
+                      void* lam_in, void* stream);
+
+/* Sets the mesh state from a nodal theta' field (elements x (N+1)^d doubles, host or device):
+ * Theta' = 0, U = 0, rho' = -rho_bar theta' / (theta0 + theta') (same balance as dg_set_bubble). */
+dg_status dg_set_theta(dg_mesh* mesh, const double* theta, int where);
+
+/* lam_theta = (d state(theta) / d theta)^T lam_q for the map of dg_set_theta (device). */
+dg_status dg_theta_vjp(dg_mesh* mesh, const double* theta, const void* lam_q, double* lam_theta,
+                       void* stream);
+
+/* out = d KE / dq for KE = sum w_i w_j (w_k) |J| |U|^2 / (2 rho) (the kinetic-energy integral of
+ * dg_integrals) at the caller's state q (device). */
+dg_status dg_ke_grad(dg_mesh* mesh, const void* q, void* out, void* stream);
 
 /* Tuning options.  DG_OPT_STAGE_KERNEL selects the fused stage kernel's thread layout:
  * 0 = one thread per vertical node column, 1 = one thread per node, 2 = one thread per column

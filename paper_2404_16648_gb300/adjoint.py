@@ -1,0 +1,68 @@
+"""Sensitivity of a forecast diagnostic to the initial theta' field, behind torch.autograd.
+
+J(theta') = kinetic-energy integral after `nsteps` SSP-RK3 steps from the hydrostatic-pressure
+state of the nodal field theta' (the use case of variational data assimilation).  The forward
+pass steps through the C ABI and keeps a checkpoint of the state every `every` steps; the
+backward pass recomputes each segment's states from its checkpoint and runs the hand-written
+step transposes (dg_step_vjp) in reverse, then the transpose of the initial-state map
+(dg_theta_vjp).  Every operation runs in the library's kernels; this module only orders calls.
+"""
+import torch
+
+
+def _final_state(mesh, theta, dt, nsteps, every):
+    mesh.set_theta(theta)
+    q = torch.empty(mesh.state_shape, dtype=torch.float64, device=theta.device)
+    mesh.get_state(q)
+    checkpoints = []
+    for i in range(nsteps):
+        if i % every == 0:
+            checkpoints.append(q.clone())
+        mesh.step_state(q, q, dt)
+    return q, checkpoints
+
+
+def final_ke(mesh, theta, dt, nsteps):
+    """J(theta') without gradient bookkeeping."""
+    mesh.set_theta(theta)
+    mesh.step(dt, nsteps)
+    return float(mesh.integrals()[2])
+
+
+class FinalKineticEnergy(torch.autograd.Function):
+    """J = KE(state after nsteps) as a differentiable function of theta' (device, FP64)."""
+
+    @staticmethod
+    def forward(ctx, theta, mesh, dt, nsteps, every):
+        q, checkpoints = _final_state(mesh, theta, dt, nsteps, every)
+        mesh.set_state(q)
+        J = float(mesh.integrals()[2])
+        ctx.mesh, ctx.dt, ctx.nsteps, ctx.every = mesh, dt, nsteps, every
+        ctx.save_for_backward(theta, q, *checkpoints)
+        return torch.tensor(J, dtype=torch.float64, device=theta.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        mesh, dt, nsteps, every = ctx.mesh, ctx.dt, ctx.nsteps, ctx.every
+        theta, qT, *checkpoints = ctx.saved_tensors
+        lam = mesh.ke_grad(qT) * grad_out
+        spare = torch.empty_like(lam)
+        for seg in reversed(range(len(checkpoints))):
+            start = seg * every
+            stop = min(start + every, nsteps)
+            states = [checkpoints[seg]]
+            for _ in range(start, stop - 1):
+                states.append(mesh.step_state(states[-1], torch.empty_like(qT), dt))
+            for i in reversed(range(stop - start)):
+                mesh.step_vjp(states[i], dt, lam, spare)
+                lam, spare = spare, lam
+        grad_theta = mesh.theta_vjp(theta, lam)
+        return grad_theta, None, None, None, None
+
+
+def ke_gradient(mesh, theta, dt, nsteps, every=20):
+    """(J, dJ/dtheta') for a device FP64 tensor theta of shape (elements, nodes per element)."""
+    th = theta.detach().clone().requires_grad_(True)
+    J = FinalKineticEnergy.apply(th, mesh, dt, nsteps, every)
+    J.backward()
+    return float(J.item()), th.grad

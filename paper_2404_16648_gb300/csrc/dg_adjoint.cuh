@@ -1,0 +1,380 @@
+// Hand-written discrete adjoint (vector-Jacobian products) of the FP64 dGSEM right-hand side.
+//
+// For a state q and a cotangent Lambda of L(q) = dq/dt, vjp_kernel computes J(q)^T Lambda where
+// J is the Jacobian of the discrete operator of dg_device.cuh: the transpose of the volume term
+// (D^T along each axis, then the flux Jacobian transpose at each node), of the buoyancy source,
+// and of every face term.  Faces are handled by gather, like the forward: at each of its face
+// nodes an element forms the cotangent of the shared numerical flux F* from its own and its
+// neighbour's Lambda, mu* = sign c (Lambda_own - Lambda_nbr), and applies the transpose of the
+// Rusanov flux with respect to its own state.  Hanging faces go through mortar_vjp_kernel, the
+// transpose of mortar_kernel: C^T for the coarse side's back-projection, the Rusanov transpose on
+// the mortar nodes, and P^T back to the coarse trace.
+//
+// The non-smooth parts follow the derivative of the active branch: lambda = max(s-, s+) gives
+// its gradient to the low side on ties, and |u| has derivative sign(u) with sign(0) = 0 (what a
+// central finite difference sees).  The epilogue combines the product with other cotangents,
+// out = a1 A1 + a2 A2 + b (B + dt J^T Lambda), which is all the reverse SSP-RK3 step needs.
+#pragma once
+#include "dg_device.cuh"
+
+namespace dgk {
+
+struct AdjArgs {
+  const double* q;       // state [NV][plane]
+  const double* lam;     // cotangent of L [NV][plane]
+  const double* a1;      // optional [NV][plane]
+  const double* a2;      // optional
+  const double* b;       // optional
+  double* out;           // [NV][plane]
+  const double* abuf;    // mortar adjoint contributions [G][1 + 2^(d-1)][NV][NF]
+  int64_t plane;
+  int32_t E;
+  const int32_t* elem;
+  const int32_t* conn;
+  const double* bg;      // [E][N+1][4]
+  const double* ops;     // D, P0, P1, C0, C1, w, x
+  double inv2h[kMaxLevels][3];
+  double c1, c2, cb, dt;
+  PhysC ph;
+};
+
+struct MortarAdjArgs {
+  const double* q;
+  const double* lam;
+  double* abuf;
+  int64_t plane;
+  int32_t G;
+  const int32_t* groups;
+  const int32_t* elem;
+  const double* bg;
+  const double* ops;
+  double inv2h[kMaxLevels][3];
+  PhysC ph;
+};
+
+// Everything about one node's state that the Jacobians need.
+template <int D>
+struct NodeLin {
+  double rinv, u[D], Theta, P, dPdT, c;
+};
+
+template <int D>
+__device__ __forceinline__ NodeLin<D> node_lin(const double* q, double rb, double Tb, double pb,
+                                               double invTb, const PhysC& ph) {
+  NodeLin<D> L;
+  L.rinv = 1.0 / (rb + q[0]);
+#pragma unroll
+  for (int b = 0; b < D; ++b) L.u[b] = q[1 + b] * L.rinv;
+  L.Theta = Tb + q[D + 1];
+  L.P = pb + pressure_pert<kSeries>(q[D + 1], invTb, pb, ph);
+  L.dPdT = ph.gamma * L.P / L.Theta;                 // dP/dTheta of the EOS of Sec. 2.1
+  L.c = sqrt(ph.gamma * L.P * L.rinv);
+  return L;
+}
+
+// out += J_a(q)^T mu with J_a = dF_a/dq (perturbation variables).
+template <int D>
+__device__ __forceinline__ void flux_jac_t(const NodeLin<D>& L, int a, const double* mu, double* out) {
+  double mu_u = 0.0;
+#pragma unroll
+  for (int b = 0; b < D; ++b) mu_u += mu[1 + b] * L.u[b];
+  const double ua = L.u[a];
+  out[0] += -ua * mu_u - mu[D + 1] * L.Theta * ua * L.rinv;
+#pragma unroll
+  for (int c = 0; c < D; ++c) out[1 + c] += mu[1 + c] * ua;
+  out[1 + a] += mu[0] + mu_u + mu[D + 1] * L.Theta * L.rinv;
+  out[D + 1] += mu[1 + a] * L.dPdT + mu[D + 1] * ua;
+}
+
+template <int D>
+__device__ __forceinline__ double speed_of(const NodeLin<D>& L, int a) {
+  return fabs(L.u[a]) + L.c;
+}
+
+// out += w * grad_q (|u_a| + c), c = sqrt(gamma P / rho).
+template <int D>
+__device__ __forceinline__ void speed_grad(const NodeLin<D>& L, int a, double gamma, double w,
+                                           double* out) {
+  const double ua = L.u[a];
+  const double sg = ua > 0.0 ? 1.0 : (ua < 0.0 ? -1.0 : 0.0);
+  out[0] += w * (-sg * ua * L.rinv - 0.5 * L.c * L.rinv);
+  out[1 + a] += w * sg * L.rinv;
+  out[D + 1] += w * (0.5 * gamma * L.c / L.Theta);
+}
+
+// Transpose of F* = (F(qm) + F(qp))/2 - lambda/2 (qp - qm), lambda = max(sm, sp) (low side on
+// ties), for cotangent mu: adds d F*/d qm ^T mu to om and d F*/d qp ^T mu to op (either may be
+// null when that side is not wanted).
+template <int D>
+__device__ __forceinline__ void rusanov_vjp(const double* qm, const NodeLin<D>& Lm, const double* qp,
+                                            const NodeLin<D>& Lp, int a, double gamma,
+                                            const double* mu, double* om, double* op) {
+  constexpr int NV = D + 2;
+  const double sm = speed_of<D>(Lm, a), sp = speed_of<D>(Lp, a);
+  const bool low = sm >= sp;
+  const double lam = low ? sm : sp;
+  double mud = 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) mud += mu[v] * (qp[v] - qm[v]);
+  double hm[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) hm[v] = 0.5 * mu[v];
+  if (om) {
+    flux_jac_t<D>(Lm, a, hm, om);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) om[v] += 0.5 * lam * mu[v];
+    if (low) speed_grad<D>(Lm, a, gamma, -0.5 * mud, om);
+  }
+  if (op) {
+    flux_jac_t<D>(Lp, a, hm, op);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) op[v] -= 0.5 * lam * mu[v];
+    if (!low) speed_grad<D>(Lp, a, gamma, -0.5 * mud, op);
+  }
+}
+
+template <int D, int N, int EPB>
+__global__ void __launch_bounds__(EPB * ipow(N + 1, D))
+vjp_kernel(const AdjArgs A) {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  constexpr int NSUB = 1 << (D - 1);
+  __shared__ double sD[n1 * n1];
+  __shared__ double sL[EPB][NV][NP];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n1 * n1; i += blockDim.x) sD[i] = A.ops[i];
+  const double w0 = A.ops[5 * n1 * n1];
+  const int le = tid / NP, n = tid - le * NP;
+  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const bool valid = e < A.E;
+  int idx[3];
+  idx[0] = n % n1;
+  idx[1] = (n / n1) % n1;
+  idx[2] = (D == 3) ? n / (n1 * n1) : 0;
+  const size_t base = (size_t)(valid ? e : 0) * NP + n;
+  double q[NV], lam[NV], acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    q[v] = valid ? A.q[(size_t)v * A.plane + base] : 0.0;
+    lam[v] = valid ? A.lam[(size_t)v * A.plane + base] : 0.0;
+    acc[v] = 0.0;
+    sL[le][v][n] = lam[v];
+  }
+  const int level = valid ? A.elem[e * 4] : 0;
+  const double* bgp = A.bg + ((size_t)(valid ? e : 0) * n1 + idx[D - 1]) * 4;
+  const double rb = valid ? bgp[0] : 1.0, Tb = valid ? bgp[1] : 1.0;
+  const double pb = valid ? bgp[2] : 1.0, iTb = valid ? bgp[3] : 1.0;
+  const NodeLin<D> L = node_lin<D>(q, rb, Tb, pb, iTb, A.ph);
+  __syncthreads();
+  if (!valid) return;
+  // buoyancy source -rho' g on the vertical momentum
+  acc[0] += -A.ph.g * lam[D];
+  // volume: L -= (2/h_a) D_a F_a  ->  mu_a = -(2/h_a) D_a^T Lambda, then J_a^T mu_a
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int stride = ipow(n1, a);
+    const int ia = idx[a];
+    const int b0 = n - ia * stride;
+    const double s2h = A.inv2h[level][a];
+    double mu[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < n1; ++i) s += sD[i * n1 + ia] * sL[le][v][b0 + i * stride];
+      mu[v] = -s2h * s;
+    }
+    flux_jac_t<D>(L, a, mu, acc);
+  }
+  // faces
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (idx[a] != (s ? N : 0)) continue;
+      const int32_t* c = A.conn + ((size_t)e * 2 * D + 2 * a + s) * 5;
+      const int kind = c[0];
+      const double coef = A.inv2h[level][a] / w0;
+      const double sign = s ? -1.0 : 1.0;
+      // own flux in the lift: L += sign coef (F* - F(q))
+      double m1[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) m1[v] = -sign * coef * lam[v];
+      flux_jac_t<D>(L, a, m1, acc);
+      if (kind == FACE_CONF) {
+        const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
+        const size_t no = (size_t)c[1] * NP + n + ((s ? 0 : N) - idx[a]) * stride_a;
+        double qo[NV], mu[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          qo[v] = A.q[(size_t)v * A.plane + no];
+          mu[v] = sign * coef * (lam[v] - A.lam[(size_t)v * A.plane + no]);
+        }
+        const NodeLin<D> Lo = node_lin<D>(qo, rb, Tb, pb, iTb, A.ph);
+        if (s) rusanov_vjp<D>(q, L, qo, Lo, a, A.ph.gamma, mu, acc, nullptr);
+        else   rusanov_vjp<D>(qo, Lo, q, L, a, A.ph.gamma, mu, nullptr, acc);
+      } else if (kind == FACE_WALL) {
+        double gq[NV], mu[NV], gacc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { gq[v] = q[v]; mu[v] = sign * coef * lam[v]; gacc[v] = 0.0; }
+        gq[1 + a] = -q[1 + a];
+        const NodeLin<D> Lg = node_lin<D>(gq, rb, Tb, pb, iTb, A.ph);
+        if (s) rusanov_vjp<D>(q, L, gq, Lg, a, A.ph.gamma, mu, acc, gacc);
+        else   rusanov_vjp<D>(gq, Lg, q, L, a, A.ph.gamma, mu, gacc, acc);
+        gacc[1 + a] = -gacc[1 + a];                      // mirror map is its own transpose
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += gacc[v];
+      } else {
+        int t = 0, mul = 1;
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+          if (b != a) { t += idx[b] * mul; mul *= n1; }
+        const int64_t g = (kind == FACE_FINE) ? c[2] : c[1];
+        const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
+        const double* src = A.abuf + (((size_t)g * (1 + NSUB) + slot) * NV) * NF + t;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += src[(size_t)v * NF];
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const size_t k = (size_t)v * A.plane + base;
+    double r = A.cb * ((A.b ? A.b[k] : 0.0) + A.dt * acc[v]);
+    if (A.a1) r += A.c1 * A.a1[k];
+    if (A.a2) r += A.c2 * A.a2[k];
+    A.out[k] = r;
+  }
+}
+
+// Transpose of mortar_kernel for one mortar group.  Thread (m, t) owns mortar node t of mortar
+// m.  Writes, per fine element, d/d q_fine of the mortar flux terms at its face nodes (slot 1+m)
+// and, for the coarse element, d/d q_coarse through the projection (slot 0).
+template <int D, int N>
+__global__ void __launch_bounds__((1 << (D - 1)) * ipow(N + 1, D - 1))
+mortar_vjp_kernel(const MortarAdjArgs A) {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  constexpr int NSUB = 1 << (D - 1);
+  __shared__ double sP[2][n1 * n1], sC[2][n1 * n1];
+  __shared__ double sQc[NV][NF], sMc[NV][NF];
+  __shared__ double sT[NSUB][NV][NF];
+  __shared__ double sX[NSUB][NV][NF];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n1 * n1; i += blockDim.x) {
+    sP[0][i] = A.ops[1 * n1 * n1 + i];
+    sP[1][i] = A.ops[2 * n1 * n1 + i];
+    sC[0][i] = A.ops[3 * n1 * n1 + i];
+    sC[1][i] = A.ops[4 * n1 * n1 + i];
+  }
+  const double w0 = A.ops[5 * n1 * n1];
+  const int g = blockIdx.x;
+  const int32_t* row = A.groups + (size_t)g * 7;
+  const int64_t ec = row[0];
+  const int a = row[1], side = row[2];
+  const int m = tid / NF, t = tid - m * NF;
+  const int b0 = m & 1, b1 = (m >> 1) & 1;
+  const int t0 = t % n1, t1 = t / n1;
+  const int64_t ef = row[3 + m];
+  const double cc = A.inv2h[A.elem[ec * 4]][a] / w0;        // coarse lift coefficient
+  const double cf = A.inv2h[A.elem[ef * 4]][a] / w0;        // fine lift coefficient
+  const double sign_c = side ? -1.0 : 1.0;                  // coarse outward normal
+  const double sign_f = -sign_c;                            // fine outward normal
+  for (int i = tid; i < NV * NF; i += blockDim.x) {
+    const int v = i / NF, tt = i - v * NF;
+    const size_t k = (size_t)v * A.plane + (size_t)ec * NP + face_node<D, N>(a, side, tt);
+    sQc[v][tt] = A.q[k];
+    sMc[v][tt] = sign_c * cc * A.lam[k];                    // cotangent of F~ at coarse nodes
+  }
+  __syncthreads();
+  // projected coarse state on mortar m (forward), first and second tangential passes
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < n1; ++j) s += sP[b0][t0 * n1 + j] * sQc[v][j + n1 * t1];
+    sT[m][v][t] = s;
+  }
+  __syncthreads();
+  double qc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (D == 3) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < n1; ++j) s += sP[b1][t1 * n1 + j] * sT[m][v][t0 + n1 * j];
+      qc[v] = s;
+    } else {
+      qc[v] = sT[m][v][t];
+    }
+  }
+  __syncthreads();
+  // C^T of the back-projection: mu*_m = (C_b1 x C_b0)^T mu~ (first pass along t1 in 3D)
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (D == 3) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < n1; ++j) s += sC[b1][j * n1 + t1] * sMc[v][t0 + n1 * j];
+      sT[m][v][t] = s;
+    } else {
+      sT[m][v][t] = sMc[v][t];
+    }
+  }
+  __syncthreads();
+  const int nf = face_node<D, N>(a, 1 - side, t);
+  double qf[NV], mu[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < n1; ++j) s += sC[b0][j * n1 + t0] * sT[m][v][j + n1 * t1];
+    const size_t k = (size_t)v * A.plane + (size_t)ef * NP + nf;
+    qf[v] = A.q[k];
+    mu[v] = s + sign_f * cf * A.lam[k];                     // plus the fine lift's cotangent
+  }
+  const int kf = (D == 3) ? nf / (n1 * n1) : nf / n1;
+  const double* bd = A.bg + ((size_t)ef * n1 + kf) * 4;
+  const NodeLin<D> Lf = node_lin<D>(qf, bd[0], bd[1], bd[2], bd[3], A.ph);
+  const NodeLin<D> Lc = node_lin<D>(qc, bd[0], bd[1], bd[2], bd[3], A.ph);
+  double gf[NV], gc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) { gf[v] = 0.0; gc[v] = 0.0; }
+  if (side) rusanov_vjp<D>(qc, Lc, qf, Lf, a, A.ph.gamma, mu, gc, gf);
+  else      rusanov_vjp<D>(qf, Lf, qc, Lc, a, A.ph.gamma, mu, gf, gc);
+  double* ab = A.abuf + ((size_t)g * (1 + NSUB) * NV) * NF;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    ab[((size_t)(1 + m) * NV + v) * NF + t] = gf[v];
+    sX[m][v][t] = gc[v];
+  }
+  __syncthreads();
+  // P^T back to the coarse trace: first along t0 ...
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < n1; ++j) s += sP[b0][j * n1 + t0] * sX[m][v][j + n1 * t1];
+    sT[m][v][t] = s;
+  }
+  __syncthreads();
+  // ... then along t1, summed over the mortars
+  if (m == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double acc = 0.0;
+      for (int mm = 0; mm < NSUB; ++mm) {
+        if (D == 3) {
+          const int c1 = (mm >> 1) & 1;
+          double s = 0.0;
+#pragma unroll
+          for (int j = 0; j < n1; ++j) s += sP[c1][j * n1 + t1] * sT[mm][v][t0 + n1 * j];
+          acc += s;
+        } else {
+          acc += sT[mm][v][t];
+        }
+      }
+      ab[(size_t)v * NF + t] = acc;
+    }
+  }
+}
+
+}  // namespace dgk

@@ -41,6 +41,11 @@ struct dg_mesh {
   void* d_ppscratch = nullptr; // P' plane of a caller's state in dg_rhs
   bool pp_valid = false;       // P' plane of q[0] matches q[0]
   int variant = 2;             // stage kernel layout (DG_OPT_STAGE_KERNEL)
+  // adjoint / pure-step workspace, allocated on first use for the current mesh size
+  void* adj_q[3] = {nullptr, nullptr, nullptr};   // states with P' planes
+  double* adj_l[2] = {nullptr, nullptr};          // cotangents
+  double* d_abuf = nullptr;                       // mortar adjoint contributions
+  int64_t adj_E = -1, adj_G = -1;
   void* d_ops = nullptr;       // precision T
   double* d_opsd = nullptr;    // FP64: D, P0, P1, C0, C1, w, x
   double* d_partial = nullptr;
@@ -247,9 +252,156 @@ dg_status init_device_tables(dg_mesh* m) {
   return DG_OK;
 }
 
+// Workspace of dg_step_state / dg_step_vjp for the current mesh size.
+dg_status ensure_adjoint_ws(dg_mesh* m) {
+  if (m->adj_E == m->E && m->adj_G == m->G) return DG_OK;
+  for (int i = 0; i < 3; ++i) { dfree(m->adj_q[i]); m->adj_q[i] = nullptr; }
+  for (int i = 0; i < 2; ++i) { dfree(m->adj_l[i]); m->adj_l[i] = nullptr; }
+  dfree(m->d_abuf); m->d_abuf = nullptr;
+  m->adj_E = m->adj_G = -1;
+  const size_t pl = (size_t)(plane(m) > 0 ? plane(m) : 1);
+  for (int i = 0; i < 3; ++i) CU(cudaMalloc(&m->adj_q[i], (m->NV + 1) * pl * m->tsize));
+  for (int i = 0; i < 2; ++i) CU(cudaMalloc(&m->adj_l[i], m->NV * pl * sizeof(double)));
+  if (m->G > 0) CU(cudaMalloc(&m->d_abuf, (size_t)m->G * (1 + m->NSUB) * m->NV * m->NF * sizeof(double)));
+  m->adj_E = m->E;
+  m->adj_G = m->G;
+  return DG_OK;
+}
+
+// Copies a caller state (NV planes) into a workspace buffer and fills its P' plane.
+dg_status stage_in(dg_mesh* m, const void* q, void* buf, cudaStream_t s) {
+  const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
+  CU(cudaMemcpyAsync(buf, q, bytes, cudaMemcpyDeviceToDevice, s));
+  const void* theta = (const char*)buf + (size_t)(m->NV - 1) * plane(m) * m->tsize;
+  CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->ph, pp_plane(m, buf), s));
+  return DG_OK;
+}
+
+// The three Shu-Osher stages of one step on workspace buffers: b0 -> b1 -> b2 -> b0.
+dg_status rk3_on(dg_mesh* m, void* b0, void* b1, void* b2, double dt, cudaStream_t s) {
+  dg_status st = launch_rhs_pass(m, b0, pp_plane(m, b0), b0, b1, pp_plane(m, b1), 1, dt, 0.0, 1.0, s);
+  if (st == DG_OK) st = launch_rhs_pass(m, b1, pp_plane(m, b1), b0, b2, pp_plane(m, b2), 1, dt, 0.75, 0.25, s);
+  if (st == DG_OK) st = launch_rhs_pass(m, b2, pp_plane(m, b2), b0, b0, pp_plane(m, b0), 1, dt, 1.0 / 3.0, 2.0 / 3.0, s);
+  return st;
+}
+
+// out = c1 a1 + c2 a2 + cb (b + dt J(q)^T lam), with the mortar transposes first.
+dg_status vjp_pass(dg_mesh* m, const double* q, const double* lam, const double* a1, double c1,
+                   const double* a2, double c2, const double* b, double cb, double dt, double* out,
+                   cudaStream_t s) {
+  if (m->G > 0) {
+    dgk::MortarAdjArgs M{};
+    M.q = q; M.lam = lam; M.abuf = m->d_abuf; M.plane = plane(m); M.G = (int32_t)m->G;
+    M.groups = m->d_groups; M.elem = m->d_elem; M.bg = m->d_bg; M.ops = m->d_opsd; M.ph = m->ph;
+    for (int l = 0; l < dgk::kMaxLevels; ++l)
+      for (int a = 0; a < 3; ++a) M.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+    if (!dgk::launch_mortar_vjp(m->D, m->N, M, s)) return fail(m, DG_ERR_UNSUPPORTED, "mortar adjoint not compiled");
+    CU(cudaGetLastError());
+  }
+  dgk::AdjArgs A{};
+  A.q = q; A.lam = lam; A.a1 = a1; A.a2 = a2; A.b = b; A.out = out; A.abuf = m->d_abuf;
+  A.plane = plane(m); A.E = (int32_t)m->E; A.elem = m->d_elem; A.conn = m->d_conn; A.bg = m->d_bg;
+  A.ops = m->d_opsd; A.c1 = c1; A.c2 = c2; A.cb = cb; A.dt = dt; A.ph = m->ph;
+  for (int l = 0; l < dgk::kMaxLevels; ++l)
+    for (int a = 0; a < 3; ++a) A.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+  if (!dgk::launch_vjp(m->D, m->N, A, s)) return fail(m, DG_ERR_UNSUPPORTED, "adjoint kernel not compiled");
+  CU(cudaGetLastError());
+  return DG_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void* stream) {
+  if (!m || !q || !lam || !out) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
+  dg_status st = ensure_adjoint_ws(m);
+  if (st != DG_OK) return st;
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  return vjp_pass(m, (const double*)q, (const double*)lam, nullptr, 0.0, nullptr, 0.0, nullptr, 1.0,
+                  1.0, (double*)out, s);
+}
+
+dg_status dg_step_state(dg_mesh* m, const void* q_in, void* q_out, double dt, int32_t nsteps,
+                        void* stream) {
+  if (!m || !q_in || !q_out || nsteps < 0 || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  dg_status st = ensure_adjoint_ws(m);
+  if (st != DG_OK) return st;
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  st = stage_in(m, q_in, m->adj_q[0], s);
+  for (int32_t i = 0; st == DG_OK && i < nsteps; ++i) st = rk3_on(m, m->adj_q[0], m->adj_q[1], m->adj_q[2], dt, s);
+  if (st != DG_OK) return st;
+  CU(cudaMemcpyAsync(q_out, m->adj_q[0], (size_t)m->NV * plane(m) * m->tsize, cudaMemcpyDeviceToDevice, s));
+  return DG_OK;
+}
+
+dg_status dg_step_vjp(dg_mesh* m, const void* q_in, double dt, const void* lam_out, void* lam_in,
+                      void* stream) {
+  if (!m || !q_in || !lam_out || !lam_in || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (lam_out == lam_in) return fail(m, DG_ERR_ARG, "lam_out and lam_in must not alias");
+  if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
+  dg_status st = ensure_adjoint_ws(m);
+  if (st != DG_OK) return st;
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  // recompute the stage states q, q1, q2 of this step
+  void* b0 = m->adj_q[0];
+  void* b1 = m->adj_q[1];
+  void* b2 = m->adj_q[2];
+  st = stage_in(m, q_in, b0, s);
+  if (st == DG_OK) st = launch_rhs_pass(m, b0, pp_plane(m, b0), b0, b1, pp_plane(m, b1), 1, dt, 0.0, 1.0, s);
+  if (st == DG_OK) st = launch_rhs_pass(m, b1, pp_plane(m, b1), b0, b2, pp_plane(m, b2), 1, dt, 0.75, 0.25, s);
+  if (st != DG_OK) return st;
+  const double* lo = (const double*)lam_out;
+  double* l2 = m->adj_l[0];
+  double* l1 = m->adj_l[1];
+  // q3 = 1/3 q + 2/3 (q2 + dt L(q2)):   lam_q2 = 2/3 (lam + dt J(q2)^T lam)
+  st = vjp_pass(m, (const double*)b2, lo, nullptr, 0.0, nullptr, 0.0, lo, 2.0 / 3.0, dt, l2, s);
+  // q2 = 3/4 q + 1/4 (q1 + dt L(q1)):   lam_q1 = 1/4 (lam_q2 + dt J(q1)^T lam_q2)
+  if (st == DG_OK) st = vjp_pass(m, (const double*)b1, l2, nullptr, 0.0, nullptr, 0.0, l2, 0.25, dt, l1, s);
+  // q1 = q + dt L(q):   lam_q = 1/3 lam + 3/4 lam_q2 + lam_q1 + dt J(q)^T lam_q1
+  if (st == DG_OK)
+    st = vjp_pass(m, (const double*)b0, l1, lo, 1.0 / 3.0, l2, 0.75, l1, 1.0, dt, (double*)lam_in, s);
+  return st;
+}
+
+dg_status dg_set_theta(dg_mesh* m, const double* theta, int where) {
+  if (!m || !theta || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
+  const size_t bytes = (size_t)plane(m) * sizeof(double);
+  const double* src = theta;
+  double* tmp = nullptr;
+  if (where == DG_HOST) {
+    CU(cudaMalloc(&tmp, bytes > 0 ? bytes : 8));
+    CU(cudaMemcpy(tmp, theta, bytes, cudaMemcpyHostToDevice));
+    src = tmp;
+  }
+  cudaError_t e = dgk::launch_theta_state(m->prec, (int32_t)m->E, m->n1, m->D, m->d_bg, src,
+                                          m->ph.theta0, m->q[0], plane(m), m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "theta state failed: %s", cudaGetErrorString(e));
+  m->pp_valid = false;
+  return DG_OK;
+}
+
+dg_status dg_theta_vjp(dg_mesh* m, const double* theta, const void* lam_q, double* lam_theta,
+                       void* stream) {
+  if (!m || !theta || !lam_q || !lam_theta) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  CU(dgk::launch_theta_vjp((int32_t)m->E, m->n1, m->D, m->d_bg, theta, m->ph.theta0,
+                           (const double*)lam_q, lam_theta, s));
+  return DG_OK;
+}
+
+dg_status dg_ke_grad(dg_mesh* m, const void* q, void* out, void* stream) {
+  if (!m || !q || !out) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  CU(dgk::launch_ke_grad((int32_t)m->E, m->n1, m->D, m->d_elem, d_w(m), m->root_h, m->d_bg,
+                         (const double*)q, plane(m), (double*)out, s));
+  return DG_OK;
+}
 
 dg_status dg_set_option(dg_mesh* m, int32_t option, int64_t value) {
   if (!m) return DG_ERR_ARG;
@@ -331,6 +483,9 @@ void dg_mesh_destroy(dg_mesh* m) {
   dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
   dfree(m->d_bgf); dfree(m->d_ppscratch);
   dfree(m->d_ops); dfree(m->d_opsd); dfree(m->d_partial); dfree(m->d_out); dfree(m->d_bad);
+  for (int i = 0; i < 3; ++i) dfree(m->adj_q[i]);
+  for (int i = 0; i < 2; ++i) dfree(m->adj_l[i]);
+  dfree(m->d_abuf);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   delete m;
 }
@@ -381,7 +536,8 @@ dg_status dg_get_state(dg_mesh* m, void* q, int where) {
   return DG_OK;
 }
 
-dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) {
+// Evaluates the bubble at the nodes: into the state (theta_out == nullptr) or as theta' itself.
+static dg_status bubble_eval(dg_mesh* m, const dg_bubble_desc* b, double* theta_out) {
   if (!m || !b) return fail(m, DG_ERR_ARG, "bad argument");
   for (int a = 0; a < m->D; ++a)
     if (!(b->radius[a] > 0.0)) return fail(m, DG_ERR_ARG, "bubble radius must be positive");
@@ -399,12 +555,19 @@ dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) {
   m->pp_valid = false;
   cudaError_t e = dgk::launch_bubble(m->prec, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), m->root_h,
                                      m->d_bg, b->center, b->radius, b->amp, b->n_rff, scale, dk, dp,
-                                     m->ph.theta0, m->q[0], plane(m), m->stream);
+                                     m->ph.theta0, m->q[0], plane(m), theta_out, m->stream);
   cudaError_t e2 = cudaStreamSynchronize(m->stream);
   dfree(dk); dfree(dp);
   if (e != cudaSuccess || e2 != cudaSuccess)
     return fail(m, DG_ERR_CUDA, "bubble kernel failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
   return DG_OK;
+}
+
+dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) { return bubble_eval(m, b, nullptr); }
+
+dg_status dg_bubble_theta(dg_mesh* m, const dg_bubble_desc* b, double* theta) {
+  if (!m || !theta) return fail(m, DG_ERR_ARG, "bad argument");
+  return bubble_eval(m, b, theta);
 }
 
 dg_status dg_rhs(dg_mesh* m, const void* q, void* dqdt, void* stream) {

@@ -3,6 +3,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dg_adjoint.cuh"
 #include "dg_device.cuh"
 
 namespace dgk {
@@ -34,7 +35,8 @@ cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* ele
                           const double* xi, const double* root_h, const double* bg,
                           const double* center, const double* radius, double amp, int n_rff,
                           double rff_scale, const double* rff_k, const double* rff_phase,
-                          double theta0, void* q, int64_t plane, cudaStream_t s);
+                          double theta0, void* q, int64_t plane, double* theta_out,
+                          cudaStream_t s);
 cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
                              int64_t plane, double theta0, double* out, cudaStream_t s);
 size_t integrals_scratch_doubles();
@@ -45,5 +47,17 @@ cudaError_t launch_integrals(int prec, int32_t E, int n1, int D, const int32_t* 
 cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, const int32_t* tmap,
                             const double* ops, const void* qold, int64_t plane_old, void* qnew,
                             int64_t plane_new, cudaStream_t s);
+
+// Adjoint (FP64): right-hand-side vector-Jacobian products and their helpers.
+bool launch_vjp(int D, int N, const AdjArgs& A, cudaStream_t s);
+bool launch_mortar_vjp(int D, int N, const MortarAdjArgs& A, cudaStream_t s);
+cudaError_t launch_theta_state(int prec, int32_t E, int n1, int D, const double* bg,
+                               const double* theta, double theta0, void* q, int64_t plane,
+                               cudaStream_t s);
+cudaError_t launch_theta_vjp(int32_t E, int n1, int D, const double* bg, const double* theta,
+                             double theta0, const double* lam_q, double* lam_theta, cudaStream_t s);
+cudaError_t launch_ke_grad(int32_t E, int n1, int D, const int32_t* elem, const double* w,
+                          const double* root_h, const double* bg, const double* q, int64_t plane,
+                          double* out, cudaStream_t s);
 
 }  // namespace dgk

@@ -43,7 +43,8 @@ __global__ void bubble_kernel(int32_t E, int n1, int D, const int32_t* elem, con
                               double rh0, double rh1, double rh2, const double* bg,
                               double c0, double c1, double c2, double r0, double r1, double r2,
                               double amp, int n_rff, double rff_scale, const double* rff_k,
-                              const double* rff_phase, double theta0, T* q, int64_t plane) {
+                              const double* rff_phase, double theta0, T* q, int64_t plane,
+                              double* theta_out) {
   const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)E * NP) return;
@@ -70,6 +71,7 @@ __global__ void bubble_kernel(int32_t E, int n1, int D, const int32_t* elem, con
     }
     th = th + rff_scale * acc;
   }
+  if (theta_out) { theta_out[i] = th; return; }
   const double rb = bg[(e * n1 + idx[D - 1]) * 4];
   q[i] = (T)(-rb * th / (theta0 + th));
   for (int v = 1; v < D + 2; ++v) q[(int64_t)v * plane + i] = (T)0;
@@ -277,7 +279,8 @@ cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* ele
                           const double* xi, const double* root_h, const double* bg,
                           const double* center, const double* radius, double amp, int n_rff,
                           double rff_scale, const double* rff_k, const double* rff_phase,
-                          double theta0, void* q, int64_t plane, cudaStream_t s) {
+                          double theta0, void* q, int64_t plane, double* theta_out,
+                          cudaStream_t s) {
   const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
   const int64_t n = (int64_t)E * NP;
   if (n == 0) return cudaSuccess;
@@ -285,11 +288,11 @@ cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* ele
   if (prec == 0)
     bubble_kernel<double><<<blocks, 256, 0, s>>>(E, n1, D, elem, xi, root_h[0], root_h[1], root_h[2], bg,
         center[0], center[1], center[2], radius[0], radius[1], radius[2], amp, n_rff, rff_scale,
-        rff_k, rff_phase, theta0, (double*)q, plane);
+        rff_k, rff_phase, theta0, (double*)q, plane, theta_out);
   else
     bubble_kernel<float><<<blocks, 256, 0, s>>>(E, n1, D, elem, xi, root_h[0], root_h[1], root_h[2], bg,
         center[0], center[1], center[2], radius[0], radius[1], radius[2], amp, n_rff, rff_scale,
-        rff_k, rff_phase, theta0, (float*)q, plane);
+        rff_k, rff_phase, theta0, (float*)q, plane, theta_out);
   return cudaGetLastError();
 }
 

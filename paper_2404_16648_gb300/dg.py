@@ -25,8 +25,10 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_bubble", "dg_rhs", "dg_step",
             "dg_adapt", "dg_indicator", "dg_integrals", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
             "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
-            "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_last_error",
-            "dg_version"]
+            "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
+            "dg_step_state", "dg_step_vjp", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
+            "dg_bubble_theta",
+            "dg_last_error", "dg_version"]
 
 
 class MeshDesc(ctypes.Structure):
@@ -100,6 +102,13 @@ def load_library(path=None):
         "dg_forest_regrid": (i32, [vp, ctypes.POINTER(ctypes.c_uint8), i32, i32, vp, sz,
                                    ctypes.POINTER(ctypes.c_int64)]),
         "dg_integrals_noalloc": (i32, [ctypes.POINTER(MeshDesc), vp, i64, vp, vp, vp]),
+        "dg_rhs_vjp": (i32, [vp, vp, vp, vp, vp]),
+        "dg_step_state": (i32, [vp, vp, vp, dbl, i32, vp]),
+        "dg_step_vjp": (i32, [vp, vp, dbl, vp, vp, vp]),
+        "dg_set_theta": (i32, [vp, vp, ctypes.c_int]),
+        "dg_theta_vjp": (i32, [vp, vp, vp, vp, vp]),
+        "dg_ke_grad": (i32, [vp, vp, vp, vp]),
+        "dg_bubble_theta": (i32, [vp, ctypes.POINTER(BubbleDesc), vp]),
         "dg_last_error": (ctypes.c_char_p, [vp]),
         "dg_version": (ctypes.c_char_p, []),
     }
@@ -227,6 +236,17 @@ class Mesh:
         return out
 
     def set_bubble(self, center, radius, amp, rff=None):
+        self._bubble(center, radius, amp, rff, None)
+
+    def bubble_theta(self, center, radius, amp, rff=None, out=None):
+        """The bubble's theta' at every node as a device FP64 tensor (elements, nodes)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.num_elements, self.np_), dtype=torch.float64, device="cuda")
+        self._bubble(center, radius, amp, rff, out)
+        return out
+
+    def _bubble(self, center, radius, amp, rff, theta_out):
         b = BubbleDesc()
         for a in range(3):
             b.center[a] = float(center[a]) if a < len(center) else 0.0
@@ -244,7 +264,10 @@ class Mesh:
             b.rff_sigma = sigma
             b.rff_k = k3.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             b.rff_phase = ph.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        self._check(self.lib.dg_set_bubble(self.h, ctypes.byref(b)))
+        if theta_out is None:
+            self._check(self.lib.dg_set_bubble(self.h, ctypes.byref(b)))
+        else:
+            self._check(self.lib.dg_bubble_theta(self.h, ctypes.byref(b), ctypes.c_void_p(theta_out.data_ptr())))
         del keep
 
     # ------------------------------------------------------------------ hot path
@@ -257,6 +280,55 @@ class Mesh:
             raise ValueError("dg_rhs takes device tensors")
         self._check(self.lib.dg_rhs(self.h, ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                     self._stream_ptr(stream)))
+        return out
+
+    # ------------------------------------------------------------------ adjoint (FP64)
+    def rhs_vjp(self, q, lam, out=None, stream=None):
+        """J(q)^T lam for device tensors."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(q)
+        self._check(self.lib.dg_rhs_vjp(self.h, ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), self._stream_ptr(stream)))
+        return out
+
+    def step_state(self, q_in, q_out, dt, nsteps=1, stream=None):
+        """nsteps SSP-RK3 steps from device tensor q_in into q_out (may be the same tensor)."""
+        self._check(self.lib.dg_step_state(self.h, ctypes.c_void_p(q_in.data_ptr()),
+                                           ctypes.c_void_p(q_out.data_ptr()), float(dt), int(nsteps),
+                                           self._stream_ptr(stream)))
+        return q_out
+
+    def step_vjp(self, q_in, dt, lam_out, lam_in=None, stream=None):
+        torch = _torch()
+        if lam_in is None:
+            lam_in = torch.empty_like(lam_out)
+        self._check(self.lib.dg_step_vjp(self.h, ctypes.c_void_p(q_in.data_ptr()), float(dt),
+                                         ctypes.c_void_p(lam_out.data_ptr()), ctypes.c_void_p(lam_in.data_ptr()),
+                                         self._stream_ptr(stream)))
+        return lam_in
+
+    def set_theta(self, theta):
+        """Initial state from a nodal theta' field [E, (N+1)^d] (numpy or device tensor)."""
+        if tuple(theta.shape) != (self.num_elements, self.np_):
+            raise ValueError("theta shape must be (elements, nodes per element)")
+        p, where = _ptr(theta)
+        self._check(self.lib.dg_set_theta(self.h, ctypes.c_void_p(p), where))
+
+    def theta_vjp(self, theta, lam_q, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(theta)
+        self._check(self.lib.dg_theta_vjp(self.h, ctypes.c_void_p(theta.data_ptr()), ctypes.c_void_p(lam_q.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), self._stream_ptr(stream)))
+        return out
+
+    def ke_grad(self, q, out=None, stream=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty_like(q)
+        self._check(self.lib.dg_ke_grad(self.h, ctypes.c_void_p(q.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                        self._stream_ptr(stream)))
         return out
 
     def step(self, dt, nsteps=1, stream=None):
