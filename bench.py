@@ -218,6 +218,37 @@ def run_e2e(pkg, m, cfg, steps, regrid_every):
                 d2h_bytes_per_step=d2h // steps)
 
 
+def run_adjoint(pkg):
+    """Adjoint/forward time ratio on the 3D adjoint workload (12^3 elements, N = 5, FP64, bubble
+    plus Gaussian random theta', 200 steps, checkpoints every 20): time of J(theta') alone
+    against the time of J and dJ/dtheta' through the hand-written adjoint."""
+    import torch
+    from paper_2404_16648_gb300 import adjoint as ladj
+    cfg = workloads.ADJOINT_3D
+    m = pkg.Mesh(3, cfg["N"], cfg["base"], cfg["length"])
+    r = cfg["rff"]
+    theta = m.bubble_theta(**cfg["bubble"], rff=workloads.rff_draws(3, r["sigma"], r["length"], r["features"]))
+    dt, nsteps = cfg["dt"], cfg["steps"]
+    ladj.ke_gradient(m, theta, dt, 4, every=2)          # warm-up of both paths
+    torch.cuda.synchronize()
+    fwd, grad = [], []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        ladj.final_ke(m, theta, dt, nsteps)
+        torch.cuda.synchronize()
+        fwd.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        ladj.ke_gradient(m, theta, dt, nsteps, every=20)
+        torch.cuda.synchronize()
+        grad.append(time.perf_counter() - t0)
+    f, g = min(fwd), min(grad)
+    nodes = m.num_nodes
+    m.close()
+    return {"workload": cfg["name"], "steps": nsteps, "checkpoint_every": 20, "forward_ms": 1e3 * f,
+            "gradient_ms": 1e3 * g, "adjoint_over_forward": g / f,
+            "forward_dof_stage_per_s": 3 * nsteps * nodes / f}
+
+
 def oracle_sample(cfg, n_elem=1024, reps=1, warmup=0):
     """Times the oracle on a bounded sample: per repetition, three RHS evaluations (one RK3
     step's worth) restricted to a contiguous block of elements of the adapted mesh."""
@@ -249,6 +280,7 @@ def main():
     ap.add_argument("--config", default=workloads.BUBBLE_3D["name"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2],
                     help="stage kernel layout: 0 column, 1 node-per-thread, 2 column with "
                          "asynchronous staging (default: the library's)")
@@ -320,6 +352,8 @@ def main():
                                      "peak_kind": "derived: 152 SMs x max SM clock x 4 FP64 flop/clk"},
                         "integrals": r64["integrals"]}
         line["fp32_over_fp64"] = value / v64
+    if not args.no_adjoint:
+        line["adjoint"] = run_adjoint(pkg)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, nel, E, sec = oracle_sample(cfg, n_elem=1024, reps=1)
         line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
