@@ -195,6 +195,32 @@ dg_status dg_theta_vjp(dg_mesh* mesh, const double* theta, const void* lam_q, do
  * dg_integrals) at the caller's state q (device). */
 dg_status dg_ke_grad(dg_mesh* mesh, const void* q, void* out, void* stream);
 
+/* ---- Batched solves: many independent meshes advanced together.  The batch groups its
+ * meshes by (precision, dimension, N); per SSP-RK3 stage it makes one stage launch per group that
+ * covers every element of every member (per-member arguments in a device table, a block ->
+ * (member, first element) map), plus each member's own mortar launches.  A step is captured
+ * once into a CUDA graph and replayed.  The members keep their state in their own buffers
+ * (dg_get_state etc. work as usual); a member must not be regridded while in a batch
+ * (DG_ERR_STATE).  Members may have different sizes, degrees and precisions. */
+typedef struct dg_batch dg_batch;
+
+/* `meshes`: `count` distinct meshes (not owned). */
+dg_status dg_batch_create(dg_mesh* const* meshes, int32_t count, dg_batch** out);
+void dg_batch_destroy(dg_batch* batch);
+/* Per-member time step (count doubles, host). */
+dg_status dg_batch_set_dt(dg_batch* batch, const double* dt);
+/* nsteps steps of every member, asynchronous on the batch's own stream, ordered after work
+ * already queued on each member's stream and before later work there.  use_graph != 0 replays a
+ * captured step graph; 0 launches directly (same kernels, same results). */
+dg_status dg_batch_run(dg_batch* batch, int32_t nsteps, int32_t use_graph);
+dg_status dg_batch_sync(dg_batch* batch);
+/* Autotuner: times the node-per-thread and the asynchronous-column stage layouts of each group
+ * on its members (reps launches each, state untouched) and keeps the faster one; the choice is
+ * also applied to each member's own launches.  `layouts` (count int32, may be NULL) receives
+ * the chosen layout per member (1 or 2, see DG_OPT_STAGE_KERNEL). */
+dg_status dg_batch_autotune(dg_batch* batch, int32_t reps, int32_t* layouts);
+const char* dg_batch_last_error(const dg_batch* batch);
+
 /* Tuning options.  DG_OPT_STAGE_KERNEL selects the fused stage kernel's thread layout:
  * 0 = one thread per vertical node column, 1 = one thread per node, 2 = one thread per column
  * with all operands staged into shared memory by asynchronous copies (default).  All compute

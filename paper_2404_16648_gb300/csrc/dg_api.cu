@@ -18,45 +18,7 @@
 #include "dg_launch.hpp"
 #include "tree.hpp"
 
-struct dg_mesh {
-  dg_mesh_desc desc{};
-  int D = 2, N = 1, n1 = 2, NP = 4, NV = 4, NSUB = 2, NF = 2;
-  int prec = 0;
-  size_t tsize = 8;
-  cudaStream_t stream = nullptr;
-  dgl::Forest forest;
-  dgl::Basis1D basis;
-  dgk::PhysC ph{};
-  double root_h[3] = {1, 1, 1};
-  int64_t E = 0, G = 0, cap = 0;
-  std::vector<int32_t> conf, mort, bnd;
-  // device buffers
-  void* q[3] = {nullptr, nullptr, nullptr};
-  int32_t* d_elem = nullptr;
-  int32_t* d_conn = nullptr;
-  int32_t* d_groups = nullptr;
-  double* d_bg = nullptr;
-  float* d_bgf = nullptr;      // FP32 copy of the background (FP32 path)
-  void* d_mbuf = nullptr;
-  void* d_ppscratch = nullptr; // P' plane of a caller's state in dg_rhs
-  bool pp_valid = false;       // P' plane of q[0] matches q[0]
-  int variant = 2;             // stage kernel layout (DG_OPT_STAGE_KERNEL)
-  // adjoint / pure-step workspace, allocated on first use for the current mesh size
-  void* adj_q[3] = {nullptr, nullptr, nullptr};   // states with P' planes
-  double* adj_l[2] = {nullptr, nullptr};          // cotangents
-  double* d_abuf = nullptr;                       // mortar adjoint contributions
-  int64_t adj_E = -1, adj_G = -1;
-  void* d_ops = nullptr;       // precision T
-  double* d_opsd = nullptr;    // FP64: D, P0, P1, C0, C1, w, x
-  double* d_partial = nullptr;
-  double* d_out = nullptr;
-  int* d_bad = nullptr;
-  // timing
-  bool timing = false;
-  std::vector<cudaEvent_t> ev;
-  size_t ev_used = 0;
-  std::string err;
-};
+#include "dg_mesh.hpp"
 
 namespace {
 
@@ -80,7 +42,14 @@ dg_status fail(dg_mesh* m, dg_status st, const char* fmt, ...) {
 
 void dfree(void* p) { if (p) cudaFree(p); }
 
+}  // namespace
+
+namespace dgi {
 int64_t plane(const dg_mesh* m) { return m->E * m->NP; }
+}  // namespace dgi
+using dgi::plane;
+
+namespace {
 
 dg_status upload_ops(dg_mesh* m) {
   const int nn = m->n1 * m->n1;
@@ -177,38 +146,73 @@ dg_status alloc_states(dg_mesh* m, void* q[3]) {
   return DG_OK;
 }
 
-void* pp_plane(const dg_mesh* m, void* q) {
-  return (char*)q + (size_t)m->NV * plane(m) * m->tsize;
-}
-
 const void* bgt(const dg_mesh* m) {
   return m->prec == DG_FP64 ? (const void*)m->d_bg : (const void*)m->d_bgf;
 }
 
-dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const void* qn, void* out,
-                          void* pp_out, int mode, double dt, double ca, double cb, cudaStream_t s) {
-  if (m->G > 0) {
-    dgk::MortarArgs M{qs, pp_in, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, bgt(m),
-                      m->d_ops, (float)m->ph.gamma, m->ph};
-    bool ok = m->prec == DG_FP64
-                  ? (m->D == 2 ? dgk::launch_mortar_f64_2d(m->N, M, s) : dgk::launch_mortar_f64_3d(m->N, M, s))
-                  : (m->D == 2 ? dgk::launch_mortar_f32_2d(m->N, M, s) : dgk::launch_mortar_f32_3d(m->N, M, s));
-    if (!ok) return fail(m, DG_ERR_UNSUPPORTED, "mortar kernel for N=%d not compiled", m->N);
-    CU(cudaGetLastError());
-  }
-  dgk::StageArgs A{};
-  A.qs = qs; A.pp_in = pp_in; A.qn = qn; A.out = out; A.pp_out = pp_out; A.mbuf = m->d_mbuf;
-  A.plane = plane(m); A.E = (int32_t)m->E;
-  A.elem = m->d_elem; A.conn = m->d_conn; A.bg = m->d_bg; A.bgt = bgt(m); A.ops = m->d_ops;
+}  // namespace
+
+namespace dgi {
+
+void* pp_plane(const dg_mesh* m, void* q) {
+  return (char*)q + (size_t)m->NV * plane(m) * m->tsize;
+}
+
+void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const void* qn, void* out,
+                     void* pp_out, int mode, double dt, double ca, double cb, dgk::StageArgs* A) {
+  A->qs = qs; A->pp_in = pp_in; A->qn = qn; A->out = out; A->pp_out = pp_out; A->mbuf = m->d_mbuf;
+  A->plane = plane(m); A->E = (int32_t)m->E;
+  A->elem = m->d_elem; A->conn = m->d_conn; A->bg = m->d_bg; A->bgt = bgt(m); A->ops = m->d_ops;
   for (int l = 0; l < dgk::kMaxLevels; ++l)
     for (int a = 0; a < 3; ++a) {
       // 2/h = (2/h_root) 2^level: power-of-two scaling is exact
-      A.inv2hd[l][a] = std::ldexp(2.0 / m->root_h[a], l);
-      A.inv2hf[l][a] = (float)A.inv2hd[l][a];
+      A->inv2hd[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+      A->inv2hf[l][a] = (float)A->inv2hd[l][a];
     }
-  A.dt = dt; A.ca = ca; A.cb = cb; A.mode = mode; A.variant = m->variant; A.ph = m->ph;
-  A.plane32 = (int32_t)plane(m);
-  A.gammaf = (float)m->ph.gamma; A.gf = (float)m->ph.g;
+  A->dt = dt; A->ca = ca; A->cb = cb; A->mode = mode; A->variant = m->variant; A->ph = m->ph;
+  A->plane32 = (int32_t)plane(m);
+  A->gammaf = (float)m->ph.gamma; A->gf = (float)m->ph.g;
+}
+
+dg_status set_error(dg_mesh* m, dg_status st, const char* msg) {
+  if (m) m->err = msg;
+  return st;
+}
+
+dg_status launch_mortars(dg_mesh* m, const void* qs, const void* pp_in, cudaStream_t s) {
+  if (m->G == 0) return DG_OK;
+  dgk::MortarArgs M{qs, pp_in, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, bgt(m),
+                    m->d_ops, (float)m->ph.gamma, m->ph};
+  bool ok = m->prec == DG_FP64
+                ? (m->D == 2 ? dgk::launch_mortar_f64_2d(m->N, M, s) : dgk::launch_mortar_f64_3d(m->N, M, s))
+                : (m->D == 2 ? dgk::launch_mortar_f32_2d(m->N, M, s) : dgk::launch_mortar_f32_3d(m->N, M, s));
+  if (!ok) return set_error(m, DG_ERR_UNSUPPORTED, "mortar kernel not compiled");
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(m, DG_ERR_CUDA, cudaGetErrorString(e));
+  return DG_OK;
+}
+
+dg_status ensure_pp(dg_mesh* m, cudaStream_t s) {
+  if (m->pp_valid) return DG_OK;
+  const void* theta = (const char*)m->q[0] + (size_t)(m->NV - 1) * plane(m) * m->tsize;
+  cudaError_t e = dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->ph,
+                                     pp_plane(m, m->q[0]), s);
+  if (e != cudaSuccess) return set_error(m, DG_ERR_CUDA, cudaGetErrorString(e));
+  m->pp_valid = true;
+  return DG_OK;
+}
+
+}  // namespace dgi
+using dgi::pp_plane;
+
+namespace {
+
+dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const void* qn, void* out,
+                          void* pp_out, int mode, double dt, double ca, double cb, cudaStream_t s) {
+  dg_status st = dgi::launch_mortars(m, qs, pp_in, s);
+  if (st != DG_OK) return st;
+  dgk::StageArgs A{};
+  dgi::fill_stage_args(m, qs, pp_in, qn, out, pp_out, mode, dt, ca, cb, &A);
   const bool timed = m->timing && mode == 1;
   if (timed) {
     while (m->ev.size() < m->ev_used + 2) {
@@ -584,9 +588,9 @@ dg_status dg_step(dg_mesh* m, double dt, int32_t nsteps, void* stream) {
   void* p0 = pp_plane(m, m->q[0]);
   void* p1 = pp_plane(m, m->q[1]);
   void* p2 = pp_plane(m, m->q[2]);
-  if (!m->pp_valid && nsteps > 0) {
-    const void* theta = (const char*)m->q[0] + (size_t)(m->NV - 1) * plane(m) * m->tsize;
-    CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->ph, p0, s));
+  if (nsteps > 0) {
+    dg_status st0 = dgi::ensure_pp(m, s);
+    if (st0 != DG_OK) return st0;
   }
   for (int32_t it = 0; it < nsteps; ++it) {
     // Shu-Osher SSP-RK3: q1 = q + dt L(q); q2 = 3/4 q + 1/4 (q1 + dt L(q1));
@@ -597,7 +601,6 @@ dg_status dg_step(dg_mesh* m, double dt, int32_t nsteps, void* stream) {
     if (st == DG_OK) st = launch_rhs_pass(m, m->q[2], p2, m->q[0], m->q[0], p0, 1, dt, 1.0 / 3.0, 2.0 / 3.0, s);
     if (st != DG_OK) return st;
   }
-  if (nsteps > 0) m->pp_valid = true;
   return DG_OK;
 }
 

@@ -35,6 +35,14 @@ enum { FACE_WALL = 0, FACE_CONF = 1, FACE_FINE = 2, FACE_COARSE = 3 };
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
+// Elements per CTA of the node-per-thread layout and of the column layouts.
+__host__ __device__ constexpr int epb_node(int D, int N) {
+  return ipow(N + 1, D) >= 128 ? 1 : 256 / ipow(N + 1, D);
+}
+__host__ __device__ constexpr int epb_col(int D, int N) {
+  return ipow(N + 1, D - 1) >= 64 ? 1 : (128 / ipow(N + 1, D - 1) > 0 ? 128 / ipow(N + 1, D - 1) : 1);
+}
+
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
@@ -204,9 +212,9 @@ __device__ __forceinline__ int face_node(int a, int side, int t) {
   return idx[0] + n1 * (idx[1] + n1 * idx[2]);
 }
 
+// Body of the node-per-thread stage kernel for the EPB elements e0, e0 + 1, ... of mesh A.
 template <class T, int D, int N, int EPB>
-__global__ void __launch_bounds__(EPB * ipow(N + 1, D))
-stage_kernel(const StageArgs A) {
+__device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
   constexpr int NSUB = 1 << (D - 1);
   __shared__ T sD[n1 * n1];
@@ -217,7 +225,7 @@ stage_kernel(const StageArgs A) {
   const T w0 = ops[5 * n1 * n1];
   const T gamma = gamma_of<T>(A.ph, A.gammaf);
   const int le = tid / NP, n = tid - le * NP;
-  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const int64_t e = e0 + le;
   const bool valid = e < A.E;
   int idx[3];
   idx[0] = n % n1;
@@ -341,6 +349,20 @@ stage_kernel(const StageArgs A) {
       (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
 }
 
+template <class T, int D, int N, int EPB>
+__global__ void __launch_bounds__(EPB * ipow(N + 1, D))
+stage_kernel(const __grid_constant__ StageArgs A) {
+  stage_body_node<T, D, N, EPB>(A, (int64_t)blockIdx.x * EPB);
+}
+
+// Batched form: block b works on mesh tab[map[b].x], elements from map[b].y.
+template <class T, int D, int N, int EPB>
+__global__ void __launch_bounds__(EPB * ipow(N + 1, D))
+stage_kernel_batched(const StageArgs* __restrict__ tab, const int2* __restrict__ map) {
+  const int2 bm = map[blockIdx.x];
+  stage_body_node<T, D, N, EPB>(tab[bm.x], (int64_t)bm.y);
+}
+
 // P' of every node of a state (FP64 evaluation, stored in T): used when a state enters from
 // outside the time loop (set_state, initial condition, transfer, dg_rhs input).
 template <class T>
@@ -358,7 +380,7 @@ __global__ void pprime_kernel(int64_t total, int NP, int n1, int D, const T* the
 // One CTA per mortar group; NSUB * NF threads: thread (m, t) owns mortar node t of mortar m.
 template <class T, int D, int N>
 __global__ void __launch_bounds__((1 << (D - 1)) * ipow(N + 1, D - 1))
-mortar_kernel(const MortarArgs A) {
+mortar_kernel(const __grid_constant__ MortarArgs A) {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
   constexpr int NSUB = 1 << (D - 1);
   __shared__ T sP[2][n1 * n1], sC[2][n1 * n1];

@@ -25,6 +25,12 @@ cudaError_t init_stage_f64_2d(const double* dtab_all);
 cudaError_t init_stage_f64_3d(const double* dtab_all);
 cudaError_t init_stage_f32_2d(const double* dtab_all);
 cudaError_t init_stage_f32_3d(const double* dtab_all);
+// Stage kernels over many meshes at once (tab: per-mesh arguments on the device, map: per block
+// the mesh index and its first element); layout 1 node-per-thread, 2 column with async staging.
+cudaError_t launch_stage_batched_f64_2d(int N, int layout, const StageArgs* tab, const int2* map, int nblocks, cudaStream_t s);
+cudaError_t launch_stage_batched_f64_3d(int N, int layout, const StageArgs* tab, const int2* map, int nblocks, cudaStream_t s);
+cudaError_t launch_stage_batched_f32_2d(int N, int layout, const StageArgs* tab, const int2* map, int nblocks, cudaStream_t s);
+cudaError_t launch_stage_batched_f32_3d(int N, int layout, const StageArgs* tab, const int2* map, int nblocks, cudaStream_t s);
 
 cudaError_t launch_background(int32_t E, int n1, int D, const int32_t* elem, const double* xi,
                               double root_hz, const PhysC& ph, double* bg, float* bgf,

@@ -1,0 +1,68 @@
+// Internal definition of the dg_mesh handle, shared by the C ABI units (dg_api.cu, dg_batch.cu).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dg.h"
+#include "basis.hpp"
+#include "dg_launch.hpp"
+#include "tree.hpp"
+
+struct dg_mesh {
+  dg_mesh_desc desc{};
+  int D = 2, N = 1, n1 = 2, NP = 4, NV = 4, NSUB = 2, NF = 2;
+  int prec = 0;
+  size_t tsize = 8;
+  cudaStream_t stream = nullptr;
+  dgl::Forest forest;
+  dgl::Basis1D basis;
+  dgk::PhysC ph{};
+  double root_h[3] = {1, 1, 1};
+  int64_t E = 0, G = 0, cap = 0;
+  std::vector<int32_t> conf, mort, bnd;
+  // device buffers
+  void* q[3] = {nullptr, nullptr, nullptr};
+  int32_t* d_elem = nullptr;
+  int32_t* d_conn = nullptr;
+  int32_t* d_groups = nullptr;
+  double* d_bg = nullptr;
+  float* d_bgf = nullptr;      // FP32 copy of the background (FP32 path)
+  void* d_mbuf = nullptr;
+  void* d_ppscratch = nullptr; // P' plane of a caller's state in dg_rhs
+  bool pp_valid = false;       // P' plane of q[0] matches q[0]
+  int variant = 2;             // stage kernel layout (DG_OPT_STAGE_KERNEL)
+  // adjoint / pure-step workspace, allocated on first use for the current mesh size
+  void* adj_q[3] = {nullptr, nullptr, nullptr};   // states with P' planes
+  double* adj_l[2] = {nullptr, nullptr};          // cotangents
+  double* d_abuf = nullptr;                       // mortar adjoint contributions
+  int64_t adj_E = -1, adj_G = -1;
+  void* d_ops = nullptr;       // precision T
+  double* d_opsd = nullptr;    // FP64: D, P0, P1, C0, C1, w, x
+  double* d_partial = nullptr;
+  double* d_out = nullptr;
+  int* d_bad = nullptr;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  std::string err;
+};
+
+
+namespace dgi {
+
+int64_t plane(const dg_mesh* m);
+void* pp_plane(const dg_mesh* m, void* q);
+// Arguments of one fused stage launch on mesh m (mode 1: Shu-Osher combination).
+void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const void* qn, void* out,
+                     void* pp_out, int mode, double dt, double ca, double cb, dgk::StageArgs* A);
+// Launches the mortar kernel of mesh m for stage input qs (no-op without hanging faces).
+dg_status launch_mortars(dg_mesh* m, const void* qs, const void* pp_in, cudaStream_t s);
+// Makes the P' plane of m->q[0] current.
+dg_status ensure_pp(dg_mesh* m, cudaStream_t s);
+dg_status set_error(dg_mesh* m, dg_status st, const char* msg);
+
+}  // namespace dgi

@@ -62,9 +62,9 @@ __host__ __device__ constexpr size_t async_smem_bytes() {
   return sizeof(T) * ((size_t)EPB * async_elem_words<T, D, N>() + (size_t)(N + 1) * (N + 1));
 }
 
+// Body for the EPB elements e0, e0 + 1, ... of mesh A.
 template <class T, int D, int N, int EPB>
-__global__ void __launch_bounds__(EPB * ipow(N + 1, D - 1))
-stage_kernel_async(const StageArgs A) {
+__device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0) {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
   constexpr int NSUB = 1 << (D - 1);
   constexpr int NT = D - 1;
@@ -82,7 +82,7 @@ stage_kernel_async(const StageArgs A) {
   T* sNb = base + RA + RQ;            // [2D][NV + 1][NF]
   T* sBg = base + RA + RQ + RN;       // [n1][4]
   T* sDh = reinterpret_cast<T*>(smem_raw) + EPB * EW;
-  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const int64_t e = e0 + le;
   const bool valid = e < A.E;
   const int ci = t % n1, cj = (D == 3) ? t / n1 : 0;
   const int P = A.plane32;
@@ -334,6 +334,20 @@ stage_kernel_async(const StageArgs A) {
     const double* bd = A.bg + ((size_t)e * n1 + k) * 4;
     ppo[n] = (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
   }
+}
+
+template <class T, int D, int N, int EPB>
+__global__ void __launch_bounds__(EPB * ipow(N + 1, D - 1))
+stage_kernel_async(const __grid_constant__ StageArgs A) {
+  stage_body_async<T, D, N, EPB>(A, (int64_t)blockIdx.x * EPB);
+}
+
+// Batched form: block b works on mesh tab[map[b].x], elements from map[b].y.
+template <class T, int D, int N, int EPB>
+__global__ void __launch_bounds__(EPB * ipow(N + 1, D - 1))
+stage_kernel_async_batched(const StageArgs* __restrict__ tab, const int2* __restrict__ map) {
+  const int2 bm = map[blockIdx.x];
+  stage_body_async<T, D, N, EPB>(tab[bm.x], (int64_t)bm.y);
 }
 
 }  // namespace dgk

@@ -52,7 +52,7 @@ __host__ __device__ constexpr size_t col_smem_bytes() {
 
 template <class T, int D, int N, int EPB>
 __global__ void __launch_bounds__(EPB * ipow(N + 1, D - 1))
-stage_kernel_col(const StageArgs A) {
+stage_kernel_col(const __grid_constant__ StageArgs A) {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
   constexpr int NSUB = 1 << (D - 1);
   constexpr int NT = D - 1;                 // horizontal axes

@@ -9,4 +9,8 @@ bool launch_mortar_f32_3d(int N, const MortarArgs& A, cudaStream_t s) {
   return mortar_dispatch<float, 3>(N, A, s);
 }
 cudaError_t init_stage_f32_3d(const double* dtab_all) { return upload_dtab(dtab_all); }
+cudaError_t launch_stage_batched_f32_3d(int N, int layout, const StageArgs* tab, const int2* map,
+                                        int nblocks, cudaStream_t s) {
+  return batched_dispatch<float, 3>(N, layout, tab, map, nblocks, s);
+}
 }  // namespace dgk

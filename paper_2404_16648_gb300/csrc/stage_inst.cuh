@@ -9,7 +9,7 @@ namespace {
 template <class T, int D, int N>
 void run_stage_node(const StageArgs& A, cudaStream_t s) {
   constexpr int NP = ipow(N + 1, D);
-  constexpr int EPB = NP >= 128 ? 1 : 256 / NP;
+  constexpr int EPB = epb_node(D, N);
   const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
   if (blocks) stage_kernel<T, D, N, EPB><<<blocks, EPB * NP, 0, s>>>(A);
 }
@@ -17,7 +17,7 @@ void run_stage_node(const StageArgs& A, cudaStream_t s) {
 template <class T, int D, int N>
 cudaError_t run_stage_col(const StageArgs& A, cudaStream_t s) {
   constexpr int NF = ipow(N + 1, D - 1);
-  constexpr int EPB = NF >= 64 ? 1 : (128 / NF > 0 ? 128 / NF : 1);
+  constexpr int EPB = epb_col(D, N);
   constexpr size_t smem = col_smem_bytes<T, D, N, EPB>();
   static bool configured = false;
   if (!configured) {
@@ -34,7 +34,7 @@ cudaError_t run_stage_col(const StageArgs& A, cudaStream_t s) {
 template <class T, int D, int N>
 cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
   constexpr int NF = ipow(N + 1, D - 1);
-  constexpr int EPB = NF >= 64 ? 1 : (128 / NF > 0 ? 128 / NF : 1);
+  constexpr int EPB = epb_col(D, N);
   constexpr size_t smem = async_smem_bytes<T, D, N, EPB>();
   static bool configured = false;
   if (!configured) {
@@ -46,6 +46,47 @@ cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
   const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
   if (blocks) stage_kernel_async<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
   return cudaSuccess;
+}
+
+// Batched launch over many meshes: layout 1 (node) or 2 (column, asynchronous staging).
+template <class T, int D, int N>
+cudaError_t run_stage_batched(int layout, const StageArgs* tab, const int2* map, int nblocks,
+                              cudaStream_t s) {
+  if (layout == 1) {
+    constexpr int EPB = epb_node(D, N);
+    if (nblocks <= 0) return cudaSuccess;
+    stage_kernel_batched<T, D, N, EPB><<<nblocks, EPB * ipow(N + 1, D), 0, s>>>(tab, map);
+    return cudaGetLastError();
+  }
+  constexpr int NF = ipow(N + 1, D - 1);
+  constexpr int EPB = epb_col(D, N);
+  constexpr size_t smem = async_smem_bytes<T, D, N, EPB>();
+  static bool configured = false;
+  if (!configured) {   // done on the first call, also with nblocks == 0 (before a capture)
+    cudaError_t e = cudaFuncSetAttribute(stage_kernel_async_batched<T, D, N, EPB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (nblocks <= 0) return cudaSuccess;
+  stage_kernel_async_batched<T, D, N, EPB><<<nblocks, EPB * NF, smem, s>>>(tab, map);
+  return cudaGetLastError();
+}
+
+template <class T, int D>
+cudaError_t batched_dispatch(int N, int layout, const StageArgs* tab, const int2* map, int nblocks,
+                             cudaStream_t s) {
+  switch (N) {
+    case 1: return run_stage_batched<T, D, 1>(layout, tab, map, nblocks, s);
+    case 2: return run_stage_batched<T, D, 2>(layout, tab, map, nblocks, s);
+    case 3: return run_stage_batched<T, D, 3>(layout, tab, map, nblocks, s);
+    case 4: return run_stage_batched<T, D, 4>(layout, tab, map, nblocks, s);
+    case 5: return run_stage_batched<T, D, 5>(layout, tab, map, nblocks, s);
+    case 6: return run_stage_batched<T, D, 6>(layout, tab, map, nblocks, s);
+    case 7: return run_stage_batched<T, D, 7>(layout, tab, map, nblocks, s);
+    case 8: return run_stage_batched<T, D, 8>(layout, tab, map, nblocks, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class T, int D, int N>

@@ -27,7 +27,8 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
             "dg_step_state", "dg_step_vjp", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
-            "dg_bubble_theta",
+            "dg_bubble_theta", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
+            "dg_batch_run", "dg_batch_sync", "dg_batch_autotune", "dg_batch_last_error",
             "dg_last_error", "dg_version"]
 
 
@@ -109,6 +110,13 @@ def load_library(path=None):
         "dg_theta_vjp": (i32, [vp, vp, vp, vp, vp]),
         "dg_ke_grad": (i32, [vp, vp, vp, vp]),
         "dg_bubble_theta": (i32, [vp, ctypes.POINTER(BubbleDesc), vp]),
+        "dg_batch_create": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]),
+        "dg_batch_destroy": (None, [vp]),
+        "dg_batch_set_dt": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
+        "dg_batch_run": (i32, [vp, i32, i32]),
+        "dg_batch_sync": (i32, [vp]),
+        "dg_batch_autotune": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int32)]),
+        "dg_batch_last_error": (ctypes.c_char_p, [vp]),
         "dg_last_error": (ctypes.c_char_p, [vp]),
         "dg_version": (ctypes.c_char_p, []),
     }
@@ -429,6 +437,53 @@ class Forest:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             self.lib.dg_forest_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many meshes advanced together (dg_batch_*)."""
+
+    def __init__(self, meshes, dt):
+        self.lib = load_library()
+        self.meshes = list(meshes)           # keep the meshes alive as long as the batch
+        arr = (ctypes.c_void_p * len(self.meshes))(*[m.h.value for m in self.meshes])
+        h = ctypes.c_void_p()
+        st = self.lib.dg_batch_create(arr, len(self.meshes), ctypes.byref(h))
+        if st != DG_OK:
+            raise DGError(st, "dg_batch_create failed")
+        self.h = h
+        self.set_dt(dt)
+
+    def _check(self, st):
+        if st != DG_OK:
+            raise DGError(st, self.lib.dg_batch_last_error(self.h).decode())
+
+    def set_dt(self, dt):
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (len(self.meshes),)))
+        self._check(self.lib.dg_batch_set_dt(self.h, d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def run(self, nsteps, graph=True, sync=True):
+        self._check(self.lib.dg_batch_run(self.h, int(nsteps), 1 if graph else 0))
+        if sync:
+            self.sync()
+
+    def sync(self):
+        self._check(self.lib.dg_batch_sync(self.h))
+
+    def autotune(self, reps=5):
+        out = np.zeros(len(self.meshes), dtype=np.int32)
+        self._check(self.lib.dg_batch_autotune(self.h, int(reps), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.dg_batch_destroy(self.h)
             self.h = ctypes.c_void_p()
 
     def __del__(self):

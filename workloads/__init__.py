@@ -45,6 +45,28 @@ ADJOINT_3D = dict(name="adjoint3d_12cube_N5", dim=3, N=5, base=(12, 12, 12),
 
 CONFIGS = {c["name"]: c for c in (RTB_2D, COLD_2D, BUBBLE_3D, ADJOINT_3D)}
 
+# Batched 2D bubbles: 256 instances on [0, 1000]^2 with seeded radius U[150, 400] m, amplitude
+# U[0.1, 2] K, centre (500, 350) m, mesh 10x10 ... 64x32, N in {3..7}, precision 50/50, 500 steps.
+BATCH_MESHES = ((10, 10), (16, 16), (20, 16), (32, 16), (32, 32), (48, 24), (64, 32))
+BATCH_2D = dict(name="batch2d_256_bubbles", count=256, steps=500, length=(1000.0, 1000.0))
+
+
+def batch_instances(count=256, seed=4, meshes=BATCH_MESHES):
+    """Seeded instance descriptions of the batched workload.  dt is half of the explicit limit
+    estimate h_min / ((2N + 1) c) with c = 360 m/s."""
+    g = rng(seed, 7)
+    out = []
+    for i in range(count):
+        base = meshes[int(g.integers(len(meshes)))]
+        N = int(g.integers(3, 8))
+        prec = "fp32" if g.random() < 0.5 else "fp64"
+        radius = float(g.uniform(150.0, 400.0))
+        amp = float(g.uniform(0.1, 2.0))
+        hmin = min(1000.0 / base[0], 1000.0 / base[1])
+        out.append(dict(base=base, N=N, precision=prec, dt=0.5 * hmin / ((2 * N + 1) * 360.0),
+                        bubble=dict(center=(500.0, 350.0), radius=(radius, radius), amp=amp / 2.0)))
+    return out
+
 
 def scaled(cfg, base_div=1, N=None):
     """A smaller copy of a workload (same physics, fewer root cells and/or lower degree)."""
