@@ -249,6 +249,58 @@ def run_adjoint(pkg):
             "forward_dof_stage_per_s": 3 * nsteps * nodes / f}
 
 
+def run_batch(pkg, steps=500, compare_steps=50):
+    """Batched workload: 256 seeded 2D bubble instances (mesh 10x10 ... 64x32, N 3..7, FP32/FP64
+    50/50, per-instance dt), autotuned layouts, `steps` graph-replayed SSP-RK3 steps; and the same
+    instances advanced one mesh launch at a time for `compare_steps` steps."""
+    import torch
+    cfg = workloads.BATCH_2D
+    inst = workloads.batch_instances(cfg["count"])
+
+    def make():
+        ms = []
+        for d in inst:
+            m = pkg.Mesh(2, d["N"], d["base"], cfg["length"], precision=d["precision"])
+            m.set_bubble(**d["bubble"])
+            ms.append(m)
+        return ms
+
+    meshes = make()
+    dts = [d["dt"] for d in inst]
+    nodes = sum(m.num_nodes for m in meshes)
+    batch = pkg.Batch(meshes, dts)
+    layouts = batch.autotune(reps=3)
+    batch.run(2, graph=True)                      # warm-up (graph capture)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    batch.run(steps, graph=True, sync=False)
+    batch.sync()
+    t_batch = time.perf_counter() - t0
+    # one mesh launch at a time
+    singles = make()
+    for m, lay in zip(singles, layouts):
+        m.set_stage_kernel(int(lay))
+    for m, dt in zip(singles, dts):
+        m.step(dt, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(compare_steps):
+        for m, dt in zip(singles, dts):
+            m.step(dt, 1)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    batch.close()
+    for m in meshes + singles:
+        m.close()
+    rate_b = 3 * steps * nodes / t_batch
+    rate_s = 3 * compare_steps * nodes / t_single
+    return {"workload": cfg["name"], "instances": len(inst), "nodes_per_variable": nodes,
+            "steps": steps, "value": rate_b, "unit": METRIC, "ms_per_step": 1e3 * t_batch / steps,
+            "one_at_a_time_value": rate_s, "speedup_vs_one_at_a_time": rate_b / rate_s,
+            "layouts": {"node": int(np.sum(layouts == 1)), "column_async": int(np.sum(layouts == 2))}}
+
+
 def oracle_sample(cfg, n_elem=1024, reps=1, warmup=0):
     """Times the oracle on a bounded sample: per repetition, three RHS evaluations (one RK3
     step's worth) restricted to a contiguous block of elements of the adapted mesh."""
@@ -281,6 +333,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2],
                     help="stage kernel layout: 0 column, 1 node-per-thread, 2 column with "
                          "asynchronous staging (default: the library's)")
@@ -354,6 +407,8 @@ def main():
         line["fp32_over_fp64"] = value / v64
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(pkg)
+    if not args.no_batch:
+        line["batch"] = run_batch(pkg)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, nel, E, sec = oracle_sample(cfg, n_elem=1024, reps=1)
         line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",

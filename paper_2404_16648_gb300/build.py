@@ -62,6 +62,10 @@ def build(verbose=False, jobs=None):
     def compile_one(item):
         src, obj = item
         cmd = [nvcc] + _flags() + ["-c", src, "-o", obj]
+        if os.path.basename(src).startswith("stage_"):
+            # no implicit multiply-add contraction in the stage kernels: every fused multiply-add
+            # is an explicit fma(), so the single-mesh and batched instantiations round alike
+            cmd.insert(1, "-fmad=false")
         if src.endswith(".cpp"):
             cmd = [nvcc] + _flags() + ["-x", "cu", "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -270,7 +270,7 @@ __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) 
         T s = (T)0;
 #pragma unroll
         for (int m = 0; m < n1; ++m) s = fma(sD[ia * n1 + m], sF[le][v][b0 + m * stride], s);
-        acc[v] -= inv2h[a] * s;
+        acc[v] = fma(-inv2h[a], s, acc[v]);
       }
     }
     __syncthreads();

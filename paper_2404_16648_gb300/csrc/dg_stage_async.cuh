@@ -162,7 +162,7 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
       T s = (T)0;
 #pragma unroll
       for (int m = 0; m < n1; ++m) s = fma(dtab<T>(dtab_offset(N) + k * n1 + m), Fz[v][m], s);
-      acc[v][k] -= inv2h[D - 1] * s;
+      acc[v][k] = fma(-inv2h[D - 1], s, acc[v][k]);
     }
   __syncthreads();
   auto line_dot = [&](const T* row, const T* Dr) {
@@ -189,7 +189,7 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int k = 0; k < n1; ++k) acc[v][k] -= inv2h[0] * line_dot(&sA[v * NP + NF * k + n1 * cj], Dr);
+      for (int k = 0; k < n1; ++k) acc[v][k] = fma(-inv2h[0], line_dot(&sA[v * NP + NF * k + n1 * cj], Dr), acc[v][k]);
   }
   if (D == 3) {
     // y fluxes recomputed from the staged state into the same tile, transposed so that the
@@ -218,7 +218,7 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
       for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int k = 0; k < n1; ++k)
-          acc[v][k] -= inv2h[1] * line_dot(&sA[v * NP + NF * k + n1 * ci], Dr);
+          acc[v][k] = fma(-inv2h[1], line_dot(&sA[v * NP + NF * k + n1 * ci], Dr), acc[v][k]);
     }
   }
   __syncthreads();

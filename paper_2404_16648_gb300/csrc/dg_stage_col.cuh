@@ -139,7 +139,7 @@ stage_kernel_col(const __grid_constant__ StageArgs A) {
       T s = (T)0;
 #pragma unroll
       for (int m = 0; m < n1; ++m) s = fma(dtab<T>(dtab_offset(N) + k * n1 + m), Fz[v][m], s);
-      acc[v][k] -= inv2h[D - 1] * s;
+      acc[v][k] = fma(-inv2h[D - 1], s, acc[v][k]);
     }
   __syncthreads();
   // ---- horizontal derivatives through shared memory (contiguous lines, vector loads)
@@ -168,7 +168,7 @@ stage_kernel_col(const __grid_constant__ StageArgs A) {
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int k = 0; k < n1; ++k)
-        acc[v][k] -= inv2h[0] * line_dot(&sFh[le][0][v][NF * k + n1 * cj], Dr);
+        acc[v][k] = fma(-inv2h[0], line_dot(&sFh[le][0][v][NF * k + n1 * cj], Dr), acc[v][k]);
     if (D == 3) {
 #pragma unroll
       for (int m = 0; m < n1; ++m) Dr[m] = sDh[cj * n1 + m];
@@ -176,7 +176,7 @@ stage_kernel_col(const __grid_constant__ StageArgs A) {
       for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int k = 0; k < n1; ++k)
-          acc[v][k] -= inv2h[1] * line_dot(&sFh[le][NT - 1][v][NF * k + n1 * ci], Dr);
+          acc[v][k] = fma(-inv2h[1], line_dot(&sFh[le][NT - 1][v][NF * k + n1 * ci], Dr), acc[v][k]);
     }
   }
   __syncthreads();
