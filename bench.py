@@ -120,6 +120,26 @@ def build_mesh(pkg, cfg, precision):
     return m
 
 
+def measured_traffic(D, N, precision, layout):
+    """DRAM bytes per node of each stage launch from the committed ncu record, if that record
+    was taken on the current kernel sources and configuration; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "stage_traffic_bubble3d_N7.json")
+    try:
+        rec = json.load(open(path))
+    except OSError:
+        return None
+    if (D, N, precision, layout) != (3, 7, "fp32", 2):
+        return None
+    h = hashlib.sha1()
+    for f in rec["sources"]:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != rec["sources_sha1"]:
+        return None
+    b = rec["bytes_per_node"]
+    return [b["stage1"], b["stage2"], b["stage3"]]
+
+
 def stage_bytes(E, NP, NV, b, n1, D):
     """Algorithmic HBM bytes of the three stage launches of one RK3 step: stage 1 reads q^n and
     writes q^1; stages 2 and 3 read q^s and q^n and write the next state; every launch reads
@@ -160,6 +180,8 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
     alg_bytes = 0
     alg_flops = 0
     launches = 0
+    per_node = measured_traffic(D, N, precision, 2 if STAGE_KERNEL in (None, 2) else STAGE_KERNEL)
+    traffic = 0.0
     ev0.record()
     for i in range(steps):
         E = m.num_elements
@@ -167,6 +189,8 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
         dof_stage += 3 * E * NP
         alg_bytes += stage_bytes(E, NP, NV, b, n1, D)
         alg_flops += stage_flops(E, NP, NV, n1, D)
+        if per_node:
+            traffic += E * NP * sum(per_node)
         launches += 3 * (1 + (m.num_mortars > 0))   # stage (+ mortar) launches per step
         if regrid_every and (i + 1) % regrid_every == 0:
             m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
@@ -182,7 +206,8 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
     out = dict(ms=ms, dof_stage=dof_stage, stage_ms=stage_ms, stage_launches=stage_launches,
                alg_bytes=alg_bytes, alg_flops=alg_flops, launches=launches, clocks=clocks,
                elements=m.num_elements, nodes=m.num_nodes, integrals=integ.tolist(),
-               state_bytes=NV * m.num_nodes * b, mortars=m.num_mortars)
+               state_bytes=NV * m.num_nodes * b, mortars=m.num_mortars,
+               traffic_per_launch=(traffic / (3 * steps)) if per_node else None)
     return m, out
 
 
@@ -393,7 +418,12 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "stage_kernel", "achieved": achieved,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
-                         "traffic": None, "stage_ms_per_launch": r32["stage_ms"] / max(1, r32["stage_launches"])},
+                         "traffic": r32["traffic_per_launch"],
+                         "traffic_note": "ncu dram read+write per node of each stage launch "
+                                         "(profiles/stage_traffic_bubble3d_N7.json) scaled to this run's "
+                                         "nodes; null when the kernel sources changed",
+                         "algorithmic_bytes_per_launch": r32["alg_bytes"] / (3 * args.steps),
+                         "stage_ms_per_launch": r32["stage_ms"] / max(1, r32["stage_launches"])},
             "clocks": r32["clocks"], "e2e": e2e}
     if r64 is not None:
         v64 = world * r64["dof_stage"] / (r64["ms"] / 1e3)
