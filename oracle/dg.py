@@ -233,6 +233,87 @@ def rhs(mesh, q, elems=None):
     return out
 
 
+def viscous_primitives(mesh, q):
+    """phi = (u_0, .., u_{d-1}, theta') with theta' = (Theta' - theta0 rho') / rho, the exact
+    rewriting of (Theta_bar + Theta')/(rho_bar + rho') - theta0 for Theta_bar = rho_bar theta0."""
+    d = mesh.d
+    rb, _, _ = mesh.bg
+    rho = rb + q[0]
+    phi = np.empty((d + 1,) + q.shape[1:], dtype=q.dtype)
+    phi[:d] = q[1:1 + d] / rho
+    phi[d] = (q[1 + d] - mesh.K.theta0 * q[0]) / rho
+    return phi, rho
+
+
+def _central_face_pass(mesh, X, conf, mort, bnd, out, scale_wall):
+    """Adds the strong-form lift of central face values to out[..., a, :]:
+    out_a += n_a (2/h_a)/w0 (X* - X_own) at face nodes, X* = (X- + X+)/2 on conforming faces and
+    mortars (coarse values projected with P, results returned with sum_m C F*_m); on walls
+    X* = X_own when scale_wall is None, else X* = 0 (no flux through the wall).
+    X: [ncomp, d, E, NP] (the a-th component is the one used on faces of axis a)."""
+    d = mesh.d
+    w0 = mesh.basis.weights[0]
+    B = mesh.basis
+
+    def lift(e, a, s, Xs, Xo):
+        idx = mesh.trace_index(a, s)
+        n_a = 1.0 if s == 1 else -1.0
+        out[:, a, e, idx] += n_a * (2.0 / mesh.h[e, a]) / w0 * (Xs - Xo)
+
+    for (m, p, a) in conf:
+        xm = X[:, a, m][:, mesh.trace_index(a, 1)]
+        xp = X[:, a, p][:, mesh.trace_index(a, 0)]
+        xs = 0.5 * (xm + xp)
+        lift(m, a, 1, xs, xm)
+        lift(p, a, 0, xs, xp)
+    if scale_wall is not None:
+        for (e, a, s) in bnd:
+            xo = X[:, a, e][:, mesh.trace_index(a, s)]
+            lift(e, a, s, 0.0 * xo, xo)
+    for (ec, a, s, fines) in mort:
+        tang = [t for t in range(d) if t != a]
+        xc = X[:, a, ec][:, mesh.trace_index(a, s)]
+        acc = np.zeros_like(xc)
+        for f in fines:
+            cf = mesh.forest.leaves[f][1]
+            xproj = xc
+            for t_i, t in enumerate(tang):
+                xproj = mesh.apply_face_1d(B.P[cf[t] & 1], xproj, t_i)
+            xf = X[:, a, f][:, mesh.trace_index(a, 1 - s)]
+            xs = 0.5 * (xproj + xf)
+            lift(f, a, 1 - s, xs, xf)
+            back = xs
+            for t_i, t in enumerate(tang):
+                back = mesh.apply_face_1d(B.C[cf[t] & 1], back, t_i)
+            acc = acc + back
+        lift(ec, a, s, acc, xc)
+
+
+def viscous_rhs(mesh, q, nu):
+    """Viscous tendency nabla . (nu rho nabla phi) on momentum and Theta' by BR1 (Bassi & Rebay
+    1997): pass 1 the DG gradient sigma of phi with central face values, pass 2 the strong-form
+    divergence of G = nu rho sigma with central fluxes; no viscous flux through walls.  The paper
+    names an artificial viscosity mu (Sec. 4.3) without its operator; this is the reading used."""
+    d = mesh.d
+    conf, mort, bnd = mesh.forest.face_lists()
+    phi, rho = viscous_primitives(mesh, q)
+    # pass 1: sigma[c, a] = d phi_c / d x_a
+    sigma = np.empty((d + 1, d) + q.shape[1:], dtype=q.dtype)
+    for a in range(d):
+        sigma[:, a] = (2.0 / mesh.h[:, a])[None, :, None] * mesh.apply_1d(mesh.basis.D, phi, a)
+    X = np.broadcast_to(phi[:, None], sigma.shape).copy()
+    _central_face_pass(mesh, X, conf, mort, bnd, sigma, None)
+    # pass 2: V_c = sum_a d/dx_a (nu rho sigma[c, a])
+    G = nu * rho[None, None] * sigma
+    div = np.zeros_like(G)
+    for a in range(d):
+        div[:, a] = (2.0 / mesh.h[:, a])[None, :, None] * mesh.apply_1d(mesh.basis.D, G[:, a], a)
+    _central_face_pass(mesh, G, conf, mort, bnd, div, 0.0)
+    V = np.zeros_like(q)
+    V[1:2 + d] = div.sum(axis=1)
+    return V
+
+
 def ssprk3_step(q, dt, L):
     """One SSP-RK3 step (Shu-Osher form) of dq/dt = L(q)."""
     q1 = q + dt * L(q)
@@ -240,9 +321,10 @@ def ssprk3_step(q, dt, L):
     return (1.0 / 3.0) * q + (2.0 / 3.0) * (q2 + dt * L(q2))
 
 
-def step(mesh, q, dt, nsteps=1):
+def step(mesh, q, dt, nsteps=1, nu=0.0):
+    L = (lambda s: rhs(mesh, s)) if nu == 0.0 else (lambda s: rhs(mesh, s) + viscous_rhs(mesh, s, nu))
     for _ in range(nsteps):
-        q = ssprk3_step(q, dt, lambda s: rhs(mesh, s))
+        q = ssprk3_step(q, dt, L)
     return q
 
 
