@@ -63,7 +63,9 @@ typedef struct {
   int32_t precision;    /* DG_FP64 or DG_FP32_PERT (FP32 state and flux arithmetic; FP64 for
                            the background, the pressure perturbation and the integrals) */
   double theta0, p0, g, R, cp;
-  double nu;            /* artificial viscosity (m^2/s); only 0 is supported */
+  double nu;            /* artificial viscosity (m^2/s), >= 0.  nu > 0 adds the BR1 term
+                           div(nu rho grad phi), phi = (u, theta'), to momentum and Theta'
+                           (FP64 meshes only; not in the adjoint or in batches) */
 } dg_mesh_desc;
 
 /* Cosine-bell potential-temperature bubble (Sec. 4.2 Eq. cosine-bell, Sec. 4.3):

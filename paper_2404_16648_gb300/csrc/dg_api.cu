@@ -118,6 +118,8 @@ dg_status rebuild_topology(dg_mesh* m) {
   dfree(m->d_bgf); dfree(m->d_ppscratch);
   m->d_elem = nullptr; m->d_conn = nullptr; m->d_groups = nullptr; m->d_bg = nullptr; m->d_mbuf = nullptr;
   m->d_bgf = nullptr; m->d_ppscratch = nullptr;
+  dfree(m->d_sigma); dfree(m->d_V); dfree(m->d_vbuf);
+  m->d_sigma = nullptr; m->d_V = nullptr; m->d_vbuf = nullptr;
   CU(cudaMalloc(&m->d_elem, elem.size() * sizeof(int32_t)));
   CU(cudaMemcpy(m->d_elem, elem.data(), elem.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CU(cudaMalloc(&m->d_conn, conn.size() * sizeof(int32_t)));
@@ -130,6 +132,12 @@ dg_status rebuild_topology(dg_mesh* m) {
   CU(cudaMalloc(&m->d_bg, (size_t)m->E * m->n1 * 4 * sizeof(double)));
   if (m->prec == DG_FP32_PERT) CU(cudaMalloc(&m->d_bgf, (size_t)m->E * m->n1 * 4 * sizeof(float)));
   CU(cudaMalloc(&m->d_ppscratch, (size_t)(m->E > 0 ? plane(m) : 1) * m->tsize));
+  if (m->desc.nu > 0.0) {
+    const size_t pl = (size_t)(plane(m) > 0 ? plane(m) : 1);
+    CU(cudaMalloc(&m->d_sigma, (size_t)(m->D + 1) * m->D * pl * sizeof(double)));
+    CU(cudaMalloc(&m->d_V, (size_t)(m->D + 1) * pl * sizeof(double)));
+    if (m->G > 0) CU(cudaMalloc(&m->d_vbuf, (size_t)m->G * (1 + m->NSUB) * (m->D + 1) * m->NF * sizeof(double)));
+  }
   CU(dgk::launch_background((int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), m->root_h[m->D - 1],
                             m->ph, m->d_bg, m->d_bgf, m->stream));
   m->pp_valid = false;
@@ -231,6 +239,24 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
     CU(cudaEventRecord(m->ev[m->ev_used + 1], s));
     m->ev_used += 2;
   }
+  if (m->desc.nu > 0.0) {
+    // BR1 viscous tendency of the stage input, added as cb dt V (the stage combination is linear
+    // in the tendency); P' of the output is refreshed after the Theta' update
+    dgk::ViscArgs V{};
+    V.q = (const double*)qs; V.sigma = m->d_sigma; V.V = m->d_V; V.vbuf = m->d_vbuf;
+    V.plane = plane(m); V.E = (int32_t)m->E; V.G = (int32_t)m->G; V.elem = m->d_elem;
+    V.conn = m->d_conn; V.groups = m->d_groups; V.bg = m->d_bg; V.ops = m->d_opsd;
+    for (int l = 0; l < dgk::kMaxLevels; ++l)
+      for (int a = 0; a < 3; ++a) V.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+    V.nu = m->desc.nu; V.theta0 = m->ph.theta0;
+    for (int pass = 1; pass <= 2; ++pass) {
+      if (!dgk::launch_viscous_pass(m->D, m->N, V, pass, s))
+        return fail(m, DG_ERR_UNSUPPORTED, "viscous kernels for N=%d not compiled", m->N);
+      CU(cudaGetLastError());
+    }
+    CU(dgk::launch_visc_add((int32_t)m->E, m->n1, m->D, m->d_V, mode == 1 ? cb * dt : 1.0, (double*)out,
+                            plane(m), m->d_bg, m->ph, mode == 1 ? (double*)pp_out : nullptr, s));
+  }
   return DG_OK;
 }
 
@@ -320,6 +346,7 @@ extern "C" {
 dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void* stream) {
   if (!m || !q || !lam || !out) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
+  if (m->desc.nu > 0.0) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint has no viscous term");
   dg_status st = ensure_adjoint_ws(m);
   if (st != DG_OK) return st;
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
@@ -345,6 +372,7 @@ dg_status dg_step_vjp(dg_mesh* m, const void* q_in, double dt, const void* lam_o
   if (!m || !q_in || !lam_out || !lam_in || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (lam_out == lam_in) return fail(m, DG_ERR_ARG, "lam_out and lam_in must not alias");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
+  if (m->desc.nu > 0.0) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint has no viscous term");
   dg_status st = ensure_adjoint_ws(m);
   if (st != DG_OK) return st;
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
@@ -429,7 +457,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   if (desc->N < 1 || desc->N > DG_MAX_N) return DG_ERR_ARG;
   if (desc->max_level < 0 || desc->max_level > DG_MAX_LEVEL) return DG_ERR_ARG;
   if (desc->precision != DG_FP64 && desc->precision != DG_FP32_PERT) return DG_ERR_ARG;
-  if (desc->nu != 0.0) return DG_ERR_UNSUPPORTED;
+  if (!(desc->nu >= 0.0)) return DG_ERR_ARG;
+  if (desc->nu > 0.0 && desc->precision != DG_FP64) return DG_ERR_UNSUPPORTED;   // viscous: FP64
   for (int a = 0; a < desc->dim; ++a) {
     if (desc->base[a] < 1 || !(desc->length[a] > 0.0)) return DG_ERR_ARG;
     if (((int64_t)desc->base[a] << desc->max_level) >= (1 << 19)) return DG_ERR_ARG;
@@ -486,6 +515,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   for (int i = 0; i < 3; ++i) dfree(m->q[i]);
   dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
   dfree(m->d_bgf); dfree(m->d_ppscratch);
+  dfree(m->d_sigma); dfree(m->d_V); dfree(m->d_vbuf);
   dfree(m->d_ops); dfree(m->d_opsd); dfree(m->d_partial); dfree(m->d_out); dfree(m->d_bad);
   for (int i = 0; i < 3; ++i) dfree(m->adj_q[i]);
   for (int i = 0; i < 2; ++i) dfree(m->adj_l[i]);

@@ -5,6 +5,7 @@
 
 #include "dg_adjoint.cuh"
 #include "dg_device.cuh"
+#include "dg_viscous.cuh"
 
 namespace dgk {
 
@@ -53,6 +54,12 @@ cudaError_t launch_integrals(int prec, int32_t E, int n1, int D, const int32_t* 
 cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, const int32_t* tmap,
                             const double* ops, const void* qold, int64_t plane_old, void* qnew,
                             int64_t plane_new, cudaStream_t s);
+
+// BR1 viscous term (FP64): pass 1 writes sigma, pass 2 writes V (mortar values included).
+bool launch_viscous_pass(int D, int N, const ViscArgs& A, int pass, cudaStream_t s);
+cudaError_t launch_visc_add(int32_t E, int n1, int D, const double* V, double coef, double* out,
+                            int64_t plane, const double* bg, const PhysC& ph, double* pp,
+                            cudaStream_t s);
 
 // Adjoint (FP64): right-hand-side vector-Jacobian products and their helpers.
 bool launch_vjp(int D, int N, const AdjArgs& A, cudaStream_t s);

@@ -39,6 +39,10 @@ struct dg_mesh {
   double* adj_l[2] = {nullptr, nullptr};          // cotangents
   double* d_abuf = nullptr;                       // mortar adjoint contributions
   int64_t adj_E = -1, adj_G = -1;
+  // viscous term (nu > 0, FP64): gradients, tendency, mortar values
+  double* d_sigma = nullptr;
+  double* d_V = nullptr;
+  double* d_vbuf = nullptr;
   void* d_ops = nullptr;       // precision T
   double* d_opsd = nullptr;    // FP64: D, P0, P1, C0, C1, w, x
   double* d_partial = nullptr;
