@@ -92,12 +92,13 @@ def _dist():
     return world, rank, local
 
 
-def _barrier_max(t, world):
+def _barrier_max(t, world, device="cuda"):
+    """Maximum over ranks of a time (the slowest rank defines the job time)."""
     if world == 1:
         return t
     import torch
     import torch.distributed as dist
-    x = torch.tensor([t], dtype=torch.float64, device="cuda")
+    x = torch.tensor([t], dtype=torch.float64, device=device)
     dist.all_reduce(x, op=dist.ReduceOp.MAX)
     return float(x.item())
 

@@ -283,6 +283,16 @@ dg_status dg_forest_faces(const dg_forest* forest, int64_t counts[3], int32_t* c
 dg_status dg_forest_regrid(dg_forest* forest, const uint8_t* flags, int32_t buffer,
                            int32_t max_level, int32_t* transfer, size_t cap, int64_t* new_size);
 
+/* Space-filling-curve partition of the leaf order into nparts contiguous ranges (element counts
+ * differing by at most one): starts[p] .. starts[p+1]-1 belong to part p; starts holds
+ * nparts + 1 entries.  Sec. 3.1 names SFC partitioning as the scalable alternative to METIS. */
+dg_status dg_forest_partition(const dg_forest* forest, int32_t nparts, int64_t* starts);
+/* Faces of part `part` (of the partition above) whose other side lies in another part, as rows
+ * of 5 int32: local element, axis, side, remote element, remote part; a coarse face gives one row
+ * per fine neighbour.  *count receives the row count; rows (capacity `cap` rows) may be NULL. */
+dg_status dg_forest_halo(const dg_forest* forest, int32_t nparts, int32_t part, int32_t* rows,
+                         size_t cap, int64_t* count);
+
 /* Detail of the last error on this mesh (never NULL). */
 const char* dg_last_error(const dg_mesh* mesh);
 

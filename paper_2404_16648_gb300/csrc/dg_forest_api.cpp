@@ -80,4 +80,24 @@ dg_status dg_forest_regrid(dg_forest* forest, const uint8_t* flags, int32_t buff
   return DG_OK;
 }
 
+dg_status dg_forest_partition(const dg_forest* forest, int32_t nparts, int64_t* starts) {
+  if (!forest || !starts || nparts < 1) return DG_ERR_ARG;
+  std::vector<int64_t> st;
+  forest->f.partition(nparts, &st);
+  for (int p = 0; p <= nparts; ++p) starts[p] = st[p];
+  return DG_OK;
+}
+
+dg_status dg_forest_halo(const dg_forest* forest, int32_t nparts, int32_t part, int32_t* rows,
+                         size_t cap, int64_t* count) {
+  if (!forest || !count || nparts < 1 || part < 0 || part >= nparts) return DG_ERR_ARG;
+  std::vector<int64_t> st;
+  forest->f.partition(nparts, &st);
+  std::vector<int32_t> r;
+  forest->f.halo(st, part, &r);
+  *count = (int64_t)r.size() / 5;
+  if (rows && cap >= r.size() / 5) std::memcpy(rows, r.data(), r.size() * sizeof(int32_t));
+  return DG_OK;
+}
+
 }  // extern "C"

@@ -206,6 +206,35 @@ void Forest::face_lists(std::vector<int32_t>* conf, std::vector<int32_t>* mort,
   }
 }
 
+void Forest::partition(int nparts, std::vector<int64_t>* starts) const {
+  starts->assign(nparts + 1, 0);
+  for (int p = 0; p <= nparts; ++p) (*starts)[p] = (size() * p) / nparts;
+}
+
+void Forest::halo(const std::vector<int64_t>& starts, int part, std::vector<int32_t>* rows) const {
+  rows->clear();
+  const int nparts = (int)starts.size() - 1;
+  auto owner = [&](int64_t e) {
+    int p = (int)(std::upper_bound(starts.begin(), starts.end(), e) - starts.begin()) - 1;
+    return std::min(std::max(p, 0), nparts - 1);
+  };
+  for (int64_t e = starts[part]; e < starts[part + 1]; ++e)
+    for (int a = 0; a < dim_; ++a)
+      for (int s = 0; s < 2; ++s) {
+        FaceInfo fi = classify((int32_t)e, a, s);
+        int cnt = 0;
+        if (fi.kind == FACE_CONF || fi.kind == FACE_FINE) cnt = 1;
+        else if (fi.kind == FACE_COARSE) cnt = 1 << (dim_ - 1);
+        for (int k = 0; k < cnt; ++k) {
+          const int32_t nb = fi.nb[k];
+          const int op = owner(nb);
+          if (op == part) continue;
+          rows->push_back((int32_t)e); rows->push_back(a); rows->push_back(s);
+          rows->push_back(nb); rows->push_back(op);
+        }
+      }
+}
+
 void Forest::connectivity(const std::vector<int32_t>& mort, std::vector<int32_t>* conn) const {
   // Rows {kind, a, b, c, d} per element face f = 2*axis + side:
   //   WALL {0}; CONF {1, neighbour}; FINE {2, coarse element, mortar group, sub-face};

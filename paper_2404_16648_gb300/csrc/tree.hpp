@@ -63,6 +63,15 @@ class Forest {
   void face_lists(std::vector<int32_t>* conf, std::vector<int32_t>* mort,
                   std::vector<int32_t>* bnd) const;
 
+  // Space-filling-curve partition: nparts contiguous ranges of the leaf (Morton) order with
+  // element counts that differ by at most one; starts has nparts + 1 entries.
+  void partition(int nparts, std::vector<int64_t>* starts) const;
+  // Faces of part `part` whose other side belongs to another part, as rows
+  // {local element, axis, side, remote element, remote part}; one row per neighbour element
+  // (a coarse face lists each fine neighbour).  These are the traces a rank would receive
+  // before each right-hand-side evaluation.
+  void halo(const std::vector<int64_t>& starts, int part, std::vector<int32_t>* rows) const;
+
   // Per element, per face f = 2*axis + side, 5 int32 (see tree.cpp); `mort` from face_lists.
   void connectivity(const std::vector<int32_t>& mort, std::vector<int32_t>* conn) const;
 

@@ -27,7 +27,7 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
             "dg_step_state", "dg_step_vjp", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
-            "dg_bubble_theta", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
+            "dg_bubble_theta", "dg_forest_partition", "dg_forest_halo", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
             "dg_batch_run", "dg_batch_sync", "dg_batch_autotune", "dg_batch_last_error",
             "dg_last_error", "dg_version"]
 
@@ -110,6 +110,8 @@ def load_library(path=None):
         "dg_theta_vjp": (i32, [vp, vp, vp, vp, vp]),
         "dg_ke_grad": (i32, [vp, vp, vp, vp]),
         "dg_bubble_theta": (i32, [vp, ctypes.POINTER(BubbleDesc), vp]),
+        "dg_forest_partition": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int64)]),
+        "dg_forest_halo": (i32, [vp, i32, i32, vp, sz, ctypes.POINTER(ctypes.c_int64)]),
         "dg_batch_create": (i32, [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]),
         "dg_batch_destroy": (None, [vp]),
         "dg_batch_set_dt": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
@@ -433,6 +435,22 @@ class Forest:
         if st != DG_OK:
             raise DGError(st, "dg_forest_regrid failed")
         return tr[:9 * n.value].reshape(n.value, 9)
+
+    def partition(self, nparts):
+        starts = np.zeros(nparts + 1, dtype=np.int64)
+        st = self.lib.dg_forest_partition(self.h, nparts, starts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+        if st != DG_OK:
+            raise DGError(st, "dg_forest_partition failed")
+        return starts
+
+    def halo(self, nparts, part):
+        n = ctypes.c_int64()
+        self.lib.dg_forest_halo(self.h, nparts, part, None, 0, ctypes.byref(n))
+        rows = np.zeros((n.value, 5), dtype=np.int32)
+        st = self.lib.dg_forest_halo(self.h, nparts, part, rows.ctypes.data, n.value, ctypes.byref(n))
+        if st != DG_OK:
+            raise DGError(st, "dg_forest_halo failed")
+        return rows
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
