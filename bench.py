@@ -158,6 +158,62 @@ def stage_flops(E, NP, NV, n1, D):
     return 3 * E * NP * per_node
 
 
+def paired_meshes(pkg, cfg):
+    """An FP64 and an FP32-perturbation mesh of the workload with identical trees: the initial
+    adaptation is driven by the FP64 mesh's theta' indicator and applied to both as flags."""
+    import numpy as np
+    ms = [pkg.Mesh(cfg["dim"], cfg["N"], cfg["base"], cfg["length"], max_level=cfg["max_level"],
+                   precision=p) for p in ("fp64", "fp32")]
+    for _ in range(cfg["max_level"]):
+        ms[0].set_bubble(**cfg["bubble"])
+        flags = (ms[0].indicator() > cfg["threshold"]).astype(np.uint8)
+        for m in ms:
+            m.adapt(flags=flags, buffer=cfg["buffer"])
+    for m in ms:
+        m.set_bubble(**cfg["bubble"])
+    return ms
+
+
+def fp32_accuracy(pkg, cfg, steps):
+    """FP32-perturbation path against the FP64 path after `steps` SSP-RK3 steps of the workload,
+    regridding both every `regrid_every` steps with the FP64 mesh's flags so that the trees stay
+    identical.  Returns max |theta' error| (K), max |w error| (m/s), the relative differences of
+    total mass and energy, and each path's relative mass change over the run."""
+    import numpy as np
+    import torch
+    m64, m32 = paired_meshes(pkg, cfg)
+    I0 = [m.integrals() for m in (m64, m32)]
+    every = cfg.get("regrid_every") or steps
+    done = 0
+    while done < steps:
+        k = min(every, steps - done)
+        for m in (m64, m32):
+            m.step(cfg["dt"], k)
+        done += k
+        if cfg.get("regrid_every") and done < steps:
+            flags = (m64.indicator() > cfg["threshold"]).astype(np.uint8)
+            for m in (m64, m32):
+                m.adapt(flags=flags, buffer=cfg["buffer"])
+    assert np.array_equal(m64.leaves(), m32.leaves())
+    p64, p32 = m64.primitives(), m32.primitives()
+    D = cfg["dim"]
+    I1 = [m.integrals() for m in (m64, m32)]
+    out = {"steps": steps, "elements": m64.num_elements,
+           "theta_max_abs_err_K": float((p32[D] - p64[D]).abs().max()),
+           "theta_max_abs_K": float(p64[D].abs().max()),
+           "w_max_abs_err": float((p32[D - 1] - p64[D - 1]).abs().max()),
+           "w_max_abs": float(p64[D - 1].abs().max()),
+           "mass_rel_err": abs(I1[1][0] - I1[0][0]) / I1[0][0],
+           "energy_rel_err": abs(I1[1][1] - I1[0][1]) / abs(I1[0][1]),
+           "mass_drift_fp64": abs(I1[0][0] - I0[0][0]) / I0[0][0],
+           "mass_drift_fp32": abs(I1[1][0] - I0[1][0]) / I0[1][0],
+           "reference": "FP64 path on the same trees (matches the oracle to 1e-12 per RHS)"}
+    for m in (m64, m32):
+        m.close()
+    torch.cuda.synchronize()
+    return out
+
+
 def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, world=1):
     import torch
     m = build_mesh(pkg, cfg, precision)
@@ -360,6 +416,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the FP32-vs-FP64 field comparison over the workload's full step count")
     ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2],
                     help="stage kernel layout: 0 column, 1 node-per-thread, 2 column with "
                          "asynchronous staging (default: the library's)")
@@ -436,6 +494,8 @@ def main():
                                      "peak_kind": "derived: 152 SMs x max SM clock x 4 FP64 flop/clk"},
                         "integrals": r64["integrals"]}
         line["fp32_over_fp64"] = value / v64
+    if not args.no_accuracy and cfg.get("threshold") is not None:
+        line["fp32_accuracy"] = fp32_accuracy(pkg, cfg, cfg["steps"])
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(pkg)
     if not args.no_batch:

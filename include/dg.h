@@ -159,6 +159,14 @@ dg_status dg_adapt(dg_mesh* mesh, const dg_adapt_params* params, dg_adapt_report
 /* Per-element refinement indicator max_n |theta'| (FP64), written to host `out` (E doubles). */
 dg_status dg_indicator(dg_mesh* mesh, double* out, size_t cap);
 
+/* Primitive diagnostics of the current state in FP64 (the fields reported in Sec. 4.3): device
+ * `out` receives dim + 1 planes of E * (N+1)^dim doubles in the state's [element][node] order,
+ * planes 0 .. dim-1 the velocity components U_a / rho, plane dim the potential temperature
+ * perturbation theta' = (Theta_bar + Theta') / (rho_bar + rho') - theta0.  `cap` counts doubles;
+ * DG_ERR_ARG if it is too small.  The caller owns `out`; asynchronous on `stream` (NULL: the
+ * mesh's stream). */
+dg_status dg_primitives(dg_mesh* mesh, double* out, size_t cap, void* stream);
+
 /* Domain integrals with weights w_i w_j (w_k) |J|, accumulated in FP64 with compensated
  * (Neumaier) sums and a fixed reduction order: out = {mass, total energy
  * (p cv/R + |U|^2/(2 rho) + rho g z), kinetic energy, volume, perturbation mass int rho'}.

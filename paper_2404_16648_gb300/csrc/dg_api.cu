@@ -647,6 +647,17 @@ dg_status dg_indicator(dg_mesh* m, double* out, size_t cap) {
   return DG_OK;
 }
 
+dg_status dg_primitives(dg_mesh* m, double* out, size_t cap, void* stream) {
+  if (!m || (!out && m->E > 0)) return fail(m, DG_ERR_ARG, "bad argument");
+  const size_t need = (size_t)(m->D + 1) * (size_t)m->E * (size_t)m->NP;
+  if (cap < need) return fail(m, DG_ERR_ARG, "output holds %zu doubles, %zu needed", cap, need);
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  cudaError_t e = dgk::launch_primitives(m->prec, (int32_t)m->E, m->n1, m->D, m->d_bg, m->q[0], plane(m),
+                                         m->ph.theta0, out, s);
+  if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "primitives failed: %s", cudaGetErrorString(e));
+  return DG_OK;
+}
+
 dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   if (!m || !p) return fail(m, DG_ERR_ARG, "bad argument");
   if (p->buffer < 0) return fail(m, DG_ERR_ARG, "buffer must be >= 0");

@@ -46,6 +46,8 @@ cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* ele
                           cudaStream_t s);
 cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
                              int64_t plane, double theta0, double* out, cudaStream_t s);
+cudaError_t launch_primitives(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
+                              int64_t plane, double theta0, double* out, cudaStream_t s);
 size_t integrals_scratch_doubles();
 cudaError_t launch_integrals(int prec, int32_t E, int n1, int D, const int32_t* elem,
                              const double* xi, const double* w, const double* root_h,

@@ -102,6 +102,24 @@ __global__ void indicator_kernel(int32_t E, int n1, int D, const double* bg, con
   if (threadIdx.x == 0) out[e] = red[0];
 }
 
+// Primitive diagnostics per node in FP64: out[a] = U_a / rho (a < D), out[D] = theta'
+// = (Theta_bar + Theta') / (rho_bar + rho') - theta0; planes of length E * NP.
+template <class T>
+__global__ void primitives_kernel(int32_t E, int n1, int D, const double* bg, const T* q,
+                                  int64_t plane, double theta0, double* out) {
+  const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
+  const int64_t total = (int64_t)E * NP;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int64_t e = i / NP;
+  const int n = (int)(i - e * NP);
+  const int k = D == 3 ? n / (n1 * n1) : n / n1;
+  const double* b = bg + (e * n1 + k) * 4;
+  const double rho = b[0] + (double)q[i];
+  for (int a = 0; a < D; ++a) out[a * total + i] = (double)q[(int64_t)(1 + a) * plane + i] / rho;
+  out[D * total + i] = (b[1] + (double)q[(int64_t)(D + 1) * plane + i]) / rho - theta0;
+}
+
 // Neumaier-compensated accumulator.
 struct Comp {
   double s, c;
@@ -301,6 +319,17 @@ cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* b
   if (E == 0) return cudaSuccess;
   if (prec == 0) indicator_kernel<double><<<E, 256, 0, s>>>(E, n1, D, bg, (const double*)q, plane, theta0, out);
   else indicator_kernel<float><<<E, 256, 0, s>>>(E, n1, D, bg, (const float*)q, plane, theta0, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_primitives(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
+                              int64_t plane, double theta0, double* out, cudaStream_t s) {
+  const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
+  const int64_t total = (int64_t)E * NP;
+  if (total == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  if (prec == 0) primitives_kernel<double><<<grid, 256, 0, s>>>(E, n1, D, bg, (const double*)q, plane, theta0, out);
+  else primitives_kernel<float><<<grid, 256, 0, s>>>(E, n1, D, bg, (const float*)q, plane, theta0, out);
   return cudaGetLastError();
 }
 

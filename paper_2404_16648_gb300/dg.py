@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 
 # every symbol include/dg.h declares
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_nodes", "dg_get_leaves",
             "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_bubble", "dg_rhs", "dg_step",
-            "dg_adapt", "dg_indicator", "dg_integrals", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
+            "dg_adapt", "dg_indicator", "dg_primitives", "dg_integrals", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
             "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
             "dg_step_state", "dg_step_vjp", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
@@ -91,6 +91,7 @@ def load_library(path=None):
         "dg_step": (i32, [vp, dbl, i32, vp]),
         "dg_adapt": (i32, [vp, ctypes.POINTER(AdaptParams), ctypes.POINTER(AdaptReport)]),
         "dg_indicator": (i32, [vp, ctypes.POINTER(ctypes.c_double), sz]),
+        "dg_primitives": (i32, [vp, vp, sz, vp]),
         "dg_integrals": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
         "dg_set_option": (i32, [vp, i32, i64]),
         "dg_enable_timing": (i32, [vp, i32]),
@@ -364,6 +365,18 @@ class Mesh:
     def indicator(self):
         out = np.zeros(self.num_elements)
         self._check(self.lib.dg_indicator(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size))
+        return out
+
+    def primitives(self, out=None, stream=None):
+        """FP64 device tensor [dim + 1, E, NP]: velocity components, then theta'."""
+        import torch
+        shape = (self.dim + 1, self.num_elements, (self.N + 1) ** self.dim)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() < shape[0] * shape[1] * shape[2]:
+            raise ValueError("out must be a contiguous FP64 tensor of shape %s" % (shape,))
+        self._check(self.lib.dg_primitives(self.h, ctypes.c_void_p(out.data_ptr()), out.numel(),
+                                           self._stream_ptr(stream)))
         return out
 
     def integrals(self, check=True):
