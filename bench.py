@@ -56,10 +56,15 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + CLOCK_QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        # the timed region starts only once nvidia-smi has produced its first sample
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -130,7 +135,7 @@ def measured_traffic(D, N, precision, layout):
         rec = json.load(open(path))
     except OSError:
         return None
-    if (D, N, precision, layout) != (3, 7, "fp32", 2):
+    if (D, N, precision, layout) != (3, 7, "fp32", rec.get("layout", 2)):
         return None
     h = hashlib.sha1()
     for f in rec["sources"]:
@@ -237,7 +242,8 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
     alg_bytes = 0
     alg_flops = 0
     launches = 0
-    per_node = measured_traffic(D, N, precision, 2 if STAGE_KERNEL in (None, 2) else STAGE_KERNEL)
+    default_layout = 3 if (precision == "fp32" and D == 3) else 2
+    per_node = measured_traffic(D, N, precision, default_layout if STAGE_KERNEL is None else STAGE_KERNEL)
     traffic = 0.0
     ev0.record()
     for i in range(steps):
@@ -408,7 +414,7 @@ def oracle_sample(cfg, n_elem=1024, reps=1, warmup=0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=workloads.BUBBLE_3D["name"])
@@ -418,9 +424,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP32-vs-FP64 field comparison over the workload's full step count")
-    ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2],
+    ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2, 3],
                     help="stage kernel layout: 0 column, 1 node-per-thread, 2 column with "
-                         "asynchronous staging (default: the library's)")
+                         "asynchronous staging, 3 as 2 with two threads per column "
+                         "(default: the library's)")
     args = ap.parse_args()
     global STAGE_KERNEL
     STAGE_KERNEL = args.stage_kernel
@@ -471,7 +478,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config,
             "precision_path": "FP32 state/flux arithmetic; FP64 background, p' and integrals",
-            "stage_kernel": {None: "default", 0: "column", 1: "node", 2: "column-async"}[STAGE_KERNEL],
+            "stage_kernel": {None: "default", 0: "column", 1: "node", 2: "column-async", 3: "half-column-async"}[STAGE_KERNEL],
             "elements": r32["elements"], "nodes_per_variable": r32["nodes"],
             "gpu_launches": r32["launches"], "mortar_groups": r32["mortars"],
             "roofline": {"bound": "hbm", "kernel": "stage_kernel", "achieved": achieved,

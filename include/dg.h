@@ -170,6 +170,8 @@ dg_status dg_primitives(dg_mesh* mesh, double* out, size_t cap, void* stream);
 /* Domain integrals with weights w_i w_j (w_k) |J|, accumulated in FP64 with compensated
  * (Neumaier) sums and a fixed reduction order: out = {mass, total energy
  * (p cv/R + |U|^2/(2 rho) + rho g z), kinetic energy, volume, perturbation mass int rho'}.
+ * The background parts (int rho_bar, int (p_bar cv/R + rho_bar g z), volume) are summed once
+ * per mesh topology and added to the state parts with their rounding errors.
  * Synchronous; DG_ERR_STATE if a non-finite value was met (out is still written). */
 dg_status dg_integrals(dg_mesh* mesh, double out[DG_NUM_INTEGRALS]);
 
@@ -233,8 +235,10 @@ const char* dg_batch_last_error(const dg_batch* batch);
 
 /* Tuning options.  DG_OPT_STAGE_KERNEL selects the fused stage kernel's thread layout:
  * 0 = one thread per vertical node column, 1 = one thread per node, 2 = one thread per column
- * with all operands staged into shared memory by asynchronous copies (default).  All compute
- * the same operator; the option exists for tuning and cross-checking. */
+ * with all operands staged into shared memory by asynchronous copies, 3 = as 2 with two
+ * threads per column (3D with odd N; other shapes run layout 2).  Default: 3 for FP32 3D
+ * meshes, 2 otherwise.  All compute the same operator; the option exists for tuning and
+ * cross-checking. */
 enum { DG_OPT_STAGE_KERNEL = 1 };
 dg_status dg_set_option(dg_mesh* mesh, int32_t option, int64_t value);
 

@@ -115,9 +115,9 @@ dg_status rebuild_topology(dg_mesh* m) {
     for (int a = 0; a < 3; ++a) elem[e * 4 + 1 + a] = L[e].c[a];
   }
   dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
-  dfree(m->d_bgf); dfree(m->d_ppscratch);
+  dfree(m->d_bgf); dfree(m->d_bgc); dfree(m->d_ppscratch);
   m->d_elem = nullptr; m->d_conn = nullptr; m->d_groups = nullptr; m->d_bg = nullptr; m->d_mbuf = nullptr;
-  m->d_bgf = nullptr; m->d_ppscratch = nullptr;
+  m->d_bgf = nullptr; m->d_bgc = nullptr; m->d_ppscratch = nullptr;
   dfree(m->d_sigma); dfree(m->d_V); dfree(m->d_vbuf);
   m->d_sigma = nullptr; m->d_V = nullptr; m->d_vbuf = nullptr;
   CU(cudaMalloc(&m->d_elem, elem.size() * sizeof(int32_t)));
@@ -130,7 +130,10 @@ dg_status rebuild_topology(dg_mesh* m) {
     CU(cudaMalloc(&m->d_mbuf, (size_t)m->G * (1 + m->NSUB) * m->NV * m->NF * m->tsize));
   }
   CU(cudaMalloc(&m->d_bg, (size_t)m->E * m->n1 * 4 * sizeof(double)));
-  if (m->prec == DG_FP32_PERT) CU(cudaMalloc(&m->d_bgf, (size_t)m->E * m->n1 * 4 * sizeof(float)));
+  if (m->prec == DG_FP32_PERT) {
+    CU(cudaMalloc(&m->d_bgf, (size_t)m->E * m->n1 * 4 * sizeof(float)));
+    CU(cudaMalloc(&m->d_bgc, (size_t)m->E * m->n1 * sizeof(double)));
+  }
   CU(cudaMalloc(&m->d_ppscratch, (size_t)(m->E > 0 ? plane(m) : 1) * m->tsize));
   if (m->desc.nu > 0.0) {
     const size_t pl = (size_t)(plane(m) > 0 ? plane(m) : 1);
@@ -139,8 +142,9 @@ dg_status rebuild_topology(dg_mesh* m) {
     if (m->G > 0) CU(cudaMalloc(&m->d_vbuf, (size_t)m->G * (1 + m->NSUB) * (m->D + 1) * m->NF * sizeof(double)));
   }
   CU(dgk::launch_background((int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), m->root_h[m->D - 1],
-                            m->ph, m->d_bg, m->d_bgf, m->stream));
+                            m->ph, m->d_bg, m->d_bgf, m->d_bgc, m->stream));
   m->pp_valid = false;
+  m->bgint_valid = false;
   return DG_OK;
 }
 
@@ -170,7 +174,7 @@ void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const 
                      void* pp_out, int mode, double dt, double ca, double cb, dgk::StageArgs* A) {
   A->qs = qs; A->pp_in = pp_in; A->qn = qn; A->out = out; A->pp_out = pp_out; A->mbuf = m->d_mbuf;
   A->plane = plane(m); A->E = (int32_t)m->E;
-  A->elem = m->d_elem; A->conn = m->d_conn; A->bg = m->d_bg; A->bgt = bgt(m); A->ops = m->d_ops;
+  A->elem = m->d_elem; A->conn = m->d_conn; A->bg = m->d_bg; A->bgt = bgt(m); A->bgc = m->d_bgc; A->ops = m->d_ops;
   for (int l = 0; l < dgk::kMaxLevels; ++l)
     for (int a = 0; a < 3; ++a) {
       // 2/h = (2/h_root) 2^level: power-of-two scaling is exact
@@ -190,7 +194,7 @@ dg_status set_error(dg_mesh* m, dg_status st, const char* msg) {
 dg_status launch_mortars(dg_mesh* m, const void* qs, const void* pp_in, cudaStream_t s) {
   if (m->G == 0) return DG_OK;
   dgk::MortarArgs M{qs, pp_in, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, bgt(m),
-                    m->d_ops, (float)m->ph.gamma, m->ph};
+                    m->d_bgc, m->d_ops, (float)m->ph.gamma, m->ph};
   bool ok = m->prec == DG_FP64
                 ? (m->D == 2 ? dgk::launch_mortar_f64_2d(m->N, M, s) : dgk::launch_mortar_f64_3d(m->N, M, s))
                 : (m->D == 2 ? dgk::launch_mortar_f32_2d(m->N, M, s) : dgk::launch_mortar_f32_3d(m->N, M, s));
@@ -203,7 +207,7 @@ dg_status launch_mortars(dg_mesh* m, const void* qs, const void* pp_in, cudaStre
 dg_status ensure_pp(dg_mesh* m, cudaStream_t s) {
   if (m->pp_valid) return DG_OK;
   const void* theta = (const char*)m->q[0] + (size_t)(m->NV - 1) * plane(m) * m->tsize;
-  cudaError_t e = dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->ph,
+  cudaError_t e = dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->d_bgc, m->ph,
                                      pp_plane(m, m->q[0]), s);
   if (e != cudaSuccess) return set_error(m, DG_ERR_CUDA, cudaGetErrorString(e));
   m->pp_valid = true;
@@ -303,7 +307,7 @@ dg_status stage_in(dg_mesh* m, const void* q, void* buf, cudaStream_t s) {
   const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
   CU(cudaMemcpyAsync(buf, q, bytes, cudaMemcpyDeviceToDevice, s));
   const void* theta = (const char*)buf + (size_t)(m->NV - 1) * plane(m) * m->tsize;
-  CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->ph, pp_plane(m, buf), s));
+  CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->d_bgc, m->ph, pp_plane(m, buf), s));
   return DG_OK;
 }
 
@@ -438,7 +442,7 @@ dg_status dg_ke_grad(dg_mesh* m, const void* q, void* out, void* stream) {
 dg_status dg_set_option(dg_mesh* m, int32_t option, int64_t value) {
   if (!m) return DG_ERR_ARG;
   if (option == DG_OPT_STAGE_KERNEL) {
-    if (value < 0 || value > 2) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0, 1 or 2");
+    if (value < 0 || value > 3) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0, 1, 2 or 3");
     m->variant = (int)value;
     return DG_OK;
   }
@@ -474,6 +478,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   m->NV = m->D + 2; m->NSUB = 1 << (m->D - 1);
   m->prec = desc->precision;
   m->tsize = m->prec == DG_FP64 ? sizeof(double) : sizeof(float);
+  m->variant = (m->prec == DG_FP32_PERT && m->D == 3) ? 3 : 2;   // fastest measured layouts
   m->stream = (cudaStream_t)stream;
   m->ph.theta0 = desc->theta0; m->ph.p0 = desc->p0; m->ph.g = desc->g; m->ph.R = desc->R;
   m->ph.cp = desc->cp; m->ph.cv = desc->cp - desc->R; m->ph.gamma = desc->cp / (desc->cp - desc->R);
@@ -484,6 +489,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
       c = c * (m->ph.gamma - (k - 1)) / k;
       m->ph.binom[k - 1] = c;
     }
+    for (int k = 0; k < 3; ++k) m->ph.rel[k] = (float)(m->ph.binom[k + 1] / m->ph.gamma);
   }
   int base[3] = {desc->base[0], desc->base[1], desc->dim == 3 ? desc->base[2] : 1};
   for (int a = 0; a < 3; ++a) m->root_h[a] = a < m->D ? desc->length[a] / base[a] : 1.0;
@@ -514,7 +520,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   if (m->stream) cudaStreamSynchronize(m->stream); else cudaDeviceSynchronize();
   for (int i = 0; i < 3; ++i) dfree(m->q[i]);
   dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
-  dfree(m->d_bgf); dfree(m->d_ppscratch);
+  dfree(m->d_bgf); dfree(m->d_bgc); dfree(m->d_ppscratch);
   dfree(m->d_sigma); dfree(m->d_V); dfree(m->d_vbuf);
   dfree(m->d_ops); dfree(m->d_opsd); dfree(m->d_partial); dfree(m->d_out); dfree(m->d_bad);
   for (int i = 0; i < 3; ++i) dfree(m->adj_q[i]);
@@ -608,7 +614,7 @@ dg_status dg_rhs(dg_mesh* m, const void* q, void* dqdt, void* stream) {
   if (!m || !q || !dqdt) return fail(m, DG_ERR_ARG, "bad argument");
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
   const void* theta = (const char*)q + (size_t)(m->NV - 1) * plane(m) * m->tsize;
-  CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->ph, m->d_ppscratch, s));
+  CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->d_bgc, m->ph, m->d_ppscratch, s));
   return launch_rhs_pass(m, q, m->d_ppscratch, nullptr, dqdt, nullptr, 0, 0.0, 0.0, 1.0, s);
 }
 
@@ -715,15 +721,43 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   return DG_OK;
 }
 
+// a + b as an unevaluated pair: returns fl(a + b), *err the exact remainder (Knuth's TwoSum).
+static double two_sum(double a, double b, double* err) {
+  const double t = a + b;
+  const double bb = t - a;
+  *err = (a - (t - bb)) + (b - bb);
+  return t;
+}
+
+// The background sums (int rho_bar, int (p_bar cv/R + rho_bar g z), volume) depend on the mesh
+// alone and are taken once per topology; each call sums the parts that carry the state and
+// adds the two compensated results with their rounding errors.
 dg_status dg_integrals(dg_mesh* m, double out[DG_NUM_INTEGRALS]) {
   if (!m || !out) return fail(m, DG_ERR_ARG, "bad argument");
+  if (!m->bgint_valid) {
+    CU(dgk::launch_integrals(m->prec, true, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), d_w(m), m->root_h,
+                             m->d_bg, nullptr, plane(m), m->ph, m->d_partial, m->d_bad, m->d_out, m->stream));
+    CU(cudaMemcpyAsync(m->bgint, m->d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    m->bgint_valid = true;
+  }
   CU(cudaMemsetAsync(m->d_bad, 0, sizeof(int), m->stream));
-  CU(dgk::launch_integrals(m->prec, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), d_w(m), m->root_h,
+  CU(dgk::launch_integrals(m->prec, false, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), d_w(m), m->root_h,
                            m->d_bg, m->q[0], plane(m), m->ph, m->d_partial, m->d_bad, m->d_out, m->stream));
+  double S[6];
   int bad = 0;
-  CU(cudaMemcpyAsync(out, m->d_out, DG_NUM_INTEGRALS * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  CU(cudaMemcpyAsync(S, m->d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   CU(cudaMemcpyAsync(&bad, m->d_bad, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
   CU(cudaStreamSynchronize(m->stream));
+  const double* B = m->bgint;
+  double e0, e1;
+  const double t0 = two_sum(B[0], S[0], &e0);
+  const double t1 = two_sum(B[1], S[1], &e1);
+  out[0] = t0 + (e0 + (B[3] + S[3]));          // mass
+  out[1] = t1 + (e1 + (B[4] + S[4]));          // total energy
+  out[2] = S[2];                               // kinetic energy
+  out[3] = B[2];                               // volume
+  out[4] = S[0];                               // perturbation mass
   if (bad) return fail(m, DG_ERR_STATE, "non-finite value in the state");
   return DG_OK;
 }

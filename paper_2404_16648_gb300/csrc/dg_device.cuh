@@ -29,6 +29,7 @@ constexpr int kSeries = 11;      // binomial-series terms kept for the FP64 pres
 struct PhysC {
   double theta0, p0, g, R, cp, cv, gamma;
   double binom[kSeries];         // binom(gamma, k) for k = 1..kSeries
+  float rel[3];                  // binom(gamma, k) / gamma for k = 2..4 (FP32 path's correction)
 };
 
 enum { FACE_WALL = 0, FACE_CONF = 1, FACE_FINE = 2, FACE_COARSE = 3 };
@@ -73,8 +74,38 @@ __device__ __forceinline__ double pressure_pert(double tp, double invTb, double 
   return __dmul_rn(pb, expm1(__dmul_rn(ph.gamma, log1p(x))));
 }
 
-template <class T> struct SeriesTerms { static constexpr int K = kSeries; };
-template <> struct SeriesTerms<float> { static constexpr int K = 4; };
+// P' for the FP32 path, stored in FP32: with c = gamma P_bar / Theta_bar (FP64, per z-level),
+//   P' = A (1 + s),  A = Theta' c,  s = sum_{k=2..4} binom(gamma, k)/gamma x^(k-1),
+// A and A + A s in FP64, s in FP32.  |s| < 0.7 % for |x| <= 2^-5, so the FP32 rounding of s
+// moves P' by < 1e-9 relative and the truncation after x^4 by < 8e-9, both below the FP32
+// rounding (6e-8) of the stored result: the value is the FP64 evaluation rounded to FP32 up to
+// rare one-ulp ties, with 5 FP64 operations instead of 9.  Larger |x| use the full FP64 form
+// with the row bd = (rho_bar, Theta_bar, p_bar, 1/Theta_bar) of the FP64 background.
+__device__ __forceinline__ float pressure_pert_f32(float tp, float invTbf, double c, const double* bd,
+                                                   const PhysC& ph) {
+  const float x = __fmul_rn(tp, invTbf);
+  if (fabsf(x) <= 0.03125f) {
+    const float s = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, ph.rel[2], ph.rel[1]), ph.rel[0]));
+    const double A = __dmul_rn((double)tp, c);
+    return (float)__fma_rn(A, (double)s, A);
+  }
+  return (float)pressure_pert<kSeries>((double)tp, bd[3], bd[2], ph);
+}
+
+// P' of a node in the arithmetic type T: FP64 series (T = double) or the form above.  invTb is
+// 1/Theta_bar in T (the background table of the path), bd the FP64 background row, bc -> c.
+template <class T>
+__device__ __forceinline__ T pprime_of(T tp, T invTb, const double* bd, const double* bc, const PhysC& ph);
+template <>
+__device__ __forceinline__ double pprime_of<double>(double tp, double invTb, const double* bd, const double*,
+                                                    const PhysC& ph) {
+  return pressure_pert<kSeries>(tp, invTb, bd[2], ph);
+}
+template <>
+__device__ __forceinline__ float pprime_of<float>(float tp, float invTb, const double* bd, const double* bc,
+                                                  const PhysC& ph) {
+  return pressure_pert_f32(tp, invTb, *bc, bd, ph);
+}
 
 // Background and pressure at one node, in the flux arithmetic type T.
 template <class T>
@@ -161,6 +192,7 @@ struct StageArgs {
   const int32_t* conn;   // [E][2d][5] (see tree.cpp)
   const double* bg;      // [E][N+1][4]: rho_bar, Theta_bar, p_bar, 1/Theta_bar (FP64)
   const void* bgt;       // [E][N+1][4]: the same in T (the FP64 array itself when T = double)
+  const double* bgc;     // [E][N+1]: gamma p_bar / Theta_bar (FP32 path's P'; null for FP64)
   const void* ops;       // (T) D, P0, P1, C0, C1 (n1 x n1 each), w (n1)
   float inv2hf[kMaxLevels][3];    // 2/h per level and axis
   double inv2hd[kMaxLevels][3];
@@ -181,6 +213,7 @@ struct MortarArgs {
   const int32_t* groups; // [G][7]: coarse element, axis, side, fine elements (Morton order)
   const double* bg;
   const void* bgt;
+  const double* bgc;
   const void* ops;
   float gammaf;
   PhysC ph;
@@ -344,9 +377,9 @@ __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) 
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];
-  const double* bd = A.bg + ((size_t)e * n1 + idx[D - 1]) * 4;
+  const size_t zk = (size_t)e * n1 + idx[D - 1];
   ((T*)A.pp_out)[e * NP + n] =
-      (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
+      pprime_of<T>(qnew[D + 1], ((const T*)A.bgt)[zk * 4 + 3], A.bg + zk * 4, A.bgc + zk, A.ph);
 }
 
 template <class T, int D, int N, int EPB>
@@ -367,14 +400,14 @@ stage_kernel_batched(const StageArgs* __restrict__ tab, const int2* __restrict__
 // outside the time loop (set_state, initial condition, transfer, dg_rhs input).
 template <class T>
 __global__ void pprime_kernel(int64_t total, int NP, int n1, int D, const T* theta_plane,
-                              const double* bg, PhysC ph, T* pp) {
+                              const double* bg, const double* bgc, PhysC ph, T* pp) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
   const int64_t e = i / NP;
   const int n = (int)(i - e * NP);
   const int k = D == 3 ? n / (n1 * n1) : n / n1;
-  const double* b = bg + (e * n1 + k) * 4;
-  pp[i] = (T)pressure_pert<SeriesTerms<T>::K>((double)theta_plane[i], b[3], b[2], ph);
+  const int64_t zk = e * n1 + k;
+  pp[i] = pprime_of<T>(theta_plane[i], (T)bg[zk * 4 + 3], bg + zk * 4, bgc + zk, ph);
 }
 
 // One CTA per mortar group; NSUB * NF threads: thread (m, t) owns mortar node t of mortar m.
@@ -442,11 +475,11 @@ mortar_kernel(const __grid_constant__ MortarArgs A) {
     qc[v] = sM[m][v][t];
   }
   const int kf = (D == 3) ? nf / (n1 * n1) : nf / n1;
-  const double* bd = A.bg + ((size_t)ef * n1 + kf) * 4;
+  const size_t zf = (size_t)ef * n1 + kf;
   const T* bt = (const T*)A.bgt + ((size_t)ef * n1 + kf) * 4;
   const NodeBg<T> bgf{bt[0], bt[1], bt[2]};
   const T ppf = ((const T*)A.pp_in)[(size_t)ef * NP + nf];
-  const T ppc = (T)pressure_pert<SeriesTerms<T>::K>((double)qc[D + 1], bd[3], bd[2], A.ph);
+  const T ppc = pprime_of<T>(qc[D + 1], bt[3], A.bg + zf * 4, A.bgc + zf, A.ph);
   const T gamma = gamma_of<T>(A.ph, A.gammaf);
   T Ff[NV], Fc[NV];
   const T sf = face_side<T, D>(qf, bgf, ppf, a, gamma, Ff);

@@ -35,9 +35,9 @@ cudaError_t launch_stage_batched_f32_3d(int N, int layout, const StageArgs* tab,
 
 cudaError_t launch_background(int32_t E, int n1, int D, const int32_t* elem, const double* xi,
                               double root_hz, const PhysC& ph, double* bg, float* bgf,
-                              cudaStream_t s);
+                              double* bgc, cudaStream_t s);
 cudaError_t launch_pprime(int prec, int32_t E, int n1, int D, const void* theta_plane,
-                          const double* bg, const PhysC& ph, void* pp, cudaStream_t s);
+                          const double* bg, const double* bgc, const PhysC& ph, void* pp, cudaStream_t s);
 cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* elem,
                           const double* xi, const double* root_h, const double* bg,
                           const double* center, const double* radius, double amp, int n_rff,
@@ -49,7 +49,10 @@ cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* b
 cudaError_t launch_primitives(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
                               int64_t plane, double theta0, double* out, cudaStream_t s);
 size_t integrals_scratch_doubles();
-cudaError_t launch_integrals(int prec, int32_t E, int n1, int D, const int32_t* elem,
+// Three compensated sums (see dg_misc.cu) into out[0..2], their rounding errors into out[3..5]:
+// background = true: int rho_bar, int (p_bar cv/R + rho_bar g z), volume;
+// background = false: int rho', int (P' cv/R + |U|^2/(2 rho) + rho' g z), int |U|^2/(2 rho).
+cudaError_t launch_integrals(int prec, bool background, int32_t E, int n1, int D, const int32_t* elem,
                              const double* xi, const double* w, const double* root_h,
                              const double* bg, const void* q, int64_t plane, const PhysC& ph,
                              double* partial, int* bad, double* out, cudaStream_t s);

@@ -30,10 +30,11 @@ struct dg_mesh {
   int32_t* d_groups = nullptr;
   double* d_bg = nullptr;
   float* d_bgf = nullptr;      // FP32 copy of the background (FP32 path)
+  double* d_bgc = nullptr;     // gamma p_bar / Theta_bar per z-level (FP32 path's P')
   void* d_mbuf = nullptr;
   void* d_ppscratch = nullptr; // P' plane of a caller's state in dg_rhs
   bool pp_valid = false;       // P' plane of q[0] matches q[0]
-  int variant = 2;             // stage kernel layout (DG_OPT_STAGE_KERNEL)
+  int variant = 2;             // stage kernel layout (DG_OPT_STAGE_KERNEL); set at creation
   // adjoint / pure-step workspace, allocated on first use for the current mesh size
   void* adj_q[3] = {nullptr, nullptr, nullptr};   // states with P' planes
   double* adj_l[2] = {nullptr, nullptr};          // cotangents
@@ -47,6 +48,8 @@ struct dg_mesh {
   double* d_opsd = nullptr;    // FP64: D, P0, P1, C0, C1, w, x
   double* d_partial = nullptr;
   double* d_out = nullptr;
+  double bgint[6] = {0, 0, 0, 0, 0, 0};   // background sums of the integrals (see dg_integrals)
+  bool bgint_valid = false;
   int* d_bad = nullptr;
   // timing
   bool timing = false;

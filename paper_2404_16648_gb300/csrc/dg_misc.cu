@@ -18,7 +18,7 @@ __device__ __forceinline__ double node_coord(int c, double xi, double h) {
 // p_bar := P(Theta_bar) = p0 (R Theta_bar / p0)^gamma so that a fluid at rest has P' = 0.
 __global__ void background_kernel(int32_t E, int n1, int D, const int32_t* elem,
                                   const double* xi, double root_hz, PhysC ph, double* bg,
-                                  float* bgf) {
+                                  float* bgf, double* bgc) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)E * n1) return;
   const int64_t e = i / n1;
@@ -35,6 +35,7 @@ __global__ void background_kernel(int32_t E, int n1, int D, const int32_t* elem,
   if (bgf) {
     float* f = bgf + i * 4;
     f[0] = (float)rb; f[1] = (float)Tb; f[2] = (float)pb; f[3] = (float)(1.0 / Tb);
+    bgc[i] = ph.gamma * pb / Tb;
   }
 }
 
@@ -131,83 +132,120 @@ struct Comp {
   __device__ void merge(const Comp& o) { add(o.s); c += o.c; }
 };
 
-constexpr int kIntBlocks = 512;
+constexpr int kIntBlocks = 1216;    // 8 per SM
 constexpr int kIntThreads = 256;
+constexpr int kMaxNP = 729;          // (N + 1)^3 for N = 8
 
-// Partial integrals: each block reduces a fixed grid-stride slice in a fixed tree order.
-template <class T>
+// Compensated partial sums over the nodes, weights w_i w_j (w_k) |J|.  The total energy
+// p cv/R + |U|^2/(2 rho) + rho g z splits into a part of the background alone and a part that
+// carries the state, and so does the mass:
+//   BG = true:  {int rho_bar, int (p_bar cv/R + rho_bar g z), int 1}   (once per mesh)
+//   BG = false: {int rho', int (P' cv/R + |U|^2/(2 rho) + rho' g z), int |U|^2/(2 rho)}
+// Each thread sums its nodes of one element in plain FP64 and adds that subtotal to its
+// Neumaier accumulator; blocks then reduce in a fixed tree order, and a final pass walks the
+// block partials in order, so the result is deterministic.  Node weights and z-levels come
+// from per-block tables, so no node needs an integer division.
+template <class T, bool BG>
 __global__ void __launch_bounds__(kIntThreads)
 integrals_partial(int32_t E, int n1, int D, const int32_t* elem, const double* xi,
                   const double* w, double rh0, double rh1, double rh2, const double* bg,
                   const T* q, int64_t plane, PhysC ph, double* partial, int* bad) {
-  const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
-  const int64_t total = (int64_t)E * NP;
-  Comp acc[NUM_INTEGRALS];
-  for (int k = 0; k < NUM_INTEGRALS; ++k) acc[k] = Comp{0.0, 0.0};
+  __shared__ double sW[kMaxNP];
+  __shared__ double sXh[9];
+  __shared__ unsigned char sK[kMaxNP];
+  const int tid = threadIdx.x;
+  const int NF = D == 3 ? n1 * n1 : n1;
+  const int NP = NF * n1;
+  for (int n = tid; n < NP; n += blockDim.x) {
+    const int i = n % n1, k = n / NF;
+    double wn = w[i];
+    if (D == 3) wn = wn * w[(n / n1) % n1];
+    sW[n] = wn * w[k];
+    sK[n] = (unsigned char)k;
+  }
+  if (tid < n1) sXh[tid] = (xi[tid] + 1.0) * 0.5;
+  __syncthreads();
+  const int epi = NP >= (int)blockDim.x ? 1 : (int)blockDim.x / NP;   // elements per pass
+  const int le = epi > 1 ? tid / NP : 0;
+  const int n0 = epi > 1 ? tid - le * NP : tid;
+  const int nstride = epi > 1 ? NP : (int)blockDim.x;
   const double rh[3] = {rh0, rh1, rh2};
+  const double cvR = ph.cv / ph.R;
+  Comp acc[3];
+  for (int k = 0; k < 3; ++k) acc[k] = Comp{0.0, 0.0};
   int nonfinite = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = i / NP;
-    const int n = (int)(i - e * NP);
-    int idx[3] = {n % n1, (n / n1) % n1, D == 3 ? n / (n1 * n1) : 0};
+  for (int64_t eb = (int64_t)blockIdx.x * epi; eb < E; eb += (int64_t)gridDim.x * epi) {
+    const int64_t e = eb + le;
+    if (le >= epi || e >= E) continue;
     const int level = elem[e * 4];
-    double wn = 1.0, J = 1.0, z = 0.0;
-    for (int a = 0; a < D; ++a) {
-      const double h = ldexp(rh[a], -level);
-      wn = wn * w[idx[a]];
-      J = J * (h * 0.5);
-      if (a == D - 1) z = node_coord(elem[e * 4 + 1 + a], xi[idx[a]], h);
+    double J = 1.0;
+    for (int a = 0; a < D; ++a) J = J * (ldexp(rh[a], -level) * 0.5);
+    const double hz = ldexp(rh[D - 1], -level);
+    const double cz = (double)elem[e * 4 + D];
+    double l0 = 0.0, l1 = 0.0, l2 = 0.0;
+    for (int n = n0; n < NP; n += nstride) {
+      const int k = sK[n];
+      const double W = sW[n] * J;
+      const double* b = bg + (e * n1 + k) * 4;
+      const double z = (cz + sXh[k]) * hz;
+      if (BG) {
+        const double rb = b[0];
+        l0 += W * rb;
+        l1 += W * (b[2] * cvR + rb * ph.g * z);
+        l2 += W;
+      } else {
+        const int64_t i = e * NP + n;
+        const double rp = (double)q[i];
+        const double rho = b[0] + rp;
+        double u2 = 0.0;
+        for (int a = 0; a < D; ++a) {
+          const double U = (double)q[(int64_t)(1 + a) * plane + i];
+          u2 = u2 + U * U;
+        }
+        const double ke = 0.5 * u2 / rho;
+        const double pp = pressure_pert<kSeries>((double)q[(int64_t)(D + 1) * plane + i], b[3], b[2], ph);
+        const double ep = pp * cvR + ke + rp * ph.g * z;
+        if (!isfinite(rho) || !isfinite(ep)) nonfinite = 1;
+        l0 += W * rp;
+        l1 += W * ep;
+        l2 += W * ke;
+      }
     }
-    const double W = wn * J;
-    const double* b = bg + (e * n1 + idx[D - 1]) * 4;
-    const double rp = (double)q[i];
-    const double rho = b[0] + rp;
-    double u2 = 0.0;
-    for (int a = 0; a < D; ++a) {
-      const double U = (double)q[(int64_t)(1 + a) * plane + i];
-      u2 = u2 + U * U;
-    }
-    const double ke = 0.5 * u2 / rho;
-    const double tp = (double)q[(int64_t)(D + 1) * plane + i];
-    const double pp = pressure_pert<kSeries>(tp, b[3], b[2], ph);
-    const double p = b[2] + pp;
-    const double en = p * ph.cv / ph.R + ke + rho * ph.g * z;
-    if (!isfinite(rho) || !isfinite(en)) nonfinite = 1;
-    acc[0].add(W * rho);
-    acc[1].add(W * en);
-    acc[2].add(W * ke);
-    acc[3].add(W);
-    acc[4].add(W * rp);
+    acc[0].add(l0);
+    acc[1].add(l1);
+    acc[2].add(l2);
   }
   if (nonfinite) atomicOr(bad, 1);
-  __shared__ double ss[NUM_INTEGRALS][kIntThreads], sc[NUM_INTEGRALS][kIntThreads];
-  for (int k = 0; k < NUM_INTEGRALS; ++k) { ss[k][threadIdx.x] = acc[k].s; sc[k][threadIdx.x] = acc[k].c; }
+  __shared__ double ss[3][kIntThreads], sc[3][kIntThreads];
+  for (int k = 0; k < 3; ++k) { ss[k][tid] = acc[k].s; sc[k][tid] = acc[k].c; }
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int k = 0; k < NUM_INTEGRALS; ++k) {
-        Comp a{ss[k][threadIdx.x], sc[k][threadIdx.x]};
-        a.merge(Comp{ss[k][threadIdx.x + s], sc[k][threadIdx.x + s]});
-        ss[k][threadIdx.x] = a.s; sc[k][threadIdx.x] = a.c;
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (tid < st)
+      for (int k = 0; k < 3; ++k) {
+        Comp a{ss[k][tid], sc[k][tid]};
+        a.merge(Comp{ss[k][tid + st], sc[k][tid + st]});
+        ss[k][tid] = a.s; sc[k][tid] = a.c;
       }
     __syncthreads();
   }
-  if (threadIdx.x == 0)
-    for (int k = 0; k < NUM_INTEGRALS; ++k) {
-      partial[(blockIdx.x * NUM_INTEGRALS + k) * 2] = ss[k][0];
-      partial[(blockIdx.x * NUM_INTEGRALS + k) * 2 + 1] = sc[k][0];
+  if (tid == 0)
+    for (int k = 0; k < 3; ++k) {
+      partial[(blockIdx.x * 3 + k) * 2] = ss[k][0];
+      partial[(blockIdx.x * 3 + k) * 2 + 1] = sc[k][0];
     }
 }
 
-// Final pass: one thread per integral walks the block partials in order.
+// Final pass: one thread per sum walks the block partials in order; out[k] = s + c rounded and
+// out[3 + k] its rounding error, so that a later sum of two such results loses nothing.
 __global__ void integrals_final(int nblocks, const double* partial, double* out) {
   const int k = threadIdx.x;
-  if (k >= NUM_INTEGRALS) return;
+  if (k >= 3) return;
   Comp a{0.0, 0.0};
   for (int b = 0; b < nblocks; ++b)
-    a.merge(Comp{partial[(b * NUM_INTEGRALS + k) * 2], partial[(b * NUM_INTEGRALS + k) * 2 + 1]});
-  out[k] = a.s + a.c;
+    a.merge(Comp{partial[(b * 3 + k) * 2], partial[(b * 3 + k) * 2 + 1]});
+  const double t = a.s + a.c;
+  out[k] = t;
+  out[3 + k] = a.c - (t - a.s);     // rounding error of t (|s| >= |c| for a compensated sum)
 }
 
 // Conservative transfer after a regrid (Sec. 3.3), one CTA per new element, FP64 arithmetic:
@@ -273,23 +311,23 @@ __global__ void transfer_kernel(int32_t Enew, int n1, int D, const int32_t* tmap
 
 cudaError_t launch_background(int32_t E, int n1, int D, const int32_t* elem, const double* xi,
                               double root_hz, const PhysC& ph, double* bg, float* bgf,
-                              cudaStream_t s) {
+                              double* bgc, cudaStream_t s) {
   const int64_t n = (int64_t)E * n1;
   if (n == 0) return cudaSuccess;
-  background_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, n1, D, elem, xi, root_hz, ph, bg, bgf);
+  background_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, n1, D, elem, xi, root_hz, ph, bg, bgf, bgc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pprime(int prec, int32_t E, int n1, int D, const void* theta_plane,
-                          const double* bg, const PhysC& ph, void* pp, cudaStream_t s) {
+                          const double* bg, const double* bgc, const PhysC& ph, void* pp, cudaStream_t s) {
   const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
   const int64_t n = (int64_t)E * NP;
   if (n == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((n + 255) / 256);
   if (prec == 0)
-    pprime_kernel<double><<<blocks, 256, 0, s>>>(n, NP, n1, D, (const double*)theta_plane, bg, ph, (double*)pp);
+    pprime_kernel<double><<<blocks, 256, 0, s>>>(n, NP, n1, D, (const double*)theta_plane, bg, bgc, ph, (double*)pp);
   else
-    pprime_kernel<float><<<blocks, 256, 0, s>>>(n, NP, n1, D, (const float*)theta_plane, bg, ph, (float*)pp);
+    pprime_kernel<float><<<blocks, 256, 0, s>>>(n, NP, n1, D, (const float*)theta_plane, bg, bgc, ph, (float*)pp);
   return cudaGetLastError();
 }
 
@@ -333,18 +371,23 @@ cudaError_t launch_primitives(int prec, int32_t E, int n1, int D, const double* 
   return cudaGetLastError();
 }
 
-size_t integrals_scratch_doubles() { return (size_t)kIntBlocks * NUM_INTEGRALS * 2; }
+size_t integrals_scratch_doubles() { return (size_t)kIntBlocks * 3 * 2; }
 
-cudaError_t launch_integrals(int prec, int32_t E, int n1, int D, const int32_t* elem,
+cudaError_t launch_integrals(int prec, bool background, int32_t E, int n1, int D, const int32_t* elem,
                              const double* xi, const double* w, const double* root_h,
                              const double* bg, const void* q, int64_t plane, const PhysC& ph,
                              double* partial, int* bad, double* out, cudaStream_t s) {
-  if (prec == 0)
-    integrals_partial<double><<<kIntBlocks, kIntThreads, 0, s>>>(E, n1, D, elem, xi, w, root_h[0],
-        root_h[1], root_h[2], bg, (const double*)q, plane, ph, partial, bad);
+  if (n1 * n1 * n1 > kMaxNP || n1 > 9) return cudaErrorInvalidValue;
+  const double r0 = root_h[0], r1 = root_h[1], r2 = root_h[2];
+  if (background)
+    integrals_partial<double, true><<<kIntBlocks, kIntThreads, 0, s>>>(E, n1, D, elem, xi, w, r0, r1, r2, bg,
+        (const double*)nullptr, plane, ph, partial, bad);
+  else if (prec == 0)
+    integrals_partial<double, false><<<kIntBlocks, kIntThreads, 0, s>>>(E, n1, D, elem, xi, w, r0, r1, r2, bg,
+        (const double*)q, plane, ph, partial, bad);
   else
-    integrals_partial<float><<<kIntBlocks, kIntThreads, 0, s>>>(E, n1, D, elem, xi, w, root_h[0],
-        root_h[1], root_h[2], bg, (const float*)q, plane, ph, partial, bad);
+    integrals_partial<float, false><<<kIntBlocks, kIntThreads, 0, s>>>(E, n1, D, elem, xi, w, r0, r1, r2, bg,
+        (const float*)q, plane, ph, partial, bad);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   integrals_final<<<1, 32, 0, s>>>(kIntBlocks, partial, out);

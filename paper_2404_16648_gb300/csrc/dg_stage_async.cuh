@@ -44,6 +44,7 @@ __device__ __forceinline__ void stage_run(T* dst, const T* src, int count, int l
 //   sQ        (NV + 1) x NP     state and P'
 //   sNb       2d x (NV + 1) x NF  neighbour traces / mortar fluxes per face
 //   sBg       n1 x 4            background column (T)
+//   sBc       n1 doubles        gamma p_bar / Theta_bar per z-level (FP32 path's P')
 // plus the derivative matrix once.
 template <class T, int D, int N>
 __host__ __device__ constexpr int async_region_a() {
@@ -55,7 +56,8 @@ __host__ __device__ constexpr int async_region_a() {
 template <class T, int D, int N>
 __host__ __device__ constexpr int async_elem_words() {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
-  return async_region_a<T, D, N>() + ((NV + 1) * NP + 3) / 4 * 4 + (2 * D * (NV + 1) * NF + 3) / 4 * 4 + n1 * 4;
+  return async_region_a<T, D, N>() + ((NV + 1) * NP + 3) / 4 * 4 + (2 * D * (NV + 1) * NF + 3) / 4 * 4 + n1 * 4 +
+         ((n1 * (int)(8 / sizeof(T))) + 3) / 4 * 4;
 }
 template <class T, int D, int N, int EPB>
 __host__ __device__ constexpr size_t async_smem_bytes() {
@@ -81,6 +83,7 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
   T* sQ = base + RA;                  // [NV + 1][NP]
   T* sNb = base + RA + RQ;            // [2D][NV + 1][NF]
   T* sBg = base + RA + RQ + RN;       // [n1][4]
+  double* sBc = reinterpret_cast<double*>(sBg + n1 * 4);   // [n1] (FP32 path)
   T* sDh = reinterpret_cast<T*>(smem_raw) + EPB * EW;
   const int64_t e = e0 + le;
   const bool valid = e < A.E;
@@ -93,6 +96,7 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
     for (int v = 0; v < NV; ++v) stage_run<T>(sQ + v * NP, qe + v * P, NP, t, NF);
     stage_run<T>(sQ + NV * NP, (const T*)A.pp_in + e * NP, NP, t, NF);
     stage_run<T>(sBg, (const T*)A.bgt + e * n1 * 4, n1 * 4, t, NF);
+    if (sizeof(T) == 4) stage_run<double>(sBc, A.bgc + e * n1, n1, t, NF);
   }
   const T* ops = (const T*)A.ops;
   for (int x = tid; x < n1 * n1; x += blockDim.x) sDh[x] = ops[x];
@@ -331,8 +335,7 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
       qnew[v] = first ? qsv + dt * acc[v][k] : ca * qn_col[v][k] + cb * (qsv + dt * acc[v][k]);
       oute[v * P + n] = qnew[v];
     }
-    const double* bd = A.bg + ((size_t)e * n1 + k) * 4;
-    ppo[n] = (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
+    ppo[n] = pprime_of<T>(qnew[D + 1], sBg[k * 4 + 3], A.bg + ((size_t)e * n1 + k) * 4, sBc + k, A.ph);
   }
 }
 

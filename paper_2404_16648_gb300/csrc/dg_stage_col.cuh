@@ -292,8 +292,8 @@ stage_kernel_col(const __grid_constant__ StageArgs A) {
       qnew[v] = first ? qsv + dt * acc[v][k] : ca * qne[v * P + n] + cb * (qsv + dt * acc[v][k]);
       oute[v * P + n] = qnew[v];
     }
-    const double* bd = A.bg + ((size_t)e * n1 + k) * 4;
-    ppo[n] = (T)pressure_pert<SeriesTerms<T>::K>((double)qnew[D + 1], bd[3], bd[2], A.ph);
+    const size_t zk = (size_t)e * n1 + k;
+    ppo[n] = pprime_of<T>(qnew[D + 1], ((const T*)A.bgt)[zk * 4 + 3], A.bg + zk * 4, A.bgc + zk, A.ph);
   }
 }
 

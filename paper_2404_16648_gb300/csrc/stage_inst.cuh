@@ -1,7 +1,7 @@
 // Instantiates the stage and mortar kernels of one (precision, dimension) for N = 1..8.
 // Included by stage_<prec>_<dim>.cu with DG_T and DG_D defined.
 #include "dg_launch.hpp"
-#include "dg_stage_async.cuh"
+#include "dg_stage_half.cuh"
 
 namespace dgk {
 namespace {
@@ -46,6 +46,25 @@ cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
   const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
   if (blocks) stage_kernel_async<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
   return cudaSuccess;
+}
+
+// Layout 3 (3D, odd N); other shapes take layout 2.
+template <class T, int D, int N>
+cudaError_t run_stage_half(const StageArgs& A, cudaStream_t s) {
+  if constexpr (D == 3 && N % 2 == 1) {
+    constexpr size_t smem = half_smem_bytes<T, N>();
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(stage_kernel_half<T, N>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    if (A.E) stage_kernel_half<T, N><<<(unsigned)A.E, HalfCfg<N>::THREADS, smem, s>>>(A);
+    return cudaSuccess;
+  } else {
+    return run_stage_async<T, D, N>(A, s);
+  }
 }
 
 // Batched launch over many meshes: layout 1 (node) or 2 (column, asynchronous staging).
@@ -93,6 +112,7 @@ template <class T, int D, int N>
 void run_stage(const StageArgs& A, cudaStream_t s) {
   if (A.variant == 1) run_stage_node<T, D, N>(A, s);
   else if (A.variant == 2) run_stage_async<T, D, N>(A, s);
+  else if (A.variant == 3) run_stage_half<T, D, N>(A, s);
   else run_stage_col<T, D, N>(A, s);
 }
 

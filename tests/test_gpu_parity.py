@@ -64,10 +64,12 @@ MESHES = [
     (3, 7, (2, 2, 2), (2000.0, 2000.0, 2000.0), ((0.3, 6),)),
     (2, 1, (3, 2), (300.0, 200.0), ((0.5, 7),)),
     (3, 8, (1, 2, 1), (1000.0, 2000.0, 1000.0), ((0.5, 8),)),
+    (3, 5, (2, 1, 2), (2000.0, 1000.0, 2000.0), ((0.4, 9),)),
+    (3, 1, (2, 2, 3), (2000.0, 2000.0, 3000.0), ((0.3, 10), (0.3, 11))),
 ]
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3])
 @pytest.mark.parametrize("dim,N,base,length,rounds", MESHES)
 def test_rhs_parity_fp64(pkg, dim, N, base, length, rounds, layout):
     lm, om = _pair(pkg, dim, N, base, length, flags_rounds=rounds)
@@ -89,7 +91,7 @@ def test_rest_state_exactly_zero(pkg, precision):
     assert torch.count_nonzero(out).item() == 0
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3])
 @pytest.mark.parametrize("dim,N,base,length,rounds", MESHES)
 def test_rhs_parity_fp32_perturbation(pkg, dim, N, base, length, rounds, layout):
     # FP32 state and flux arithmetic, FP64 background and pressure perturbation.  Bound: the
@@ -126,7 +128,7 @@ def test_step_parity_rising_bubble(pkg):
     assert _rel_err(got - q0, want - q0) <= 1e-11
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3])
 def test_step_parity_hanging_3d(pkg, layout):
     lm, om = _pair(pkg, 3, 3, (2, 2, 2), (2000.0,) * 3, flags_rounds=((0.3, 11),))
     lm.set_stage_kernel(layout)
