@@ -478,7 +478,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   m->NV = m->D + 2; m->NSUB = 1 << (m->D - 1);
   m->prec = desc->precision;
   m->tsize = m->prec == DG_FP64 ? sizeof(double) : sizeof(float);
-  m->variant = (m->prec == DG_FP32_PERT && m->D == 3) ? 3 : 2;   // fastest measured layouts
+  m->variant = m->D == 3 ? 3 : 2;   // fastest measured layouts (3 falls back to 2 for even N)
   m->stream = (cudaStream_t)stream;
   m->ph.theta0 = desc->theta0; m->ph.p0 = desc->p0; m->ph.g = desc->g; m->ph.R = desc->R;
   m->ph.cp = desc->cp; m->ph.cv = desc->cp - desc->R; m->ph.gamma = desc->cp / (desc->cp - desc->R);
