@@ -13,7 +13,11 @@ Modules (each function cites the passage of arXiv 2404.16648 it restates):
 * ``forest``  -- forest of quad/oct-trees with active-leaf storage, regrid with buffer B,
                  2:1 balance, conforming/mortar/boundary face lists (Sec. 3.1, 3.2.1, 4.3).
 * ``dg``      -- strong-form dGSEM right-hand side with mortars, SSP-RK3, conservative
-                 parent<->child transfer, integrals, initial conditions (Sec. 2.2, 3.3, 4.3).
+                 parent<->child transfer, integrals, initial conditions (Sec. 2.2, 3.3, 4.3),
+                 and the BR1 reading of the artificial viscosity named in Sec. 4.3.
+* ``adjoint`` -- the discrete adjoint of the right-hand side and of the SSP-RK3 step by
+                 complex-step Jacobian columns, and the gradient of the final kinetic energy
+                 with respect to the initial theta' field.
 
 Parity status of each function is stated in its docstring; every function here is pinned by
 ``tests/test_oracle_*.py`` against closed forms, invariants or brute force, except the

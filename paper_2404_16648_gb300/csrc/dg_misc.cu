@@ -235,17 +235,34 @@ integrals_partial(int32_t E, int n1, int D, const int32_t* elem, const double* x
     }
 }
 
-// Final pass: one thread per sum walks the block partials in order; out[k] = s + c rounded and
+// Final pass, one CTA of kIntThreads: thread t merges a fixed contiguous run of block partials
+// in order, then the threads reduce in a fixed tree (deterministic).  out[k] = s + c rounded,
 // out[3 + k] its rounding error, so that a later sum of two such results loses nothing.
-__global__ void integrals_final(int nblocks, const double* partial, double* out) {
-  const int k = threadIdx.x;
-  if (k >= 3) return;
-  Comp a{0.0, 0.0};
-  for (int b = 0; b < nblocks; ++b)
-    a.merge(Comp{partial[(b * 3 + k) * 2], partial[(b * 3 + k) * 2 + 1]});
-  const double t = a.s + a.c;
-  out[k] = t;
-  out[3 + k] = a.c - (t - a.s);     // rounding error of t (|s| >= |c| for a compensated sum)
+__global__ void __launch_bounds__(kIntThreads) integrals_final(int nblocks, const double* partial, double* out) {
+  __shared__ double ss[3][kIntThreads], sc[3][kIntThreads];
+  const int tid = threadIdx.x;
+  const int run = (nblocks + kIntThreads - 1) / kIntThreads;
+  const int b0 = tid * run, b1 = min(nblocks, b0 + run);
+  for (int k = 0; k < 3; ++k) {
+    Comp a{0.0, 0.0};
+    for (int b = b0; b < b1; ++b) a.merge(Comp{partial[(b * 3 + k) * 2], partial[(b * 3 + k) * 2 + 1]});
+    ss[k][tid] = a.s; sc[k][tid] = a.c;
+  }
+  __syncthreads();
+  for (int st = kIntThreads / 2; st > 0; st >>= 1) {
+    if (tid < st)
+      for (int k = 0; k < 3; ++k) {
+        Comp a{ss[k][tid], sc[k][tid]};
+        a.merge(Comp{ss[k][tid + st], sc[k][tid + st]});
+        ss[k][tid] = a.s; sc[k][tid] = a.c;
+      }
+    __syncthreads();
+  }
+  if (tid < 3) {
+    const double t = ss[tid][0] + sc[tid][0];
+    out[tid] = t;
+    out[3 + tid] = sc[tid][0] - (t - ss[tid][0]);   // |s| >= |c| for a compensated sum
+  }
 }
 
 // Conservative transfer after a regrid (Sec. 3.3), one CTA per new element, FP64 arithmetic:
@@ -390,7 +407,7 @@ cudaError_t launch_integrals(int prec, bool background, int32_t E, int n1, int D
         (const float*)q, plane, ph, partial, bad);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
-  integrals_final<<<1, 32, 0, s>>>(kIntBlocks, partial, out);
+  integrals_final<<<1, kIntThreads, 0, s>>>(kIntBlocks, partial, out);
   return cudaGetLastError();
 }
 
