@@ -42,6 +42,24 @@ dg_status fail(dg_mesh* m, dg_status st, const char* fmt, ...) {
 
 void dfree(void* p) { if (p) cudaFree(p); }
 
+// Grow-only device buffer: reallocates, with a quarter of headroom, only when `bytes` exceeds
+// the capacity (the old contents are not kept).
+template <class P>
+cudaError_t reserve(P*& p, size_t& cap, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (p && cap >= bytes) return cudaSuccess;
+  dfree(p);
+  p = nullptr;
+  cap = 0;
+  const size_t want = bytes + bytes / 4;
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, want);
+  if (e != cudaSuccess) return e;
+  p = (P*)v;
+  cap = want;
+  return cudaSuccess;
+}
+
 }  // namespace
 
 namespace dgi {
@@ -114,32 +132,26 @@ dg_status rebuild_topology(dg_mesh* m) {
     elem[e * 4] = L[e].level;
     for (int a = 0; a < 3; ++a) elem[e * 4 + 1 + a] = L[e].c[a];
   }
-  dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
-  dfree(m->d_bgf); dfree(m->d_bgc); dfree(m->d_ppscratch);
-  m->d_elem = nullptr; m->d_conn = nullptr; m->d_groups = nullptr; m->d_bg = nullptr; m->d_mbuf = nullptr;
-  m->d_bgf = nullptr; m->d_bgc = nullptr; m->d_ppscratch = nullptr;
-  dfree(m->d_sigma); dfree(m->d_V); dfree(m->d_vbuf);
-  m->d_sigma = nullptr; m->d_V = nullptr; m->d_vbuf = nullptr;
-  CU(cudaMalloc(&m->d_elem, elem.size() * sizeof(int32_t)));
+  CU(reserve(m->d_elem, m->c_elem, elem.size() * sizeof(int32_t)));
   CU(cudaMemcpy(m->d_elem, elem.data(), elem.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-  CU(cudaMalloc(&m->d_conn, conn.size() * sizeof(int32_t)));
+  CU(reserve(m->d_conn, m->c_conn, conn.size() * sizeof(int32_t)));
   CU(cudaMemcpy(m->d_conn, conn.data(), conn.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   if (m->G > 0) {
-    CU(cudaMalloc(&m->d_groups, m->mort.size() * sizeof(int32_t)));
+    CU(reserve(m->d_groups, m->c_groups, m->mort.size() * sizeof(int32_t)));
     CU(cudaMemcpy(m->d_groups, m->mort.data(), m->mort.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    CU(cudaMalloc(&m->d_mbuf, (size_t)m->G * (1 + m->NSUB) * m->NV * m->NF * m->tsize));
+    CU(reserve(m->d_mbuf, m->c_mbuf, (size_t)m->G * (1 + m->NSUB) * m->NV * m->NF * m->tsize));
   }
-  CU(cudaMalloc(&m->d_bg, (size_t)m->E * m->n1 * 4 * sizeof(double)));
+  CU(reserve(m->d_bg, m->c_bg, (size_t)m->E * m->n1 * 4 * sizeof(double)));
   if (m->prec == DG_FP32_PERT) {
-    CU(cudaMalloc(&m->d_bgf, (size_t)m->E * m->n1 * 4 * sizeof(float)));
-    CU(cudaMalloc(&m->d_bgc, (size_t)m->E * m->n1 * sizeof(double)));
+    CU(reserve(m->d_bgf, m->c_bgf, (size_t)m->E * m->n1 * 4 * sizeof(float)));
+    CU(reserve(m->d_bgc, m->c_bgc, (size_t)m->E * m->n1 * sizeof(double)));
   }
-  CU(cudaMalloc(&m->d_ppscratch, (size_t)(m->E > 0 ? plane(m) : 1) * m->tsize));
+  CU(reserve(m->d_ppscratch, m->c_pps, (size_t)(m->E > 0 ? plane(m) : 1) * m->tsize));
   if (m->desc.nu > 0.0) {
     const size_t pl = (size_t)(plane(m) > 0 ? plane(m) : 1);
-    CU(cudaMalloc(&m->d_sigma, (size_t)(m->D + 1) * m->D * pl * sizeof(double)));
-    CU(cudaMalloc(&m->d_V, (size_t)(m->D + 1) * pl * sizeof(double)));
-    if (m->G > 0) CU(cudaMalloc(&m->d_vbuf, (size_t)m->G * (1 + m->NSUB) * (m->D + 1) * m->NF * sizeof(double)));
+    CU(reserve(m->d_sigma, m->c_sigma, (size_t)(m->D + 1) * m->D * pl * sizeof(double)));
+    CU(reserve(m->d_V, m->c_V, (size_t)(m->D + 1) * pl * sizeof(double)));
+    if (m->G > 0) CU(reserve(m->d_vbuf, m->c_vbuf, (size_t)m->G * (1 + m->NSUB) * (m->D + 1) * m->NF * sizeof(double)));
   }
   CU(dgk::launch_background((int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), m->root_h[m->D - 1],
                             m->ph, m->d_bg, m->d_bgf, m->d_bgc, m->stream));
@@ -149,12 +161,10 @@ dg_status rebuild_topology(dg_mesh* m) {
 }
 
 // Each state buffer holds the NV variable planes followed by the P' plane of that state.
-dg_status alloc_states(dg_mesh* m, void* q[3]) {
-  const size_t bytes = (size_t)(m->NV + 1) * plane(m) * m->tsize;
-  for (int i = 0; i < 3; ++i) {
-    q[i] = nullptr;
-    CU(cudaMalloc(&q[i], bytes > 0 ? bytes : 16));
-  }
+size_t state_bytes(const dg_mesh* m) { return (size_t)(m->NV + 1) * plane(m) * m->tsize; }
+
+dg_status alloc_states(dg_mesh* m) {
+  for (int i = 0; i < 3; ++i) CU(reserve(m->q[i], m->q_cap[i], state_bytes(m)));
   return DG_OK;
 }
 
@@ -498,7 +508,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   dg_status st = init_device_tables(m);
   if (st == DG_OK) st = upload_ops(m);
   if (st == DG_OK) st = rebuild_topology(m);
-  if (st == DG_OK) st = alloc_states(m, m->q);
+  if (st == DG_OK) st = alloc_states(m);
   if (st == DG_OK) {
     if (cudaMalloc(&m->d_partial, dgk::integrals_scratch_doubles() * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&m->d_out, 8 * sizeof(double)) != cudaSuccess ||
@@ -519,6 +529,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   if (!m) return;
   if (m->stream) cudaStreamSynchronize(m->stream); else cudaDeviceSynchronize();
   for (int i = 0; i < 3; ++i) dfree(m->q[i]);
+  dfree(m->q_spare); dfree(m->d_tm); dfree(m->d_ind);
   dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
   dfree(m->d_bgf); dfree(m->d_bgc); dfree(m->d_ppscratch);
   dfree(m->d_sigma); dfree(m->d_V); dfree(m->d_vbuf);
@@ -642,13 +653,12 @@ dg_status dg_step(dg_mesh* m, double dt, int32_t nsteps, void* stream) {
 
 dg_status dg_indicator(dg_mesh* m, double* out, size_t cap) {
   if (!m || !out || cap < (size_t)m->E) return fail(m, DG_ERR_ARG, "bad argument");
-  double* d = nullptr;
-  CU(cudaMalloc(&d, (size_t)(m->E > 0 ? m->E : 1) * sizeof(double)));
+  CU(reserve(m->d_ind, m->c_ind, (size_t)(m->E > 0 ? m->E : 1) * sizeof(double)));
+  double* d = m->d_ind;
   cudaError_t e = dgk::launch_indicator(m->prec, (int32_t)m->E, m->n1, m->D, m->d_bg, m->q[0], plane(m),
                                         m->ph.theta0, d, m->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)m->E * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-  cudaFree(d);
   if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "indicator failed: %s", cudaGetErrorString(e));
   return DG_OK;
 }
@@ -694,23 +704,24 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
     tm[i * 9] = tmap[i].kind;
     for (int k = 0; k < 8; ++k) tm[i * 9 + 1 + k] = tmap[i].src[k];
   }
-  int32_t* d_tm = nullptr;
-  CU(cudaMalloc(&d_tm, tm.size() * sizeof(int32_t) + 4));
-  CU(cudaMemcpy(d_tm, tm.data(), tm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CU(reserve(m->d_tm, m->c_tm, tm.size() * sizeof(int32_t) + 4));
+  CU(cudaMemcpy(m->d_tm, tm.data(), tm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   m->forest = std::move(nf);
-  void* oldq[3] = {m->q[0], m->q[1], m->q[2]};
+  ++m->generation;
   dg_status st = rebuild_topology(m);
-  void* newq[3] = {nullptr, nullptr, nullptr};
-  if (st == DG_OK) st = alloc_states(m, newq);
-  if (st == DG_OK) {
-    cudaError_t e = dgk::launch_transfer(m->prec, (int32_t)m->E, m->n1, m->D, d_tm, m->d_opsd, oldq[0],
-                                         plane_old, newq[0], plane(m), m->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-    if (e != cudaSuccess) st = fail(m, DG_ERR_CUDA, "transfer failed: %s", cudaGetErrorString(e));
-  }
-  cudaFree(d_tm);
   if (st != DG_OK) return st;
-  for (int i = 0; i < 3; ++i) { dfree(oldq[i]); m->q[i] = newq[i]; }
+  // the transfer reads q^n and writes the spare buffer, which then becomes q^n; the stage
+  // buffers q[1], q[2] hold no state between steps and only need the new size
+  CU(reserve(m->q_spare, m->q_spare_cap, state_bytes(m)));
+  for (int i = 1; i < 3; ++i) CU(reserve(m->q[i], m->q_cap[i], state_bytes(m)));
+  {
+    cudaError_t e = dgk::launch_transfer(m->prec, (int32_t)m->E, m->n1, m->D, m->d_tm, m->d_opsd, m->q[0],
+                                         plane_old, m->q_spare, plane(m), m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "transfer failed: %s", cudaGetErrorString(e));
+  }
+  std::swap(m->q[0], m->q_spare);
+  std::swap(m->q_cap[0], m->q_spare_cap);
   m->pp_valid = false;
   if (rep) {
     rep->elements_before = E_old;

@@ -25,6 +25,7 @@ struct dg_batch {
   };
   std::vector<dg_mesh*> meshes;
   std::vector<int64_t> elements;         // element counts when the batch was built
+  std::vector<int64_t> generations;      // regrid generations when the batch was built
   std::vector<double> dt;
   std::vector<Group> groups;
   cudaStream_t stream = nullptr;
@@ -129,6 +130,7 @@ dg_status dg_batch_create(dg_mesh* const* meshes, int32_t count, dg_batch** out)
       if (meshes[j] == m) { delete b; return DG_ERR_ARG; }   // each mesh once
     b->meshes.push_back(m);
     b->elements.push_back(m->E);
+    b->generations.push_back(m->generation);
     b->dt.push_back(0.0);
     auto key = std::make_tuple(m->prec, m->D, m->N);
     auto it = gid.find(key);
@@ -193,7 +195,8 @@ dg_status dg_batch_set_dt(dg_batch* b, const double* dt) {
 dg_status dg_batch_run(dg_batch* b, int32_t nsteps, int32_t use_graph) {
   if (!b || nsteps < 0) return DG_ERR_ARG;
   for (size_t i = 0; i < b->meshes.size(); ++i) {
-    if (b->meshes[i]->E != b->elements[i]) return bfail(b, DG_ERR_STATE, "a mesh was regridded after dg_batch_create");
+    if (b->meshes[i]->E != b->elements[i] || b->meshes[i]->generation != b->generations[i])
+      return bfail(b, DG_ERR_STATE, "a mesh was regridded after dg_batch_create");
     if (!(b->dt[i] > 0.0)) return bfail(b, DG_ERR_ARG, "dt not set (dg_batch_set_dt)");
   }
   if (b->tables_dirty) {

@@ -23,8 +23,17 @@ struct dg_mesh {
   double root_h[3] = {1, 1, 1};
   int64_t E = 0, G = 0, cap = 0;
   std::vector<int32_t> conf, mort, bnd;
-  // device buffers
+  // device buffers; every size-dependent one grows only (capacity in bytes, with headroom), so a
+  // regrid that keeps the mesh near its size allocates nothing
   void* q[3] = {nullptr, nullptr, nullptr};
+  size_t q_cap[3] = {0, 0, 0};
+  void* q_spare = nullptr;     // receives the transferred state at the next regrid
+  size_t q_spare_cap = 0;
+  int64_t generation = 0;      // incremented by every dg_adapt
+  size_t c_elem = 0, c_conn = 0, c_groups = 0, c_bg = 0, c_mbuf = 0, c_bgf = 0, c_bgc = 0, c_pps = 0;
+  size_t c_sigma = 0, c_V = 0, c_vbuf = 0, c_tm = 0, c_ind = 0;
+  int32_t* d_tm = nullptr;     // transfer map of the last regrid
+  double* d_ind = nullptr;     // refinement indicator
   int32_t* d_elem = nullptr;
   int32_t* d_conn = nullptr;
   int32_t* d_groups = nullptr;

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <deque>
+#include <thread>
 
 namespace dgl {
 
@@ -21,11 +22,45 @@ Forest::Forest(int dim, const int base[3], int max_level) : dim_(dim), max_level
   set_leaves(std::move(roots));
 }
 
+static uint64_t mix64(uint64_t x) {   // splitmix64 finaliser
+  x ^= x >> 30; x *= 0xbf58476d1ce4e5b9ULL;
+  x ^= x >> 27; x *= 0x94d049bb133111ebULL;
+  return x ^ (x >> 31);
+}
+static constexpr uint64_t kEmpty = ~0ULL;   // never a key: levels < 32, coordinates < 2^19
+
 void Forest::set_leaves(std::vector<Leaf> leaves) {
   leaves_ = std::move(leaves);
-  index_.clear();
-  index_.reserve(leaves_.size() * 2);
-  for (size_t i = 0; i < leaves_.size(); ++i) index_[key(leaves_[i].level, leaves_[i].c)] = (int32_t)i;
+  uint64_t cap = 16;
+  while (cap < 2 * (uint64_t)leaves_.size()) cap <<= 1;
+  hkeys_.assign(cap, kEmpty);
+  hvals_.assign(cap, -1);
+  hmask_ = cap - 1;
+  for (size_t i = 0; i < leaves_.size(); ++i) {
+    const uint64_t k = key(leaves_[i].level, leaves_[i].c);
+    uint64_t h = mix64(k) & hmask_;
+    while (hkeys_[h] != kEmpty && hkeys_[h] != k) h = (h + 1) & hmask_;
+    hkeys_[h] = k;
+    hvals_[h] = (int32_t)i;
+  }
+  // face table; every entry depends on its own face only, so the split over threads does not
+  // change the result
+  const int64_t n = (int64_t)leaves_.size();
+  faces_.assign((size_t)n * dim_ * 2, FaceInfo{FACE_WALL, {-1, -1, -1, -1}});
+  auto fill = [this](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e)
+      for (int a = 0; a < dim_; ++a)
+        for (int s = 0; s < 2; ++s) faces_[((size_t)e * dim_ + a) * 2 + s] = classify((int32_t)e, a, s);
+  };
+  int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  if (n < 8192) nt = 1;
+  if (nt == 1) {
+    fill(0, n);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t) th.emplace_back(fill, n * t / nt, n * (t + 1) / nt);
+    for (auto& x : th) x.join();
+  }
 }
 
 int32_t Forest::root_index(const Leaf& l) const {
@@ -35,9 +70,14 @@ int32_t Forest::root_index(const Leaf& l) const {
 }
 
 int32_t Forest::find(int level, const int32_t c[3]) const {
-  if (level < 0) return -1;
-  auto it = index_.find(key(level, c));
-  return it == index_.end() ? -1 : it->second;
+  if (level < 0 || hkeys_.empty()) return -1;
+  const uint64_t k = key(level, c);
+  uint64_t h = mix64(k) & hmask_;
+  while (hkeys_[h] != kEmpty) {
+    if (hkeys_[h] == k) return hvals_[h];
+    h = (h + 1) & hmask_;
+  }
+  return -1;
 }
 
 FaceInfo Forest::classify(int32_t e, int axis, int side) const {
@@ -72,7 +112,7 @@ void Forest::neighbours(int32_t e, std::vector<int32_t>* out) const {
   out->clear();
   for (int a = 0; a < dim_; ++a)
     for (int s = 0; s < 2; ++s) {
-      FaceInfo fi = classify(e, a, s);
+      const FaceInfo& fi = face(e, a, s);
       if (fi.kind == FACE_CONF || fi.kind == FACE_FINE) out->push_back(fi.nb[0]);
       else if (fi.kind == FACE_COARSE)
         for (int k = 0; k < (1 << (dim_ - 1)); ++k) out->push_back(fi.nb[k]);
@@ -90,7 +130,7 @@ bool Forest::regrid(const std::vector<uint8_t>& tag, int B, int max_level, Fores
   for (int64_t e = 0; e < n; ++e) {
     for (int a = 0; a < dim_; ++a)
       for (int s = 0; s < 2; ++s)
-        if (classify((int32_t)e, a, s).kind < 0) { *err = "forest is not 2:1 balanced"; return false; }
+        if (face((int32_t)e, a, s).kind < 0) { *err = "forest is not 2:1 balanced"; return false; }
     neighbours((int32_t)e, &tmp);
     adj.insert(adj.end(), tmp.begin(), tmp.end());
     off[e + 1] = (int32_t)adj.size();
@@ -190,12 +230,12 @@ void Forest::face_lists(std::vector<int32_t>* conf, std::vector<int32_t>* mort,
   conf->clear(); mort->clear(); bnd->clear();
   for (int64_t e = 0; e < size(); ++e) {
     for (int a = 0; a < dim_; ++a) {
-      FaceInfo fi = classify((int32_t)e, a, 1);
+      const FaceInfo& fi = face((int32_t)e, a, 1);
       if (fi.kind == FACE_CONF) { conf->push_back((int32_t)e); conf->push_back(fi.nb[0]); conf->push_back(a); }
     }
     for (int a = 0; a < dim_; ++a)
       for (int s = 0; s < 2; ++s) {
-        FaceInfo fi = classify((int32_t)e, a, s);
+        const FaceInfo& fi = face((int32_t)e, a, s);
         if (fi.kind == FACE_COARSE) {
           mort->push_back((int32_t)e); mort->push_back(a); mort->push_back(s);
           for (int k = 0; k < 4; ++k) mort->push_back(k < (1 << (dim_ - 1)) ? fi.nb[k] : -1);
@@ -221,7 +261,7 @@ void Forest::halo(const std::vector<int64_t>& starts, int part, std::vector<int3
   for (int64_t e = starts[part]; e < starts[part + 1]; ++e)
     for (int a = 0; a < dim_; ++a)
       for (int s = 0; s < 2; ++s) {
-        FaceInfo fi = classify((int32_t)e, a, s);
+        const FaceInfo& fi = face((int32_t)e, a, s);
         int cnt = 0;
         if (fi.kind == FACE_CONF || fi.kind == FACE_FINE) cnt = 1;
         else if (fi.kind == FACE_COARSE) cnt = 1 << (dim_ - 1);
@@ -245,7 +285,7 @@ void Forest::connectivity(const std::vector<int32_t>& mort, std::vector<int32_t>
   for (int64_t e = 0; e < size(); ++e)
     for (int a = 0; a < dim_; ++a)
       for (int s = 0; s < 2; ++s) {
-        FaceInfo fi = classify((int32_t)e, a, s);
+        const FaceInfo& fi = face((int32_t)e, a, s);
         int32_t* r = conn->data() + ((size_t)e * nf + 2 * a + s) * 5;
         r[0] = fi.kind;
         if (fi.kind == FACE_CONF) r[1] = fi.nb[0];

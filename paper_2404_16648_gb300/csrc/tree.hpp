@@ -8,7 +8,6 @@
 #pragma once
 #include <cstdint>
 #include <string>
-#include <unordered_map>
 #include <vector>
 
 namespace dgl {
@@ -53,6 +52,8 @@ class Forest {
   // -1 if (level, c) is not a leaf.
   int32_t find(int level, const int32_t c[3]) const;
   FaceInfo classify(int32_t e, int axis, int side) const;
+  // classify() of every face, tabulated once per leaf set: face(e, a, s).
+  const FaceInfo& face(int32_t e, int axis, int side) const { return faces_[((size_t)e * dim_ + axis) * 2 + side]; }
 
   // One regrid pass.  Returns false (with `err`) if the forest is not 2:1 balanced.
   bool regrid(const std::vector<uint8_t>& tag, int B, int max_level, Forest* out,
@@ -85,7 +86,11 @@ class Forest {
   int base_[3] = {1, 1, 1};
   int max_level_ = 0;
   std::vector<Leaf> leaves_;
-  std::unordered_map<uint64_t, int32_t> index_;
+  // open-addressing index key(level, c) -> leaf, linear probing, power-of-two capacity
+  std::vector<uint64_t> hkeys_;
+  std::vector<int32_t> hvals_;
+  uint64_t hmask_ = 0;
+  std::vector<FaceInfo> faces_;   // [leaf][axis][side]
 };
 
 }  // namespace dgl
