@@ -242,7 +242,7 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
     alg_bytes = 0
     alg_flops = 0
     launches = 0
-    default_layout = 3 if D == 3 else 2
+    default_layout = 3 if (precision == "fp32" and D == 3) else 2
     per_node = measured_traffic(D, N, precision, default_layout if STAGE_KERNEL is None else STAGE_KERNEL)
     traffic = 0.0
     regrid_s = []

@@ -195,6 +195,18 @@ dg_status dg_step_state(dg_mesh* mesh, const void* q_in, void* q_out, double dt,
 dg_status dg_step_vjp(dg_mesh* mesh, const void* q_in, double dt, const void* lam_out,
                       void* lam_in, void* stream);
 
+/* One SSP-RK3 step from q_in (NV planes, device, FP64) to q_out that also keeps the step's three
+ * stage inputs q, q1, q2 in `record`: a caller-owned device buffer of 3 x (NV + 1) x E x
+ * (N+1)^dim doubles, each stage input stored as its NV planes followed by its P' plane.
+ * dg_step_vjp_record then transposes the step without recomputing it (the checkpointed
+ * gradient recomputes each segment once and keeps these records). */
+dg_status dg_step_record(dg_mesh* mesh, const void* q_in, void* q_out, void* record, double dt,
+                         void* stream);
+/* lam_in = (d step / d q_in)^T lam_out for the step held in `record` (see dg_step_record); the
+ * same result as dg_step_vjp on that step's q_in.  lam_in must not alias lam_out. */
+dg_status dg_step_vjp_record(dg_mesh* mesh, const void* record, double dt, const void* lam_out,
+                             void* lam_in, void* stream);
+
 /* Sets the mesh state from a nodal theta' field (elements x (N+1)^d doubles, host or device):
  * Theta' = 0, U = 0, rho' = -rho_bar theta' / (theta0 + theta') (same balance as dg_set_bubble). */
 dg_status dg_set_theta(dg_mesh* mesh, const double* theta, int where);
@@ -236,8 +248,8 @@ const char* dg_batch_last_error(const dg_batch* batch);
 /* Tuning options.  DG_OPT_STAGE_KERNEL selects the fused stage kernel's thread layout:
  * 0 = one thread per vertical node column, 1 = one thread per node, 2 = one thread per column
  * with all operands staged into shared memory by asynchronous copies, 3 = as 2 with two
- * threads per column (3D with odd N; other shapes run layout 2).  Default: 3 for 3D meshes,
- * 2 for 2D.  All compute the same operator; the option exists for tuning and
+ * threads per column (3D with odd N; other shapes run layout 2).  Default: 3 for FP32 3D
+ * meshes, 2 otherwise.  All compute the same operator; the option exists for tuning and
  * cross-checking. */
 enum { DG_OPT_STAGE_KERNEL = 1 };
 dg_status dg_set_option(dg_mesh* mesh, int32_t option, int64_t value);

@@ -3,9 +3,9 @@
 J(theta') = kinetic-energy integral after `nsteps` SSP-RK3 steps from the hydrostatic-pressure
 state of the nodal field theta' (the use case of variational data assimilation).  The forward
 pass steps through the C ABI and keeps a checkpoint of the state every `every` steps; the
-backward pass recomputes each segment's states from its checkpoint and runs the hand-written
-step transposes (dg_step_vjp) in reverse, then the transpose of the initial-state map
-(dg_theta_vjp).  Every operation runs in the library's kernels; this module only orders calls.
+backward pass recomputes each segment once from its checkpoint, keeping every step's stage
+inputs (dg_step_record), runs the hand-written step transposes on them (dg_step_vjp_record) in
+reverse, then the transpose of the initial-state map (dg_theta_vjp).  Every operation runs in the library's kernels; this module only orders calls.
 """
 import torch
 
@@ -47,14 +47,19 @@ class FinalKineticEnergy(torch.autograd.Function):
         theta, qT, *checkpoints = ctx.saved_tensors
         lam = mesh.ke_grad(qT) * grad_out
         spare = torch.empty_like(lam)
+        q = torch.empty_like(qT)
         for seg in reversed(range(len(checkpoints))):
             start = seg * every
             stop = min(start + every, nsteps)
-            states = [checkpoints[seg]]
-            for _ in range(start, stop - 1):
-                states.append(mesh.step_state(states[-1], torch.empty_like(qT), dt))
-            for i in reversed(range(stop - start)):
-                mesh.step_vjp(states[i], dt, lam, spare)
+            # recompute the segment once, keeping every step's stage inputs
+            records = []
+            q.copy_(checkpoints[seg])
+            for _ in range(start, stop):
+                rec = torch.empty(mesh.record_shape, dtype=torch.float64, device=qT.device)
+                mesh.step_record(q, q, rec, dt)
+                records.append(rec)
+            for rec in reversed(records):
+                mesh.step_vjp_record(rec, dt, lam, spare)
                 lam, spare = spare, lam
         grad_theta = mesh.theta_vjp(theta, lam)
         return grad_theta, None, None, None, None

@@ -21,6 +21,7 @@ namespace dgk {
 
 struct AdjArgs {
   const double* q;       // state [NV][plane]
+  const double* pp;      // P' of q, one plane (as the forward stage kernels read it)
   const double* lam;     // cotangent of L [NV][plane]
   const double* a1;      // optional [NV][plane]
   const double* a2;      // optional
@@ -40,6 +41,7 @@ struct AdjArgs {
 
 struct MortarAdjArgs {
   const double* q;
+  const double* pp;      // P' plane of q
   const double* lam;
   double* abuf;
   int64_t plane;
@@ -52,24 +54,31 @@ struct MortarAdjArgs {
   PhysC ph;
 };
 
-// Everything about one node's state that the Jacobians need.
+// Everything about one node's state that the Jacobians need (the sound speed c is formed only
+// where a face needs it, see sound_speed).
 template <int D>
 struct NodeLin {
-  double rinv, u[D], Theta, P, dPdT, c;
+  double rinv, u[D], Theta, P, dPdT;
 };
 
+// pp = P' of the node: read from the state's P' plane (the value the forward pass used), or
+// pressure_pert of Theta' where no plane exists.
 template <int D>
 __device__ __forceinline__ NodeLin<D> node_lin(const double* q, double rb, double Tb, double pb,
-                                               double invTb, const PhysC& ph) {
+                                               double pp, const PhysC& ph) {
   NodeLin<D> L;
   L.rinv = 1.0 / (rb + q[0]);
 #pragma unroll
   for (int b = 0; b < D; ++b) L.u[b] = q[1 + b] * L.rinv;
   L.Theta = Tb + q[D + 1];
-  L.P = pb + pressure_pert<kSeries>(q[D + 1], invTb, pb, ph);
+  L.P = pb + pp;
   L.dPdT = ph.gamma * L.P / L.Theta;                 // dP/dTheta of the EOS of Sec. 2.1
-  L.c = sqrt(ph.gamma * L.P * L.rinv);
   return L;
+}
+
+template <int D>
+__device__ __forceinline__ double sound_speed(const NodeLin<D>& L, double gamma) {
+  return sqrt(gamma * L.P * L.rinv);
 }
 
 // out += J_a(q)^T mu with J_a = dF_a/dq (perturbation variables).
@@ -87,19 +96,19 @@ __device__ __forceinline__ void flux_jac_t(const NodeLin<D>& L, int a, const dou
 }
 
 template <int D>
-__device__ __forceinline__ double speed_of(const NodeLin<D>& L, int a) {
-  return fabs(L.u[a]) + L.c;
+__device__ __forceinline__ double speed_of(const NodeLin<D>& L, double c, int a) {
+  return fabs(L.u[a]) + c;
 }
 
 // out += w * grad_q (|u_a| + c), c = sqrt(gamma P / rho).
 template <int D>
-__device__ __forceinline__ void speed_grad(const NodeLin<D>& L, int a, double gamma, double w,
-                                           double* out) {
+__device__ __forceinline__ void speed_grad(const NodeLin<D>& L, double c, int a, double gamma,
+                                           double w, double* out) {
   const double ua = L.u[a];
   const double sg = ua > 0.0 ? 1.0 : (ua < 0.0 ? -1.0 : 0.0);
-  out[0] += w * (-sg * ua * L.rinv - 0.5 * L.c * L.rinv);
+  out[0] += w * (-sg * ua * L.rinv - 0.5 * c * L.rinv);
   out[1 + a] += w * sg * L.rinv;
-  out[D + 1] += w * (0.5 * gamma * L.c / L.Theta);
+  out[D + 1] += w * (0.5 * gamma * c / L.Theta);
 }
 
 // Transpose of F* = (F(qm) + F(qp))/2 - lambda/2 (qp - qm), lambda = max(sm, sp) (low side on
@@ -110,7 +119,8 @@ __device__ __forceinline__ void rusanov_vjp(const double* qm, const NodeLin<D>& 
                                             const NodeLin<D>& Lp, int a, double gamma,
                                             const double* mu, double* om, double* op) {
   constexpr int NV = D + 2;
-  const double sm = speed_of<D>(Lm, a), sp = speed_of<D>(Lp, a);
+  const double cm = sound_speed<D>(Lm, gamma), cp = sound_speed<D>(Lp, gamma);
+  const double sm = speed_of<D>(Lm, cm, a), sp = speed_of<D>(Lp, cp, a);
   const bool low = sm >= sp;
   const double lam = low ? sm : sp;
   double mud = 0.0;
@@ -123,13 +133,13 @@ __device__ __forceinline__ void rusanov_vjp(const double* qm, const NodeLin<D>& 
     flux_jac_t<D>(Lm, a, hm, om);
 #pragma unroll
     for (int v = 0; v < NV; ++v) om[v] += 0.5 * lam * mu[v];
-    if (low) speed_grad<D>(Lm, a, gamma, -0.5 * mud, om);
+    if (low) speed_grad<D>(Lm, cm, a, gamma, -0.5 * mud, om);
   }
   if (op) {
     flux_jac_t<D>(Lp, a, hm, op);
 #pragma unroll
     for (int v = 0; v < NV; ++v) op[v] -= 0.5 * lam * mu[v];
-    if (!low) speed_grad<D>(Lp, a, gamma, -0.5 * mud, op);
+    if (!low) speed_grad<D>(Lp, cp, a, gamma, -0.5 * mud, op);
   }
 }
 
@@ -162,8 +172,9 @@ vjp_kernel(const AdjArgs A) {
   const int level = valid ? A.elem[e * 4] : 0;
   const double* bgp = A.bg + ((size_t)(valid ? e : 0) * n1 + idx[D - 1]) * 4;
   const double rb = valid ? bgp[0] : 1.0, Tb = valid ? bgp[1] : 1.0;
-  const double pb = valid ? bgp[2] : 1.0, iTb = valid ? bgp[3] : 1.0;
-  const NodeLin<D> L = node_lin<D>(q, rb, Tb, pb, iTb, A.ph);
+  const double pb = valid ? bgp[2] : 1.0;
+  const double ppn = valid ? A.pp[base] : 0.0;
+  const NodeLin<D> L = node_lin<D>(q, rb, Tb, pb, ppn, A.ph);
   __syncthreads();
   if (!valid) return;
   // buoyancy source -rho' g on the vertical momentum
@@ -209,7 +220,7 @@ vjp_kernel(const AdjArgs A) {
           qo[v] = A.q[(size_t)v * A.plane + no];
           mu[v] = sign * coef * (lam[v] - A.lam[(size_t)v * A.plane + no]);
         }
-        const NodeLin<D> Lo = node_lin<D>(qo, rb, Tb, pb, iTb, A.ph);
+        const NodeLin<D> Lo = node_lin<D>(qo, rb, Tb, pb, A.pp[no], A.ph);
         if (s) rusanov_vjp<D>(q, L, qo, Lo, a, A.ph.gamma, mu, acc, nullptr);
         else   rusanov_vjp<D>(qo, Lo, q, L, a, A.ph.gamma, mu, nullptr, acc);
       } else if (kind == FACE_WALL) {
@@ -217,7 +228,7 @@ vjp_kernel(const AdjArgs A) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) { gq[v] = q[v]; mu[v] = sign * coef * lam[v]; gacc[v] = 0.0; }
         gq[1 + a] = -q[1 + a];
-        const NodeLin<D> Lg = node_lin<D>(gq, rb, Tb, pb, iTb, A.ph);
+        const NodeLin<D> Lg = node_lin<D>(gq, rb, Tb, pb, ppn, A.ph);
         if (s) rusanov_vjp<D>(q, L, gq, Lg, a, A.ph.gamma, mu, acc, gacc);
         else   rusanov_vjp<D>(gq, Lg, q, L, a, A.ph.gamma, mu, gacc, acc);
         gacc[1 + a] = -gacc[1 + a];                      // mirror map is its own transpose
@@ -333,8 +344,9 @@ mortar_vjp_kernel(const MortarAdjArgs A) {
   }
   const int kf = (D == 3) ? nf / (n1 * n1) : nf / n1;
   const double* bd = A.bg + ((size_t)ef * n1 + kf) * 4;
-  const NodeLin<D> Lf = node_lin<D>(qf, bd[0], bd[1], bd[2], bd[3], A.ph);
-  const NodeLin<D> Lc = node_lin<D>(qc, bd[0], bd[1], bd[2], bd[3], A.ph);
+  const NodeLin<D> Lf = node_lin<D>(qf, bd[0], bd[1], bd[2], A.pp[(size_t)ef * NP + nf], A.ph);
+  const NodeLin<D> Lc = node_lin<D>(qc, bd[0], bd[1], bd[2], pressure_pert<kSeries>(qc[D + 1], bd[3], bd[2], A.ph),
+                                    A.ph);
   double gf[NV], gc[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) { gf[v] = 0.0; gc[v] = 0.0; }

@@ -330,12 +330,12 @@ dg_status rk3_on(dg_mesh* m, void* b0, void* b1, void* b2, double dt, cudaStream
 }
 
 // out = c1 a1 + c2 a2 + cb (b + dt J(q)^T lam), with the mortar transposes first.
-dg_status vjp_pass(dg_mesh* m, const double* q, const double* lam, const double* a1, double c1,
-                   const double* a2, double c2, const double* b, double cb, double dt, double* out,
-                   cudaStream_t s) {
+dg_status vjp_pass(dg_mesh* m, const double* q, const double* pp, const double* lam, const double* a1,
+                   double c1, const double* a2, double c2, const double* b, double cb, double dt,
+                   double* out, cudaStream_t s) {
   if (m->G > 0) {
     dgk::MortarAdjArgs M{};
-    M.q = q; M.lam = lam; M.abuf = m->d_abuf; M.plane = plane(m); M.G = (int32_t)m->G;
+    M.q = q; M.pp = pp; M.lam = lam; M.abuf = m->d_abuf; M.plane = plane(m); M.G = (int32_t)m->G;
     M.groups = m->d_groups; M.elem = m->d_elem; M.bg = m->d_bg; M.ops = m->d_opsd; M.ph = m->ph;
     for (int l = 0; l < dgk::kMaxLevels; ++l)
       for (int a = 0; a < 3; ++a) M.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
@@ -343,7 +343,7 @@ dg_status vjp_pass(dg_mesh* m, const double* q, const double* lam, const double*
     CU(cudaGetLastError());
   }
   dgk::AdjArgs A{};
-  A.q = q; A.lam = lam; A.a1 = a1; A.a2 = a2; A.b = b; A.out = out; A.abuf = m->d_abuf;
+  A.q = q; A.pp = pp; A.lam = lam; A.a1 = a1; A.a2 = a2; A.b = b; A.out = out; A.abuf = m->d_abuf;
   A.plane = plane(m); A.E = (int32_t)m->E; A.elem = m->d_elem; A.conn = m->d_conn; A.bg = m->d_bg;
   A.ops = m->d_opsd; A.c1 = c1; A.c2 = c2; A.cb = cb; A.dt = dt; A.ph = m->ph;
   for (int l = 0; l < dgk::kMaxLevels; ++l)
@@ -357,6 +357,24 @@ dg_status vjp_pass(dg_mesh* m, const double* q, const double* lam, const double*
 
 extern "C" {
 
+// Transpose of one SSP-RK3 step given its three stage inputs b0 = q, b1 = q1, b2 = q2 (each
+// NV planes followed by its P' plane).
+dg_status step_transpose(dg_mesh* m, const double* b0, const double* b1, const double* b2, double dt,
+                         const double* lo, double* lam_in, cudaStream_t s) {
+  double* l2 = m->adj_l[0];
+  double* l1 = m->adj_l[1];
+  const double* p0 = (const double*)pp_plane(m, (void*)b0);
+  const double* p1 = (const double*)pp_plane(m, (void*)b1);
+  const double* p2 = (const double*)pp_plane(m, (void*)b2);
+  // q3 = 1/3 q + 2/3 (q2 + dt L(q2)):   lam_q2 = 2/3 (lam + dt J(q2)^T lam)
+  dg_status st = vjp_pass(m, b2, p2, lo, nullptr, 0.0, nullptr, 0.0, lo, 2.0 / 3.0, dt, l2, s);
+  // q2 = 3/4 q + 1/4 (q1 + dt L(q1)):   lam_q1 = 1/4 (lam_q2 + dt J(q1)^T lam_q2)
+  if (st == DG_OK) st = vjp_pass(m, b1, p1, l2, nullptr, 0.0, nullptr, 0.0, l2, 0.25, dt, l1, s);
+  // q1 = q + dt L(q):   lam_q = 1/3 lam + 3/4 lam_q2 + lam_q1 + dt J(q)^T lam_q1
+  if (st == DG_OK) st = vjp_pass(m, b0, p0, l1, lo, 1.0 / 3.0, l2, 0.75, l1, 1.0, dt, lam_in, s);
+  return st;
+}
+
 dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void* stream) {
   if (!m || !q || !lam || !out) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
@@ -364,8 +382,10 @@ dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void
   dg_status st = ensure_adjoint_ws(m);
   if (st != DG_OK) return st;
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
-  return vjp_pass(m, (const double*)q, (const double*)lam, nullptr, 0.0, nullptr, 0.0, nullptr, 1.0,
-                  1.0, (double*)out, s);
+  const void* theta = (const char*)q + (size_t)(m->NV - 1) * plane(m) * m->tsize;
+  CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->d_bgc, m->ph, m->d_ppscratch, s));
+  return vjp_pass(m, (const double*)q, (const double*)m->d_ppscratch, (const double*)lam, nullptr, 0.0,
+                  nullptr, 0.0, nullptr, 1.0, 1.0, (double*)out, s);
 }
 
 dg_status dg_step_state(dg_mesh* m, const void* q_in, void* q_out, double dt, int32_t nsteps,
@@ -398,17 +418,41 @@ dg_status dg_step_vjp(dg_mesh* m, const void* q_in, double dt, const void* lam_o
   if (st == DG_OK) st = launch_rhs_pass(m, b0, pp_plane(m, b0), b0, b1, pp_plane(m, b1), 1, dt, 0.0, 1.0, s);
   if (st == DG_OK) st = launch_rhs_pass(m, b1, pp_plane(m, b1), b0, b2, pp_plane(m, b2), 1, dt, 0.75, 0.25, s);
   if (st != DG_OK) return st;
-  const double* lo = (const double*)lam_out;
-  double* l2 = m->adj_l[0];
-  double* l1 = m->adj_l[1];
-  // q3 = 1/3 q + 2/3 (q2 + dt L(q2)):   lam_q2 = 2/3 (lam + dt J(q2)^T lam)
-  st = vjp_pass(m, (const double*)b2, lo, nullptr, 0.0, nullptr, 0.0, lo, 2.0 / 3.0, dt, l2, s);
-  // q2 = 3/4 q + 1/4 (q1 + dt L(q1)):   lam_q1 = 1/4 (lam_q2 + dt J(q1)^T lam_q2)
-  if (st == DG_OK) st = vjp_pass(m, (const double*)b1, l2, nullptr, 0.0, nullptr, 0.0, l2, 0.25, dt, l1, s);
-  // q1 = q + dt L(q):   lam_q = 1/3 lam + 3/4 lam_q2 + lam_q1 + dt J(q)^T lam_q1
+  return step_transpose(m, (const double*)b0, (const double*)b1, (const double*)b2, dt,
+                        (const double*)lam_out, (double*)lam_in, s);
+}
+
+dg_status dg_step_record(dg_mesh* m, const void* q_in, void* q_out, void* record, double dt, void* stream) {
+  if (!m || !q_in || !q_out || !record || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
+  if (m->desc.nu > 0.0) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint has no viscous term");
+  dg_status st = ensure_adjoint_ws(m);
+  if (st != DG_OK) return st;
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  const size_t sb = (size_t)(m->NV + 1) * plane(m);      // doubles per recorded state
+  double* r0 = (double*)record;
+  double* r1 = r0 + sb;
+  double* r2 = r1 + sb;
+  st = stage_in(m, q_in, r0, s);
+  if (st == DG_OK) st = launch_rhs_pass(m, r0, pp_plane(m, r0), r0, r1, pp_plane(m, r1), 1, dt, 0.0, 1.0, s);
+  if (st == DG_OK) st = launch_rhs_pass(m, r1, pp_plane(m, r1), r0, r2, pp_plane(m, r2), 1, dt, 0.75, 0.25, s);
   if (st == DG_OK)
-    st = vjp_pass(m, (const double*)b0, l1, lo, 1.0 / 3.0, l2, 0.75, l1, 1.0, dt, (double*)lam_in, s);
+    st = launch_rhs_pass(m, r2, pp_plane(m, r2), r0, q_out, pp_plane(m, m->adj_q[0]), 1, dt, 1.0 / 3.0, 2.0 / 3.0, s);
   return st;
+}
+
+dg_status dg_step_vjp_record(dg_mesh* m, const void* record, double dt, const void* lam_out, void* lam_in,
+                             void* stream) {
+  if (!m || !record || !lam_out || !lam_in || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (lam_out == lam_in) return fail(m, DG_ERR_ARG, "lam_out and lam_in must not alias");
+  if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
+  if (m->desc.nu > 0.0) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint has no viscous term");
+  dg_status st = ensure_adjoint_ws(m);
+  if (st != DG_OK) return st;
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  const size_t sb = (size_t)(m->NV + 1) * plane(m);
+  const double* r0 = (const double*)record;
+  return step_transpose(m, r0, r0 + sb, r0 + 2 * sb, dt, (const double*)lam_out, (double*)lam_in, s);
 }
 
 dg_status dg_set_theta(dg_mesh* m, const double* theta, int where) {
@@ -488,7 +532,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   m->NV = m->D + 2; m->NSUB = 1 << (m->D - 1);
   m->prec = desc->precision;
   m->tsize = m->prec == DG_FP64 ? sizeof(double) : sizeof(float);
-  m->variant = m->D == 3 ? 3 : 2;   // fastest measured layouts (3 falls back to 2 for even N)
+  m->variant = (m->prec == DG_FP32_PERT && m->D == 3) ? 3 : 2;   // fastest measured layouts
   m->stream = (cudaStream_t)stream;
   m->ph.theta0 = desc->theta0; m->ph.p0 = desc->p0; m->ph.g = desc->g; m->ph.R = desc->R;
   m->ph.cp = desc->cp; m->ph.cv = desc->cp - desc->R; m->ph.gamma = desc->cp / (desc->cp - desc->R);

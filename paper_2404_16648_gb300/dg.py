@@ -26,7 +26,7 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_adapt", "dg_indicator", "dg_primitives", "dg_integrals", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
             "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
-            "dg_step_state", "dg_step_vjp", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
+            "dg_step_state", "dg_step_vjp", "dg_step_record", "dg_step_vjp_record", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
             "dg_bubble_theta", "dg_forest_partition", "dg_forest_halo", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
             "dg_batch_run", "dg_batch_sync", "dg_batch_autotune", "dg_batch_last_error",
             "dg_last_error", "dg_version"]
@@ -107,6 +107,8 @@ def load_library(path=None):
         "dg_rhs_vjp": (i32, [vp, vp, vp, vp, vp]),
         "dg_step_state": (i32, [vp, vp, vp, dbl, i32, vp]),
         "dg_step_vjp": (i32, [vp, vp, dbl, vp, vp, vp]),
+        "dg_step_record": (i32, [vp, vp, vp, vp, ctypes.c_double, vp]),
+        "dg_step_vjp_record": (i32, [vp, vp, ctypes.c_double, vp, vp, vp]),
         "dg_set_theta": (i32, [vp, vp, ctypes.c_int]),
         "dg_theta_vjp": (i32, [vp, vp, vp, vp, vp]),
         "dg_ke_grad": (i32, [vp, vp, vp, vp]),
@@ -319,6 +321,27 @@ class Mesh:
                                          self._stream_ptr(stream)))
         return lam_in
 
+    @property
+    def record_shape(self):
+        """Shape of a dg_step_record buffer: 3 stage inputs x (NV + 1) planes x elements x nodes."""
+        return (3, self.nv + 1, self.num_elements, (self.N + 1) ** self.dim)
+
+    def step_record(self, q_in, q_out, record, dt, stream=None):
+        self._check(self.lib.dg_step_record(self.h, ctypes.c_void_p(q_in.data_ptr()),
+                                            ctypes.c_void_p(q_out.data_ptr()),
+                                            ctypes.c_void_p(record.data_ptr()), float(dt),
+                                            self._stream_ptr(stream)))
+        return q_out
+
+    def step_vjp_record(self, record, dt, lam_out, lam_in=None, stream=None):
+        torch = _torch()
+        if lam_in is None:
+            lam_in = torch.empty_like(lam_out)
+        self._check(self.lib.dg_step_vjp_record(self.h, ctypes.c_void_p(record.data_ptr()), float(dt),
+                                                ctypes.c_void_p(lam_out.data_ptr()),
+                                                ctypes.c_void_p(lam_in.data_ptr()), self._stream_ptr(stream)))
+        return lam_in
+
     def set_theta(self, theta):
         """Initial state from a nodal theta' field [E, (N+1)^d] (numpy or device tensor)."""
         if tuple(theta.shape) != (self.num_elements, self.np_):
@@ -389,7 +412,7 @@ class Mesh:
     def set_stage_kernel(self, layout):
         """0: one thread per vertical node column; 1: one thread per node; 2: column layout with
         asynchronous staging of every operand in shared memory; 3: as 2 with two threads per
-        column (3D, odd N).  Default: 3 for 3D meshes, 2 for 2D."""
+        column (3D, odd N).  Default: 3 for FP32 3D meshes, 2 otherwise."""
         self._check(self.lib.dg_set_option(self.h, 1, int(layout)))
 
     def enable_timing(self, on=True):
