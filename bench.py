@@ -280,7 +280,7 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
     return m, out
 
 
-def run_e2e(pkg, m, cfg, steps, regrid_every):
+def run_e2e(pkg, m, cfg, steps, regrid_every, world=1):
     """Same metric through the public API with host buffers: each step copies the state in from
     pinned host memory, advances one step and copies the state and the integrals back."""
     import torch
@@ -291,6 +291,7 @@ def run_e2e(pkg, m, cfg, steps, regrid_every):
     torch.cuda.synchronize()
     h2d = d2h = 0
     dof = 0
+    _barrier(world)
     t0 = time.perf_counter()
     for i in range(steps):
         if tuple(host.shape) != m.state_shape:
@@ -307,8 +308,8 @@ def run_e2e(pkg, m, cfg, steps, regrid_every):
         if regrid_every and (i + 1) % regrid_every == 0:
             m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
     torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    return dict(value=dof / sec, unit=METRIC, h2d_bytes_per_step=h2d // steps,
+    sec = _barrier_max(time.perf_counter() - t0, world)      # the slowest rank sets the job time
+    return dict(value=world * dof / sec, unit=METRIC, h2d_bytes_per_step=h2d // steps,
                 d2h_bytes_per_step=d2h // steps)
 
 
@@ -471,7 +472,7 @@ def main():
     peaks, peak_kind = _peaks()
     sampler = ClockSampler(local)
     m32, r32 = run_path(pkg, cfg, "fp32", args.steps, args.warmup, regrid_every, sampler, world)
-    e2e = run_e2e(pkg, m32, cfg, max(4, min(args.steps, 20)), regrid_every)
+    e2e = run_e2e(pkg, m32, cfg, max(4, min(args.steps, 20)), regrid_every, world)
     m32.close()
     r64 = None
     if not args.no_fp64:
