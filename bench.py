@@ -344,6 +344,39 @@ def run_adjoint(pkg):
             "forward_dof_stage_per_s": 3 * nsteps * nodes / f}
 
 
+def run_cold2d(pkg, steps=200):
+    """The 2D tree-AMR cold bubble with viscosity (32 x 8 roots on 25.6 x 6.4 km, N = 5, up to 3
+    levels, nu = 75 m^2/s by BR1, FP64, regrid every 10 steps inside the timed region)."""
+    import torch
+    cfg = workloads.COLD_2D
+    m = pkg.Mesh(2, cfg["N"], cfg["base"], cfg["length"], max_level=cfg["max_level"], nu=cfg["nu"])
+    pkg.adapt_initial(m, cfg["bubble"], cfg["threshold"], cfg["buffer"])
+    m.step(cfg["dt"], 10)
+    m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
+    torch.cuda.synchronize()
+    M0 = m.integrals()
+    NP = (cfg["N"] + 1) ** 2
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    dof = 0
+    ev0.record()
+    for i in range(steps):
+        dof += 3 * m.num_elements * NP
+        m.step(cfg["dt"], 1)
+        if (i + 1) % cfg["regrid_every"] == 0:
+            m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    M1 = m.integrals()
+    out = {"workload": cfg["name"], "precision": "fp64", "nu": cfg["nu"], "steps": steps,
+           "regrid_every": cfg["regrid_every"], "elements": m.num_elements, "mortar_groups": m.num_mortars,
+           "value": dof / (ms / 1e3), "unit": METRIC, "ms_per_step": ms / steps,
+           "mass_rel_change": abs(M1[0] - M0[0]) / M0[0]}
+    m.close()
+    return out
+
+
 def run_batch(pkg, steps=500, compare_steps=50):
     """Batched workload: 256 seeded 2D bubble instances (mesh 10x10 ... 64x32, N 3..7, FP32/FP64
     50/50, per-instance dt), autotuned layouts, `steps` graph-replayed SSP-RK3 steps; and the same
@@ -429,6 +462,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-cold2d", action="store_true",
+                    help="skip the 2D viscous cold-bubble leg")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP32-vs-FP64 field comparison over the workload's full step count")
     ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2, 3],
@@ -517,6 +552,8 @@ def main():
         line["adjoint"] = run_adjoint(pkg)
     if not args.no_batch:
         line["batch"] = run_batch(pkg)
+    if not args.no_cold2d:
+        line["cold2d"] = run_cold2d(pkg)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, nel, E, sec = oracle_sample(cfg, n_elem=1024, reps=1)
         line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",

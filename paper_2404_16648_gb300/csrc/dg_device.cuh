@@ -65,6 +65,15 @@ template <int K>
 __device__ __forceinline__ double pressure_pert(double tp, double invTb, double pb,
                                                 const PhysC& ph) {
   const double x = tp * invTb;
+  if (fabs(x) <= 0.0009765625) {
+    // |x| <= 2^-10: six terms; the first term left out, binom(gamma, 7) x^7 with
+    // |binom(gamma, 7)| < 5e-3, is below 4e-24 P_bar, i.e. 3e-21 of P', far under its rounding
+    constexpr int K6 = K < 6 ? K : 6;
+    double p = ph.binom[K6 - 1];
+#pragma unroll
+    for (int k = K6 - 2; k >= 0; --k) p = fma(p, x, ph.binom[k]);
+    return __dmul_rn(pb, __dmul_rn(p, x));
+  }
   if (fabs(x) <= 0.03125) {
     double p = ph.binom[K - 1];
 #pragma unroll

@@ -261,8 +261,16 @@ __device__ __forceinline__ void stage_body_half(const StageArgs& A, int64_t e) {
     for (int r = 0; r < K2; ++r) {
       T Dr[n1];
       const T* row = sDz + (h * K2 + r) * n1;
+      if constexpr (VEC) {
 #pragma unroll
-      for (int j = 0; j < n1; ++j) Dr[j] = row[j];
+        for (int j = 0; j < n1; j += 4) {
+          const float4 d4 = *reinterpret_cast<const float4*>(row + j);
+          Dr[j] = (T)d4.x; Dr[j + 1] = (T)d4.y; Dr[j + 2] = (T)d4.z; Dr[j + 3] = (T)d4.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < n1; ++j) Dr[j] = row[j];
+      }
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         T s = (T)0;

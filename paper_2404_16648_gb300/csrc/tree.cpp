@@ -29,6 +29,17 @@ static uint64_t mix64(uint64_t x) {   // splitmix64 finaliser
 }
 static constexpr uint64_t kEmpty = ~0ULL;   // never a key: levels < 32, coordinates < 2^19
 
+// fn(e0, e1) over [0, n) split into contiguous ranges on up to 16 threads (one below 8192).
+template <class F>
+static void parallel_ranges(int64_t n, F fn) {
+  int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
+  if (n < 8192) nt = 1;
+  if (nt == 1) { fn((int64_t)0, n); return; }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t) th.emplace_back(fn, n * t / nt, n * (t + 1) / nt);
+  for (auto& x : th) x.join();
+}
+
 void Forest::set_leaves(std::vector<Leaf> leaves) {
   leaves_ = std::move(leaves);
   uint64_t cap = 16;
@@ -47,20 +58,11 @@ void Forest::set_leaves(std::vector<Leaf> leaves) {
   // change the result
   const int64_t n = (int64_t)leaves_.size();
   faces_.assign((size_t)n * dim_ * 2, FaceInfo{FACE_WALL, {-1, -1, -1, -1}});
-  auto fill = [this](int64_t e0, int64_t e1) {
+  parallel_ranges(n, [this](int64_t e0, int64_t e1) {
     for (int64_t e = e0; e < e1; ++e)
       for (int a = 0; a < dim_; ++a)
         for (int s = 0; s < 2; ++s) faces_[((size_t)e * dim_ + a) * 2 + s] = classify((int32_t)e, a, s);
-  };
-  int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
-  if (n < 8192) nt = 1;
-  if (nt == 1) {
-    fill(0, n);
-  } else {
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t) th.emplace_back(fill, n * t / nt, n * (t + 1) / nt);
-    for (auto& x : th) x.join();
-  }
+  });
 }
 
 int32_t Forest::root_index(const Leaf& l) const {

@@ -25,10 +25,10 @@ RTB_2D = dict(name="rtb2d_10x10_N4", dim=2, N=4, base=(10, 10), length=(1000.0, 
               dt=0.02, steps=100, threshold=None, buffer=2, regrid_every=None)
 
 # 2D x-z, 32 x 8 base, N = 5, up to 3 levels: cold bubble (theta' = -7.5 (1 + cos(pi r)))
-# dt reading: 0.01 s (0.05 s is above the explicit limit at 100 m); viscosity not supported
+# dt reading: 0.01 s (0.05 s is above the explicit limit at 100 m); viscosity 75 m^2/s (BR1)
 COLD_2D = dict(name="cold2d_32x8_N5_L3", dim=2, N=5, base=(32, 8), length=(25600.0, 6400.0),
                max_level=3, bubble=dict(center=(0.0, 3000.0), radius=(4000.0, 2000.0), amp=-7.5),
-               dt=0.01, steps=2000, threshold=0.1, buffer=2, regrid_every=10)
+               dt=0.01, steps=2000, threshold=0.1, buffer=2, regrid_every=10, nu=75.0)
 
 # 3D octree, 16^3 base, N = 7, 2 extra levels where |theta'| > 0.05 K: warm bubble
 # theta' = 2 (1 + cos(pi r / 2 km)) at (5, 5, 2) km; dt reading 0.005 s; buffer reading B = 2
