@@ -35,6 +35,7 @@ struct AdjArgs {
   const double* bg;      // [E][N+1][4]
   const double* ops;     // D, P0, P1, C0, C1, w, x
   double inv2h[kMaxLevels][3];
+  double lift[kMaxLevels][3];   // (2/h_a) / w0 per level and axis
   double c1, c2, cb, dt;
   PhysC ph;
 };
@@ -58,7 +59,7 @@ struct MortarAdjArgs {
 // where a face needs it, see sound_speed).
 template <int D>
 struct NodeLin {
-  double rinv, u[D], Theta, P, dPdT;
+  double rinv, u[D], Theta, iTheta, P, dPdT;
 };
 
 // pp = P' of the node: read from the state's P' plane (the value the forward pass used), or
@@ -71,8 +72,9 @@ __device__ __forceinline__ NodeLin<D> node_lin(const double* q, double rb, doubl
 #pragma unroll
   for (int b = 0; b < D; ++b) L.u[b] = q[1 + b] * L.rinv;
   L.Theta = Tb + q[D + 1];
+  L.iTheta = 1.0 / L.Theta;
   L.P = pb + pp;
-  L.dPdT = ph.gamma * L.P / L.Theta;                 // dP/dTheta of the EOS of Sec. 2.1
+  L.dPdT = ph.gamma * L.P * L.iTheta;                // dP/dTheta of the EOS of Sec. 2.1
   return L;
 }
 
@@ -108,7 +110,7 @@ __device__ __forceinline__ void speed_grad(const NodeLin<D>& L, double c, int a,
   const double sg = ua > 0.0 ? 1.0 : (ua < 0.0 ? -1.0 : 0.0);
   out[0] += w * (-sg * ua * L.rinv - 0.5 * c * L.rinv);
   out[1 + a] += w * sg * L.rinv;
-  out[D + 1] += w * (0.5 * gamma * c / L.Theta);
+  out[D + 1] += w * (0.5 * gamma * c * L.iTheta);
 }
 
 // Transpose of F* = (F(qm) + F(qp))/2 - lambda/2 (qp - qm), lambda = max(sm, sp) (low side on
@@ -143,6 +145,43 @@ __device__ __forceinline__ void rusanov_vjp(const double* qm, const NodeLin<D>& 
   }
 }
 
+// Rusanov transpose seen from one side only (the element's own node on a conforming face): the
+// flux-Jacobian part 0.5 mu is returned as a cotangent `cot` (applied later through the node's
+// J_a^T together with its other cotangents along axis a); acc gets the dissipation and
+// wave-speed parts.  The neighbour enters through its state qo and wave speed so alone.
+template <int D>
+__device__ __forceinline__ void rusanov_vjp_own(const double* q, const NodeLin<D>& L, double c_own,
+                                                const double* qo, double so, int a, bool own_low,
+                                                double gamma, const double* mu, double* cot, double* acc) {
+  constexpr int NV = D + 2;
+  const double s_own = speed_of<D>(L, c_own, a);
+  const double sm = own_low ? s_own : so, sp = own_low ? so : s_own;
+  const bool low = sm >= sp;
+  const double lam = low ? sm : sp;
+  double mud = 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) mud += own_low ? mu[v] * (qo[v] - q[v]) : mu[v] * (q[v] - qo[v]);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) cot[v] += 0.5 * mu[v];
+  if (own_low) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] += 0.5 * lam * mu[v];
+    if (low) speed_grad<D>(L, c_own, a, gamma, -0.5 * mud, acc);
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] -= 0.5 * lam * mu[v];
+    if (!low) speed_grad<D>(L, c_own, a, gamma, -0.5 * mud, acc);
+  }
+}
+
+// |u_a| + c of a neighbour node (all the transpose needs from it).
+template <int D>
+__device__ __forceinline__ double neighbour_speed(const double* q, double rb, double pb, double pp, int a,
+                                                  double gamma) {
+  const double rinv = 1.0 / (rb + q[0]);
+  return fabs(q[1 + a] * rinv) + sqrt(gamma * (pb + pp) * rinv);
+}
+
 template <int D, int N, int EPB>
 __global__ void __launch_bounds__(EPB * ipow(N + 1, D))
 vjp_kernel(const AdjArgs A) {
@@ -152,7 +191,6 @@ vjp_kernel(const AdjArgs A) {
   __shared__ double sL[EPB][NV][NP];
   const int tid = threadIdx.x;
   for (int i = tid; i < n1 * n1; i += blockDim.x) sD[i] = A.ops[i];
-  const double w0 = A.ops[5 * n1 * n1];
   const int le = tid / NP, n = tid - le * NP;
   const int64_t e = (int64_t)blockIdx.x * EPB + le;
   const bool valid = e < A.E;
@@ -179,24 +217,26 @@ vjp_kernel(const AdjArgs A) {
   if (!valid) return;
   // buoyancy source -rho' g on the vertical momentum
   acc[0] += -A.ph.g * lam[D];
-  // volume: L -= (2/h_a) D_a F_a  ->  mu_a = -(2/h_a) D_a^T Lambda, then J_a^T mu_a
+  // Every own-node term along axis a goes through J_a(q)^T: the volume cotangent
+  // mu_a = -(2/h_a) D_a^T Lambda, the face lift's -n (2/h)/w0 Lambda and the Rusanov flux part
+  // are summed in cot[a] first and transposed once per axis.
+  double cot[D][NV];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     const int stride = ipow(n1, a);
     const int ia = idx[a];
     const int b0 = n - ia * stride;
     const double s2h = A.inv2h[level][a];
-    double mu[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       double s = 0.0;
 #pragma unroll
       for (int i = 0; i < n1; ++i) s += sD[i * n1 + ia] * sL[le][v][b0 + i * stride];
-      mu[v] = -s2h * s;
+      cot[a][v] = -s2h * s;
     }
-    flux_jac_t<D>(L, a, mu, acc);
   }
   // faces
+  double c_own = -1.0;                         // sound speed of this node, formed on first use
 #pragma unroll
   for (int a = 0; a < D; ++a) {
 #pragma unroll
@@ -204,13 +244,11 @@ vjp_kernel(const AdjArgs A) {
       if (idx[a] != (s ? N : 0)) continue;
       const int32_t* c = A.conn + ((size_t)e * 2 * D + 2 * a + s) * 5;
       const int kind = c[0];
-      const double coef = A.inv2h[level][a] / w0;
+      const double coef = A.lift[level][a];
       const double sign = s ? -1.0 : 1.0;
       // own flux in the lift: L += sign coef (F* - F(q))
-      double m1[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) m1[v] = -sign * coef * lam[v];
-      flux_jac_t<D>(L, a, m1, acc);
+      for (int v = 0; v < NV; ++v) cot[a][v] += -sign * coef * lam[v];
       if (kind == FACE_CONF) {
         const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
         const size_t no = (size_t)c[1] * NP + n + ((s ? 0 : N) - idx[a]) * stride_a;
@@ -220,9 +258,9 @@ vjp_kernel(const AdjArgs A) {
           qo[v] = A.q[(size_t)v * A.plane + no];
           mu[v] = sign * coef * (lam[v] - A.lam[(size_t)v * A.plane + no]);
         }
-        const NodeLin<D> Lo = node_lin<D>(qo, rb, Tb, pb, A.pp[no], A.ph);
-        if (s) rusanov_vjp<D>(q, L, qo, Lo, a, A.ph.gamma, mu, acc, nullptr);
-        else   rusanov_vjp<D>(qo, Lo, q, L, a, A.ph.gamma, mu, nullptr, acc);
+        if (c_own < 0.0) c_own = sound_speed<D>(L, A.ph.gamma);
+        const double so = neighbour_speed<D>(qo, rb, pb, A.pp[no], a, A.ph.gamma);
+        rusanov_vjp_own<D>(q, L, c_own, qo, so, a, s == 1, A.ph.gamma, mu, cot[a], acc);
       } else if (kind == FACE_WALL) {
         double gq[NV], mu[NV], gacc[NV];
 #pragma unroll
@@ -247,6 +285,8 @@ vjp_kernel(const AdjArgs A) {
       }
     }
   }
+#pragma unroll
+  for (int a = 0; a < D; ++a) flux_jac_t<D>(L, a, cot[a], acc);
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const size_t k = (size_t)v * A.plane + base;

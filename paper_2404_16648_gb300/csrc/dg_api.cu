@@ -347,7 +347,10 @@ dg_status vjp_pass(dg_mesh* m, const double* q, const double* pp, const double* 
   A.plane = plane(m); A.E = (int32_t)m->E; A.elem = m->d_elem; A.conn = m->d_conn; A.bg = m->d_bg;
   A.ops = m->d_opsd; A.c1 = c1; A.c2 = c2; A.cb = cb; A.dt = dt; A.ph = m->ph;
   for (int l = 0; l < dgk::kMaxLevels; ++l)
-    for (int a = 0; a < 3; ++a) A.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+    for (int a = 0; a < 3; ++a) {
+      A.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+      A.lift[l][a] = A.inv2h[l][a] / m->basis.w[0];
+    }
   if (!dgk::launch_vjp(m->D, m->N, A, s)) return fail(m, DG_ERR_UNSUPPORTED, "adjoint kernel not compiled");
   CU(cudaGetLastError());
   return DG_OK;
