@@ -190,6 +190,9 @@ void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const 
       // 2/h = (2/h_root) 2^level: power-of-two scaling is exact
       A->inv2hd[l][a] = std::ldexp(2.0 / m->root_h[a], l);
       A->inv2hf[l][a] = (float)A->inv2hd[l][a];
+      // the same quotient the kernels formed per face: T(2/h) / T(w0), one IEEE division
+      A->liftd[l][a] = A->inv2hd[l][a] / m->basis.w[0];
+      A->liftf[l][a] = A->inv2hf[l][a] / (float)m->basis.w[0];
     }
   A->dt = dt; A->ca = ca; A->cb = cb; A->mode = mode; A->variant = m->variant; A->ph = m->ph;
   A->plane32 = (int32_t)plane(m);

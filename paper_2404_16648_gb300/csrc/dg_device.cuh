@@ -205,6 +205,8 @@ struct StageArgs {
   const void* ops;       // (T) D, P0, P1, C0, C1 (n1 x n1 each), w (n1)
   float inv2hf[kMaxLevels][3];    // 2/h per level and axis
   double inv2hd[kMaxLevels][3];
+  float liftf[kMaxLevels][3];     // face lift factor (2/h) / w0 per level and axis
+  double liftd[kMaxLevels][3];
   double dt, ca, cb;
   int32_t mode;
   int32_t variant;       // 0: column kernel, 1: node-per-thread kernel, 2: column kernel with async staging
@@ -230,6 +232,14 @@ struct MortarArgs {
 
 template <class T> __device__ __forceinline__ T gamma_of(const PhysC& ph, float gf) {
   return sizeof(T) == 4 ? (T)gf : (T)ph.gamma;
+}
+
+template <class T> __device__ __forceinline__ T lift_of(const StageArgs& A, int level, int a);
+template <> __device__ __forceinline__ float lift_of<float>(const StageArgs& A, int level, int a) {
+  return A.liftf[level][a];
+}
+template <> __device__ __forceinline__ double lift_of<double>(const StageArgs& A, int level, int a) {
+  return A.liftd[level][a];
 }
 
 template <class T> __device__ __forceinline__ T inv2h_of(const StageArgs& A, int level, int a);
@@ -264,7 +274,6 @@ __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) 
   const int tid = threadIdx.x;
   const T* ops = (const T*)A.ops;
   for (int i = tid; i < n1 * n1; i += blockDim.x) sD[i] = ops[i];
-  const T w0 = ops[5 * n1 * n1];
   const T gamma = gamma_of<T>(A.ph, A.gammaf);
   const int le = tid / NP, n = tid - le * NP;
   const int64_t e = e0 + le;
@@ -283,11 +292,12 @@ __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) 
   for (int v = 0; v < NV; ++v) { q[v] = (T)0; acc[v] = (T)0; }
 #pragma unroll
   for (int a = 0; a < D; ++a) inv2h[a] = (T)0;
+  int level = 0;
   if (valid) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) q[v] = qe[v * P + n];
     pp = ppe[n];
-    const int level = A.elem[e * 4];
+    level = A.elem[e * 4];
 #pragma unroll
     for (int a = 0; a < D; ++a) inv2h[a] = inv2h_of<T>(A, level, a);
     const T* b = (const T*)A.bgt + ((size_t)e * n1 + idx[D - 1]) * 4;
@@ -362,7 +372,7 @@ __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) 
 #pragma unroll
         for (int v = 0; v < NV; ++v) Fs[v] = src[(size_t)v * NF];
       }
-      const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
+      const T coef = s ? -lift_of<T>(A, level, a) : lift_of<T>(A, level, a);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += coef * (Fs[v] - Fo[v]);
     }

@@ -126,7 +126,6 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
     }
   }
   cp_async_commit();
-  const T w0 = ops[5 * n1 * n1];
   const T gamma = gamma_of<T>(A.ph, A.gammaf);
   const T g = sizeof(T) == 4 ? (T)A.gf : (T)A.ph.g;
   T inv2h[D];
@@ -270,7 +269,7 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
 #pragma unroll
       for (int v = 0; v < NV; ++v) Fs[v] = nb[v * NF + fn];
     }
-    const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
+    const T coef = s ? -lift_of<T>(A, level, a) : lift_of<T>(A, level, a);
 #pragma unroll
     for (int v = 0; v < NV; ++v) L[v] = coef * (Fs[v] - Fo[v]);
   };

@@ -74,7 +74,6 @@ stage_kernel_col(const __grid_constant__ StageArgs A) {
   const int ci = t % n1, cj = (D == 3) ? t / n1 : 0;
   const T* ops = (const T*)A.ops;
   for (int x = tid; x < n1 * n1; x += blockDim.x) sDh[x] = ops[x];
-  const T w0 = ops[5 * n1 * n1];
   const T gamma = gamma_of<T>(A.ph, A.gammaf);
   const T g = sizeof(T) == 4 ? (T)A.gf : (T)A.ph.g;
   const int P = A.plane32;
@@ -222,7 +221,7 @@ stage_kernel_col(const __grid_constant__ StageArgs A) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) Fs[v] = src[(size_t)v * NF];
     }
-    const T coef = s ? -(inv2h[a] / w0) : inv2h[a] / w0;
+    const T coef = s ? -lift_of<T>(A, level, a) : lift_of<T>(A, level, a);
 #pragma unroll
     for (int v = 0; v < NV; ++v) L[v] = coef * (Fs[v] - Fo[v]);
   };

@@ -170,7 +170,6 @@ __device__ __forceinline__ void stage_body_half(const StageArgs& A, int64_t e) {
   for (int a = 0; a < 2; ++a) kindH[a] = hok ? stage_face(a, hs, hfn) : FACE_WALL;
   if (colok) kindV = stage_face(2, h, t);
   cp_async_commit();
-  const T w0 = ops[5 * n1 * n1];
   const T gamma = gamma_of<T>(A.ph, A.gammaf);
   const T g = sizeof(T) == 4 ? (T)A.gf : (T)A.ph.g;
   const int level = A.elem[e * 4];
@@ -179,7 +178,7 @@ __device__ __forceinline__ void stage_body_half(const StageArgs& A, int64_t e) {
   for (int a = 0; a < D; ++a) inv2h[a] = inv2h_of<T>(A, level, a);
   T lc[D];                                 // lift factors (2/h_a) / w0
 #pragma unroll
-  for (int a = 0; a < D; ++a) lc[a] = inv2h[a] / w0;
+  for (int a = 0; a < D; ++a) lc[a] = lift_of<T>(A, level, a);
   // F* - F(own) on face (a, s) at face node fn, given the own node's state and normal flux Fo;
   // returns the lift n_a (2/h_a)/w0 (F* - F(own)).
   auto face_lift = [&](auto axis, int s, int kind, int fn, const T* q, T pp, const NodeBg<T>& bg,
