@@ -45,6 +45,13 @@ ADJOINT_3D = dict(name="adjoint3d_12cube_N5", dim=3, N=5, base=(12, 12, 12),
 
 CONFIGS = {c["name"]: c for c in (RTB_2D, COLD_2D, BUBBLE_3D, ADJOINT_3D)}
 
+# Swirling deformational flow (Sec. 4.2, after LeVeque): tracer cosine bell (h_max = 1) at
+# (0.25, 0.25) with r_c = 0.25 on [0, 1]^2, 16 x 16 roots, N = 4, one extra level where |C| > 0.05
+# (reading), buffer 2, period T = 5 with 80 regrids; dt reading 2.5e-3 (2000 steps).
+LEVEQUE_2D = dict(name="leveque2d_16x16_N4_L1", dim=2, N=4, base=(16, 16), length=(1.0, 1.0),
+                  max_level=1, bubble=dict(center=(0.25, 0.25), radius=(0.25, 0.25), amp=0.5),
+                  period=5.0, dt=2.5e-3, steps=2000, threshold=0.05, buffer=2, regrid_every=25)
+
 # Batched 2D bubbles: 256 instances on [0, 1000]^2 with seeded radius U[150, 400] m, amplitude
 # U[0.1, 2] K, centre (500, 350) m, mesh 10x10 ... 64x32, N in {3..7}, precision 50/50, 500 steps.
 BATCH_MESHES = ((10, 10), (16, 16), (20, 16), (32, 16), (32, 32), (48, 24), (64, 32))
@@ -96,6 +103,12 @@ def random_state(nv, E, NP, seed, rho_scale=1e-3, u_scale=2.0, theta_scale=0.3, 
     q[1:nv - 1] = u_scale * g.standard_normal((nv - 2, E, NP))
     q[nv - 1] = theta_scale * g.standard_normal((E, NP))
     return q.astype(dtype)
+
+
+def random_scalar(E, NP, seed, scale=1.0, offset=0.0):
+    """White-noise scalar field [E, NP] (a tracer), offset + scale * N(0, 1)."""
+    g = rng(4000 + int(seed))
+    return offset + scale * g.standard_normal((E, NP))
 
 
 def random_flags(n, p, seed):
