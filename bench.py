@@ -377,6 +377,55 @@ def run_cold2d(pkg, steps=200):
     return out
 
 
+def run_leveque(pkg):
+    """Swirling deformational flow (Sec. 4.2): tracer bell on [0, 1]^2, 16 x 16 roots, N = 4,
+    one level where |C| > 0.05, buffer 2, T = 5 in 2000 steps with 80 regrids, mortar and
+    point-interpolation hanging faces, and uniform 16 x 16 and 32 x 32 grids; the paper times
+    these runs (11 s, 18 s and 51 s on its hardware)."""
+    import torch
+    cfg = workloads.LEVEQUE_2D
+    NP = (cfg["N"] + 1) ** 2
+    out = {"workload": cfg["name"], "steps": cfg["steps"], "period": cfg["period"]}
+    for name, mode, base, L in (("amr_mortar", "mortar", cfg["base"], 1), ("amr_interp", "interp", cfg["base"], 1),
+                                ("uniform16", "mortar", cfg["base"], 0), ("uniform32", "mortar", (32, 32), 0)):
+        m = pkg.Mesh(2, cfg["N"], base, cfg["length"], max_level=L, equations="tracer", face_mode=mode,
+                     wind_period=cfg["period"])
+        if L:
+            pkg.adapt_initial(m, cfg["bubble"], cfg["threshold"], cfg["buffer"])
+        else:
+            m.set_bubble(**cfg["bubble"])
+        m0 = m.integrals()[0]
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        dof = 0
+        regrids = 0
+        ev0.record()
+        for _ in range(cfg["steps"] // cfg["regrid_every"]):
+            dof += 3 * cfg["regrid_every"] * m.num_elements * NP
+            m.step(cfg["dt"], cfg["regrid_every"])
+            if L:
+                m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
+                regrids += 1
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        C = m.get_state()
+        m.set_bubble(**cfg["bubble"])
+        C0 = m.get_state()
+        m.set_state(C)
+        drift = abs(m.integrals()[0] - m0) / m0
+        m.set_state((C - C0) ** 2)
+        e2 = m.integrals()[0]
+        m.set_state(C0 ** 2)
+        n2 = m.integrals()[0]
+        out[name] = {"seconds": ms / 1e3, "value": dof / (ms / 1e3), "unit": METRIC, "regrids": regrids,
+                     "elements_at_T": m.num_elements, "tracer_rel_change": drift,
+                     "l2_rel_error_at_T": float(np.sqrt(e2 / n2))}
+        m.close()
+    return out
+
+
 def run_batch(pkg, steps=500, compare_steps=50):
     """Batched workload: 256 seeded 2D bubble instances (mesh 10x10 ... 64x32, N 3..7, FP32/FP64
     50/50, per-instance dt), autotuned layouts, `steps` graph-replayed SSP-RK3 steps; and the same
@@ -464,6 +513,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-cold2d", action="store_true",
                     help="skip the 2D viscous cold-bubble leg")
+    ap.add_argument("--no-leveque", action="store_true",
+                    help="skip the tracer swirling-flow leg")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP32-vs-FP64 field comparison over the workload's full step count")
     ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2, 3],
@@ -554,6 +605,8 @@ def main():
         line["batch"] = run_batch(pkg)
     if not args.no_cold2d:
         line["cold2d"] = run_cold2d(pkg)
+    if not args.no_leveque:
+        line["leveque"] = run_leveque(pkg)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, nel, E, sec = oracle_sample(cfg, n_elem=1024, reps=1)
         line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",

@@ -47,6 +47,8 @@ typedef enum {
 enum { DG_FP64 = 0, DG_FP32_PERT = 1 };   /* dg_mesh_desc.precision */
 enum { DG_HOST = 0, DG_DEVICE = 1 };      /* where a state pointer lives */
 enum { DG_CRIT_THETA = 0, DG_CRIT_FLAGS = 1 };  /* dg_adapt_params.criterion */
+enum { DG_EQ_EULER = 0, DG_EQ_TRACER = 1 };     /* dg_mesh_desc.equations */
+enum { DG_FACE_MORTAR = 0, DG_FACE_INTERP = 1 };  /* dg_mesh_desc.face_mode */
 
 #define DG_NUM_INTEGRALS 5
 #define DG_MAX_N 8
@@ -66,6 +68,18 @@ typedef struct {
   double nu;            /* artificial viscosity (m^2/s), >= 0.  nu > 0 adds the BR1 term
                            div(nu rho grad phi), phi = (u, theta'), to momentum and Theta'
                            (FP64 meshes only; not in the adjoint or in batches) */
+  /* Fields below are zero for the Euler equations (the default of a zero-initialised desc). */
+  int32_t equations;    /* DG_EQ_EULER, or DG_EQ_TRACER: one passive tracer C with
+                           dC/dt + div(C u) = 0 under the prescribed swirling wind of Sec. 4.2,
+                           u = sin^2(pi x) sin(2 pi y) g, v = -sin^2(pi y) sin(2 pi x) g,
+                           g = cos(pi t / T), coordinates in the box's units (2D, FP64, nu = 0;
+                           the state has one plane; upwind face flux; no flux through walls) */
+  int32_t face_mode;    /* hanging faces of a tracer mesh: DG_FACE_MORTAR (Sec. 3.3: the coarse
+                           side receives the projected mortar fluxes, conservative) or
+                           DG_FACE_INTERP (the coarse side solves its own flux against the fine
+                           traces evaluated at its nodes: the non-conservative point-to-point
+                           interpolation compared in Sec. 4.2); Euler meshes use mortars */
+  double wind_period;   /* T of the prescribed wind (tracer meshes), > 0 */
 } dg_mesh_desc;
 
 /* Cosine-bell potential-temperature bubble (Sec. 4.2 Eq. cosine-bell, Sec. 4.3):
@@ -158,6 +172,17 @@ dg_status dg_adapt(dg_mesh* mesh, const dg_adapt_params* params, dg_adapt_report
 
 /* Per-element refinement indicator max_n |theta'| (FP64), written to host `out` (E doubles). */
 dg_status dg_indicator(dg_mesh* mesh, double* out, size_t cap);
+
+/* Model time of the mesh state; dg_step advances it by nsteps x dt.  A tracer mesh evaluates its
+ * wind at the SSP-RK3 stage times t, t + dt, t + dt/2, and dg_rhs at t.  Euler meshes carry the
+ * time along unused.  dg_get_time returns 0 for a NULL mesh. */
+dg_status dg_set_time(dg_mesh* mesh, double t);
+double dg_get_time(const dg_mesh* mesh);
+
+/* Tracer meshes reuse the calls above: dg_set_bubble sets C = amp (1 + cos(pi r)) (the bell of
+ * Sec. 4.2 with amp = h_max / 2; the random-field terms must be absent), dg_indicator and the
+ * DG_CRIT_THETA criterion of dg_adapt use max |C| per element, dg_integrals returns
+ * {int C, 0, 0, volume, int C}; dg_primitives, the adjoint and batches reject them. */
 
 /* Primitive diagnostics of the current state in FP64 (the fields reported in Sec. 4.3): device
  * `out` receives dim + 1 planes of E * (N+1)^dim doubles in the state's [element][node] order,

@@ -122,6 +122,17 @@ Basis1D make_basis(int N) {
     }
   std::vector<double> tmp(n1);
   for (int c = 0; c < 2; ++c) {
+    b.G[c].assign(n1 * n1, 0.0);
+    for (int i = 0; i < n1; ++i) {
+      const bool mid = std::fabs(b.x[i]) < 1e-14;
+      const bool inside = c == 0 ? b.x[i] < 0.0 : b.x[i] > 0.0;
+      const double wt = mid ? 0.5 : (inside ? 1.0 : 0.0);
+      if (wt == 0.0) continue;
+      lagrange_at(b.x, lam, 2.0 * b.x[i] - (2.0 * c - 1.0), tmp.data());
+      for (int j = 0; j < n1; ++j) b.G[c][i * n1 + j] = wt * tmp[j];
+    }
+  }
+  for (int c = 0; c < 2; ++c) {
     const double off = 2.0 * c - 1.0;
     b.P[c].assign(n1 * n1, 0.0);
     for (int i = 0; i < n1; ++i) {

@@ -79,6 +79,8 @@ dg_status upload_ops(dg_mesh* m) {
   od.insert(od.end(), m->basis.C[1].begin(), m->basis.C[1].end());
   od.insert(od.end(), m->basis.w.begin(), m->basis.w.end());
   od.insert(od.end(), m->basis.x.begin(), m->basis.x.end());
+  od.insert(od.end(), m->basis.G[0].begin(), m->basis.G[0].end());
+  od.insert(od.end(), m->basis.G[1].begin(), m->basis.G[1].end());
   (void)nn;
   CU(cudaMalloc(&m->d_opsd, od.size() * sizeof(double)));
   CU(cudaMemcpy(m->d_opsd, od.data(), od.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -218,7 +220,7 @@ dg_status launch_mortars(dg_mesh* m, const void* qs, const void* pp_in, cudaStre
 }
 
 dg_status ensure_pp(dg_mesh* m, cudaStream_t s) {
-  if (m->pp_valid) return DG_OK;
+  if (m->pp_valid || m->tracer) return DG_OK;           // a tracer state has no pressure
   const void* theta = (const char*)m->q[0] + (size_t)(m->NV - 1) * plane(m) * m->tsize;
   cudaError_t e = dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->d_bgc, m->ph,
                                      pp_plane(m, m->q[0]), s);
@@ -232,8 +234,38 @@ using dgi::pp_plane;
 
 namespace {
 
+// Tracer stage (or pure RHS) with the wind factor m->stage_g: hanging faces, then the stage.
+dg_status tracer_pass(dg_mesh* m, const void* cs, const void* cn, void* out, int mode, double dt,
+                      double ca, double cb, cudaStream_t s) {
+  if (m->G > 0) {
+    dgk::TracerMortarArgs M{};
+    M.cs = (const double*)cs; M.mbuf = (double*)m->d_mbuf; M.plane = plane(m); M.G = (int32_t)m->G;
+    M.groups = m->d_groups; M.elem = m->d_elem; M.ops = m->d_opsd;
+    M.root_h[0] = m->root_h[0]; M.root_h[1] = m->root_h[1];
+    M.g = m->stage_g; M.interp = m->desc.face_mode == DG_FACE_INTERP;
+    if (!dgk::launch_tracer_mortar(m->N, M, s)) return fail(m, DG_ERR_UNSUPPORTED, "tracer N=%d not compiled", m->N);
+    CU(cudaGetLastError());
+  }
+  dgk::TracerArgs A{};
+  A.cs = (const double*)cs; A.cn = (const double*)cn; A.out = (double*)out; A.mbuf = (const double*)m->d_mbuf;
+  A.plane = plane(m); A.E = (int32_t)m->E; A.elem = m->d_elem; A.conn = m->d_conn; A.ops = m->d_opsd;
+  A.root_h[0] = m->root_h[0]; A.root_h[1] = m->root_h[1];
+  for (int l = 0; l < dgk::kMaxLevels; ++l)
+    for (int a = 0; a < 2; ++a) {
+      A.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+      A.lift[l][a] = A.inv2h[l][a] / m->basis.w[0];
+    }
+  A.g = m->stage_g; A.dt = dt; A.ca = ca; A.cb = cb; A.mode = mode;
+  if (!dgk::launch_tracer_stage(m->N, A, s)) return fail(m, DG_ERR_UNSUPPORTED, "tracer N=%d not compiled", m->N);
+  CU(cudaGetLastError());
+  return DG_OK;
+}
+
+double wind_factor(const dg_mesh* m, double t) { return std::cos(M_PI * t / m->desc.wind_period); }
+
 dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const void* qn, void* out,
                           void* pp_out, int mode, double dt, double ca, double cb, cudaStream_t s) {
+  if (m->tracer) return tracer_pass(m, qs, qn, out, mode, dt, ca, cb, s);
   dg_status st = dgi::launch_mortars(m, qs, pp_in, s);
   if (st != DG_OK) return st;
   dgk::StageArgs A{};
@@ -383,6 +415,7 @@ dg_status step_transpose(dg_mesh* m, const double* b0, const double* b1, const d
 
 dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void* stream) {
   if (!m || !q || !lam || !out) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
   if (m->desc.nu > 0.0) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint has no viscous term");
   dg_status st = ensure_adjoint_ws(m);
@@ -397,6 +430,7 @@ dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void
 dg_status dg_step_state(dg_mesh* m, const void* q_in, void* q_out, double dt, int32_t nsteps,
                         void* stream) {
   if (!m || !q_in || !q_out || nsteps < 0 || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   dg_status st = ensure_adjoint_ws(m);
   if (st != DG_OK) return st;
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
@@ -410,6 +444,7 @@ dg_status dg_step_state(dg_mesh* m, const void* q_in, void* q_out, double dt, in
 dg_status dg_step_vjp(dg_mesh* m, const void* q_in, double dt, const void* lam_out, void* lam_in,
                       void* stream) {
   if (!m || !q_in || !lam_out || !lam_in || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (lam_out == lam_in) return fail(m, DG_ERR_ARG, "lam_out and lam_in must not alias");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
   if (m->desc.nu > 0.0) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint has no viscous term");
@@ -430,6 +465,7 @@ dg_status dg_step_vjp(dg_mesh* m, const void* q_in, double dt, const void* lam_o
 
 dg_status dg_step_record(dg_mesh* m, const void* q_in, void* q_out, void* record, double dt, void* stream) {
   if (!m || !q_in || !q_out || !record || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
   if (m->desc.nu > 0.0) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint has no viscous term");
   dg_status st = ensure_adjoint_ws(m);
@@ -450,6 +486,7 @@ dg_status dg_step_record(dg_mesh* m, const void* q_in, void* q_out, void* record
 dg_status dg_step_vjp_record(dg_mesh* m, const void* record, double dt, const void* lam_out, void* lam_in,
                              void* stream) {
   if (!m || !record || !lam_out || !lam_in || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (lam_out == lam_in) return fail(m, DG_ERR_ARG, "lam_out and lam_in must not alias");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
   if (m->desc.nu > 0.0) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint has no viscous term");
@@ -463,6 +500,7 @@ dg_status dg_step_vjp_record(dg_mesh* m, const void* record, double dt, const vo
 
 dg_status dg_set_theta(dg_mesh* m, const double* theta, int where) {
   if (!m || !theta || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   const size_t bytes = (size_t)plane(m) * sizeof(double);
   const double* src = theta;
   double* tmp = nullptr;
@@ -483,6 +521,7 @@ dg_status dg_set_theta(dg_mesh* m, const double* theta, int where) {
 dg_status dg_theta_vjp(dg_mesh* m, const double* theta, const void* lam_q, double* lam_theta,
                        void* stream) {
   if (!m || !theta || !lam_q || !lam_theta) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
   CU(dgk::launch_theta_vjp((int32_t)m->E, m->n1, m->D, m->d_bg, theta, m->ph.theta0,
@@ -492,6 +531,7 @@ dg_status dg_theta_vjp(dg_mesh* m, const double* theta, const void* lam_q, doubl
 
 dg_status dg_ke_grad(dg_mesh* m, const void* q, void* out, void* stream) {
   if (!m || !q || !out) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
   CU(dgk::launch_ke_grad((int32_t)m->E, m->n1, m->D, m->d_elem, d_w(m), m->root_h, m->d_bg,
@@ -508,6 +548,14 @@ dg_status dg_set_option(dg_mesh* m, int32_t option, int64_t value) {
   }
   return fail(m, DG_ERR_ARG, "unknown option %d", option);
 }
+
+dg_status dg_set_time(dg_mesh* m, double t) {
+  if (!m || !std::isfinite(t)) return fail(m, DG_ERR_ARG, "bad argument");
+  m->time = t;
+  return DG_OK;
+}
+
+double dg_get_time(const dg_mesh* m) { return m ? m->time : 0.0; }
 
 const char* dg_version(void) { return "gb300-dgsem 0.1 (sm_103a)"; }
 
@@ -529,13 +577,22 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   }
   if (!(desc->p0 > 0.0) || !(desc->R > 0.0) || !(desc->cp > desc->R) || !(desc->theta0 > 0.0))
     return DG_ERR_ARG;
+  if (desc->equations != DG_EQ_EULER && desc->equations != DG_EQ_TRACER) return DG_ERR_ARG;
+  if (desc->face_mode != DG_FACE_MORTAR && desc->face_mode != DG_FACE_INTERP) return DG_ERR_ARG;
+  if (desc->equations == DG_EQ_TRACER) {
+    if (desc->dim != 2 || desc->precision != DG_FP64 || desc->nu != 0.0) return DG_ERR_UNSUPPORTED;
+    if (!(desc->wind_period > 0.0)) return DG_ERR_ARG;
+  } else if (desc->face_mode != DG_FACE_MORTAR) {
+    return DG_ERR_UNSUPPORTED;
+  }
   m = new (std::nothrow) dg_mesh();
   if (!m) return DG_ERR_OOM;
   m->desc = *desc;
   m->D = desc->dim; m->N = desc->N; m->n1 = m->N + 1;
   m->NP = m->D == 3 ? m->n1 * m->n1 * m->n1 : m->n1 * m->n1;
   m->NF = m->D == 3 ? m->n1 * m->n1 : m->n1;
-  m->NV = m->D + 2; m->NSUB = 1 << (m->D - 1);
+  m->tracer = desc->equations == DG_EQ_TRACER;
+  m->NV = m->tracer ? 1 : m->D + 2; m->NSUB = 1 << (m->D - 1);
   m->prec = desc->precision;
   m->tsize = m->prec == DG_FP64 ? sizeof(double) : sizeof(float);
   m->variant = (m->prec == DG_FP32_PERT && m->D == 3) ? 3 : 2;   // fastest measured layouts
@@ -664,16 +721,33 @@ static dg_status bubble_eval(dg_mesh* m, const dg_bubble_desc* b, double* theta_
   return DG_OK;
 }
 
-dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) { return bubble_eval(m, b, nullptr); }
+dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) {
+  if (m && b && m->tracer) {
+    if (b->n_rff != 0) return fail(m, DG_ERR_ARG, "a tracer bell takes no random field");
+    for (int a = 0; a < 2; ++a)
+      if (!(b->radius[a] > 0.0)) return fail(m, DG_ERR_ARG, "radius must be positive");
+    cudaError_t e = dgk::launch_tracer_bell((int32_t)m->E, m->n1, m->d_elem, d_x(m), m->root_h, b->center,
+                                            b->radius, b->amp, (double*)m->q[0], m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "tracer bell failed: %s", cudaGetErrorString(e));
+    return DG_OK;
+  }
+  return bubble_eval(m, b, nullptr);
+}
 
 dg_status dg_bubble_theta(dg_mesh* m, const dg_bubble_desc* b, double* theta) {
   if (!m || !theta) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "no theta' field on a tracer mesh");
   return bubble_eval(m, b, theta);
 }
 
 dg_status dg_rhs(dg_mesh* m, const void* q, void* dqdt, void* stream) {
   if (!m || !q || !dqdt) return fail(m, DG_ERR_ARG, "bad argument");
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  if (m->tracer) {
+    m->stage_g = wind_factor(m, m->time);
+    return launch_rhs_pass(m, q, nullptr, nullptr, dqdt, nullptr, 0, 0.0, 0.0, 1.0, s);
+  }
   const void* theta = (const char*)q + (size_t)(m->NV - 1) * plane(m) * m->tsize;
   CU(dgk::launch_pprime(m->prec, (int32_t)m->E, m->n1, m->D, theta, m->d_bg, m->d_bgc, m->ph, m->d_ppscratch, s));
   return launch_rhs_pass(m, q, m->d_ppscratch, nullptr, dqdt, nullptr, 0, 0.0, 0.0, 1.0, s);
@@ -692,11 +766,17 @@ dg_status dg_step(dg_mesh* m, double dt, int32_t nsteps, void* stream) {
   for (int32_t it = 0; it < nsteps; ++it) {
     // Shu-Osher SSP-RK3: q1 = q + dt L(q); q2 = 3/4 q + 1/4 (q1 + dt L(q1));
     // q^{n+1} = 1/3 q + 2/3 (q2 + dt L(q2)), the last one written over q^n (each thread reads
-    // q^n only at its own node, and the stage reads P' of q2, not of q^n)
+    // q^n only at its own node, and the stage reads P' of q2, not of q^n).  The stages sit at
+    // t, t + dt and t + dt/2 (the tracer's wind is evaluated there).
+    const double t = m->time;
+    m->stage_g = m->tracer ? wind_factor(m, t) : 1.0;
     dg_status st = launch_rhs_pass(m, m->q[0], p0, m->q[0], m->q[1], p1, 1, dt, 0.0, 1.0, s);
+    m->stage_g = m->tracer ? wind_factor(m, t + dt) : 1.0;
     if (st == DG_OK) st = launch_rhs_pass(m, m->q[1], p1, m->q[0], m->q[2], p2, 1, dt, 0.75, 0.25, s);
+    m->stage_g = m->tracer ? wind_factor(m, t + 0.5 * dt) : 1.0;
     if (st == DG_OK) st = launch_rhs_pass(m, m->q[2], p2, m->q[0], m->q[0], p0, 1, dt, 1.0 / 3.0, 2.0 / 3.0, s);
     if (st != DG_OK) return st;
+    m->time = t + dt;
   }
   return DG_OK;
 }
@@ -705,8 +785,10 @@ dg_status dg_indicator(dg_mesh* m, double* out, size_t cap) {
   if (!m || !out || cap < (size_t)m->E) return fail(m, DG_ERR_ARG, "bad argument");
   CU(reserve(m->d_ind, m->c_ind, (size_t)(m->E > 0 ? m->E : 1) * sizeof(double)));
   double* d = m->d_ind;
-  cudaError_t e = dgk::launch_indicator(m->prec, (int32_t)m->E, m->n1, m->D, m->d_bg, m->q[0], plane(m),
-                                        m->ph.theta0, d, m->stream);
+  cudaError_t e = m->tracer
+                      ? dgk::launch_tracer_indicator((int32_t)m->E, m->n1, (const double*)m->q[0], d, m->stream)
+                      : dgk::launch_indicator(m->prec, (int32_t)m->E, m->n1, m->D, m->d_bg, m->q[0], plane(m),
+                                              m->ph.theta0, d, m->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, (size_t)m->E * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "indicator failed: %s", cudaGetErrorString(e));
@@ -715,6 +797,7 @@ dg_status dg_indicator(dg_mesh* m, double* out, size_t cap) {
 
 dg_status dg_primitives(dg_mesh* m, double* out, size_t cap, void* stream) {
   if (!m || (!out && m->E > 0)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   const size_t need = (size_t)(m->D + 1) * (size_t)m->E * (size_t)m->NP;
   if (cap < need) return fail(m, DG_ERR_ARG, "output holds %zu doubles, %zu needed", cap, need);
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
@@ -765,7 +848,7 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   CU(reserve(m->q_spare, m->q_spare_cap, state_bytes(m)));
   for (int i = 1; i < 3; ++i) CU(reserve(m->q[i], m->q_cap[i], state_bytes(m)));
   {
-    cudaError_t e = dgk::launch_transfer(m->prec, (int32_t)m->E, m->n1, m->D, m->d_tm, m->d_opsd, m->q[0],
+    cudaError_t e = dgk::launch_transfer(m->prec, (int32_t)m->E, m->n1, m->D, m->NV, m->d_tm, m->d_opsd, m->q[0],
                                          plane_old, m->q_spare, plane(m), m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "transfer failed: %s", cudaGetErrorString(e));
@@ -795,6 +878,19 @@ static double two_sum(double a, double b, double* err) {
 // adds the two compensated results with their rounding errors.
 dg_status dg_integrals(dg_mesh* m, double out[DG_NUM_INTEGRALS]) {
   if (!m || !out) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) {
+    double r[2] = {0.0, 0.0};
+    int bad = 0;
+    CU(cudaMemsetAsync(m->d_bad, 0, sizeof(int), m->stream));
+    CU(dgk::launch_tracer_total((int32_t)m->E, m->n1, m->d_elem, d_w(m), m->root_h, (const double*)m->q[0],
+                                m->d_partial, m->d_bad, m->d_out, m->stream));
+    CU(cudaMemcpyAsync(r, m->d_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaMemcpyAsync(&bad, m->d_bad, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    out[0] = r[0]; out[1] = 0.0; out[2] = 0.0; out[3] = r[1]; out[4] = r[0];
+    if (bad) return fail(m, DG_ERR_STATE, "non-finite value in the state");
+    return DG_OK;
+  }
   if (!m->bgint_valid) {
     CU(dgk::launch_integrals(m->prec, true, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), d_w(m), m->root_h,
                              m->d_bg, nullptr, plane(m), m->ph, m->d_partial, m->d_bad, m->d_out, m->stream));

@@ -125,7 +125,7 @@ dg_status dg_batch_create(dg_mesh* const* meshes, int32_t count, dg_batch** out)
   for (int32_t i = 0; i < count; ++i) {
     dg_mesh* m = meshes[i];
     if (!m) { delete b; return DG_ERR_ARG; }
-    if (m->desc.nu > 0.0) { delete b; return DG_ERR_UNSUPPORTED; }   // batched path is inviscid
+    if (m->desc.nu > 0.0 || m->tracer) { delete b; return DG_ERR_UNSUPPORTED; }   // inviscid Euler only
     for (int32_t j = 0; j < i; ++j)
       if (meshes[j] == m) { delete b; return DG_ERR_ARG; }   // each mesh once
     b->meshes.push_back(m);

@@ -5,11 +5,25 @@
 
 #include "dg_adjoint.cuh"
 #include "dg_device.cuh"
+#include "dg_tracer.cuh"
 #include "dg_viscous.cuh"
 
 namespace dgk {
 
 constexpr int NUM_INTEGRALS = 5;
+
+// Tracer meshes (tracer_f64.cu): stage, hanging faces (mortar or point interpolation), initial
+// bell, indicator max |C| and the compensated totals {int C, volume} into out[0..1].
+bool launch_tracer_stage(int N, const TracerArgs& A, cudaStream_t s);
+bool launch_tracer_mortar(int N, const TracerMortarArgs& A, cudaStream_t s);
+cudaError_t launch_tracer_bell(int32_t E, int n1, const int32_t* elem, const double* xi,
+                               const double* root_h, const double* center, const double* radius,
+                               double amp, double* C, cudaStream_t s);
+cudaError_t launch_tracer_indicator(int32_t E, int n1, const double* C, double* out, cudaStream_t s);
+size_t tracer_total_scratch_doubles();
+cudaError_t launch_tracer_total(int32_t E, int n1, const int32_t* elem, const double* w,
+                                const double* root_h, const double* C, double* partial, int* bad,
+                                double* out, cudaStream_t s);
 
 // Fused RK stage (or pure RHS) and mortar launches; return false when (D, N) is not compiled.
 bool launch_stage_f64_2d(int N, const StageArgs& A, cudaStream_t s);
@@ -56,7 +70,7 @@ cudaError_t launch_integrals(int prec, bool background, int32_t E, int n1, int D
                              const double* xi, const double* w, const double* root_h,
                              const double* bg, const void* q, int64_t plane, const PhysC& ph,
                              double* partial, int* bad, double* out, cudaStream_t s);
-cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, const int32_t* tmap,
+cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, int nv, const int32_t* tmap,
                             const double* ops, const void* qold, int64_t plane_old, void* qnew,
                             int64_t plane_new, cudaStream_t s);
 

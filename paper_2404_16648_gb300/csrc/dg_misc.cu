@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kIntThreads) integrals_final(int nblocks, cons
 template <class T>
 __global__ void transfer_kernel(int32_t Enew, int n1, int D, const int32_t* tmap,
                                 const double* ops, const T* qold, int64_t plane_old, T* qnew,
-                                int64_t plane_new) {
+                                int64_t plane_new, int nv) {
   extern __shared__ double sm[];
   const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
   const int nn = n1 * n1;
@@ -286,7 +286,6 @@ __global__ void transfer_kernel(int32_t Enew, int n1, int D, const int32_t* tmap
   const int kind = row[0];
   const int n = threadIdx.x;
   int idx[3] = {n % n1, (n / n1) % n1, D == 3 ? n / (n1 * n1) : 0};
-  const int nv = D + 2;
   __syncthreads();
   for (int v = 0; v < nv; ++v) {
     if (kind == 0) {
@@ -411,7 +410,7 @@ cudaError_t launch_integrals(int prec, bool background, int32_t E, int n1, int D
   return cudaGetLastError();
 }
 
-cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, const int32_t* tmap,
+cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, int nv, const int32_t* tmap,
                             const double* ops, const void* qold, int64_t plane_old, void* qnew,
                             int64_t plane_new, cudaStream_t s) {
   if (Enew == 0) return cudaSuccess;
@@ -420,10 +419,10 @@ cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, const int32_t
   const size_t smem = (size_t)(4 * n1 * n1 + 3 * NP) * sizeof(double);
   if (prec == 0)
     transfer_kernel<double><<<Enew, threads, smem, s>>>(Enew, n1, D, tmap, ops, (const double*)qold,
-                                                        plane_old, (double*)qnew, plane_new);
+                                                        plane_old, (double*)qnew, plane_new, nv);
   else
     transfer_kernel<float><<<Enew, threads, smem, s>>>(Enew, n1, D, tmap, ops, (const float*)qold,
-                                                       plane_old, (float*)qnew, plane_new);
+                                                       plane_old, (float*)qnew, plane_new, nv);
   return cudaGetLastError();
 }
 

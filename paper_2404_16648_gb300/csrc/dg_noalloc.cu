@@ -163,6 +163,7 @@ extern "C" dg_status dg_integrals_noalloc(const dg_mesh_desc* desc, const int32_
   if (!desc || !elem || !q || !out || num_elements < 0) return DG_ERR_ARG;
   if ((desc->dim != 2 && desc->dim != 3) || desc->N < 1 || desc->N > DG_MAX_N) return DG_ERR_ARG;
   if (desc->precision != DG_FP64 && desc->precision != DG_FP32_PERT) return DG_ERR_ARG;
+  if (desc->equations != DG_EQ_EULER) return DG_ERR_UNSUPPORTED;
   const int D = desc->dim, n1 = desc->N + 1;
   const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
   const int64_t nodes = num_elements * NP;

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 
 # every symbol include/dg.h declares
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_nodes", "dg_get_leaves",
             "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_bubble", "dg_rhs", "dg_step",
-            "dg_adapt", "dg_indicator", "dg_primitives", "dg_integrals", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
+            "dg_adapt", "dg_indicator", "dg_primitives", "dg_integrals", "dg_set_time", "dg_get_time", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
             "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
             "dg_step_state", "dg_step_vjp", "dg_step_record", "dg_step_vjp_record", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
@@ -37,7 +37,8 @@ class MeshDesc(ctypes.Structure):
                 ("length", ctypes.c_double * 3), ("max_level", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("theta0", ctypes.c_double), ("p0", ctypes.c_double),
                 ("g", ctypes.c_double), ("R", ctypes.c_double), ("cp", ctypes.c_double),
-                ("nu", ctypes.c_double)]
+                ("nu", ctypes.c_double), ("equations", ctypes.c_int32), ("face_mode", ctypes.c_int32),
+                ("wind_period", ctypes.c_double)]
 
 
 class BubbleDesc(ctypes.Structure):
@@ -94,6 +95,8 @@ def load_library(path=None):
         "dg_primitives": (i32, [vp, vp, sz, vp]),
         "dg_integrals": (i32, [vp, ctypes.POINTER(ctypes.c_double)]),
         "dg_set_option": (i32, [vp, i32, i64]),
+        "dg_set_time": (i32, [vp, ctypes.c_double]),
+        "dg_get_time": (ctypes.c_double, [vp]),
         "dg_enable_timing": (i32, [vp, i32]),
         "dg_stage_timing": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]),
         "dg_forest_create": (i32, [i32, ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(vp)]),
@@ -154,7 +157,8 @@ class Mesh:
     """A forest-of-trees dGSEM mesh with its state on the GPU (one dg_mesh handle)."""
 
     def __init__(self, dim, N, base, length, max_level=0, precision="fp64", theta0=300.0,
-                 p0=1.0e5, g=9.81, R=287.0, cp=1004.5, nu=0.0, stream=None):
+                 p0=1.0e5, g=9.81, R=287.0, cp=1004.5, nu=0.0, stream=None, equations="euler",
+                 face_mode="mortar", wind_period=0.0):
         self.lib = load_library()
         d = MeshDesc()
         d.dim, d.N = dim, N
@@ -164,8 +168,14 @@ class Mesh:
         d.max_level = max_level
         d.precision = DG_FP64 if precision == "fp64" else DG_FP32_PERT
         d.theta0, d.p0, d.g, d.R, d.cp, d.nu = theta0, p0, g, R, cp, nu
+        if equations not in ("euler", "tracer") or face_mode not in ("mortar", "interp"):
+            raise ValueError("equations must be 'euler' or 'tracer', face_mode 'mortar' or 'interp'")
+        d.equations = 1 if equations == "tracer" else 0
+        d.face_mode = 1 if face_mode == "interp" else 0
+        d.wind_period = wind_period
         self.desc = d
-        self.dim, self.N, self.nv = dim, N, dim + 2
+        self.equations = equations
+        self.dim, self.N, self.nv = dim, N, (1 if equations == "tracer" else dim + 2)
         self.np_ = (N + 1) ** dim
         self.precision = precision
         self.np_dtype = np.float64 if precision == "fp64" else np.float32
@@ -408,6 +418,12 @@ class Mesh:
         if check:
             self._check(st)
         return np.array(list(out))
+
+    def set_time(self, t):
+        self._check(self.lib.dg_set_time(self.h, float(t)))
+
+    def get_time(self):
+        return float(self.lib.dg_get_time(self.h))
 
     def set_stage_kernel(self, layout):
         """0: one thread per vertical node column; 1: one thread per node; 2: column layout with
