@@ -80,6 +80,9 @@ typedef struct {
                            traces evaluated at its nodes: the non-conservative point-to-point
                            interpolation compared in Sec. 4.2); Euler meshes use mortars */
   double wind_period;   /* T of the prescribed wind (tracer meshes), > 0 */
+  int32_t periodic[3];  /* 1: the two boundaries of axis a are joined (periodic neighbours
+                           replace the walls there); the vertical axis only with g = 0, where
+                           the background is uniform */
 } dg_mesh_desc;
 
 /* Cosine-bell potential-temperature bubble (Sec. 4.2 Eq. cosine-bell, Sec. 4.3):
@@ -318,6 +321,9 @@ typedef struct dg_forest dg_forest;
 dg_status dg_forest_create(int32_t dim, const int32_t base[3], int32_t max_level, dg_forest** out);
 void dg_forest_destroy(dg_forest* forest);
 int64_t dg_forest_size(const dg_forest* forest);
+/* As dg_forest_create with periodic axes (periodic[a] != 0 joins the boundaries of axis a). */
+dg_status dg_forest_create_periodic(int32_t dim, const int32_t base[3], int32_t max_level,
+                                    const int32_t periodic[3], dg_forest** out);
 /* Leaves as in dg_get_leaves. */
 dg_status dg_forest_leaves(const dg_forest* forest, int32_t* out, size_t cap);
 /* Face lists as in dg_get_faces. */

@@ -39,10 +39,12 @@ MAXL = 20   # maximum supported level depth for Morton keys
 class Forest:
     """Active leaves of a forest over a base grid of ``base`` root cells (length d)."""
 
-    def __init__(self, base, max_level, leaves=None):
+    def __init__(self, base, max_level, leaves=None, periodic=None):
         self.base = tuple(int(b) for b in base)
         self.d = len(self.base)
         self.max_level = int(max_level)
+        # periodic[a]: the two boundaries of axis a are joined (neighbour lookups wrap around)
+        self.periodic = tuple(bool(p) for p in periodic) if periodic is not None else (False,) * self.d
         if leaves is None:
             leaves = [(0, c) for c in self._root_coords()]
         self.leaves = [(int(l), tuple(int(x) for x in c)) for l, c in leaves]
@@ -97,7 +99,9 @@ class Forest:
         cn = list(c)
         cn[axis] += 1 if side == 1 else -1
         if cn[axis] < 0 or cn[axis] >= self.extent(level, axis):
-            return ("boundary", None)
+            if not self.periodic[axis]:
+                return ("boundary", None)
+            cn[axis] %= self.extent(level, axis)
         if self.is_leaf(level, cn):
             return ("same", self.index(level, cn))
         if level > 0:
@@ -194,7 +198,7 @@ class Forest:
             else:
                 new_leaves.append((l, c))
                 tmap.append(("keep", e))
-        return Forest(self.base, self.max_level, new_leaves), tmap
+        return Forest(self.base, self.max_level, new_leaves, self.periodic), tmap
 
     # ------------------------------------------------------------------ faces
     def face_lists(self):
@@ -216,14 +220,26 @@ class Forest:
 
     # ------------------------------------------------------------------ checks
     def is_balanced(self):
-        """Brute force over all leaf pairs: face-adjacent leaves differ by <= 1 level."""
+        """Brute force over all leaf pairs: face-adjacent leaves differ by <= 1 level (across a
+        periodic boundary too, by comparing with the shifted copies of the other box)."""
         boxes = [self.box(e) for e in range(len(self.leaves))]
         for i in range(len(boxes)):
             for j in range(i + 1, len(boxes)):
-                if _share_face(boxes[i], boxes[j], self.d):
+                if any(_share_face(boxes[i], b, self.d) for b in self.periodic_images(boxes[j])):
                     if abs(self.leaves[i][0] - self.leaves[j][0]) > 1:
                         return False
         return True
+
+    def periodic_images(self, box):
+        """The box and its copies shifted by one domain length along each periodic axis."""
+        out = [box]
+        for a in range(self.d):
+            if not self.periodic[a]:
+                continue
+            L = self.base[a] << MAXL
+            out = out + [[(lo + sh, hi + sh) if k == a else (lo, hi) for k, (lo, hi) in enumerate(b)]
+                         for b in out for sh in (-L, L)]
+        return out
 
     def box(self, e):
         """Leaf extent in units of the finest supported level (integers)."""

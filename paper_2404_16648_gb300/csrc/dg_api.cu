@@ -578,6 +578,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   if (!(desc->p0 > 0.0) || !(desc->R > 0.0) || !(desc->cp > desc->R) || !(desc->theta0 > 0.0))
     return DG_ERR_ARG;
   if (desc->equations != DG_EQ_EULER && desc->equations != DG_EQ_TRACER) return DG_ERR_ARG;
+  // a periodic vertical axis needs a uniform background (g = 0)
+  if (desc->periodic[desc->dim - 1] && desc->g != 0.0) return DG_ERR_UNSUPPORTED;
   if (desc->face_mode != DG_FACE_MORTAR && desc->face_mode != DG_FACE_INTERP) return DG_ERR_ARG;
   if (desc->equations == DG_EQ_TRACER) {
     if (desc->dim != 2 || desc->precision != DG_FP64 || desc->nu != 0.0) return DG_ERR_UNSUPPORTED;
@@ -610,7 +612,9 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   }
   int base[3] = {desc->base[0], desc->base[1], desc->dim == 3 ? desc->base[2] : 1};
   for (int a = 0; a < 3; ++a) m->root_h[a] = a < m->D ? desc->length[a] / base[a] : 1.0;
-  m->forest = dgl::Forest(m->D, base, desc->max_level);
+  int per[3] = {0, 0, 0};
+  for (int a = 0; a < m->D; ++a) per[a] = desc->periodic[a] ? 1 : 0;
+  m->forest = dgl::Forest(m->D, base, desc->max_level, per);
   m->basis = dgl::make_basis(m->N);
   dg_status st = init_device_tables(m);
   if (st == DG_OK) st = upload_ops(m);

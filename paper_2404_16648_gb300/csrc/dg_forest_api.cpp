@@ -15,18 +15,25 @@ struct dg_forest {
 
 extern "C" {
 
-dg_status dg_forest_create(int32_t dim, const int32_t base[3], int32_t max_level, dg_forest** out) {
+dg_status dg_forest_create_periodic(int32_t dim, const int32_t base[3], int32_t max_level,
+                                    const int32_t periodic[3], dg_forest** out) {
   if (!out || !base || (dim != 2 && dim != 3) || max_level < 0 || max_level > DG_MAX_LEVEL)
     return DG_ERR_ARG;
   for (int a = 0; a < dim; ++a)
     if (base[a] < 1 || ((int64_t)base[a] << max_level) >= (1 << 19)) return DG_ERR_ARG;
   int b[3] = {base[0], base[1], dim == 3 ? base[2] : 1};
+  int per[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) per[a] = periodic && periodic[a] ? 1 : 0;
   dg_forest* f = new (std::nothrow) dg_forest();
   if (!f) return DG_ERR_OOM;
-  f->f = dgl::Forest(dim, b, max_level);
+  f->f = dgl::Forest(dim, b, max_level, per);
   f->refresh();
   *out = f;
   return DG_OK;
+}
+
+dg_status dg_forest_create(int32_t dim, const int32_t base[3], int32_t max_level, dg_forest** out) {
+  return dg_forest_create_periodic(dim, base, max_level, nullptr, out);
 }
 
 void dg_forest_destroy(dg_forest* forest) { delete forest; }

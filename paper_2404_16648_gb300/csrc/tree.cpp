@@ -13,8 +13,10 @@ uint64_t Forest::key(int level, const int32_t c[3]) {
          ((uint64_t)(uint32_t)c[1] << 24) | ((uint64_t)(uint32_t)c[2] << 43);
 }
 
-Forest::Forest(int dim, const int base[3], int max_level) : dim_(dim), max_level_(max_level) {
+Forest::Forest(int dim, const int base[3], int max_level, const int periodic[3])
+    : dim_(dim), max_level_(max_level) {
   for (int a = 0; a < 3; ++a) base_[a] = (a < dim) ? base[a] : 1;
+  for (int a = 0; a < 3; ++a) periodic_[a] = (periodic && a < dim && periodic[a]) ? 1 : 0;
   std::vector<Leaf> roots;
   for (int z = 0; z < base_[2]; ++z)
     for (int y = 0; y < base_[1]; ++y)
@@ -87,7 +89,11 @@ FaceInfo Forest::classify(int32_t e, int axis, int side) const {
   const Leaf& L = leaves_[e];
   int32_t n[3] = {L.c[0], L.c[1], L.c[2]};
   n[axis] += side ? 1 : -1;
-  if (n[axis] < 0 || n[axis] >= extent(L.level, axis)) return fi;
+  const int32_t ext = extent(L.level, axis);
+  if (n[axis] < 0 || n[axis] >= ext) {
+    if (!periodic_[axis]) return fi;
+    n[axis] = (n[axis] + ext) % ext;
+  }
   int32_t idx = find(L.level, n);
   if (idx >= 0) { fi.kind = FACE_CONF; fi.nb[0] = idx; return fi; }
   if (L.level > 0) {
@@ -220,7 +226,7 @@ bool Forest::regrid(const std::vector<uint8_t>& tag, int B, int max_level, Fores
   }
   out->dim_ = dim_;
   out->max_level_ = max_level_;
-  for (int a = 0; a < 3; ++a) out->base_[a] = base_[a];
+  for (int a = 0; a < 3; ++a) { out->base_[a] = base_[a]; out->periodic_[a] = periodic_[a]; }
   out->set_leaves(std::move(nl));
   *n_refined = nref;
   *n_coarsened = ncoarse;

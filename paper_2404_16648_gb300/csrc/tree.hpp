@@ -40,7 +40,9 @@ struct TransferEntry {
 class Forest {
  public:
   Forest() = default;
-  Forest(int dim, const int base[3], int max_level);   // uniform level-0 forest
+  // uniform level-0 forest; periodic[a] != 0 joins the two boundaries of axis a (the neighbour
+  // lookups wrap around, so balance, buffers and face lists see the periodic neighbours)
+  Forest(int dim, const int base[3], int max_level, const int periodic[3] = nullptr);
 
   int dim() const { return dim_; }
   int max_level() const { return max_level_; }
@@ -84,6 +86,7 @@ class Forest {
 
   int dim_ = 0;
   int base_[3] = {1, 1, 1};
+  int periodic_[3] = {0, 0, 0};
   int max_level_ = 0;
   std::vector<Leaf> leaves_;
   // open-addressing index key(level, c) -> leaf, linear probing, power-of-two capacity

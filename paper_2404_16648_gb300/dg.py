@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_nodes", "dg_get_leaves",
             "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_bubble", "dg_rhs", "dg_step",
             "dg_adapt", "dg_indicator", "dg_primitives", "dg_integrals", "dg_set_time", "dg_get_time", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
-            "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
+            "dg_forest_create_periodic", "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
             "dg_step_state", "dg_step_vjp", "dg_step_record", "dg_step_vjp_record", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
             "dg_bubble_theta", "dg_forest_partition", "dg_forest_halo", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
@@ -38,7 +38,7 @@ class MeshDesc(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("theta0", ctypes.c_double), ("p0", ctypes.c_double),
                 ("g", ctypes.c_double), ("R", ctypes.c_double), ("cp", ctypes.c_double),
                 ("nu", ctypes.c_double), ("equations", ctypes.c_int32), ("face_mode", ctypes.c_int32),
-                ("wind_period", ctypes.c_double)]
+                ("wind_period", ctypes.c_double), ("periodic", ctypes.c_int32 * 3)]
 
 
 class BubbleDesc(ctypes.Structure):
@@ -100,6 +100,8 @@ def load_library(path=None):
         "dg_enable_timing": (i32, [vp, i32]),
         "dg_stage_timing": (i32, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), i32]),
         "dg_forest_create": (i32, [i32, ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(vp)]),
+        "dg_forest_create_periodic": (i32, [i32, ctypes.POINTER(ctypes.c_int32), i32, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(vp)]),
         "dg_forest_destroy": (None, [vp]),
         "dg_forest_size": (i64, [vp]),
         "dg_forest_leaves": (i32, [vp, ctypes.POINTER(ctypes.c_int32), sz]),
@@ -158,7 +160,7 @@ class Mesh:
 
     def __init__(self, dim, N, base, length, max_level=0, precision="fp64", theta0=300.0,
                  p0=1.0e5, g=9.81, R=287.0, cp=1004.5, nu=0.0, stream=None, equations="euler",
-                 face_mode="mortar", wind_period=0.0):
+                 face_mode="mortar", wind_period=0.0, periodic=(False, False, False)):
         self.lib = load_library()
         d = MeshDesc()
         d.dim, d.N = dim, N
@@ -173,6 +175,8 @@ class Mesh:
         d.equations = 1 if equations == "tracer" else 0
         d.face_mode = 1 if face_mode == "interp" else 0
         d.wind_period = wind_period
+        for a in range(3):
+            d.periodic[a] = 1 if a < len(periodic) and periodic[a] else 0
         self.desc = d
         self.equations = equations
         self.dim, self.N, self.nv = dim, N, (1 if equations == "tracer" else dim + 2)
@@ -444,11 +448,12 @@ class Mesh:
 class Forest:
     """Host-only handle on the library's forest (no GPU needed)."""
 
-    def __init__(self, dim, base, max_level):
+    def __init__(self, dim, base, max_level, periodic=(False, False, False)):
         self.lib = load_library()
         b = (ctypes.c_int32 * 3)(*[int(base[a]) if a < len(base) else 1 for a in range(3)])
+        per = (ctypes.c_int32 * 3)(*[1 if a < len(periodic) and periodic[a] else 0 for a in range(3)])
         h = ctypes.c_void_p()
-        st = self.lib.dg_forest_create(dim, b, max_level, ctypes.byref(h))
+        st = self.lib.dg_forest_create_periodic(dim, b, max_level, per, ctypes.byref(h))
         if st != DG_OK:
             raise DGError(st, "dg_forest_create failed")
         self.h = h
