@@ -426,6 +426,50 @@ def run_leveque(pkg):
     return out
 
 
+def run_vortex(pkg, t_end=3.0, dt=0.0025, regrid_every=40, thr=1e-3):
+    """Isentropic vortex (Sec. 4.1) on the periodic [0, 12]^2 box, 32 x 32 roots, N = 3, FP64:
+    one refinement level where max |rho'| > thr (flags from the state), SSP-RK3 to t = 3 s, and
+    the uniform 32 x 32 grid; the error in the paper's norm (1/N_dof) sqrt(sum |q - q_exact|^2)
+    against the exact translated vortex (paper: about 8.75e-4 after 3 s)."""
+    import torch
+    out = {"workload": "isentropic_vortex_32x32_N3_L1", "t_end": t_end, "dt": dt}
+    NP = 16
+    for name, L in (("amr", 1), ("uniform32", 0)):
+        m = pkg.Mesh(2, 3, (32, 32), (12.0, 12.0), max_level=L, theta0=1.0, p0=1.0, g=0.0, R=1.0,
+                     cp=3.5, periodic=(True, True))
+
+        def flags():
+            return (np.abs(m.get_state()[0]).reshape(-1, NP).max(axis=1) > thr).astype(np.uint8)
+        if L:
+            m.set_vortex((6.0, 6.0), 5.0, (1.0, 1.0), 0.0)
+            m.adapt(flags=flags(), buffer=1)
+        m.set_vortex((6.0, 6.0), 5.0, (1.0, 1.0), 0.0)
+        m0 = m.integrals()[0]
+        nsteps = int(round(t_end / dt))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dof = 0
+        done = 0
+        while done < nsteps:
+            k = min(regrid_every, nsteps - done)
+            dof += 3 * k * m.num_elements * NP
+            m.step(dt, k)
+            done += k
+            if L and done < nsteps:
+                m.adapt(flags=flags(), buffer=1)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        q = m.get_state()
+        drift = abs(m.integrals()[0] - m0) / m0
+        m.set_vortex((6.0, 6.0), 5.0, (1.0, 1.0), t_end)
+        e = q - m.get_state()
+        out[name] = {"seconds": sec, "value": dof / sec, "unit": METRIC, "elements": m.num_elements,
+                     "l2_paper_norm": float(np.sqrt(np.sum(e * e)) / e.size), "mass_rel_change": drift}
+        m.close()
+    out["paper_l2_at_t3"] = 8.75e-4
+    return out
+
+
 def run_batch(pkg, steps=500, compare_steps=50):
     """Batched workload: 256 seeded 2D bubble instances (mesh 10x10 ... 64x32, N 3..7, FP32/FP64
     50/50, per-instance dt), autotuned layouts, `steps` graph-replayed SSP-RK3 steps; and the same
@@ -515,6 +559,8 @@ def main():
                     help="skip the 2D viscous cold-bubble leg")
     ap.add_argument("--no-leveque", action="store_true",
                     help="skip the tracer swirling-flow leg")
+    ap.add_argument("--no-vortex", action="store_true",
+                    help="skip the isentropic-vortex leg")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP32-vs-FP64 field comparison over the workload's full step count")
     ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2, 3],
@@ -607,6 +653,8 @@ def main():
         line["cold2d"] = run_cold2d(pkg)
     if not args.no_leveque:
         line["leveque"] = run_leveque(pkg)
+    if not args.no_vortex:
+        line["vortex"] = run_vortex(pkg)
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, nel, E, sec = oracle_sample(cfg, n_elem=1024, reps=1)
         line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",

@@ -182,6 +182,20 @@ dg_status dg_indicator(dg_mesh* mesh, double* out, size_t cap);
 dg_status dg_set_time(dg_mesh* mesh, double t);
 double dg_get_time(const dg_mesh* mesh);
 
+/* Isentropic vortex of Sec. 4.1, nondimensional: free stream rho = theta = p = 1 plus the
+ * vortex of strength beta centred at center (box coordinates), carried by the stream
+ * (u_inf[0], u_inf[1]) and set at time t (centre moved by u_inf t, nearest image on periodic
+ * axes):  T = 1 - (gamma-1) beta^2 / (8 gamma pi^2) e^(1-r^2), rho = T^(1/(gamma-1)), theta = 1,
+ * (u, v) = u_inf + beta/(2 pi) e^((1-r^2)/2) (-(y - y_c), x - x_c).  Requires a 2D Euler mesh
+ * with p0 = R = theta0 = 1 and g = 0 (DG_ERR_ARG otherwise). */
+typedef struct {
+  double center[2];
+  double beta;
+  double u_inf[2];
+  double t;
+} dg_vortex_desc;
+dg_status dg_set_vortex(dg_mesh* mesh, const dg_vortex_desc* vortex);
+
 /* Tracer meshes reuse the calls above: dg_set_bubble sets C = amp (1 + cos(pi r)) (the bell of
  * Sec. 4.2 with amp = h_max / 2; the random-field terms must be absent), dg_indicator and the
  * DG_CRIT_THETA criterion of dg_adapt use max |C| per element, dg_integrals returns

@@ -739,6 +739,22 @@ dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) {
   return bubble_eval(m, b, nullptr);
 }
 
+dg_status dg_set_vortex(dg_mesh* m, const dg_vortex_desc* v) {
+  if (!m || !v) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer || m->D != 2) return fail(m, DG_ERR_ARG, "the vortex needs a 2D Euler mesh");
+  if (m->desc.p0 != 1.0 || m->desc.R != 1.0 || m->desc.theta0 != 1.0 || m->desc.g != 0.0)
+    return fail(m, DG_ERR_ARG, "the vortex is nondimensional: p0 = R = theta0 = 1, g = 0");
+  if (!std::isfinite(v->beta) || !std::isfinite(v->t)) return fail(m, DG_ERR_ARG, "bad vortex");
+  const int per[2] = {m->desc.periodic[0] ? 1 : 0, m->desc.periodic[1] ? 1 : 0};
+  cudaError_t e = dgk::launch_vortex(m->prec, (int32_t)m->E, m->n1, m->d_elem, d_x(m), m->root_h,
+                                     m->desc.length, per, v->center, v->beta, v->u_inf, v->t,
+                                     m->ph.gamma, m->d_bg, m->q[0], plane(m), m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "vortex failed: %s", cudaGetErrorString(e));
+  m->pp_valid = false;
+  return DG_OK;
+}
+
 dg_status dg_bubble_theta(dg_mesh* m, const dg_bubble_desc* b, double* theta) {
   if (!m || !theta) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "no theta' field on a tracer mesh");

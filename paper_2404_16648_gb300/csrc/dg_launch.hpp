@@ -52,6 +52,10 @@ cudaError_t launch_background(int32_t E, int n1, int D, const int32_t* elem, con
                               double* bgc, cudaStream_t s);
 cudaError_t launch_pprime(int prec, int32_t E, int n1, int D, const void* theta_plane,
                           const double* bg, const double* bgc, const PhysC& ph, void* pp, cudaStream_t s);
+cudaError_t launch_vortex(int prec, int32_t E, int n1, const int32_t* elem, const double* xi,
+                          const double* root_h, const double* length, const int* periodic,
+                          const double* center, double beta, const double* uinf, double t,
+                          double gamma, const double* bg, void* q, int64_t plane, cudaStream_t s);
 cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* elem,
                           const double* xi, const double* root_h, const double* bg,
                           const double* center, const double* radius, double amp, int n_rff,

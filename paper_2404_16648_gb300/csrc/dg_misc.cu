@@ -347,6 +347,57 @@ cudaError_t launch_pprime(int prec, int32_t E, int n1, int D, const void* theta_
   return cudaGetLastError();
 }
 
+// Isentropic vortex of Sec. 4.1 (nondimensional: p0 = R = theta0 = 1, g = 0) moved to time t:
+// T = 1 - (gamma-1) beta^2 / (8 gamma pi^2) e^(1-r^2), rho = T^(1/(gamma-1)), theta = 1,
+// (u, v) = (U, V) + beta/(2 pi) e^((1-r^2)/2) (-dy, dx); dx, dy nearest-image on joined axes.
+template <class T>
+__global__ void vortex_kernel(int32_t E, int n1, const int32_t* elem, const double* xi, double hx0,
+                              double hy0, double lx, double ly, int perx, int pery, double cx,
+                              double cy, double beta, double ux, double uy, double gamma,
+                              const double* bg, T* q, int64_t plane) {
+  const int NP = n1 * n1;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (int64_t)E * NP) return;
+  const int64_t e = k / NP;
+  const int n = (int)(k - e * NP);
+  const int i = n % n1, j = n / n1;
+  const int level = elem[e * 4];
+  const double x = node_coord(elem[e * 4 + 1], xi[i], ldexp(hx0, -level));
+  const double y = node_coord(elem[e * 4 + 2], xi[j], ldexp(hy0, -level));
+  double dx = x - cx, dy = y - cy;
+  if (perx) dx = dx - lx * floor((dx + 0.5 * lx) / lx);
+  if (pery) dy = dy - ly * floor((dy + 0.5 * ly) / ly);
+  const double r2 = dx * dx + dy * dy;
+  const double Tt = 1.0 - (gamma - 1.0) * beta * beta / (8.0 * gamma * M_PI * M_PI) * exp(1.0 - r2);
+  const double rho = pow(Tt, 1.0 / (gamma - 1.0));
+  const double amp = beta / (2.0 * M_PI) * exp(0.5 * (1.0 - r2));
+  const double u = ux - amp * dy, v = uy + amp * dx;
+  const double* b = bg + (e * n1 + j) * 4;
+  q[k] = (T)(rho - b[0]);
+  q[plane + k] = (T)(rho * u);
+  q[2 * plane + k] = (T)(rho * v);
+  q[3 * plane + k] = (T)(rho - b[1]);
+}
+
+cudaError_t launch_vortex(int prec, int32_t E, int n1, const int32_t* elem, const double* xi,
+                          const double* root_h, const double* length, const int* periodic,
+                          const double* center, double beta, const double* uinf, double t,
+                          double gamma, const double* bg, void* q, int64_t plane, cudaStream_t s) {
+  const int64_t total = (int64_t)E * n1 * n1;
+  if (total == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  const double cx = center[0] + uinf[0] * t, cy = center[1] + uinf[1] * t;
+  if (prec == 0)
+    vortex_kernel<double><<<grid, 256, 0, s>>>(E, n1, elem, xi, root_h[0], root_h[1], length[0], length[1],
+                                               periodic[0], periodic[1], cx, cy, beta, uinf[0], uinf[1],
+                                               gamma, bg, (double*)q, plane);
+  else
+    vortex_kernel<float><<<grid, 256, 0, s>>>(E, n1, elem, xi, root_h[0], root_h[1], length[0], length[1],
+                                              periodic[0], periodic[1], cx, cy, beta, uinf[0], uinf[1],
+                                              gamma, bg, (float*)q, plane);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* elem,
                           const double* xi, const double* root_h, const double* bg,
                           const double* center, const double* radius, double amp, int n_rff,

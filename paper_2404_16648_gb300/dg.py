@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 
 
 # every symbol include/dg.h declares
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_nodes", "dg_get_leaves",
-            "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_bubble", "dg_rhs", "dg_step",
+            "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_vortex", "dg_set_bubble", "dg_rhs", "dg_step",
             "dg_adapt", "dg_indicator", "dg_primitives", "dg_integrals", "dg_set_time", "dg_get_time", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
             "dg_forest_create_periodic", "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
@@ -46,6 +46,11 @@ class BubbleDesc(ctypes.Structure):
                 ("amp", ctypes.c_double), ("n_rff", ctypes.c_int32), ("rff_sigma", ctypes.c_double),
                 ("rff_k", ctypes.POINTER(ctypes.c_double)),
                 ("rff_phase", ctypes.POINTER(ctypes.c_double))]
+
+
+class VortexDesc(ctypes.Structure):
+    _fields_ = [("center", ctypes.c_double * 2), ("beta", ctypes.c_double),
+                ("u_inf", ctypes.c_double * 2), ("t", ctypes.c_double)]
 
 
 class AdaptParams(ctypes.Structure):
@@ -88,6 +93,7 @@ def load_library(path=None):
         "dg_set_state": (i32, [vp, vp, ctypes.c_int]),
         "dg_get_state": (i32, [vp, vp, ctypes.c_int]),
         "dg_set_bubble": (i32, [vp, ctypes.POINTER(BubbleDesc)]),
+        "dg_set_vortex": (i32, [vp, ctypes.POINTER(VortexDesc)]),
         "dg_rhs": (i32, [vp, vp, vp, vp]),
         "dg_step": (i32, [vp, dbl, i32, vp]),
         "dg_adapt": (i32, [vp, ctypes.POINTER(AdaptParams), ctypes.POINTER(AdaptReport)]),
@@ -264,6 +270,15 @@ class Mesh:
 
     def set_bubble(self, center, radius, amp, rff=None):
         self._bubble(center, radius, amp, rff, None)
+
+    def set_vortex(self, center, beta, u_inf, t=0.0):
+        """Isentropic vortex of Sec. 4.1 (nondimensional mesh constants) moved to time t."""
+        v = VortexDesc()
+        v.center[0], v.center[1] = float(center[0]), float(center[1])
+        v.beta = float(beta)
+        v.u_inf[0], v.u_inf[1] = float(u_inf[0]), float(u_inf[1])
+        v.t = float(t)
+        self._check(self.lib.dg_set_vortex(self.h, ctypes.byref(v)))
 
     def bubble_theta(self, center, radius, amp, rff=None, out=None):
         """The bubble's theta' at every node as a device FP64 tensor (elements, nodes)."""
