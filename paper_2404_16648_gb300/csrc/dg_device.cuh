@@ -124,10 +124,14 @@ struct NodeBg {
 
 // Reciprocal and square root used by the fluxes.  Deterministic (the same inputs give the same
 // bits wherever they are evaluated), so the two elements of a face agree bit for bit.  FP64:
-// correctly rounded.  FP32: the hardware approximations (about 1 ulp), far below the FP32 path's
-// stated error bound.
+// correctly rounded.  FP32: the hardware approximations (about 1 ulp; rho is never subnormal),
+// far below the FP32 path's stated error bound.
 __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float recip(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ double sqrt_fast(double x) { return __dsqrt_rn(x); }
 __device__ __forceinline__ float sqrt_fast(float x) { return __fmul_rn(x, rsqrtf(x)); }
 
