@@ -219,3 +219,41 @@ def test_rhs_parity_large_theta_uses_fallback_branch(pkg, precision, tol):
     got = _gpu_rhs(lm, q).astype(np.float64)
     want = odg.rhs(om, q.astype(np.float64))
     assert _rel_err(got, want) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("dim,N,base", [(2, 3, (1, 1)), (3, 3, (1, 1, 1)), (3, 7, (1, 1, 1))])
+@pytest.mark.parametrize("layout", [1, 2, 3])
+def test_single_element_mesh(pkg, precision, tol, dim, N, base, layout):
+    """One element with walls on every face: the smallest mesh the method has."""
+    import torch
+    lm = pkg.Mesh(dim, N, base, (800.0,) * dim, precision=precision)
+    lm.set_stage_kernel(layout)
+    om = odg.Mesh(ofo.Forest(base, 0), N, (800.0,) * dim)
+    assert lm.num_elements == 1 and lm.num_mortars == 0
+    q = workloads.random_state(om.nv, om.E, om.np_, seed=200 + N + dim)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    qt = torch.from_numpy(q).to(dt)
+    got = lm.rhs(qt.cuda()).double().cpu().numpy()
+    want = odg.rhs(om, qt.double().numpy())
+    assert _rel_err(got, want) <= tol
+
+
+@pytest.mark.parametrize("dim,N", [(2, 3), (3, 2)])
+def test_deep_refinement_chain(pkg, dim, N):
+    """Refining the corner element six times (a 2:1 ripple towards the coarse roots): levels
+    0 .. 6 on one mesh, every level's 2/h from the per-level tables."""
+    base = (2,) * dim
+    lm = pkg.Mesh(dim, N, base, (64000.0,) * dim, max_level=6)
+    of = ofo.Forest(base, 6)
+    for _ in range(6):
+        flags = np.zeros(len(of), np.uint8)
+        flags[0] = 1                       # the leaf at the origin corner, Morton-first
+        lm.adapt(flags=flags, buffer=0)
+        of, _ = of.regrid(flags.astype(bool), 0)
+    om = odg.Mesh(of, N, (64000.0,) * dim)
+    levels = [l for l, _ in of.leaves]
+    assert max(levels) == 6 and min(levels) <= 1 and lm.num_elements == om.E
+    assert of.is_balanced()
+    q = workloads.random_state(om.nv, om.E, om.np_, seed=300 + dim)
+    assert _rel_err(_gpu_rhs(lm, q), odg.rhs(om, q)) <= 1e-12
