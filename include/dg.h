@@ -55,7 +55,9 @@ enum { DG_FACE_MORTAR = 0, DG_FACE_INTERP = 1 };  /* dg_mesh_desc.face_mode */
 #define DG_MAX_LEVEL 12
 
 /* Mesh description.  Defaults for the physics are theta0 = 300 K, p0 = 1e5 Pa, g = 9.81,
- * R = 287, cp = 1004.5 (the paper gives none; Sec. 4.3 gives theta0 = 300 K). */
+ * R = 287, cp = 1004.5 (the paper gives none; Sec. 4.3 gives theta0 = 300 K).  The neutral
+ * background ends where its Exner function vanishes, so with g > 0 the box height must stay
+ * below cp theta0 / g (30.7 km for the defaults; DG_ERR_ARG otherwise). */
 typedef struct {
   int32_t dim;          /* 2 (x-z) or 3 */
   int32_t N;            /* polynomial degree, 1..DG_MAX_N; (N+1)^d LGL nodes per element */

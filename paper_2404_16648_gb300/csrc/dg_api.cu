@@ -578,6 +578,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   if (!(desc->p0 > 0.0) || !(desc->R > 0.0) || !(desc->cp > desc->R) || !(desc->theta0 > 0.0))
     return DG_ERR_ARG;
   if (desc->equations != DG_EQ_EULER && desc->equations != DG_EQ_TRACER) return DG_ERR_ARG;
+  // the neutral background exists below z = cp theta0 / g, where the Exner function vanishes
+  if (desc->g > 0.0 && !(desc->length[desc->dim - 1] < desc->cp * desc->theta0 / desc->g)) return DG_ERR_ARG;
   // a periodic vertical axis needs a uniform background (g = 0)
   if (desc->periodic[desc->dim - 1] && desc->g != 0.0) return DG_ERR_UNSUPPORTED;
   if (desc->face_mode != DG_FACE_MORTAR && desc->face_mode != DG_FACE_INTERP) return DG_ERR_ARG;

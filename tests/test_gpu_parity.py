@@ -244,16 +244,25 @@ def test_deep_refinement_chain(pkg, dim, N):
     """Refining the corner element six times (a 2:1 ripple towards the coarse roots): levels
     0 .. 6 on one mesh, every level's 2/h from the per-level tables."""
     base = (2,) * dim
-    lm = pkg.Mesh(dim, N, base, (64000.0,) * dim, max_level=6)
+    lm = pkg.Mesh(dim, N, base, (16000.0,) * dim, max_level=6)
     of = ofo.Forest(base, 6)
     for _ in range(6):
         flags = np.zeros(len(of), np.uint8)
         flags[0] = 1                       # the leaf at the origin corner, Morton-first
         lm.adapt(flags=flags, buffer=0)
         of, _ = of.regrid(flags.astype(bool), 0)
-    om = odg.Mesh(of, N, (64000.0,) * dim)
+    om = odg.Mesh(of, N, (16000.0,) * dim)
     levels = [l for l, _ in of.leaves]
     assert max(levels) == 6 and min(levels) <= 1 and lm.num_elements == om.E
     assert of.is_balanced()
     q = workloads.random_state(om.nv, om.E, om.np_, seed=300 + dim)
     assert _rel_err(_gpu_rhs(lm, q), odg.rhs(om, q)) <= 1e-12
+
+
+def test_box_above_the_neutral_atmosphere_is_rejected(pkg):
+    """The neutral background ends where the Exner function reaches zero, z = cp theta0 / g
+    (30.7 km for the default constants); a taller box has no background and is refused."""
+    from paper_2404_16648_gb300.dg import DGError
+    with pytest.raises(DGError):
+        pkg.Mesh(2, 3, (2, 2), (10000.0, 31000.0))
+    pkg.Mesh(2, 3, (2, 2), (10000.0, 30000.0)).close()
