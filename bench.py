@@ -46,10 +46,11 @@ def _peaks():
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, log_dir=None):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index) \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/dg_clocks_%d.csv" % os.getpid()
+        d = log_dir if log_dir else tempfile.gettempdir()
+        self.path = os.path.join(d, "clocks_rank%d_%d.csv" % (gpu_index, os.getpid()))
         self.gpu = gpu_index
 
     def start(self):
@@ -561,6 +562,8 @@ def main():
                     help="skip the tracer swirling-flow leg")
     ap.add_argument("--no-vortex", action="store_true",
                     help="skip the isentropic-vortex leg")
+    ap.add_argument("--clock-log", default=None,
+                    help="directory for the raw nvidia-smi clock samples (default: a temporary one)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP32-vs-FP64 field comparison over the workload's full step count")
     ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2, 3],
@@ -602,7 +605,7 @@ def main():
     import paper_2404_16648_gb300 as pkg
     pkg.load_library()
     peaks, peak_kind = _peaks()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(local, args.clock_log)
     m32, r32 = run_path(pkg, cfg, "fp32", args.steps, args.warmup, regrid_every, sampler, world)
     e2e = run_e2e(pkg, m32, cfg, max(4, min(args.steps, 20)), regrid_every, world)
     m32.close()
