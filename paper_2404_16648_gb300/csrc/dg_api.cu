@@ -4,6 +4,8 @@
 // for three state copies (q^n and two RK stage states), the per-element integer tables, the
 // FP64 background, the mortar flux buffer, and the integral reduction scratch.  Regrids
 // rebuild the tables and transfer q^n; the stage states are reallocated with it.
+#include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -16,6 +18,7 @@
 #include "../../include/dg.h"
 #include "basis.hpp"
 #include "dg_launch.hpp"
+#include "host_pool.hpp"
 #include "tree.hpp"
 
 #include "dg_mesh.hpp"
@@ -107,27 +110,44 @@ dg_status rebuild_topology(dg_mesh* m) {
   m->G = (int64_t)(m->mort.size() / 7);
   std::vector<int32_t> conn;
   m->forest.connectivity(m->mort, &conn);
-  // every index a kernel will follow must be in range before anything is uploaded
+  // every index a kernel will follow must be in range before anything is uploaded; the error
+  // names the first bad row
   const int nf = 2 * m->D;
-  for (int64_t r = 0; r < m->E * nf; ++r) {
-    const int32_t* c = conn.data() + r * 5;
-    bool ok = true;
-    switch (c[0]) {
-      case dgl::FACE_WALL: break;
-      case dgl::FACE_CONF: ok = c[1] >= 0 && c[1] < m->E; break;
-      case dgl::FACE_FINE: ok = c[1] >= 0 && c[1] < m->E && c[2] >= 0 && c[2] < m->G && c[3] >= 0 && c[3] < m->NSUB; break;
-      case dgl::FACE_COARSE: ok = c[1] >= 0 && c[1] < m->G; break;
-      default: ok = false;
+  const int64_t E = m->E, G = m->G;
+  const int NSUB = m->NSUB, D = m->D;
+  std::atomic<int64_t> bad_face{INT64_MAX}, bad_group{INT64_MAX};
+  auto note = [](std::atomic<int64_t>& first, int64_t r) {
+    int64_t cur = first.load(std::memory_order_relaxed);
+    while (r < cur && !first.compare_exchange_weak(cur, r, std::memory_order_relaxed)) {}
+  };
+  dgl::parallel_ranges(E * nf, 8192, [&](int64_t r0, int64_t r1) {
+    for (int64_t r = r0; r < r1; ++r) {
+      const int32_t* c = conn.data() + r * 5;
+      bool ok = true;
+      switch (c[0]) {
+        case dgl::FACE_WALL: break;
+        case dgl::FACE_CONF: ok = c[1] >= 0 && c[1] < E; break;
+        case dgl::FACE_FINE: ok = c[1] >= 0 && c[1] < E && c[2] >= 0 && c[2] < G && c[3] >= 0 && c[3] < NSUB; break;
+        case dgl::FACE_COARSE: ok = c[1] >= 0 && c[1] < G; break;
+        default: ok = false;
+      }
+      if (!ok) { note(bad_face, r); return; }
     }
-    if (!ok) return fail(m, DG_ERR_STATE, "inconsistent connectivity at element %lld face %d",
-                         (long long)(r / nf), (int)(r % nf));
+  });
+  if (bad_face.load() != INT64_MAX) {
+    const int64_t r = bad_face.load();
+    return fail(m, DG_ERR_STATE, "inconsistent connectivity at element %lld face %d", (long long)(r / nf), (int)(r % nf));
   }
-  for (int64_t g = 0; g < m->G; ++g)
-    for (int k = 0; k < 3 + m->NSUB; ++k) {
-      const int32_t v = m->mort[g * 7 + k];
-      const bool ok = k == 0 || k >= 3 ? (v >= 0 && v < m->E) : (v >= 0 && v < (k == 1 ? m->D : 2));
-      if (!ok) return fail(m, DG_ERR_STATE, "inconsistent mortar group %lld", (long long)g);
-    }
+  dgl::parallel_ranges(G, 4096, [&](int64_t g0, int64_t g1) {
+    for (int64_t g = g0; g < g1; ++g)
+      for (int k = 0; k < 3 + NSUB; ++k) {
+        const int32_t v = m->mort[g * 7 + k];
+        const bool ok = k == 0 || k >= 3 ? (v >= 0 && v < E) : (v >= 0 && v < (k == 1 ? D : 2));
+        if (!ok) { note(bad_group, g); return; }
+      }
+  });
+  if (bad_group.load() != INT64_MAX)
+    return fail(m, DG_ERR_STATE, "inconsistent mortar group %lld", (long long)bad_group.load());
   std::vector<int32_t> elem((size_t)m->E * 4);
   const auto& L = m->forest.leaves();
   for (int64_t e = 0; e < m->E; ++e) {
@@ -854,13 +874,11 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
     return fail(m, DG_ERR_STATE, "regrid failed: %s", why.c_str());
   const int64_t E_old = m->E;
   const int64_t plane_old = plane(m);
-  std::vector<int32_t> tm(tmap.size() * 9);
-  for (size_t i = 0; i < tmap.size(); ++i) {
-    tm[i * 9] = tmap[i].kind;
-    for (int k = 0; k < 8; ++k) tm[i * 9 + 1 + k] = tmap[i].src[k];
-  }
-  CU(reserve(m->d_tm, m->c_tm, tm.size() * sizeof(int32_t) + 4));
-  CU(cudaMemcpy(m->d_tm, tm.data(), tm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  // the device reads the map as rows of 9 int32 {kind, src[8]}: the host entries as they lie
+  static_assert(sizeof(dgl::TransferEntry) == 9 * sizeof(int32_t), "transfer rows are 9 int32");
+  const size_t tm_bytes = tmap.size() * sizeof(dgl::TransferEntry);
+  CU(reserve(m->d_tm, m->c_tm, tm_bytes + 4));
+  CU(cudaMemcpy(m->d_tm, tmap.data(), tm_bytes, cudaMemcpyHostToDevice));
   m->forest = std::move(nf);
   ++m->generation;
   dg_status st = rebuild_topology(m);

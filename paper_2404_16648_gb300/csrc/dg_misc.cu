@@ -2,6 +2,7 @@
 // hydrostatic background (FP64), initial bubble, refinement indicator, compensated integrals
 // and the conservative parent<->child transfer of Sec. 3.3.
 #include "dg_launch.hpp"
+#include "../../include/dg.h"
 
 #include <cmath>
 
@@ -80,27 +81,84 @@ __global__ void bubble_kernel(int32_t E, int n1, int D, const int32_t* elem, con
 
 // max over the element's nodes of |theta'|, theta' = (Theta_bar + Theta') / (rho_bar + rho')
 // - theta0, in FP64 (refinement criterion of Sec. 4.3, tagging by potential temperature).
+//
+// One warp per element.  With A = Theta_bar + Theta' and B = rho_bar + rho' (FP64 sums), the
+// rounded quotient fl(A/B) and then fl(fl(A/B) - theta0) are monotone in the exact quotient A/B,
+// so the largest |theta'| sits at the node of largest or of smallest A/B.  An FP32 estimate
+// r = fl32(A) / fl32(B) (two conversions and __fdividef, whose error is at most 2 ulp for a
+// divisor in [2^-126, 2^126]: relative error below 2^-21, plus at most 2^-126 where r falls
+// below the FP32 normal range) picks every node within 2^-18 max|r| of the largest or smallest
+// estimate, a band wider than twice the error; only those take the FP64 division, and the
+// result is the value the division at every node gives.  An element outside that range (a
+// non-finite value, B or a nonzero |A| outside [1e-30, 1e30], max|r| outside [1e-20, 1e30])
+// takes the division at every node instead.
+constexpr int kIndPerLane = (DG_MAX_N + 1) * (DG_MAX_N + 1) * (DG_MAX_N + 1) / 32 + 1;
+
 template <class T>
 __global__ void indicator_kernel(int32_t E, int n1, int D, const double* bg, const T* q,
                                  int64_t plane, double theta0, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (e >= E) return;   // whole warps leave together
   const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
-  const int64_t e = blockIdx.x;
-  __shared__ double red[256];
-  double m = 0.0;
-  for (int n = threadIdx.x; n < NP; n += blockDim.x) {
-    const int k = D == 3 ? n / (n1 * n1) : n / n1;
-    const double* b = bg + (e * n1 + k) * 4;
-    const int64_t i = e * NP + n;
-    const double th = (b[1] + (double)q[(int64_t)(D + 1) * plane + i]) / (b[0] + (double)q[i]) - theta0;
-    m = fmax(m, fabs(th));
+  const int layer = D == 3 ? n1 * n1 : n1;
+  const T* q0 = q + e * NP;
+  const T* q3 = q + (int64_t)(D + 1) * plane + e * NP;
+  const double* be = bg + e * n1 * 4;
+  float r[kIndPerLane];
+  float rmax = -INFINITY, rmin = INFINITY, amax = 0.0f;
+  bool fast = true;
+#pragma unroll
+  for (int j = 0; j < kIndPerLane; ++j) {
+    const int n = lane + 32 * j;
+    r[j] = 0.0f;
+    if (n < NP) {
+      const double* b = be + (n / layer) * 4;
+      const double A = b[1] + (double)q3[n];
+      const double B = b[0] + (double)q0[n];
+      // false for NaN too
+      fast = fast && B >= 1e-30 && B <= 1e30 && fabs(A) <= 1e30 && (fabs(A) >= 1e-30 || A == 0.0);
+      r[j] = __fdividef((float)A, (float)B);
+      rmax = fmaxf(rmax, r[j]);
+      rmin = fminf(rmin, r[j]);
+      amax = fmaxf(amax, fabsf(r[j]));
+    }
   }
-  red[threadIdx.x] = m;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   }
-  if (threadIdx.x == 0) out[e] = red[0];
+  fast = __all_sync(0xffffffffu, fast) && amax >= 1e-20f && amax <= 1e30f;
+  double m;
+  if (fast) {
+    const float band = amax * 0x1p-18f;
+    const float tmax = rmax - band, tmin = rmin + band;
+    double vmax = -INFINITY, vmin = INFINITY;
+#pragma unroll
+    for (int j = 0; j < kIndPerLane; ++j) {
+      const int n = lane + 32 * j;
+      if (n < NP && (r[j] >= tmax || r[j] <= tmin)) {
+        const double* b = be + (n / layer) * 4;
+        const double v = (b[1] + (double)q3[n]) / (b[0] + (double)q0[n]);
+        if (r[j] >= tmax) vmax = fmax(vmax, v);
+        if (r[j] <= tmin) vmin = fmin(vmin, v);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      vmin = fmin(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+    }
+    m = fmax(fabs(vmax - theta0), fabs(vmin - theta0));
+  } else {
+    m = 0.0;
+    for (int n = lane; n < NP; n += 32) {
+      const double* b = be + (n / layer) * 4;
+      m = fmax(m, fabs((b[1] + (double)q3[n]) / (b[0] + (double)q0[n]) - theta0));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  }
+  if (lane == 0) out[e] = m;
 }
 
 // Primitive diagnostics per node in FP64: out[a] = U_a / rho (a < D), out[D] = theta'
@@ -422,8 +480,9 @@ cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* ele
 cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
                              int64_t plane, double theta0, double* out, cudaStream_t s) {
   if (E == 0) return cudaSuccess;
-  if (prec == 0) indicator_kernel<double><<<E, 256, 0, s>>>(E, n1, D, bg, (const double*)q, plane, theta0, out);
-  else indicator_kernel<float><<<E, 256, 0, s>>>(E, n1, D, bg, (const float*)q, plane, theta0, out);
+  const int grid = (int)((E + 7) / 8);   // 8 warps of 32, one element each
+  if (prec == 0) indicator_kernel<double><<<grid, 256, 0, s>>>(E, n1, D, bg, (const double*)q, plane, theta0, out);
+  else indicator_kernel<float><<<grid, 256, 0, s>>>(E, n1, D, bg, (const float*)q, plane, theta0, out);
   return cudaGetLastError();
 }
 

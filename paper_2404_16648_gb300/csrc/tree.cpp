@@ -3,8 +3,9 @@
 #include "tree.hpp"
 
 #include <algorithm>
-#include <deque>
-#include <thread>
+#include <atomic>
+
+#include "host_pool.hpp"
 
 namespace dgl {
 
@@ -31,17 +32,6 @@ static uint64_t mix64(uint64_t x) {   // splitmix64 finaliser
 }
 static constexpr uint64_t kEmpty = ~0ULL;   // never a key: levels < 32, coordinates < 2^19
 
-// fn(e0, e1) over [0, n) split into contiguous ranges on up to 16 threads (one below 8192).
-template <class F>
-static void parallel_ranges(int64_t n, F fn) {
-  int nt = (int)std::min<unsigned>(16u, std::max(1u, std::thread::hardware_concurrency()));
-  if (n < 8192) nt = 1;
-  if (nt == 1) { fn((int64_t)0, n); return; }
-  std::vector<std::thread> th;
-  for (int t = 0; t < nt; ++t) th.emplace_back(fn, n * t / nt, n * (t + 1) / nt);
-  for (auto& x : th) x.join();
-}
-
 void Forest::set_leaves(std::vector<Leaf> leaves) {
   leaves_ = std::move(leaves);
   uint64_t cap = 16;
@@ -56,11 +46,10 @@ void Forest::set_leaves(std::vector<Leaf> leaves) {
     hkeys_[h] = k;
     hvals_[h] = (int32_t)i;
   }
-  // face table; every entry depends on its own face only, so the split over threads does not
-  // change the result
+  // face table; every entry depends on its own face only
   const int64_t n = (int64_t)leaves_.size();
   faces_.assign((size_t)n * dim_ * 2, FaceInfo{FACE_WALL, {-1, -1, -1, -1}});
-  parallel_ranges(n, [this](int64_t e0, int64_t e1) {
+  parallel_ranges(n, 512, [this](int64_t e0, int64_t e1) {
     for (int64_t e = e0; e < e1; ++e)
       for (int a = 0; a < dim_; ++a)
         for (int s = 0; s < 2; ++s) faces_[((size_t)e * dim_ + a) * 2 + s] = classify((int32_t)e, a, s);
@@ -116,114 +105,134 @@ FaceInfo Forest::classify(int32_t e, int axis, int side) const {
   return fi;
 }
 
-void Forest::neighbours(int32_t e, std::vector<int32_t>* out) const {
-  out->clear();
-  for (int a = 0; a < dim_; ++a)
-    for (int s = 0; s < 2; ++s) {
-      const FaceInfo& fi = face(e, a, s);
-      if (fi.kind == FACE_CONF || fi.kind == FACE_FINE) out->push_back(fi.nb[0]);
-      else if (fi.kind == FACE_COARSE)
-        for (int k = 0; k < (1 << (dim_ - 1)); ++k) out->push_back(fi.nb[k]);
-    }
-}
-
 bool Forest::regrid(const std::vector<uint8_t>& tag, int B, int max_level, Forest* out,
                     std::vector<TransferEntry>* tmap, int64_t* n_refined,
                     int64_t* n_coarsened, std::string* err) const {
   const int64_t n = size();
   const int nkids = 1 << dim_;
-  // neighbour lists (CSR)
-  std::vector<int32_t> off(n + 1, 0), adj;
-  std::vector<int32_t> tmp;
-  for (int64_t e = 0; e < n; ++e) {
-    for (int a = 0; a < dim_; ++a)
-      for (int s = 0; s < 2; ++s)
-        if (face((int32_t)e, a, s).kind < 0) { *err = "forest is not 2:1 balanced"; return false; }
-    neighbours((int32_t)e, &tmp);
-    adj.insert(adj.end(), tmp.begin(), tmp.end());
-    off[e + 1] = (int32_t)adj.size();
-  }
+  const int nsub = 1 << (dim_ - 1);
+  const int nf = 2 * dim_;
+  // neighbour lists (CSR over the face table, faces in (axis, side) order)
+  std::vector<int64_t> off(n + 1, 0);
+  std::atomic<int> unbalanced{0};
+  parallel_ranges(n, 1024, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) {
+      int64_t c = 0;
+      for (int f = 0; f < nf; ++f) {
+        const int k = faces_[(size_t)e * nf + f].kind;
+        if (k < 0) unbalanced.store(1, std::memory_order_relaxed);
+        c += (k == FACE_CONF || k == FACE_FINE) ? 1 : (k == FACE_COARSE ? nsub : 0);
+      }
+      off[e] = c;
+    }
+  });
+  if (unbalanced.load()) { *err = "forest is not 2:1 balanced"; return false; }
+  off[n] = exclusive_scan(off.data(), n);
+  std::vector<int32_t> adj((size_t)off[n]);
+  parallel_ranges(n, 1024, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) {
+      int64_t o = off[e];
+      for (int f = 0; f < nf; ++f) {
+        const FaceInfo& fi = faces_[(size_t)e * nf + f];
+        const int c = (fi.kind == FACE_CONF || fi.kind == FACE_FINE) ? 1 : (fi.kind == FACE_COARSE ? nsub : 0);
+        for (int k = 0; k < c; ++k) adj[o++] = fi.nb[k];
+      }
+    }
+  });
   // buffer: dilate the tags B times over face neighbours
-  std::vector<uint8_t> near(n), prev(n);
+  std::vector<uint8_t> near(n), prev;
   for (int64_t e = 0; e < n; ++e) near[e] = tag[e] ? 1 : 0;
   for (int it = 0; it < B; ++it) {
     prev = near;
-    for (int64_t e = 0; e < n; ++e) {
-      if (prev[e]) continue;
-      for (int32_t k = off[e]; k < off[e + 1]; ++k)
-        if (prev[adj[k]]) { near[e] = 1; break; }
-    }
+    parallel_ranges(n, 2048, [&](int64_t e0, int64_t e1) {
+      for (int64_t e = e0; e < e1; ++e) {
+        if (prev[e]) continue;
+        for (int64_t k = off[e]; k < off[e + 1]; ++k)
+          if (prev[adj[k]]) { near[e] = 1; break; }
+      }
+    });
   }
   // refinement and its 2:1 closure (least fixpoint, independent of visiting order)
   std::vector<uint8_t> ref(n, 0);
-  std::deque<int32_t> work;
+  std::vector<int32_t> work;
   for (int64_t e = 0; e < n; ++e)
     if (near[e] && leaves_[e].level < max_level) { ref[e] = 1; work.push_back((int32_t)e); }
-  while (!work.empty()) {
-    int32_t e = work.front(); work.pop_front();
-    for (int32_t k = off[e]; k < off[e + 1]; ++k) {
-      int32_t m = adj[k];
+  for (size_t head = 0; head < work.size(); ++head) {
+    const int32_t e = work[head];
+    for (int64_t k = off[e]; k < off[e + 1]; ++k) {
+      const int32_t m = adj[k];
       if (!ref[m] && leaves_[m].level < leaves_[e].level) { ref[m] = 1; work.push_back(m); }
     }
   }
-  std::vector<int32_t> target(n);
-  for (int64_t e = 0; e < n; ++e) target[e] = leaves_[e].level + ref[e];
-  // families: complete sibling groups are contiguous in Morton order, child index 0 first
+  // families: complete sibling groups are contiguous in Morton order, child index 0 first.  A
+  // family head has even coordinates and its siblings odd ones, so families never overlap and
+  // each head is judged on its own; coars = 2 at a coarsened family's head, 1 at its siblings.
   std::vector<uint8_t> coars(n, 0);
-  int64_t ncoarse = 0;
-  for (int64_t e = 0; e + nkids <= n; ++e) {
-    const Leaf& L = leaves_[e];
-    if (L.level == 0) continue;
-    if ((L.c[0] & 1) || (L.c[1] & 1) || (L.c[2] & 1)) continue;
-    bool complete = true;
-    for (int k = 1; k < nkids && complete; ++k) {
-      const Leaf& M = leaves_[e + k];
-      int32_t want[3] = {L.c[0] + (k & 1), L.c[1] + ((k >> 1) & 1), L.c[2] + ((k >> 2) & 1)};
-      if (dim_ == 2) { want[1] = L.c[1] + ((k >> 1) & 1); want[2] = 0; }
-      complete = M.level == L.level && M.c[0] == want[0] && M.c[1] == want[1] && M.c[2] == want[2];
-    }
-    if (!complete) continue;
-    bool ok = true;
-    for (int k = 0; k < nkids && ok; ++k) if (near[e + k] || ref[e + k]) ok = false;
-    for (int k = 0; k < nkids && ok; ++k) {
-      int64_t m = e + k;
-      for (int32_t j = off[m]; j < off[m + 1]; ++j) {
-        int32_t o = adj[j];
-        if (o >= e && o < e + nkids) continue;
-        if (target[o] > L.level) { ok = false; break; }
+  parallel_ranges(n, 2048, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1 && e + nkids <= n; ++e) {
+      const Leaf& L = leaves_[e];
+      if (L.level == 0) continue;
+      if ((L.c[0] & 1) || (L.c[1] & 1) || (L.c[2] & 1)) continue;
+      bool complete = true;
+      for (int k = 1; k < nkids && complete; ++k) {
+        const Leaf& M = leaves_[e + k];
+        int32_t want[3] = {L.c[0] + (k & 1), L.c[1] + ((k >> 1) & 1), L.c[2] + ((k >> 2) & 1)};
+        if (dim_ == 2) want[2] = 0;
+        complete = M.level == L.level && M.c[0] == want[0] && M.c[1] == want[1] && M.c[2] == want[2];
+      }
+      if (!complete) continue;
+      bool ok = true;
+      for (int k = 0; k < nkids && ok; ++k) if (near[e + k] || ref[e + k]) ok = false;
+      for (int k = 0; k < nkids && ok; ++k) {
+        const int64_t m = e + k;
+        for (int64_t j = off[m]; j < off[m + 1]; ++j) {
+          const int32_t o = adj[j];
+          if (o >= e && o < e + nkids) continue;
+          if (leaves_[o].level + ref[o] > L.level) { ok = false; break; }
+        }
+      }
+      if (ok) {
+        coars[e] = 2;
+        for (int k = 1; k < nkids; ++k) coars[e + k] = 1;
       }
     }
-    if (ok) { for (int k = 0; k < nkids; ++k) coars[e + k] = 1; ++ncoarse; e += nkids - 1; }
-  }
-  // emit new leaves in order
-  std::vector<Leaf> nl;
-  tmap->clear();
-  int64_t nref = 0;
+  });
+  // emit new leaves in order: a refined leaf gives its 2^d children, a coarsened family its
+  // parent (at the head), every other leaf itself
+  std::vector<int64_t> pos(n + 1);
+  int64_t nref = 0, ncoarse = 0;
   for (int64_t e = 0; e < n; ++e) {
-    const Leaf& L = leaves_[e];
-    if (ref[e]) {
-      ++nref;
-      for (int ci = 0; ci < nkids; ++ci) {
-        Leaf c{L.level + 1, {2 * L.c[0] + (ci & 1), 2 * L.c[1] + ((ci >> 1) & 1),
-                             2 * L.c[2] + ((ci >> 2) & 1)}};
-        if (dim_ == 2) c.c[2] = 0;
-        nl.push_back(c);
-        TransferEntry t{XFER_CHILD, {(int32_t)e, ci, -1, -1, -1, -1, -1, -1}};
-        tmap->push_back(t);
-      }
-    } else if (coars[e]) {
-      Leaf p{L.level - 1, {L.c[0] >> 1, L.c[1] >> 1, L.c[2] >> 1}};
-      nl.push_back(p);
-      TransferEntry t{XFER_PARENT, {-1, -1, -1, -1, -1, -1, -1, -1}};
-      for (int k = 0; k < nkids; ++k) t.src[k] = (int32_t)(e + k);
-      tmap->push_back(t);
-      e += nkids - 1;
-    } else {
-      nl.push_back(L);
-      TransferEntry t{XFER_KEEP, {(int32_t)e, -1, -1, -1, -1, -1, -1, -1}};
-      tmap->push_back(t);
-    }
+    nref += ref[e];
+    ncoarse += coars[e] == 2;
+    pos[e] = ref[e] ? nkids : (coars[e] == 1 ? 0 : 1);
   }
+  pos[n] = exclusive_scan(pos.data(), n);
+  std::vector<Leaf> nl((size_t)pos[n]);
+  tmap->assign((size_t)pos[n], TransferEntry{});
+  TransferEntry* tm = tmap->data();
+  parallel_ranges(n, 2048, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) {
+      const Leaf& L = leaves_[e];
+      int64_t o = pos[e];
+      if (ref[e]) {
+        for (int ci = 0; ci < nkids; ++ci, ++o) {
+          Leaf c{L.level + 1, {2 * L.c[0] + (ci & 1), 2 * L.c[1] + ((ci >> 1) & 1),
+                               2 * L.c[2] + ((ci >> 2) & 1)}};
+          if (dim_ == 2) c.c[2] = 0;
+          nl[o] = c;
+          tm[o] = TransferEntry{XFER_CHILD, {(int32_t)e, ci, -1, -1, -1, -1, -1, -1}};
+        }
+      } else if (coars[e] == 2) {
+        nl[o] = Leaf{L.level - 1, {L.c[0] >> 1, L.c[1] >> 1, L.c[2] >> 1}};
+        TransferEntry t{XFER_PARENT, {-1, -1, -1, -1, -1, -1, -1, -1}};
+        for (int k = 0; k < nkids; ++k) t.src[k] = (int32_t)(e + k);
+        tm[o] = t;
+      } else if (coars[e] == 0) {
+        nl[o] = L;
+        tm[o] = TransferEntry{XFER_KEEP, {(int32_t)e, -1, -1, -1, -1, -1, -1, -1}};
+      }
+    }
+  });
   out->dim_ = dim_;
   out->max_level_ = max_level_;
   for (int a = 0; a < 3; ++a) { out->base_[a] = base_[a]; out->periodic_[a] = periodic_[a]; }
@@ -235,23 +244,57 @@ bool Forest::regrid(const std::vector<uint8_t>& tag, int B, int max_level, Fores
 
 void Forest::face_lists(std::vector<int32_t>* conf, std::vector<int32_t>* mort,
                         std::vector<int32_t>* bnd) const {
-  conf->clear(); mort->clear(); bnd->clear();
-  for (int64_t e = 0; e < size(); ++e) {
-    for (int a = 0; a < dim_; ++a) {
-      const FaceInfo& fi = face((int32_t)e, a, 1);
-      if (fi.kind == FACE_CONF) { conf->push_back((int32_t)e); conf->push_back(fi.nb[0]); conf->push_back(a); }
-    }
-    for (int a = 0; a < dim_; ++a)
-      for (int s = 0; s < 2; ++s) {
-        const FaceInfo& fi = face((int32_t)e, a, s);
-        if (fi.kind == FACE_COARSE) {
-          mort->push_back((int32_t)e); mort->push_back(a); mort->push_back(s);
-          for (int k = 0; k < 4; ++k) mort->push_back(k < (1 << (dim_ - 1)) ? fi.nb[k] : -1);
-        } else if (fi.kind == FACE_WALL) {
-          bnd->push_back((int32_t)e); bnd->push_back(a); bnd->push_back(s);
+  // per element: conforming faces on the + side, then every coarse face (mortar group) and
+  // wall face in (axis, side) order; rows are placed by prefix sums of the per-element counts
+  const int64_t n = size();
+  const int nsub = 1 << (dim_ - 1);
+  std::vector<int64_t> pc(n + 1), pm(n + 1), pb(n + 1);
+  parallel_ranges(n, 2048, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) {
+      int64_t c = 0, m = 0, b = 0;
+      for (int a = 0; a < dim_; ++a) {
+        c += face((int32_t)e, a, 1).kind == FACE_CONF;
+        for (int s = 0; s < 2; ++s) {
+          const int k = face((int32_t)e, a, s).kind;
+          m += k == FACE_COARSE;
+          b += k == FACE_WALL;
         }
       }
-  }
+      pc[e] = c; pm[e] = m; pb[e] = b;
+    }
+  });
+  pc[n] = exclusive_scan(pc.data(), n);
+  pm[n] = exclusive_scan(pm.data(), n);
+  pb[n] = exclusive_scan(pb.data(), n);
+  conf->assign((size_t)pc[n] * 3, 0);
+  mort->assign((size_t)pm[n] * 7, 0);
+  bnd->assign((size_t)pb[n] * 3, 0);
+  int32_t* C = conf->data();
+  int32_t* M = mort->data();
+  int32_t* W = bnd->data();
+  parallel_ranges(n, 2048, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e) {
+      int32_t* c = C + pc[e] * 3;
+      int32_t* m = M + pm[e] * 7;
+      int32_t* w = W + pb[e] * 3;
+      for (int a = 0; a < dim_; ++a) {
+        const FaceInfo& fi = face((int32_t)e, a, 1);
+        if (fi.kind == FACE_CONF) { c[0] = (int32_t)e; c[1] = fi.nb[0]; c[2] = a; c += 3; }
+      }
+      for (int a = 0; a < dim_; ++a)
+        for (int s = 0; s < 2; ++s) {
+          const FaceInfo& fi = face((int32_t)e, a, s);
+          if (fi.kind == FACE_COARSE) {
+            m[0] = (int32_t)e; m[1] = a; m[2] = s;
+            for (int k = 0; k < 4; ++k) m[3 + k] = k < nsub ? fi.nb[k] : -1;
+            m += 7;
+          } else if (fi.kind == FACE_WALL) {
+            w[0] = (int32_t)e; w[1] = a; w[2] = s;
+            w += 3;
+          }
+        }
+    }
+  });
 }
 
 void Forest::partition(int nparts, std::vector<int64_t>* starts) const {
@@ -287,28 +330,33 @@ void Forest::connectivity(const std::vector<int32_t>& mort, std::vector<int32_t>
   // Rows {kind, a, b, c, d} per element face f = 2*axis + side:
   //   WALL {0}; CONF {1, neighbour}; FINE {2, coarse element, mortar group, sub-face};
   //   COARSE {3, mortar group}.  Mortar groups are the rows of `mort` (face_lists order).
+  // Every face belongs to at most one mortar group, so the groups fill disjoint rows.
   const int nf = 2 * dim_;
   const int nsub = 1 << (dim_ - 1);
-  conn->assign((size_t)size() * nf * 5, -1);
-  for (int64_t e = 0; e < size(); ++e)
-    for (int a = 0; a < dim_; ++a)
-      for (int s = 0; s < 2; ++s) {
-        const FaceInfo& fi = face((int32_t)e, a, s);
-        int32_t* r = conn->data() + ((size_t)e * nf + 2 * a + s) * 5;
+  conn->resize((size_t)size() * nf * 5);
+  int32_t* C = conn->data();
+  parallel_ranges(size(), 2048, [&](int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e)
+      for (int f = 0; f < nf; ++f) {
+        const FaceInfo& fi = faces_[(size_t)e * nf + f];
+        int32_t* r = C + ((size_t)e * nf + f) * 5;
         r[0] = fi.kind;
-        if (fi.kind == FACE_CONF) r[1] = fi.nb[0];
+        r[1] = fi.kind == FACE_CONF ? fi.nb[0] : -1;
+        r[2] = r[3] = r[4] = -1;
       }
-  const size_t ng = mort.size() / 7;
-  for (size_t g = 0; g < ng; ++g) {
-    const int32_t* m = mort.data() + g * 7;
-    const int32_t ec = m[0], a = m[1], s = m[2];
-    int32_t* rc = conn->data() + ((size_t)ec * nf + 2 * a + s) * 5;
-    rc[1] = (int32_t)g;
-    for (int k = 0; k < nsub; ++k) {
-      int32_t* rf = conn->data() + ((size_t)m[3 + k] * nf + 2 * a + (1 - s)) * 5;
-      rf[1] = ec; rf[2] = (int32_t)g; rf[3] = k;
+  });
+  const int64_t ng = (int64_t)(mort.size() / 7);
+  parallel_ranges(ng, 1024, [&](int64_t g0, int64_t g1) {
+    for (int64_t g = g0; g < g1; ++g) {
+      const int32_t* m = mort.data() + g * 7;
+      const int32_t ec = m[0], a = m[1], s = m[2];
+      C[((size_t)ec * nf + 2 * a + s) * 5 + 1] = (int32_t)g;
+      for (int k = 0; k < nsub; ++k) {
+        int32_t* rf = C + ((size_t)m[3 + k] * nf + 2 * a + (1 - s)) * 5;
+        rf[1] = ec; rf[2] = (int32_t)g; rf[3] = k;
+      }
     }
-  }
+  });
 }
 
 }  // namespace dgl

@@ -82,7 +82,6 @@ class Forest {
   void set_leaves(std::vector<Leaf> leaves);
   static uint64_t key(int level, const int32_t c[3]);
   int32_t extent(int level, int axis) const { return base_[axis] << level; }
-  void neighbours(int32_t e, std::vector<int32_t>* out) const;
 
   int dim_ = 0;
   int base_[3] = {1, 1, 1};
