@@ -82,68 +82,151 @@ __global__ void bubble_kernel(int32_t E, int n1, int D, const int32_t* elem, con
 // max over the element's nodes of |theta'|, theta' = (Theta_bar + Theta') / (rho_bar + rho')
 // - theta0, in FP64 (refinement criterion of Sec. 4.3, tagging by potential temperature).
 //
-// One warp per element.  With A = Theta_bar + Theta' and B = rho_bar + rho' (FP64 sums), the
-// rounded quotient fl(A/B) and then fl(fl(A/B) - theta0) are monotone in the exact quotient A/B,
-// so the largest |theta'| sits at the node of largest or of smallest A/B.  An FP32 estimate
-// r = fl32(A) / fl32(B) (two conversions and __fdividef, whose error is at most 2 ulp for a
-// divisor in [2^-126, 2^126]: relative error below 2^-21, plus at most 2^-126 where r falls
-// below the FP32 normal range) picks every node within 2^-18 max|r| of the largest or smallest
-// estimate, a band wider than twice the error; only those take the FP64 division, and the
-// result is the value the division at every node gives.  An element outside that range (a
-// non-finite value, B or a nonzero |A| outside [1e-30, 1e30], max|r| outside [1e-20, 1e30])
-// takes the division at every node instead.
-constexpr int kIndPerLane = (DG_MAX_N + 1) * (DG_MAX_N + 1) * (DG_MAX_N + 1) / 32 + 1;
+// One warp per element.  With A = Theta_bar + Theta' and B = rho_bar + rho' as FP64 forms them,
+// fl(A/B) and then fl(fl(A/B) - theta0) are monotone in the exact quotient A/B = theta0 + D/B,
+// D = A - theta0 B, so the largest |theta'| sits at the node of largest or of smallest D/B.  A
+// first pass bounds every D/B in FP32 (indicator_screen: an estimate t and an interval
+// [lo, hi] that holds D/B); a node can hold the largest D/B only if hi >= max(lo) and the
+// smallest only if lo <= min(hi).  Only those nodes take the FP64 division, and the result is
+// the value the division at every node gives.  D is formed from per-layer constants
+// C = fl64(Theta_bar - theta0 rho_bar) and the perturbations, so the interval is as narrow
+// relative to theta' as to theta: elements near the background need no more divisions than
+// the rest.  An element with a node outside the bounds' range (a non-finite value, the FP32
+// density estimate outside [1e-6, 1e30] or within 4 error bounds of zero) takes the division
+// at every node instead.
+constexpr int kIndWarps = 8;
+
+struct IndScreen {
+  float lo, hi;
+  bool ok;
+};
+
+// FP32 interval [lo, hi] around D/B for one node.  c, b0f, b1f: C, rho_bar, Theta_bar rounded to
+// FP32; thf = fl32(theta0) and dth >= |thf - theta0|.  Every FP32 operation is rounded once
+// (no contraction) and contributes at most 2^-24 of its result, every FP32 conversion 2^-24 of
+// its value, the FP64 sums 2^-53; the terms below bound these with a factor of 4 to spare.
+// Underflow adds at most 2^-126 per operation, which the 1e-36 terms cover once the density
+// estimate is at least 1e-6.  __fdividef is within 2 ulp for divisors in [2^-126, 2^126].
+template <class T>
+__device__ __forceinline__ IndScreen indicator_screen(float c, float b0f, float b1f, T q0, T q3,
+                                                      float thf, float dth) {
+  const float q0f = (float)q0, q3f = (float)q3;
+  const float p = __fmul_rn(thf, q0f);
+  const float Qh = __fsub_rn(q3f, p);
+  const float Dh = __fadd_rn(c, Qh);
+  const float bh = __fadd_rn(b0f, q0f);
+  const float a0 = fabsf(q0f), a3 = fabsf(q3f);
+  // |Dh - D| <= eD
+  float eD = __fadd_rn(__fadd_rn(fabsf(c), a3), __fmul_rn(thf, a0));
+  eD = __fadd_rn(eD, __fadd_rn(__fadd_rn(fabsf(p), fabsf(Qh)), fabsf(Dh)));
+  eD = __fmul_rn(eD, 0x1p-21f);
+  eD = __fadd_rn(eD, __fmul_rn(dth, a0));
+  // FP64 rounding of A and B: none where the perturbation is zero
+  const float rA = q3 == T(0) ? 0.0f : __fadd_rn(fabsf(b1f), a3);
+  const float rB = q0 == T(0) ? 0.0f : __fadd_rn(fabsf(b0f), a0);
+  const float big = __fadd_rn(rA, __fmul_rn(thf, rB));
+  eD = __fadd_rn(__fadd_rn(eD, __fmul_rn(big, 0x1p-50f)), 1e-36f);
+  // |bh - B| <= eB
+  float eB = __fmul_rn(__fadd_rn(__fadd_rn(fabsf(b0f), a0), fabsf(bh)), 0x1p-21f);
+  eB = __fadd_rn(__fadd_rn(eB, __fmul_rn(rB, 0x1p-50f)), 1e-36f);
+  // |t - D/B| <= 2^-21 |t| + (eD + (|D| + eD) eB / (3/4 bh)) / bh, doubled
+  const float t = __fdividef(Dh, bh);
+  float e = __fmul_rn(__fmul_rn(__fadd_rn(fabsf(Dh), eD), eB), __fdividef(2.0f, bh));
+  e = __fdividef(__fadd_rn(eD, e), bh);
+  e = __fadd_rn(__fadd_rn(__fmul_rn(fabsf(t), 0x1p-20f), e), 1e-36f);
+  e = __fmul_rn(e, 2.0f);
+  IndScreen r;
+  r.lo = __fsub_rn(t, e);
+  r.hi = __fadd_rn(t, e);
+  r.ok = bh >= 1e-6f && bh <= 1e30f && bh >= __fmul_rn(4.0f, eB) && isfinite(r.lo) && isfinite(r.hi);
+  return r;
+}
 
 template <class T>
 __global__ void indicator_kernel(int32_t E, int n1, int D, const double* bg, const T* q,
-                                 int64_t plane, double theta0, double* out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (e >= E) return;   // whole warps leave together
+                                 int64_t plane, double theta0, float thf, float dth, double* out) {
+  __shared__ float lay[kIndWarps][DG_MAX_N + 1][3];
+  __shared__ uint16_t cand[kIndWarps][(DG_MAX_N + 1) * (DG_MAX_N + 1) * (DG_MAX_N + 1)];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * kIndWarps + w;
+  if (e >= E) return;   // whole warps leave together; no block-wide barrier below
   const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
   const int layer = D == 3 ? n1 * n1 : n1;
+  // node n lies in layer (n * M) >> 20, M = ceil(2^20 / layer): exact for n < 729, layer <= 81
+  const uint32_t M = ((1u << 20) + (uint32_t)layer - 1) / (uint32_t)layer;
   const T* q0 = q + e * NP;
   const T* q3 = q + (int64_t)(D + 1) * plane + e * NP;
   const double* be = bg + e * n1 * 4;
-  float r[kIndPerLane];
-  float rmax = -INFINITY, rmin = INFINITY, amax = 0.0f;
+  if (lane < n1) {
+    const double b0 = be[lane * 4], b1 = be[lane * 4 + 1];
+    lay[w][lane][0] = (float)fma(-theta0, b0, b1);
+    lay[w][lane][1] = (float)b0;
+    lay[w][lane][2] = (float)b1;
+  }
+  __syncwarp();
+  float L = -INFINITY, U = INFINITY;
   bool fast = true;
-#pragma unroll
-  for (int j = 0; j < kIndPerLane; ++j) {
-    const int n = lane + 32 * j;
-    r[j] = 0.0f;
-    if (n < NP) {
-      const double* b = be + (n / layer) * 4;
-      const double A = b[1] + (double)q3[n];
-      const double B = b[0] + (double)q0[n];
-      // false for NaN too
-      fast = fast && B >= 1e-30 && B <= 1e30 && fabs(A) <= 1e30 && (fabs(A) >= 1e-30 || A == 0.0);
-      r[j] = __fdividef((float)A, (float)B);
-      rmax = fmaxf(rmax, r[j]);
-      rmin = fminf(rmin, r[j]);
-      amax = fmaxf(amax, fabsf(r[j]));
-    }
+  for (int n = lane; n < NP; n += 32) {
+    const int k = (int)(((uint32_t)n * M) >> 20);
+    const IndScreen s = indicator_screen<T>(lay[w][k][0], lay[w][k][1], lay[w][k][2], q0[n], q3[n], thf, dth);
+    fast = fast && s.ok;
+    L = fmaxf(L, s.lo);
+    U = fminf(U, s.hi);
   }
   for (int o = 16; o > 0; o >>= 1) {
-    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    L = fmaxf(L, __shfl_xor_sync(0xffffffffu, L, o));
+    U = fminf(U, __shfl_xor_sync(0xffffffffu, U, o));
   }
-  fast = __all_sync(0xffffffffu, fast) && amax >= 1e-20f && amax <= 1e30f;
+  fast = __all_sync(0xffffffffu, fast);
   double m;
   if (fast) {
-    const float band = amax * 0x1p-18f;
-    const float tmax = rmax - band, tmin = rmin + band;
-    double vmax = -INFINITY, vmin = INFINITY;
-#pragma unroll
-    for (int j = 0; j < kIndPerLane; ++j) {
-      const int n = lane + 32 * j;
-      if (n < NP && (r[j] >= tmax || r[j] <= tmin)) {
-        const double* b = be + (n / layer) * 4;
-        const double v = (b[1] + (double)q3[n]) / (b[0] + (double)q0[n]);
-        if (r[j] >= tmax) vmax = fmax(vmax, v);
-        if (r[j] <= tmin) vmin = fmin(vmin, v);
+    // candidates: nodes with both perturbations zero share fl(A/B) = fl(Theta_bar / rho_bar)
+    // with their layer and are marked per layer; the others are packed into a per-warp list
+    // {node, may be the largest, may be the smallest} so the divisions take ceil(count / 32)
+    // rounds of the warp
+    uint32_t cmask = 0, xmask = 0, nmask = 0, lmax = 0, lmin = 0;
+    for (int j = 0, n = lane; n < NP; ++j, n += 32) {
+      const int k = (int)(((uint32_t)n * M) >> 20);
+      const IndScreen s = indicator_screen<T>(lay[w][k][0], lay[w][k][1], lay[w][k][2], q0[n], q3[n], thf, dth);
+      const bool cmax = s.hi >= L, cmin = s.lo <= U;
+      if (!(cmax || cmin)) continue;
+      if (q0[n] == T(0) && q3[n] == T(0)) {
+        lmax |= (uint32_t)cmax << k;
+        lmin |= (uint32_t)cmin << k;
+      } else {
+        cmask |= 1u << j;
+        xmask |= (uint32_t)cmax << j;
+        nmask |= (uint32_t)cmin << j;
       }
+    }
+    const int cnt = __popc(cmask);
+    int off = cnt;   // inclusive scan over lanes, then exclusive
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, off, o);
+      if (lane >= o) off += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, off, 31);
+    off -= cnt;
+    for (uint32_t b = cmask; b; b &= b - 1) {
+      const int j = __ffs(b) - 1;
+      cand[w][off++] = (uint16_t)((lane + 32 * j) | (((xmask >> j) & 1u) << 14) | (((nmask >> j) & 1u) << 15));
+    }
+    lmax = __reduce_or_sync(0xffffffffu, lmax);
+    lmin = __reduce_or_sync(0xffffffffu, lmin);
+    __syncwarp();
+    double vmax = -INFINITY, vmin = INFINITY;
+    for (int c = lane; c < total; c += 32) {
+      const uint32_t x = cand[w][c];
+      const int n = (int)(x & 0x3fffu);
+      const int k = (int)(((uint32_t)n * M) >> 20);
+      const double v = (be[k * 4 + 1] + (double)q3[n]) / (be[k * 4] + (double)q0[n]);
+      if (x & (1u << 14)) vmax = fmax(vmax, v);
+      if (x & (1u << 15)) vmin = fmin(vmin, v);
+    }
+    if (lane < n1 && (((lmax | lmin) >> lane) & 1u)) {
+      const double v = (be[lane * 4 + 1] + 0.0) / (be[lane * 4] + 0.0);
+      if ((lmax >> lane) & 1u) vmax = fmax(vmax, v);
+      if ((lmin >> lane) & 1u) vmin = fmin(vmin, v);
     }
     for (int o = 16; o > 0; o >>= 1) {
       vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
@@ -153,8 +236,8 @@ __global__ void indicator_kernel(int32_t E, int n1, int D, const double* bg, con
   } else {
     m = 0.0;
     for (int n = lane; n < NP; n += 32) {
-      const double* b = be + (n / layer) * 4;
-      m = fmax(m, fabs((b[1] + (double)q3[n]) / (b[0] + (double)q0[n]) - theta0));
+      const int k = (int)(((uint32_t)n * M) >> 20);
+      m = fmax(m, fabs((be[k * 4 + 1] + (double)q3[n]) / (be[k * 4] + (double)q0[n]) - theta0));
     }
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   }
@@ -480,9 +563,14 @@ cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* ele
 cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
                              int64_t plane, double theta0, double* out, cudaStream_t s) {
   if (E == 0) return cudaSuccess;
-  const int grid = (int)((E + 7) / 8);   // 8 warps of 32, one element each
-  if (prec == 0) indicator_kernel<double><<<grid, 256, 0, s>>>(E, n1, D, bg, (const double*)q, plane, theta0, out);
-  else indicator_kernel<float><<<grid, 256, 0, s>>>(E, n1, D, bg, (const float*)q, plane, theta0, out);
+  const int grid = (int)((E + kIndWarps - 1) / kIndWarps);   // one warp per element
+  // theta0 in FP32 and a bound on its rounding error, rounded up
+  const float thf = (float)theta0;
+  const float dth = (float)(std::fabs((double)thf - theta0) * (1.0 + 0x1p-20));
+  if (prec == 0)
+    indicator_kernel<double><<<grid, 32 * kIndWarps, 0, s>>>(E, n1, D, bg, (const double*)q, plane, theta0, thf, dth, out);
+  else
+    indicator_kernel<float><<<grid, 32 * kIndWarps, 0, s>>>(E, n1, D, bg, (const float*)q, plane, theta0, thf, dth, out);
   return cudaGetLastError();
 }
 

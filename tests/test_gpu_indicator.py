@@ -23,10 +23,10 @@ def pkg():
     return p
 
 
-def _mesh(pkg, dim, N, precision, rounds=2):
+def _mesh(pkg, dim, N, precision, rounds=2, theta0=300.0):
     base = (6, 4) if dim == 2 else (3, 3, 2)
     length = (6000.0, 4000.0) if dim == 2 else (3000.0, 3000.0, 2000.0)
-    lm = pkg.Mesh(dim, N, base, length, max_level=2, precision=precision)
+    lm = pkg.Mesh(dim, N, base, length, max_level=2, precision=precision, theta0=theta0)
     for r in range(rounds):
         lm.adapt(flags=workloads.random_flags(lm.num_elements, 0.3, seed=17 * r + N + dim), buffer=1)
     return lm
@@ -41,11 +41,13 @@ def _set(lm, q):
     lm.set_state(q.astype(lm.np_dtype))
 
 
-@pytest.mark.parametrize("dim,N,precision", [(2, 4, "fp64"), (2, 7, "fp32"), (2, 8, "fp64"),
-                                             (3, 1, "fp32"), (3, 3, "fp64"), (3, 7, "fp32"),
-                                             (3, 8, "fp32")])
-def test_indicator_equals_division_at_every_node(pkg, dim, N, precision):
-    lm = _mesh(pkg, dim, N, precision)
+@pytest.mark.parametrize("dim,N,precision,theta0", [(2, 4, "fp64", 300.0), (2, 7, "fp32", 300.0),
+                                                    (2, 8, "fp64", 287.3), (3, 1, "fp32", 300.0),
+                                                    (3, 3, "fp64", 300.0), (3, 7, "fp32", 300.0),
+                                                    (3, 8, "fp32", 301.7)])
+def test_indicator_equals_division_at_every_node(pkg, dim, N, precision, theta0):
+    # theta0 = 287.3 and 301.7 have no exact FP32 form
+    lm = _mesh(pkg, dim, N, precision, theta0=theta0)
     E, NP = lm.num_elements, (N + 1) ** dim
     for seed, kw in ((1, {}), (2, dict(theta_scale=3.0)),
                      (3, dict(rho_scale=1e-12, theta_scale=1e-9))):   # below FP32 resolution
