@@ -879,18 +879,30 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   const size_t tm_bytes = tmap.size() * sizeof(dgl::TransferEntry);
   CU(reserve(m->d_tm, m->c_tm, tm_bytes + 4));
   CU(cudaMemcpy(m->d_tm, tmap.data(), tm_bytes, cudaMemcpyHostToDevice));
+  // the transfer reads q^n and writes the spare buffer, which then becomes q^n; it needs only
+  // the map, so it runs while the host builds the new face tables
+  const int64_t E_new = nf.size();
+  if ((int64_t)(m->NV + 1) * E_new * m->NP >= ((int64_t)1 << 31))
+    return fail(m, DG_ERR_UNSUPPORTED, "mesh too large for 32-bit state offsets (%lld elements)",
+                (long long)E_new);
+  const int64_t plane_new = E_new * m->NP;
+  CU(reserve(m->q_spare, m->q_spare_cap, (size_t)(m->NV + 1) * plane_new * m->tsize));
+  {
+    cudaError_t e = dgk::launch_transfer(m->prec, (int32_t)E_new, m->n1, m->D, m->NV, m->d_tm, m->d_opsd, m->q[0],
+                                         plane_old, m->q_spare, plane_new, m->stream);
+    if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "transfer failed: %s", cudaGetErrorString(e));
+  }
   m->forest = std::move(nf);
   ++m->generation;
   dg_status st = rebuild_topology(m);
-  if (st != DG_OK) return st;
-  // the transfer reads q^n and writes the spare buffer, which then becomes q^n; the stage
-  // buffers q[1], q[2] hold no state between steps and only need the new size
-  CU(reserve(m->q_spare, m->q_spare_cap, state_bytes(m)));
+  if (st != DG_OK) {
+    cudaStreamSynchronize(m->stream);
+    return st;
+  }
+  // the stage buffers q[1], q[2] hold no state between steps and only need the new size
   for (int i = 1; i < 3; ++i) CU(reserve(m->q[i], m->q_cap[i], state_bytes(m)));
   {
-    cudaError_t e = dgk::launch_transfer(m->prec, (int32_t)m->E, m->n1, m->D, m->NV, m->d_tm, m->d_opsd, m->q[0],
-                                         plane_old, m->q_spare, plane(m), m->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    cudaError_t e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "transfer failed: %s", cudaGetErrorString(e));
   }
   std::swap(m->q[0], m->q_spare);

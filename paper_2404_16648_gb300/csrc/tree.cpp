@@ -39,13 +39,26 @@ void Forest::set_leaves(std::vector<Leaf> leaves) {
   hkeys_.assign(cap, kEmpty);
   hvals_.assign(cap, -1);
   hmask_ = cap - 1;
-  for (size_t i = 0; i < leaves_.size(); ++i) {
-    const uint64_t k = key(leaves_[i].level, leaves_[i].c);
-    uint64_t h = mix64(k) & hmask_;
-    while (hkeys_[h] != kEmpty && hkeys_[h] != k) h = (h + 1) & hmask_;
-    hkeys_[h] = k;
-    hvals_[h] = (int32_t)i;
-  }
+  // leaves are distinct, so each key claims one slot; concurrent inserts claim slots with a
+  // compare-and-swap, and where a key lands depends on the order of inserts but find() returns
+  // the same leaf either way
+  uint64_t* K = hkeys_.data();
+  int32_t* V = hvals_.data();
+  parallel_ranges((int64_t)leaves_.size(), 4096, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      const uint64_t k = key(leaves_[i].level, leaves_[i].c);
+      uint64_t h = mix64(k) & hmask_;
+      for (;;) {
+        uint64_t seen = kEmpty;
+        if (__atomic_compare_exchange_n(&K[h], &seen, k, false, __ATOMIC_RELAXED, __ATOMIC_RELAXED) ||
+            seen == k) {
+          V[h] = (int32_t)i;
+          break;
+        }
+        h = (h + 1) & hmask_;
+      }
+    }
+  });
   // face table; every entry depends on its own face only
   const int64_t n = (int64_t)leaves_.size();
   faces_.assign((size_t)n * dim_ * 2, FaceInfo{FACE_WALL, {-1, -1, -1, -1}});
