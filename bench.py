@@ -170,6 +170,9 @@ def paired_meshes(pkg, cfg):
     import numpy as np
     ms = [pkg.Mesh(cfg["dim"], cfg["N"], cfg["base"], cfg["length"], max_level=cfg["max_level"],
                    precision=p) for p in ("fp64", "fp32")]
+    if STAGE_KERNEL is not None:
+        for m in ms:
+            m.set_stage_kernel(STAGE_KERNEL)
     for _ in range(cfg["max_level"]):
         ms[0].set_bubble(**cfg["bubble"])
         flags = (ms[0].indicator() > cfg["threshold"]).astype(np.uint8)
@@ -243,7 +246,7 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
     alg_bytes = 0
     alg_flops = 0
     launches = 0
-    default_layout = 3 if (precision == "fp32" and D == 3) else 2
+    default_layout = 4 if (precision == "fp32" and D == 3) else 2
     per_node = measured_traffic(D, N, precision, default_layout if STAGE_KERNEL is None else STAGE_KERNEL)
     traffic = 0.0
     regrid_s = []
@@ -566,7 +569,7 @@ def main():
                     help="directory for the raw nvidia-smi clock samples (default: a temporary one)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP32-vs-FP64 field comparison over the workload's full step count")
-    ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2, 3],
+    ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2, 3, 4],
                     help="stage kernel layout: 0 column, 1 node-per-thread, 2 column with "
                          "asynchronous staging, 3 as 2 with two threads per column "
                          "(default: the library's)")
@@ -620,7 +623,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config,
             "precision_path": "FP32 state/flux arithmetic; FP64 background, p' and integrals",
-            "stage_kernel": {None: "default", 0: "column", 1: "node", 2: "column-async", 3: "half-column-async"}[STAGE_KERNEL],
+            "stage_kernel": {None: "default", 0: "column", 1: "node", 2: "column-async", 3: "half-column-async", 4: "line"}[STAGE_KERNEL],
             "elements": r32["elements"], "nodes_per_variable": r32["nodes"],
             "gpu_launches": r32["launches"], "mortar_groups": r32["mortars"],
             "roofline": {"bound": "hbm", "kernel": "stage_kernel", "achieved": achieved,

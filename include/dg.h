@@ -292,7 +292,8 @@ const char* dg_batch_last_error(const dg_batch* batch);
 /* Tuning options.  DG_OPT_STAGE_KERNEL selects the fused stage kernel's thread layout:
  * 0 = one thread per vertical node column, 1 = one thread per node, 2 = one thread per column
  * with all operands staged into shared memory by asynchronous copies, 3 = as 2 with two
- * threads per column (3D with odd N; other shapes run layout 2).  Default: 3 for FP32 3D
+ * threads per column, 4 = one pass per axis with two threads per node line, fluxes kept in
+ * registers (3 and 4: 3D with odd N; other shapes run layout 2).  Default: 4 for FP32 3D
  * meshes, 2 otherwise.  All compute the same operator; the option exists for tuning and
  * cross-checking. */
 enum { DG_OPT_STAGE_KERNEL = 1 };

@@ -562,7 +562,7 @@ dg_status dg_ke_grad(dg_mesh* m, const void* q, void* out, void* stream) {
 dg_status dg_set_option(dg_mesh* m, int32_t option, int64_t value) {
   if (!m) return DG_ERR_ARG;
   if (option == DG_OPT_STAGE_KERNEL) {
-    if (value < 0 || value > 3) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0, 1, 2 or 3");
+    if (value < 0 || value > 4) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0 .. 4");
     m->variant = (int)value;
     return DG_OK;
   }
@@ -619,7 +619,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   m->NV = m->tracer ? 1 : m->D + 2; m->NSUB = 1 << (m->D - 1);
   m->prec = desc->precision;
   m->tsize = m->prec == DG_FP64 ? sizeof(double) : sizeof(float);
-  m->variant = (m->prec == DG_FP32_PERT && m->D == 3) ? 3 : 2;   // fastest measured layouts
+  m->variant = (m->prec == DG_FP32_PERT && m->D == 3) ? 4 : 2;   // fastest measured layouts
   m->stream = (cudaStream_t)stream;
   m->ph.theta0 = desc->theta0; m->ph.p0 = desc->p0; m->ph.g = desc->g; m->ph.R = desc->R;
   m->ph.cp = desc->cp; m->ph.cv = desc->cp - desc->R; m->ph.gamma = desc->cp / (desc->cp - desc->R);

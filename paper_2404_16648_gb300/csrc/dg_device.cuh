@@ -101,6 +101,25 @@ __device__ __forceinline__ float pressure_pert_f32(float tp, float invTbf, doubl
   return (float)pressure_pert<kSeries>((double)tp, bd[3], bd[2], ph);
 }
 
+// The same P' with the product A = Theta' c in FP32 pieces instead of FP64: c = chi + clo (its
+// FP32 rounding and the rounding of the rest, within 2^-48 of c), A = ahi + alo with ahi the FP32
+// product and alo the exact rounding error of tp chi (one fma) plus tp clo, so that ahi + alo is
+// within about 2^-46 of A; then P' = fl(ahi + fl(ahi s + alo)).  The inner sum is below 0.7 %
+// of A, so its rounding and the omitted alo s move the result by about 1e-9 relative, 1/60 of
+// the final rounding: the value is the FP64 evaluation rounded to FP32 up to a one-ulp difference
+// where it lies that close to a rounding boundary.  No FP64 operation on this branch.
+__device__ __forceinline__ float pressure_pert_f32ff(float tp, float invTbf, float chi, float clo,
+                                                     const double* bd, const PhysC& ph) {
+  const float x = __fmul_rn(tp, invTbf);
+  if (fabsf(x) <= 0.03125f) {
+    const float s = __fmul_rn(x, __fmaf_rn(x, __fmaf_rn(x, ph.rel[2], ph.rel[1]), ph.rel[0]));
+    const float ahi = __fmul_rn(tp, chi);
+    const float alo = __fmaf_rn(tp, clo, __fmaf_rn(tp, chi, -ahi));
+    return __fadd_rn(ahi, __fmaf_rn(ahi, s, alo));
+  }
+  return (float)pressure_pert<kSeries>((double)tp, bd[3], bd[2], ph);
+}
+
 // P' of a node in the arithmetic type T: FP64 series (T = double) or the form above.  invTb is
 // 1/Theta_bar in T (the background table of the path), bd the FP64 background row, bc -> c.
 template <class T>

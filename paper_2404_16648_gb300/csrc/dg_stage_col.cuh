@@ -28,18 +28,39 @@ constexpr int kDTabSize = dtab_offset(9);   // sum_{N=1..8} (N+1)^2
 // upload_dtab() of the same unit before its first launch.
 static __constant__ float c_dtab_f[kDTabSize];
 static __constant__ double c_dtab_d[kDTabSize];
+// The antisymmetric part (D[m][i] - D[N-m][N-i]) / 2 of each matrix.  The LGL derivative is
+// antisymmetric under the reflection x -> -x of the nodes, so this is D up to the rounding of the
+// computed nodes; being exactly antisymmetric, it lets a kernel apply the rows of the upper half
+// of a line through those of the lower half (the line layout).
+static __constant__ float c_dtab_af[kDTabSize];
+static __constant__ double c_dtab_ad[kDTabSize];
 
 static inline cudaError_t upload_dtab(const double* all) {
   float f[kDTabSize];
   for (int i = 0; i < kDTabSize; ++i) f[i] = (float)all[i];
   cudaError_t e = cudaMemcpyToSymbol(c_dtab_f, f, sizeof(f));
   if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_dtab_d, all, sizeof(double) * kDTabSize);
+  e = cudaMemcpyToSymbol(c_dtab_d, all, sizeof(double) * kDTabSize);
+  if (e != cudaSuccess) return e;
+  double a[kDTabSize];
+  for (int N = 1; N <= 8; ++N) {
+    const int o = dtab_offset(N), n1 = N + 1;
+    for (int m = 0; m < n1; ++m)
+      for (int i = 0; i < n1; ++i)
+        a[o + m * n1 + i] = 0.5 * (all[o + m * n1 + i] - all[o + (N - m) * n1 + (N - i)]);
+  }
+  for (int i = 0; i < kDTabSize; ++i) f[i] = (float)a[i];
+  e = cudaMemcpyToSymbol(c_dtab_af, f, sizeof(f));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_dtab_ad, a, sizeof(double) * kDTabSize);
 }
 
 template <class T> __device__ __forceinline__ T dtab(int i);
 template <> __device__ __forceinline__ float dtab<float>(int i) { return c_dtab_f[i]; }
 template <> __device__ __forceinline__ double dtab<double>(int i) { return c_dtab_d[i]; }
+template <class T> __device__ __forceinline__ T dtab_anti(int i);
+template <> __device__ __forceinline__ float dtab_anti<float>(int i) { return c_dtab_af[i]; }
+template <> __device__ __forceinline__ double dtab_anti<double>(int i) { return c_dtab_ad[i]; }
 
 // Dynamic shared memory of the column kernel per CTA (bytes).
 template <class T, int D, int N, int EPB>

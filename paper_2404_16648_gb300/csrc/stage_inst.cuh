@@ -2,6 +2,7 @@
 // Included by stage_<prec>_<dim>.cu with DG_T and DG_D defined.
 #include "dg_launch.hpp"
 #include "dg_stage_half.cuh"
+#include "dg_stage_line.cuh"
 
 namespace dgk {
 namespace {
@@ -67,6 +68,29 @@ cudaError_t run_stage_half(const StageArgs& A, cudaStream_t s) {
   }
 }
 
+// Layout 4 (3D, odd N); other shapes take layout 2.
+template <class T, int D, int N>
+cudaError_t run_stage_line(const StageArgs& A, cudaStream_t s) {
+  if constexpr (D == 3 && N % 2 == 1) {
+    constexpr size_t smem = line_smem_bytes<T, N>();
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(stage_kernel_line<T, N>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      // all of the unified L1/shared capacity as shared memory: 7 CTAs of the FP32 N = 7 kernel
+      e = cudaFuncSetAttribute(stage_kernel_line<T, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    if (A.E) stage_kernel_line<T, N><<<(unsigned)A.E, LineCfg<N>::THREADS, smem, s>>>(A);
+    return cudaSuccess;
+  } else {
+    return run_stage_async<T, D, N>(A, s);
+  }
+}
+
 // Batched launch over many meshes: layout 1 (node) or 2 (column, asynchronous staging).
 template <class T, int D, int N>
 cudaError_t run_stage_batched(int layout, const StageArgs* tab, const int2* map, int nblocks,
@@ -113,6 +137,7 @@ void run_stage(const StageArgs& A, cudaStream_t s) {
   if (A.variant == 1) run_stage_node<T, D, N>(A, s);
   else if (A.variant == 2) run_stage_async<T, D, N>(A, s);
   else if (A.variant == 3) run_stage_half<T, D, N>(A, s);
+  else if (A.variant == 4) run_stage_line<T, D, N>(A, s);
   else run_stage_col<T, D, N>(A, s);
 }
 
