@@ -14,6 +14,7 @@
 // The arithmetic of each flux and Rusanov evaluation is the same explicitly rounded code as in
 // dg_device.cuh, so both elements of a conforming face still compute bit-identical F*.
 #pragma once
+#include <cstring>
 #include "dg_device.cuh"
 
 namespace dgk {
@@ -34,6 +35,10 @@ static __constant__ double c_dtab_d[kDTabSize];
 // of a line through those of the lower half (the line layout).
 static __constant__ float c_dtab_af[kDTabSize];
 static __constant__ double c_dtab_ad[kDTabSize];
+// The FP32 antisymmetric entries as packed FP32 pairs: c_dtab_af2[m][i] holds entry (m, i) in
+// both halves; c_dtab_afr[m][i] for even m holds entries (m, i) and (m + 1, i).
+static __constant__ unsigned long long c_dtab_af2[kDTabSize];
+static __constant__ unsigned long long c_dtab_afr[kDTabSize];
 
 static inline cudaError_t upload_dtab(const double* all) {
   float f[kDTabSize];
@@ -51,6 +56,26 @@ static inline cudaError_t upload_dtab(const double* all) {
   }
   for (int i = 0; i < kDTabSize; ++i) f[i] = (float)a[i];
   e = cudaMemcpyToSymbol(c_dtab_af, f, sizeof(f));
+  if (e != cudaSuccess) return e;
+  unsigned long long f2[kDTabSize];
+  for (int i = 0; i < kDTabSize; ++i) {
+    uint32_t b;
+    std::memcpy(&b, &f[i], sizeof b);
+    f2[i] = ((unsigned long long)b << 32) | b;
+  }
+  e = cudaMemcpyToSymbol(c_dtab_af2, f2, sizeof(f2));
+  if (e != cudaSuccess) return e;
+  for (int N = 1; N <= 8; ++N) {
+    const int o = dtab_offset(N), n1 = N + 1;
+    for (int m = 0; m < n1; ++m)
+      for (int i = 0; i < n1; ++i) {
+        const unsigned long long lo = f2[o + m * n1 + i] & 0xffffffffull;
+        const unsigned long long hi = (m + 1 < n1) ? (f2[o + (m + 1) * n1 + i] & 0xffffffffull) : 0ull;
+        // rows are rewritten in increasing order, so rows m and m + 1 still hold the originals
+        f2[o + m * n1 + i] = (hi << 32) | lo;
+      }
+  }
+  e = cudaMemcpyToSymbol(c_dtab_afr, f2, sizeof(f2));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_dtab_ad, a, sizeof(double) * kDTabSize);
 }

@@ -78,7 +78,31 @@ __device__ __forceinline__ void stage_run_line(T* dst, const T* src, int count, 
   }
 }
 
+// Packed FP32 pairs (two floats in one 64-bit register) for fma.rn.f32x2.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t x, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x));
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // What a pass needs from the CTA: staged data, the thread's line and the element constants.
+// Elements between a CTA and the one whose data it asks the L2 for: 7 resident CTAs on each of
+// 152 SMs.
+constexpr int kLineAhead = 7 * 152;
+
 template <class T>
 struct LineCtx {
   const T* sQ;
@@ -159,18 +183,60 @@ __device__ __forceinline__ void line_pass(const LineCtx<T>& C, T (&out)[(N + 1) 
   // = other row K2 - 1 - c; node N - r (half 1) takes -D[r][c] on node N - c = own row c and
   // -D[r][K2 + c] on node K2 - 1 - c = other row K2 - 1 - c
   const T sc = h ? C.inv2h[a] : -C.inv2h[a];
+  if constexpr (VEC) {
+    // FP32: packed pairs, one fma.rn.f32x2 for two multiply-adds, each lane rounded as fmaf, so
+    // every sum is that of the scalar form below: variables 0-1 and 2-3 of one row share the
+    // coefficient (c_dtab_af2), variable 4 of rows r, r + 1 shares the flux (c_dtab_afr)
+    uint64_t Fp[K2][2], Gp[K2][2], F4[K2], G4[K2];
 #pragma unroll
-  for (int r = 0; r < K2; ++r)
+    for (int c = 0; c < K2; ++c) {
+      Fp[c][0] = f2_pack(F[c][0], F[c][1]); Fp[c][1] = f2_pack(F[c][2], F[c][3]);
+      Gp[c][0] = f2_pack(G[c][0], G[c][1]); Gp[c][1] = f2_pack(G[c][2], G[c][3]);
+      F4[c] = f2_pack(F[c][4], F[c][4]); G4[c] = f2_pack(G[c][4], G[c][4]);
+    }
+    const uint64_t sc2 = f2_pack(sc, sc);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      T s = (T)0;
+    for (int r = 0; r < K2; ++r) {
+      uint64_t s01 = 0, s23 = 0;
 #pragma unroll
-      for (int c = 0; c < K2; ++c) s = fma(dtab_anti<T>(dtab_offset(N) + r * n1 + c), F[c][v], s);
+      for (int c = 0; c < K2; ++c) {
+        const uint64_t dd = c_dtab_af2[dtab_offset(N) + r * n1 + c];
+        s01 = f2_fma(dd, Fp[c][0], s01);
+        s23 = f2_fma(dd, Fp[c][1], s23);
+      }
+#pragma unroll
+      for (int c = 0; c < K2; ++c) {
+        const uint64_t dd = c_dtab_af2[dtab_offset(N) + r * n1 + K2 + c];
+        s01 = f2_fma(dd, Gp[K2 - 1 - c][0], s01);
+        s23 = f2_fma(dd, Gp[K2 - 1 - c][1], s23);
+      }
+      f2_unpack(f2_mul(sc2, s01), out[r][0], out[r][1]);
+      f2_unpack(f2_mul(sc2, s23), out[r][2], out[r][3]);
+    }
+#pragma unroll
+    for (int r = 0; r < K2; r += 2) {
+      uint64_t s4 = 0;
+#pragma unroll
+      for (int c = 0; c < K2; ++c) s4 = f2_fma(c_dtab_afr[dtab_offset(N) + r * n1 + c], F4[c], s4);
 #pragma unroll
       for (int c = 0; c < K2; ++c)
-        s = fma(dtab_anti<T>(dtab_offset(N) + r * n1 + K2 + c), G[K2 - 1 - c][v], s);
-      out[r][v] = sc * s;
+        s4 = f2_fma(c_dtab_afr[dtab_offset(N) + r * n1 + K2 + c], G4[K2 - 1 - c], s4);
+      f2_unpack(f2_mul(sc2, s4), out[r][4], out[r + 1][4]);
     }
+  } else {
+#pragma unroll
+    for (int r = 0; r < K2; ++r)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T s = (T)0;
+#pragma unroll
+        for (int c = 0; c < K2; ++c) s = fma(dtab_anti<T>(dtab_offset(N) + r * n1 + c), F[c][v], s);
+#pragma unroll
+        for (int c = 0; c < K2; ++c)
+          s = fma(dtab_anti<T>(dtab_offset(N) + r * n1 + K2 + c), G[K2 - 1 - c][v], s);
+        out[r][v] = sc * s;
+      }
+  }
   if (!C.lok) return;
   // lift of the thread's face (a, h) at face node L
   const NodeBg<T> bgf{bgf0, bgf1, bgf2};
@@ -226,15 +292,26 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
   double* sBc = reinterpret_cast<double*>(sBg + n1 * 4);
   const int P = A.plane32;
   const T* qe = (const T*)A.qs + e * NP;
-  // ---- q^n is read only in the epilogue: ask the L2 for the element's planes now
-  if (tid == 0 && A.mode == 1 && A.ca != 0.0) {
-    const T* qne = (const T*)A.qn + e * NP;
+  // ---- q^n is read only in the epilogue: ask the L2 for the element's planes now.  The CTA
+  // that starts one resident wave later (kLineAhead elements on) finds its state, P' and face
+  // table in L2 as well, so its staging waits for L2 instead of DRAM.
+  auto prefetch_l2 = [](const void* src, int bytes) {
+    if ((((uintptr_t)src) & 15) == 0)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
+  };
+  if (tid == 0) {
+    if (A.mode == 1 && A.ca != 0.0) {
+      const T* qne = (const T*)A.qn + e * NP;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T* src = qne + (int64_t)v * P;
-      if ((((uintptr_t)src) & 15) == 0)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"((int)(NP * sizeof(T)))
-                     : "memory");
+      for (int v = 0; v < NV; ++v) prefetch_l2(qne + (int64_t)v * P, (int)(NP * sizeof(T)));
+    }
+    const int64_t ea = e + kLineAhead;
+    if (ea < A.E) {
+      const T* qa = (const T*)A.qs + ea * NP;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) prefetch_l2(qa + (int64_t)v * P, (int)(NP * sizeof(T)));
+      prefetch_l2((const T*)A.pp_in + ea * NP, (int)(NP * sizeof(T)));
+      prefetch_l2(A.conn + (size_t)ea * 2 * D * 5, 2 * D * 5 * (int)sizeof(int32_t) / 16 * 16);
     }
   }
   // ---- own state, P', background column
