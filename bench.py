@@ -622,7 +622,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config,
-            "precision_path": "FP32 state/flux arithmetic; FP64 background, p' and integrals",
+            "precision_path": "FP32 state/flux arithmetic; FP64 background and integrals; P' to FP64 accuracy before its FP32 rounding",
             "stage_kernel": {None: "default", 0: "column", 1: "node", 2: "column-async", 3: "half-column-async", 4: "line"}[STAGE_KERNEL],
             "elements": r32["elements"], "nodes_per_variable": r32["nodes"],
             "gpu_launches": r32["launches"], "mortar_groups": r32["mortars"],
