@@ -25,6 +25,8 @@ __device__ __forceinline__ void cp_async_bytes(void* smem, const void* gmem, int
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Waits until at most one committed group of this thread is still in flight.
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Copies `count` elements of T from a global run to shared memory with the threads
 // [tid0, tid0 + nthr) of the CTA; 16-byte copies when both ends allow it.

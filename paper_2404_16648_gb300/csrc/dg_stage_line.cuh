@@ -238,6 +238,7 @@ __device__ __forceinline__ void line_pass(const LineCtx<T>& C, T (&out)[(N + 1) 
       }
   }
   if (!C.lok) return;
+  if constexpr (a == 0) cp_async_wait_all();   // this thread's face copies
   // lift of the thread's face (a, h) at face node L
   const NodeBg<T> bgf{bgf0, bgf1, bgf2};
   const NodeDer<T> ndf{rinvf, thf};
@@ -320,7 +321,9 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
   stage_run_line<T, N>(sQ + NV * NP, (const T*)A.pp_in + e * NP, NP, tid, THREADS);
   stage_run<T>(sBg, (const T*)A.bgt + e * n1 * 4, n1 * 4, tid, THREADS);
   if (sizeof(T) == 4) stage_run<double>(sBc, A.bgc + e * n1, n1, tid, THREADS);
-  // ---- the faces this thread lifts: (a, h) at face node L of each axis a
+  cp_async_commit();
+  // ---- the faces this thread lifts: (a, h) at face node L of each axis a; only this thread
+  // reads them, so they form a group of their own that it waits for before its first lift
   auto stage_face = [&](int a, int s, int fn) -> int {
     const int f = 2 * a + s;
     const int32_t* c = A.conn + ((size_t)e * 2 * D + f) * 5;
@@ -354,7 +357,7 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
     inv2h[a] = inv2h_of<T>(A, level, a);
     lc[a] = lift_of<T>(A, level, a);   // (2/h_a) / w0
   }
-  cp_async_wait_all();
+  cp_async_wait_one();
   __syncthreads();
   // FP32 path: c of each z-level as two FP32 parts, in place of the double (read before the
   // epilogue, two barriers later)
