@@ -312,7 +312,13 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) prefetch_l2(qa + (int64_t)v * P, (int)(NP * sizeof(T)));
       prefetch_l2((const T*)A.pp_in + ea * NP, (int)(NP * sizeof(T)));
-      prefetch_l2(A.conn + (size_t)ea * 2 * D * 5, 2 * D * 5 * (int)sizeof(int32_t) / 16 * 16);
+      // the 120-byte conn row widened to 16-byte bounds (a bulk prefetch needs them); the conn
+      // buffer is allocated with a quarter of headroom, so the widened end stays inside it
+      const uintptr_t c0 = (uintptr_t)(A.conn + (size_t)ea * 2 * D * 5);
+      const uintptr_t c1 = c0 + 2 * D * 5 * sizeof(int32_t);
+      const uintptr_t a0 = c0 & ~(uintptr_t)15, a1 = (c1 + 15) & ~(uintptr_t)15;
+      prefetch_l2((const void*)a0, (int)(a1 - a0));
+      prefetch_l2(A.elem + (size_t)ea * 4, 16);
     }
   }
   // ---- own state, P', background column
