@@ -153,6 +153,13 @@ dg_status dg_get_faces(const dg_mesh* mesh, int64_t counts[3], int32_t* conformi
 dg_status dg_set_state(dg_mesh* mesh, const void* q, int where);
 dg_status dg_get_state(dg_mesh* mesh, void* q, int where);
 
+/* Copies the pressure perturbation P' = P(Theta_bar + Theta') - P(Theta_bar) of the current state
+ * (Sec. 2.1, perturbation form; one plane of E (N+1)^dim values in the state precision) into
+ * out (DG_HOST or DG_DEVICE, caller-owned, at least dg_num_nodes() values).  It is the plane the
+ * stage kernels read: the one the last stage produced, or, after dg_set_state or a regrid, the
+ * one evaluated from the state.  Synchronous.  DG_ERR_UNSUPPORTED for tracer meshes. */
+dg_status dg_get_pprime(dg_mesh* mesh, void* out, int where);
+
 /* Evaluates the initial condition analytically at the current nodes (FP64 on the device). */
 dg_status dg_set_bubble(dg_mesh* mesh, const dg_bubble_desc* bubble);
 

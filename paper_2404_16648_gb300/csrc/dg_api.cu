@@ -720,6 +720,17 @@ dg_status dg_get_state(dg_mesh* m, void* q, int where) {
   return DG_OK;
 }
 
+dg_status dg_get_pprime(dg_mesh* m, void* out, int where) {
+  if (!m || !out || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
+  dg_status st = dgi::ensure_pp(m, m->stream);
+  if (st != DG_OK) return st;
+  CU(cudaMemcpyAsync(out, pp_plane(m, m->q[0]), (size_t)plane(m) * m->tsize,
+                     where == DG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, m->stream));
+  CU(cudaStreamSynchronize(m->stream));
+  return DG_OK;
+}
+
 // Evaluates the bubble at the nodes: into the state (theta_out == nullptr) or as theta' itself.
 static dg_status bubble_eval(dg_mesh* m, const dg_bubble_desc* b, double* theta_out) {
   if (!m || !b) return fail(m, DG_ERR_ARG, "bad argument");

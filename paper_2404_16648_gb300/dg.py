@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 
 
 # every symbol include/dg.h declares
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_nodes", "dg_get_leaves",
-            "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_vortex", "dg_set_bubble", "dg_rhs", "dg_step",
+            "dg_get_faces", "dg_set_state", "dg_get_state", "dg_get_pprime", "dg_set_vortex", "dg_set_bubble", "dg_rhs", "dg_step",
             "dg_adapt", "dg_indicator", "dg_primitives", "dg_integrals", "dg_set_time", "dg_get_time", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
             "dg_forest_create_periodic", "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
@@ -92,6 +92,7 @@ def load_library(path=None):
         "dg_get_faces": (i32, [vp, ctypes.POINTER(ctypes.c_int64), vp, sz, vp, sz, vp, sz]),
         "dg_set_state": (i32, [vp, vp, ctypes.c_int]),
         "dg_get_state": (i32, [vp, vp, ctypes.c_int]),
+        "dg_get_pprime": (i32, [vp, vp, ctypes.c_int]),
         "dg_set_bubble": (i32, [vp, ctypes.POINTER(BubbleDesc)]),
         "dg_set_vortex": (i32, [vp, ctypes.POINTER(VortexDesc)]),
         "dg_rhs": (i32, [vp, vp, vp, vp]),
@@ -266,6 +267,15 @@ class Mesh:
             out = np.empty(self.state_shape, dtype=self.np_dtype)
         p, where = _ptr(out)
         self._check(self.lib.dg_get_state(self.h, ctypes.c_void_p(p), where))
+        return out
+
+    def pprime(self, out=None):
+        """P' plane of the current state, shape (E, (N+1)^dim), in the state precision (host
+        NumPy array unless `out` is given)."""
+        if out is None:
+            out = np.empty((self.num_elements, self.np_), dtype=self.np_dtype)
+        p, where = _ptr(out)
+        self._check(self.lib.dg_get_pprime(self.h, ctypes.c_void_p(p), where))
         return out
 
     def set_bubble(self, center, radius, amp, rff=None):

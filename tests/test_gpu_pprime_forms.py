@@ -1,0 +1,57 @@
+"""P' of the FP32 path (reading of "FP64 for the pressure perturbation": P' carried to FP64
+accuracy before its FP32 rounding).  The line stage kernel (layout 4) forms P' of its output by a
+split-FP32 product, the half-column layout and the P' kernel in FP64 arithmetic.  On the same FP32
+state the P' planes must agree bit for bit for layout 3 and within one ulp, on a small fraction of
+the nodes, for layout 4; nodes with |Theta'/Theta_bar| > 2^-5 take the FP64 form in both."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2404_16648_gb300 import build as b
+    b.build()
+    import paper_2404_16648_gb300 as p
+    return p
+
+
+def _mesh(pkg):
+    lm = pkg.Mesh(3, 7, (3, 3, 2), (3000.0, 3000.0, 2000.0), max_level=1, precision="fp32")
+    lm.adapt(flags=workloads.random_flags(lm.num_elements, 0.3, seed=77), buffer=1)
+    return lm
+
+
+def _state(lm, seed):
+    q = workloads.random_state(5, lm.num_elements, 512, seed=seed, theta_scale=2.0)
+    q[4, ::7, 5] = 20.0        # |x| above 2^-5: the full FP64 form on both sides
+    q[4, 3::11, 9] = -15.0
+    return q.astype(np.float32)
+
+
+@pytest.mark.parametrize("layout", [3, 4])
+def test_stage_pprime_against_fp64_form(pkg, layout):
+    lm = _mesh(pkg)
+    lm.set_stage_kernel(layout)
+    for seed in (1, 2):
+        lm.set_state(_state(lm, seed))
+        lm.step(0.02, 1)
+        p_stage = lm.pprime()          # written by the stage epilogue
+        q = lm.get_state()
+        lm.set_state(q)                # P' of the same state from the FP64-form kernel
+        p_ref = lm.pprime()
+        assert np.all(np.isfinite(p_ref)) and np.abs(p_ref).max() > 100.0
+        ulps = np.abs(p_stage.astype(np.float64) - p_ref) / np.spacing(np.abs(p_ref))
+        if layout == 3:
+            np.testing.assert_array_equal(p_stage, p_ref)
+        else:
+            assert ulps.max() <= 1.0
+            assert (ulps > 0).mean() <= 0.05, (ulps > 0).mean()
+            # the large-|x| nodes take the same FP64 form
+            sel = np.abs(q[4]) >= 15.0
+            np.testing.assert_array_equal(p_stage[sel], p_ref[sel])
