@@ -108,6 +108,11 @@ __device__ __forceinline__ float pressure_pert_f32(float tp, float invTbf, doubl
 // of A, so its rounding and the omitted alo s move the result by about 1e-9 relative, 1/60 of
 // the final rounding: the value is the FP64 evaluation rounded to FP32 up to a one-ulp difference
 // where it lies that close to a rounding boundary.  No FP64 operation on this branch.
+// The large-|x| branch, out of line: it is rarely taken, and inlined at every use its FP64
+// series and expm1/log1p would crowd the hot code out of the instruction cache.
+static __device__ __noinline__ float pressure_pert_f32_full(float tp, const double* bd, const PhysC& ph) {
+  return (float)pressure_pert<kSeries>((double)tp, bd[3], bd[2], ph);
+}
 __device__ __forceinline__ float pressure_pert_f32ff(float tp, float invTbf, float chi, float clo,
                                                      const double* bd, const PhysC& ph) {
   const float x = __fmul_rn(tp, invTbf);
@@ -117,7 +122,7 @@ __device__ __forceinline__ float pressure_pert_f32ff(float tp, float invTbf, flo
     const float alo = __fmaf_rn(tp, clo, __fmaf_rn(tp, chi, -ahi));
     return __fadd_rn(ahi, __fmaf_rn(ahi, s, alo));
   }
-  return (float)pressure_pert<kSeries>((double)tp, bd[3], bd[2], ph);
+  return pressure_pert_f32_full(tp, bd, ph);
 }
 
 // P' of a node in the arithmetic type T: FP64 series (T = double) or the form above.  invTb is
