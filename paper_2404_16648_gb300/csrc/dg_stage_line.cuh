@@ -449,12 +449,15 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
       continue;
     }
     T qnew[NV];
+    if (first) {   // uniform over the grid: stage 1 reads no q^n
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T qsv = sQ[v * NP + w];
-      qnew[v] = first ? qsv + dt * rhs[v] : ca * qne[v * P + n] + cb * (qsv + dt * rhs[v]);
-      oute[v * P + n] = qnew[v];
+      for (int v = 0; v < NV; ++v) qnew[v] = sQ[v * NP + w] + dt * rhs[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qnew[v] = ca * qne[v * P + n] + cb * (sQ[v * NP + w] + dt * rhs[v]);
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];
     if constexpr (sizeof(T) == 4) {
       const float2 c2 = sC2[k];
       ppo[n] = pressure_pert_f32ff(qnew[D + 1], sBg[k * 4 + 3], c2.x, c2.y, A.bg + ((size_t)e * n1 + k) * 4, A.ph);
