@@ -330,12 +330,15 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
   for (int k = 0; k < n1; ++k) {
     const int n = t + NF * k;
     T qnew[NV];
+    if (first) {   // uniform over the grid
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T qsv = sQ[v * NP + n];
-      qnew[v] = first ? qsv + dt * acc[v][k] : ca * qn_col[v][k] + cb * (qsv + dt * acc[v][k]);
-      oute[v * P + n] = qnew[v];
+      for (int v = 0; v < NV; ++v) qnew[v] = sQ[v * NP + n] + dt * acc[v][k];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qnew[v] = ca * qn_col[v][k] + cb * (sQ[v * NP + n] + dt * acc[v][k]);
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];
     ppo[n] = pprime_of<T>(qnew[D + 1], sBg[k * 4 + 3], A.bg + ((size_t)e * n1 + k) * 4, sBc + k, A.ph);
   }
 }

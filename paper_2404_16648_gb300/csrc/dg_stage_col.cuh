@@ -331,12 +331,15 @@ stage_kernel_col(const __grid_constant__ StageArgs A) {
     const int n = t + NF * k;
     const int qi = ci + P1 * (cj + JS * k);
     T qnew[NV];
+    if (first) {   // uniform over the grid: stage 1 reads no q^n
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T qsv = sQ[le][v][qi];
-      qnew[v] = first ? qsv + dt * acc[v][k] : ca * qne[v * P + n] + cb * (qsv + dt * acc[v][k]);
-      oute[v * P + n] = qnew[v];
+      for (int v = 0; v < NV; ++v) qnew[v] = sQ[le][v][qi] + dt * acc[v][k];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qnew[v] = ca * qne[v * P + n] + cb * (sQ[le][v][qi] + dt * acc[v][k]);
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];
     const size_t zk = (size_t)e * n1 + k;
     ppo[n] = pprime_of<T>(qnew[D + 1], ((const T*)A.bgt)[zk * 4 + 3], A.bg + zk * 4, A.bgc + zk, A.ph);
   }

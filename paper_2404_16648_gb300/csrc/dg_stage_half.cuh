@@ -414,12 +414,16 @@ __device__ __forceinline__ void stage_body_half(const StageArgs& A, int64_t e) {
     const int k = half_row<N>(h, r);
     const int n = t + NF * k;
     T qnew[NV];
+    if (first) {   // uniform over the grid: stage 1 reads no q^n
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T qsv = sQ[v * NP + half_swz<N>(n)];
-      qnew[v] = first ? qsv + dt * acc[v][r] : ca * qne[v * P + n] + cb * (qsv + dt * acc[v][r]);
-      oute[v * P + n] = qnew[v];
+      for (int v = 0; v < NV; ++v) qnew[v] = sQ[v * NP + half_swz<N>(n)] + dt * acc[v][r];
+    } else {
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        qnew[v] = ca * qne[v * P + n] + cb * (sQ[v * NP + half_swz<N>(n)] + dt * acc[v][r]);
     }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];
     ppo[n] = pprime_of<T>(qnew[D + 1], sBg[k * 4 + 3], A.bg + ((size_t)e * n1 + k) * 4, sBc + k, A.ph);
   }
 }
