@@ -241,6 +241,9 @@ struct StageArgs {
   int32_t plane32;       // `plane` as int32 (the host guarantees (NV+1) * plane < 2^31)
   float gammaf, gf;      // gamma and g in FP32
   PhysC ph;
+  // layout 4: the launch directly follows the mortar kernel of the same stage and may begin
+  // before it ends (programmatic dependent launch); the kernel waits for it before reading mbuf
+  int32_t after_mortar;
 };
 
 struct MortarArgs {
@@ -468,6 +471,9 @@ mortar_kernel(const __grid_constant__ MortarArgs A) {
   __shared__ T sT[NSUB][NV][NF];
   __shared__ T sM[NSUB][NV][NF];
   const int tid = threadIdx.x;
+  // a stage kernel launched after this one may start now; it waits for this grid's completion
+  // before it reads the mortar buffer
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   const T* ops = (const T*)A.ops;
   for (int i = tid; i < n1 * n1; i += blockDim.x) {
     sP[0][i] = ops[1 * n1 * n1 + i];

@@ -328,6 +328,9 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
   stage_run<T>(sBg, (const T*)A.bgt + e * n1 * 4, n1 * 4, tid, THREADS);
   if (sizeof(T) == 4) stage_run<double>(sBc, A.bgc + e * n1, n1, tid, THREADS);
   cp_async_commit();
+  // the mortar fluxes are written by the mortar kernel of this stage, which may still run when
+  // this grid was launched as its programmatic dependent (no-op otherwise)
+  if (A.after_mortar) asm volatile("griddepcontrol.wait;\n" ::: "memory");
   // ---- the faces this thread lifts: (a, h) at face node L of each axis a; only this thread
   // reads them, so they form a group of their own that it waits for before its first lift
   auto stage_face = [&](int a, int s, int fn) -> int {

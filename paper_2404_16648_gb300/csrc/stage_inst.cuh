@@ -84,8 +84,23 @@ cudaError_t run_stage_line(const StageArgs& A, cudaStream_t s) {
       if (e != cudaSuccess) return e;
       configured = true;
     }
-    if (A.E) stage_kernel_line<T, N><<<(unsigned)A.E, LineCfg<N>::THREADS, smem, s>>>(A);
-    return cudaSuccess;
+    if (!A.E) return cudaSuccess;
+    if (!A.after_mortar) {
+      stage_kernel_line<T, N><<<(unsigned)A.E, LineCfg<N>::THREADS, smem, s>>>(A);
+      return cudaSuccess;
+    }
+    // programmatic dependent launch after the mortar kernel (see stage_body_line)
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)A.E);
+    cfg.blockDim = dim3(LineCfg<N>::THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, stage_kernel_line<T, N>, A);
   } else {
     return run_stage_async<T, D, N>(A, s);
   }
