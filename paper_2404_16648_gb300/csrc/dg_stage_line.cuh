@@ -13,12 +13,11 @@
 // local orders both halves apply the same rows r < K2 to their own and the other half's
 // fluxes, half 1 with the opposite sign, so every coefficient is the same for all lanes and
 // reaches the multiply-adds as a constant operand.  Row 0 adds the lift of the face from the
-// same registers.  The
-// x pass stores its part of the right-hand side to shared memory, the y pass adds to it, and
-// the z pass (with the buoyancy term) reads it and finishes the stage: the Shu-Osher
-// combination with q^n, the output and P' of the new state.  No flux passes through shared
-// memory: per node the kernel reads the state three times and the partial right-hand side
-// twice and writes it twice.
+// same registers.  The x pass stores its part of the right-hand side to shared memory, the y
+// pass adds to it, and the z pass (with the buoyancy term) reads it and finishes the stage: the
+// Shu-Osher combination with q^n, the output and P' of the new state.  No flux passes through
+// shared memory: per node the kernel reads the state three times and the partial right-hand
+// side twice and writes it twice.
 //
 // Bank layout for N + 1 = 8 (32 banks of 4 bytes): node (i, j, k) sits at word
 // 64 k + 8 (j ^ 2 (k & 1)) + (i ^ (j & 4)).  The x pass moves a half line as one 16-byte access,
