@@ -258,8 +258,15 @@ __device__ __forceinline__ void line_pass(const LineCtx<T>& C, T (&out)[(N + 1) 
       for (int v = 0; v < NV; ++v) qo[v] = nb[v * NF + L];
       sn = face_side<T, D>(qo, bgf, nb[NV * NF + L], a, C.gamma, Fn);
     }
-    if (h) rusanov<T, D>(qf, Ff, so, qo, Fn, sn, Fs);
-    else   rusanov<T, D>(qo, Fn, sn, qf, Ff, so, Fs);
+    // Rusanov flux with the thread's side as the low one (h = 1) or the high one (h = 0): the
+    // average is symmetric and the jump changes sign (an exact negation), so one code path for
+    // both halves of the warp gives the bits of the two oriented calls
+    const T hl = mul_rn((T)0.5, so > sn ? so : sn);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T d = sub_rn(qo[v], qf[v]);
+      Fs[v] = sub_rn(mul_rn((T)0.5, add_rn(Ff[v], Fn[v])), mul_rn(hl, h ? d : -d));
+    }
   } else {
 #pragma unroll
     for (int v = 0; v < NV; ++v) Fs[v] = nb[v * NF + L];
