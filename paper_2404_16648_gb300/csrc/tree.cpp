@@ -179,7 +179,7 @@ bool Forest::regrid(const std::vector<uint8_t>& tag, int B, int max_level, Fores
   }
   // families: complete sibling groups are contiguous in Morton order, child index 0 first.  A
   // family head has even coordinates and its siblings odd ones, so families never overlap and
-  // each head is judged on its own; coars = 2 at a coarsened family's head, 1 at its siblings.
+  // each head is tested on its own; coars = 2 at a coarsened family's head, 1 at its siblings.
   std::vector<uint8_t> coars(n, 0);
   parallel_ranges(n, 2048, [&](int64_t e0, int64_t e1) {
     for (int64_t e = e0; e < e1 && e + nkids <= n; ++e) {
