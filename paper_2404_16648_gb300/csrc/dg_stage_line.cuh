@@ -273,7 +273,7 @@ __device__ __forceinline__ void line_pass(const LineCtx<T>& C, T (&out)[(N + 1) 
   }
   const T coef = h ? -C.lc[a] : C.lc[a];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) out[0][v] += coef * (Fs[v] - Ff[v]);
+  for (int v = 0; v < NV; ++v) out[0][v] = fma(coef, Fs[v] - Ff[v], out[0][v]);
 }
 
 template <class T, int N>
@@ -460,10 +460,10 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
     T qnew[NV];
     if (first) {   // uniform over the grid: stage 1 reads no q^n
 #pragma unroll
-      for (int v = 0; v < NV; ++v) qnew[v] = sQ[v * NP + w] + dt * rhs[v];
+      for (int v = 0; v < NV; ++v) qnew[v] = fma(dt, rhs[v], sQ[v * NP + w]);
     } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) qnew[v] = ca * qne[v * P + n] + cb * (sQ[v * NP + w] + dt * rhs[v]);
+      for (int v = 0; v < NV; ++v) qnew[v] = fma(ca, qne[v * P + n], cb * fma(dt, rhs[v], sQ[v * NP + w]));
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];
