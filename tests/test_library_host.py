@@ -100,3 +100,17 @@ def test_forest_rejects_bad_arguments(pkg):
     f = pkg.Forest(2, (2, 2), 1)
     with pytest.raises(ValueError):
         f.regrid(np.zeros(3, np.uint8), 1)
+
+
+def test_null_mesh_handles_are_rejected_before_any_device_call(pkg):
+    """Every mesh entry point checks its handle first, so these run without a GPU."""
+    import ctypes
+    from paper_2404_16648_gb300.dg import DG_ERR_ARG
+    lib = pkg.load_library()
+    buf = (ctypes.c_double * 8)()
+    assert lib.dg_get_pprime(None, buf, 0) == DG_ERR_ARG
+    assert lib.dg_get_state(None, buf, 0) == DG_ERR_ARG
+    assert lib.dg_set_state(None, buf, 0) == DG_ERR_ARG
+    assert lib.dg_step(None, 0.1, 1, None) == DG_ERR_ARG
+    assert lib.dg_indicator(None, buf, 8) == DG_ERR_ARG
+    assert lib.dg_integrals(None, buf) == DG_ERR_ARG
