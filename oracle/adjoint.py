@@ -8,8 +8,12 @@ So J^T lam is assembled entry by entry as (J^T lam)_j = lam . J e_j.  This is th
 flux (|u|, max) follow the derivative convention of physics.abs_cs / physics.max_cs: the active
 branch, ties to the low side, sign(0) = 0.
 
-Pinned by tests/test_oracle_adjoint.py (complex-step directional derivatives against central
-finite differences of the same oracle, the local-support shortcut against full evaluation).
+Pinned by tests/test_oracle_adjoint.py: rhs_vjp and step_vjp by the adjoint identity
+<lam, J v> = <J^T lam, v> with J v from central finite differences of dg.rhs and dg.step on
+meshes with hanging faces (2D and 3D; planted mistakes in a copy of step_vjp -- half the time
+step, lambda paired with the wrong variable, columns given to the wrong element -- fail it), the
+local-support shortcut against full evaluation, and the final-KE gradient against central
+differences.
 """
 import numpy as np
 

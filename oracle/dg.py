@@ -397,7 +397,11 @@ def bubble_theta(mesh, center, radius, amp):
 
 
 def rff_theta(mesh, sigma, kvec, phase):
-    """Random Fourier-feature field sigma sqrt(2/K) sum_k cos(k.x + phi_k) (inputs drawn outside)."""
+    """Random Fourier-feature field sigma sqrt(2/K) sum_k cos(k.x + phi_k) (inputs drawn outside).
+
+    With k ~ N(0, l^-2 I) and phi ~ U[0, 2 pi) its covariance over draws is
+    sigma^2 exp(-r^2 / (2 l^2)) (Rahimi & Recht 2007); tests/test_oracle_rff.py pins the plane
+    wave of one feature and that covariance at lags 0, l and 2 l."""
     kvec = np.asarray(kvec, dtype=np.float64)
     phase = np.asarray(phase, dtype=np.float64)
     nfeat = len(phase)
