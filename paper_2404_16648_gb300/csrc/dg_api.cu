@@ -35,6 +35,10 @@ dg_status fail(dg_mesh* m, dg_status st, const char* fmt, ...) {
   return st;
 }
 
+// Returned by every call on a mesh whose regrid failed after it had committed the new tree.
+constexpr const char* kBrokenMsg =
+    "the mesh is unusable: a regrid failed after committing its new tree; destroy the mesh";
+
 #define CU(call)                                                                     \
   do {                                                                               \
     cudaError_t e_ = (call);                                                         \
@@ -100,21 +104,29 @@ dg_status upload_ops(dg_mesh* m) {
 const double* d_w(const dg_mesh* m) { return m->d_opsd + 5 * m->n1 * m->n1; }
 const double* d_x(const dg_mesh* m) { return m->d_opsd + 5 * m->n1 * m->n1 + m->n1; }
 
-// (Re)builds the device tables for the current forest; state buffers sized for E elements.
-dg_status rebuild_topology(dg_mesh* m) {
-  m->E = m->forest.size();
-  if ((int64_t)(m->NV + 1) * m->E * m->NP >= ((int64_t)1 << 31))
+// Host tables of a forest, built and checked before anything of the mesh changes.
+struct HostTables {
+  int64_t E = 0, G = 0;
+  std::vector<int32_t> conf, mort, bnd, conn, elem;
+};
+
+// Builds the face lists, the connectivity and the element table of forest f and checks every
+// index a kernel will follow; the mesh is only read (its sizes and error string).
+dg_status build_tables(dg_mesh* m, const dgl::Forest& f, HostTables* t) {
+  t->E = f.size();
+  if ((int64_t)(m->NV + 1) * t->E * m->NP >= ((int64_t)1 << 31))
     return fail(m, DG_ERR_UNSUPPORTED, "mesh too large for 32-bit state offsets (%lld elements)",
-                (long long)m->E);
-  m->forest.face_lists(&m->conf, &m->mort, &m->bnd);
-  m->G = (int64_t)(m->mort.size() / 7);
-  std::vector<int32_t> conn;
-  m->forest.connectivity(m->mort, &conn);
+                (long long)t->E);
+  f.face_lists(&t->conf, &t->mort, &t->bnd);
+  t->G = (int64_t)(t->mort.size() / 7);
+  f.connectivity(t->mort, &t->conn);
   // every index a kernel will follow must be in range before anything is uploaded; the error
   // names the first bad row
   const int nf = 2 * m->D;
-  const int64_t E = m->E, G = m->G;
+  const int64_t E = t->E, G = t->G;
   const int NSUB = m->NSUB, D = m->D;
+  const std::vector<int32_t>& conn = t->conn;
+  const std::vector<int32_t>& mort = t->mort;
   std::atomic<int64_t> bad_face{INT64_MAX}, bad_group{INT64_MAX};
   auto note = [](std::atomic<int64_t>& first, int64_t r) {
     int64_t cur = first.load(std::memory_order_relaxed);
@@ -141,19 +153,31 @@ dg_status rebuild_topology(dg_mesh* m) {
   dgl::parallel_ranges(G, 4096, [&](int64_t g0, int64_t g1) {
     for (int64_t g = g0; g < g1; ++g)
       for (int k = 0; k < 3 + NSUB; ++k) {
-        const int32_t v = m->mort[g * 7 + k];
+        const int32_t v = mort[g * 7 + k];
         const bool ok = k == 0 || k >= 3 ? (v >= 0 && v < E) : (v >= 0 && v < (k == 1 ? D : 2));
         if (!ok) { note(bad_group, g); return; }
       }
   });
   if (bad_group.load() != INT64_MAX)
     return fail(m, DG_ERR_STATE, "inconsistent mortar group %lld", (long long)bad_group.load());
-  std::vector<int32_t> elem((size_t)m->E * 4);
-  const auto& L = m->forest.leaves();
-  for (int64_t e = 0; e < m->E; ++e) {
-    elem[e * 4] = L[e].level;
-    for (int a = 0; a < 3; ++a) elem[e * 4 + 1 + a] = L[e].c[a];
+  t->elem.assign((size_t)E * 4, 0);
+  const auto& L = f.leaves();
+  for (int64_t e = 0; e < E; ++e) {
+    t->elem[e * 4] = L[e].level;
+    for (int a = 0; a < 3; ++a) t->elem[e * 4 + 1 + a] = L[e].c[a];
   }
+  return DG_OK;
+}
+
+// Makes checked tables the mesh's own: sizes, host lists, device tables, background.
+dg_status upload_tables(dg_mesh* m, HostTables&& t) {
+  m->E = t.E;
+  m->G = t.G;
+  m->conf = std::move(t.conf);
+  m->mort = std::move(t.mort);
+  m->bnd = std::move(t.bnd);
+  const std::vector<int32_t>& conn = t.conn;
+  const std::vector<int32_t>& elem = t.elem;
   CU(reserve(m->d_elem, m->c_elem, elem.size() * sizeof(int32_t)));
   CU(cudaMemcpy(m->d_elem, elem.data(), elem.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CU(reserve(m->d_conn, m->c_conn, conn.size() * sizeof(int32_t)));
@@ -180,6 +204,14 @@ dg_status rebuild_topology(dg_mesh* m) {
   m->pp_valid = false;
   m->bgint_valid = false;
   return DG_OK;
+}
+
+// (Re)builds the device tables for the current forest (mesh creation).
+dg_status rebuild_topology(dg_mesh* m) {
+  HostTables t;
+  dg_status st = build_tables(m, m->forest, &t);
+  if (st != DG_OK) return st;
+  return upload_tables(m, std::move(t));
 }
 
 // Each state buffer holds the NV variable planes followed by the P' plane of that state.
@@ -439,6 +471,7 @@ dg_status step_transpose(dg_mesh* m, const double* b0, const double* b1, const d
 }
 
 dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !q || !lam || !out) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
@@ -454,6 +487,7 @@ dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void
 
 dg_status dg_step_state(dg_mesh* m, const void* q_in, void* q_out, double dt, int32_t nsteps,
                         void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !q_in || !q_out || nsteps < 0 || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   dg_status st = ensure_adjoint_ws(m);
@@ -468,6 +502,7 @@ dg_status dg_step_state(dg_mesh* m, const void* q_in, void* q_out, double dt, in
 
 dg_status dg_step_vjp(dg_mesh* m, const void* q_in, double dt, const void* lam_out, void* lam_in,
                       void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !q_in || !lam_out || !lam_in || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (lam_out == lam_in) return fail(m, DG_ERR_ARG, "lam_out and lam_in must not alias");
@@ -489,6 +524,7 @@ dg_status dg_step_vjp(dg_mesh* m, const void* q_in, double dt, const void* lam_o
 }
 
 dg_status dg_step_record(dg_mesh* m, const void* q_in, void* q_out, void* record, double dt, void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !q_in || !q_out || !record || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
@@ -510,6 +546,7 @@ dg_status dg_step_record(dg_mesh* m, const void* q_in, void* q_out, void* record
 
 dg_status dg_step_vjp_record(dg_mesh* m, const void* record, double dt, const void* lam_out, void* lam_in,
                              void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !record || !lam_out || !lam_in || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (lam_out == lam_in) return fail(m, DG_ERR_ARG, "lam_out and lam_in must not alias");
@@ -524,6 +561,7 @@ dg_status dg_step_vjp_record(dg_mesh* m, const void* record, double dt, const vo
 }
 
 dg_status dg_set_theta(dg_mesh* m, const double* theta, int where) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !theta || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   const size_t bytes = (size_t)plane(m) * sizeof(double);
@@ -545,6 +583,7 @@ dg_status dg_set_theta(dg_mesh* m, const double* theta, int where) {
 
 dg_status dg_theta_vjp(dg_mesh* m, const double* theta, const void* lam_q, double* lam_theta,
                        void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !theta || !lam_q || !lam_theta) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
@@ -555,6 +594,7 @@ dg_status dg_theta_vjp(dg_mesh* m, const double* theta, const void* lam_q, doubl
 }
 
 dg_status dg_ke_grad(dg_mesh* m, const void* q, void* out, void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !q || !out) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
@@ -569,6 +609,11 @@ dg_status dg_set_option(dg_mesh* m, int32_t option, int64_t value) {
   if (option == DG_OPT_STAGE_KERNEL) {
     if (value < 0 || value > 4) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0 .. 4");
     m->variant = (int)value;
+    return DG_OK;
+  }
+  if (option == DG_OPT_FAIL_NEXT_ADAPT) {
+    if (value < 0 || value > 2) return fail(m, DG_ERR_ARG, "failure injection must be 0, 1 or 2");
+    m->fail_next_adapt = (int)value;
     return DG_OK;
   }
   return fail(m, DG_ERR_ARG, "unknown option %d", option);
@@ -684,6 +729,7 @@ int64_t dg_num_nodes(const dg_mesh* m) { return m ? m->E * m->NP : 0; }
 
 dg_status dg_get_leaves(const dg_mesh* mc, int32_t* out, size_t cap) {
   dg_mesh* m = const_cast<dg_mesh*>(mc);
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !out) return DG_ERR_ARG;
   if (cap < (size_t)m->E * 5) return fail(m, DG_ERR_ARG, "leaf buffer too small");
   const auto& L = m->forest.leaves();
@@ -698,6 +744,7 @@ dg_status dg_get_leaves(const dg_mesh* mc, int32_t* out, size_t cap) {
 dg_status dg_get_faces(const dg_mesh* mc, int64_t counts[3], int32_t* conforming, size_t cap_c,
                        int32_t* mortars, size_t cap_m, int32_t* boundary, size_t cap_b) {
   dg_mesh* m = const_cast<dg_mesh*>(mc);
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !counts) return DG_ERR_ARG;
   counts[0] = (int64_t)m->conf.size() / 3;
   counts[1] = (int64_t)m->mort.size() / 7;
@@ -709,6 +756,7 @@ dg_status dg_get_faces(const dg_mesh* mc, int64_t counts[3], int32_t* conforming
 }
 
 dg_status dg_set_state(dg_mesh* m, const void* q, int where) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !q || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
   const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
   m->pp_valid = false;
@@ -718,6 +766,7 @@ dg_status dg_set_state(dg_mesh* m, const void* q, int where) {
 }
 
 dg_status dg_get_state(dg_mesh* m, void* q, int where) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !q || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
   const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
   CU(cudaMemcpyAsync(q, m->q[0], bytes, where == DG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, m->stream));
@@ -726,6 +775,7 @@ dg_status dg_get_state(dg_mesh* m, void* q, int where) {
 }
 
 dg_status dg_get_pprime(dg_mesh* m, void* out, int where) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !out || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   dg_status st = dgi::ensure_pp(m, m->stream);
@@ -738,6 +788,7 @@ dg_status dg_get_pprime(dg_mesh* m, void* out, int where) {
 
 // Evaluates the bubble at the nodes: into the state (theta_out == nullptr) or as theta' itself.
 static dg_status bubble_eval(dg_mesh* m, const dg_bubble_desc* b, double* theta_out) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !b) return fail(m, DG_ERR_ARG, "bad argument");
   for (int a = 0; a < m->D; ++a)
     if (!(b->radius[a] > 0.0)) return fail(m, DG_ERR_ARG, "bubble radius must be positive");
@@ -764,6 +815,7 @@ static dg_status bubble_eval(dg_mesh* m, const dg_bubble_desc* b, double* theta_
 }
 
 dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (m && b && m->tracer) {
     if (b->n_rff != 0) return fail(m, DG_ERR_ARG, "a tracer bell takes no random field");
     for (int a = 0; a < 2; ++a)
@@ -778,6 +830,7 @@ dg_status dg_set_bubble(dg_mesh* m, const dg_bubble_desc* b) {
 }
 
 dg_status dg_set_vortex(dg_mesh* m, const dg_vortex_desc* v) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !v) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer || m->D != 2) return fail(m, DG_ERR_ARG, "the vortex needs a 2D Euler mesh");
   if (m->desc.p0 != 1.0 || m->desc.R != 1.0 || m->desc.theta0 != 1.0 || m->desc.g != 0.0)
@@ -794,12 +847,14 @@ dg_status dg_set_vortex(dg_mesh* m, const dg_vortex_desc* v) {
 }
 
 dg_status dg_bubble_theta(dg_mesh* m, const dg_bubble_desc* b, double* theta) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !theta) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "no theta' field on a tracer mesh");
   return bubble_eval(m, b, theta);
 }
 
 dg_status dg_rhs(dg_mesh* m, const void* q, void* dqdt, void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !q || !dqdt) return fail(m, DG_ERR_ARG, "bad argument");
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
   if (m->tracer) {
@@ -812,6 +867,7 @@ dg_status dg_rhs(dg_mesh* m, const void* q, void* dqdt, void* stream) {
 }
 
 dg_status dg_step(dg_mesh* m, double dt, int32_t nsteps, void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || nsteps < 0 || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
   void* p0 = pp_plane(m, m->q[0]);
@@ -840,6 +896,7 @@ dg_status dg_step(dg_mesh* m, double dt, int32_t nsteps, void* stream) {
 }
 
 dg_status dg_indicator(dg_mesh* m, double* out, size_t cap) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !out || cap < (size_t)m->E) return fail(m, DG_ERR_ARG, "bad argument");
   CU(reserve(m->d_ind, m->c_ind, (size_t)(m->E > 0 ? m->E : 1) * sizeof(double)));
   double* d = m->d_ind;
@@ -854,6 +911,7 @@ dg_status dg_indicator(dg_mesh* m, double* out, size_t cap) {
 }
 
 dg_status dg_primitives(dg_mesh* m, double* out, size_t cap, void* stream) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || (!out && m->E > 0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   const size_t need = (size_t)(m->D + 1) * (size_t)m->E * (size_t)m->NP;
@@ -867,9 +925,12 @@ dg_status dg_primitives(dg_mesh* m, double* out, size_t cap, void* stream) {
 
 dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   if (!m || !p) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (p->buffer < 0) return fail(m, DG_ERR_ARG, "buffer must be >= 0");
   const int maxl = p->max_level < 0 ? m->desc.max_level : p->max_level;
   if (maxl > m->desc.max_level) return fail(m, DG_ERR_ARG, "max_level above the mesh limit");
+  const int inject = m->fail_next_adapt;
+  m->fail_next_adapt = 0;
   std::vector<uint8_t> tag((size_t)m->E, 0);
   if (p->criterion == DG_CRIT_FLAGS) {
     if (!p->flags) return fail(m, DG_ERR_ARG, "flags missing");
@@ -890,36 +951,50 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
     return fail(m, DG_ERR_STATE, "regrid failed: %s", why.c_str());
   const int64_t E_old = m->E;
   const int64_t plane_old = plane(m);
-  // the device reads the map as rows of 9 int32 {kind, src[8]}: the host entries as they lie
-  static_assert(sizeof(dgl::TransferEntry) == 9 * sizeof(int32_t), "transfer rows are 9 int32");
-  const size_t tm_bytes = tmap.size() * sizeof(dgl::TransferEntry);
-  CU(reserve(m->d_tm, m->c_tm, tm_bytes + 4));
-  CU(cudaMemcpy(m->d_tm, tmap.data(), tm_bytes, cudaMemcpyHostToDevice));
-  // the transfer reads q^n and writes the spare buffer, which then becomes q^n; it needs only
-  // the map, so it runs while the host builds the new face tables
   const int64_t E_new = nf.size();
   if ((int64_t)(m->NV + 1) * E_new * m->NP >= ((int64_t)1 << 31))
     return fail(m, DG_ERR_UNSUPPORTED, "mesh too large for 32-bit state offsets (%lld elements)",
                 (long long)E_new);
   const int64_t plane_new = E_new * m->NP;
+  // Until the new forest is committed below, every failure leaves the mesh as it was: the
+  // transfer map and the spare state are scratch, and the stage buffers q[1], q[2] hold nothing
+  // between steps (growing them keeps the old mesh valid).
+  // the device reads the map as rows of 9 int32 {kind, src[8]}: the host entries as they lie
+  static_assert(sizeof(dgl::TransferEntry) == 9 * sizeof(int32_t), "transfer rows are 9 int32");
+  const size_t tm_bytes = tmap.size() * sizeof(dgl::TransferEntry);
+  CU(reserve(m->d_tm, m->c_tm, tm_bytes + 4));
+  CU(cudaMemcpy(m->d_tm, tmap.data(), tm_bytes, cudaMemcpyHostToDevice));
   CU(reserve(m->q_spare, m->q_spare_cap, (size_t)(m->NV + 1) * plane_new * m->tsize));
+  const size_t sb_new = (size_t)(m->NV + 1) * plane_new * m->tsize;
+  for (int i = 1; i < 3; ++i) CU(reserve(m->q[i], m->q_cap[i], sb_new));
+  // the transfer reads q^n and writes the spare buffer, which then becomes q^n; it needs only
+  // the map, so it runs while the host builds the new face tables
   {
     cudaError_t e = dgk::launch_transfer(m->prec, (int32_t)E_new, m->n1, m->D, m->NV, m->d_tm, m->d_opsd, m->q[0],
                                          plane_old, m->q_spare, plane_new, m->stream);
     if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "transfer failed: %s", cudaGetErrorString(e));
   }
-  m->forest = std::move(nf);
-  ++m->generation;
-  dg_status st = rebuild_topology(m);
+  HostTables tables;
+  dg_status st = inject == 1 ? fail(m, DG_ERR_STATE, "injected failure before the commit")
+                             : build_tables(m, nf, &tables);
   if (st != DG_OK) {
-    cudaStreamSynchronize(m->stream);
+    cudaStreamSynchronize(m->stream);   // the transfer wrote only the spare buffer
     return st;
   }
-  // the stage buffers q[1], q[2] hold no state between steps and only need the new size
-  for (int i = 1; i < 3; ++i) CU(reserve(m->q[i], m->q_cap[i], state_bytes(m)));
-  {
+  // commit: from here a failure leaves device tables of mixed sizes, so the mesh is marked
+  // unusable and every later call on it is refused
+  m->forest = std::move(nf);
+  ++m->generation;
+  st = inject == 2 ? fail(m, DG_ERR_OOM, "injected failure after the commit")
+                   : upload_tables(m, std::move(tables));
+  if (st == DG_OK) {
     cudaError_t e = cudaStreamSynchronize(m->stream);
-    if (e != cudaSuccess) return fail(m, DG_ERR_CUDA, "transfer failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) st = fail(m, DG_ERR_CUDA, "transfer failed: %s", cudaGetErrorString(e));
+  }
+  if (st != DG_OK) {
+    cudaStreamSynchronize(m->stream);
+    m->broken = true;
+    return st;
   }
   std::swap(m->q[0], m->q_spare);
   std::swap(m->q_cap[0], m->q_spare_cap);
@@ -945,6 +1020,7 @@ static double two_sum(double a, double b, double* err) {
 // alone and are taken once per topology; each call sums the parts that carry the state and
 // adds the two compensated results with their rounding errors.
 dg_status dg_integrals(dg_mesh* m, double out[DG_NUM_INTEGRALS]) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !out) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) {
     double r[2] = {0.0, 0.0};
@@ -994,6 +1070,7 @@ dg_status dg_enable_timing(dg_mesh* m, int32_t enable) {
 }
 
 dg_status dg_stage_timing(dg_mesh* m, double* total_ms, int64_t* launches, int32_t reset) {
+  if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
   if (!m || !total_ms || !launches) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->ev_used > 0) CU(cudaEventSynchronize(m->ev[m->ev_used - 1]));
   double sum = 0.0;

@@ -125,6 +125,7 @@ dg_status dg_batch_create(dg_mesh* const* meshes, int32_t count, dg_batch** out)
   for (int32_t i = 0; i < count; ++i) {
     dg_mesh* m = meshes[i];
     if (!m) { delete b; return DG_ERR_ARG; }
+    if (m->broken) { delete b; return DG_ERR_STATE; }   // a regrid of this mesh failed after its commit
     if (m->desc.nu > 0.0 || m->tracer) { delete b; return DG_ERR_UNSUPPORTED; }   // inviscid Euler only
     for (int32_t j = 0; j < i; ++j)
       if (meshes[j] == m) { delete b; return DG_ERR_ARG; }   // each mesh once
@@ -195,7 +196,7 @@ dg_status dg_batch_set_dt(dg_batch* b, const double* dt) {
 dg_status dg_batch_run(dg_batch* b, int32_t nsteps, int32_t use_graph) {
   if (!b || nsteps < 0) return DG_ERR_ARG;
   for (size_t i = 0; i < b->meshes.size(); ++i) {
-    if (b->meshes[i]->E != b->elements[i] || b->meshes[i]->generation != b->generations[i])
+    if (b->meshes[i]->broken || b->meshes[i]->E != b->elements[i] || b->meshes[i]->generation != b->generations[i])
       return bfail(b, DG_ERR_STATE, "a mesh was regridded after dg_batch_create");
     if (!(b->dt[i] > 0.0)) return bfail(b, DG_ERR_ARG, "dt not set (dg_batch_set_dt)");
   }

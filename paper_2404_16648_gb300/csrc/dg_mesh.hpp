@@ -44,6 +44,8 @@ struct dg_mesh {
   void* d_ppscratch = nullptr; // P' plane of a caller's state in dg_rhs
   bool pp_valid = false;       // P' plane of q[0] matches q[0]
   int variant = 2;             // stage kernel layout (DG_OPT_STAGE_KERNEL); set at creation
+  int fail_next_adapt = 0;     // DG_OPT_FAIL_NEXT_ADAPT: host-side failure injection for tests
+  bool broken = false;         // a regrid failed after its commit: every later call is refused
   bool tracer = false;         // DG_EQ_TRACER: one passive tracer plane, prescribed wind
   double time = 0.0;           // model time of the state (dg_set_time, advanced by dg_step)
   double stage_g = 1.0;        // tracer wind factor cos(pi t / T) of the stage being launched

@@ -166,12 +166,15 @@ extern "C" dg_status dg_integrals_noalloc(const dg_mesh_desc* desc, const int32_
   if (desc->equations != DG_EQ_EULER) return DG_ERR_UNSUPPORTED;
   const int D = desc->dim, n1 = desc->N + 1;
   const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
+  // beyond the static scratch (compared before multiplying, so no product can wrap)
+  if (num_elements > dgk::kNoAllocMaxNodes / NP) return DG_ERR_ARG;
   const int64_t nodes = num_elements * NP;
-  if (nodes > dgk::kNoAllocMaxNodes) return DG_ERR_ARG;   // beyond the static scratch
   if (!(desc->cp > desc->R) || !(desc->R > 0.0) || !(desc->p0 > 0.0) || !(desc->theta0 > 0.0))
     return DG_ERR_ARG;
   for (int a = 0; a < D; ++a)
     if (desc->base[a] < 1 || !(desc->length[a] > 0.0)) return DG_ERR_ARG;
+  // the neutral background exists below z = cp theta0 / g (the same rule as dg_mesh_create)
+  if (desc->g > 0.0 && !(desc->length[D - 1] < desc->cp * desc->theta0 / desc->g)) return DG_ERR_ARG;
   double* scratch = nullptr;
   if (dgk::scratch_address(&scratch) != cudaSuccess) return DG_ERR_CUDA;
   dgk::PhysC ph{};

@@ -5,6 +5,7 @@
 // first find the helpers awake; the first loop of a regrid pays the wake-up.
 #include "host_pool.hpp"
 
+#include <pthread.h>
 #include <unistd.h>
 
 #include <algorithm>
@@ -93,7 +94,16 @@ class WorkerPool {
 std::mutex g_pool_mu;
 WorkerPool* g_pool = nullptr;
 
+// fork() copies g_pool_mu in whatever state it has at that moment: were another thread inside
+// pool(), the child would inherit a mutex that no thread of its own ever releases.  The handlers
+// take it around fork(), so both processes resume with it free.  (The child never touches the
+// parent's pool object or its mutexes: it builds a pool of its own.)
+void fork_prepare() { g_pool_mu.lock(); }
+void fork_release() { g_pool_mu.unlock(); }
+const int g_atfork = pthread_atfork(fork_prepare, fork_release, fork_release);
+
 WorkerPool* pool() {
+  (void)g_atfork;
   std::lock_guard<std::mutex> lk(g_pool_mu);
   // a forked child inherits the pool object but none of its threads: it starts a new one (the
   // parent's copy is left in place, unused)

@@ -1,18 +1,44 @@
 // Instantiates the stage and mortar kernels of one (precision, dimension) for N = 1..8.
 // Included by stage_<prec>_<dim>.cu with DG_T and DG_D defined.
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "dg_launch.hpp"
 #include "dg_stage_half.cuh"
 #include "dg_stage_line.cuh"
 
 namespace dgk {
+// Function attributes (dynamic shared-memory limit, carveout) belong to a device's context: a
+// kernel is configured once per (kernel, device), under a mutex, so concurrent host threads and
+// a second GPU in the same process each see a configured kernel.  Shared by every stage unit
+// (an inline function's statics are one object across translation units).
+inline cudaError_t configure_kernel(const void* fn, size_t smem, bool max_carveout) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({fn, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && max_carveout)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  done.insert({fn, dev});
+  return cudaSuccess;
+}
+
 namespace {
 
 template <class T, int D, int N>
 void run_stage_node(const StageArgs& A, cudaStream_t s) {
   constexpr int NP = ipow(N + 1, D);
   constexpr int EPB = epb_node(D, N);
+  constexpr size_t smem = node_smem_bytes<T, D, N, EPB>();
   const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
-  if (blocks) stage_kernel<T, D, N, EPB><<<blocks, EPB * NP, 0, s>>>(A);
+  if (blocks) stage_kernel<T, D, N, EPB><<<blocks, EPB * NP, smem, s>>>(A);
 }
 
 template <class T, int D, int N>
@@ -20,12 +46,9 @@ cudaError_t run_stage_col(const StageArgs& A, cudaStream_t s) {
   constexpr int NF = ipow(N + 1, D - 1);
   constexpr int EPB = epb_col(D, N);
   constexpr size_t smem = col_smem_bytes<T, D, N, EPB>();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel_col<T, D, N, EPB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = configure_kernel((const void*)stage_kernel_col<T, D, N, EPB>, smem, false);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
   if (blocks) stage_kernel_col<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
@@ -37,12 +60,9 @@ cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
   constexpr int NF = ipow(N + 1, D - 1);
   constexpr int EPB = epb_col(D, N);
   constexpr size_t smem = async_smem_bytes<T, D, N, EPB>();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel_async<T, D, N, EPB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = configure_kernel((const void*)stage_kernel_async<T, D, N, EPB>, smem, false);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
   if (blocks) stage_kernel_async<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
@@ -54,12 +74,9 @@ template <class T, int D, int N>
 cudaError_t run_stage_half(const StageArgs& A, cudaStream_t s) {
   if constexpr (D == 3 && N % 2 == 1) {
     constexpr size_t smem = half_smem_bytes<T, N>();
-    static bool configured = false;
-    if (!configured) {
-      cudaError_t e = cudaFuncSetAttribute(stage_kernel_half<T, N>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+      cudaError_t e = configure_kernel((const void*)stage_kernel_half<T, N>, smem, false);
       if (e != cudaSuccess) return e;
-      configured = true;
     }
     if (A.E) stage_kernel_half<T, N><<<(unsigned)A.E, HalfCfg<N>::THREADS, smem, s>>>(A);
     return cudaSuccess;
@@ -73,16 +90,10 @@ template <class T, int D, int N>
 cudaError_t run_stage_line(const StageArgs& A, cudaStream_t s) {
   if constexpr (D == 3 && N % 2 == 1) {
     constexpr size_t smem = line_smem_bytes<T, N>();
-    static bool configured = false;
-    if (!configured) {
-      cudaError_t e = cudaFuncSetAttribute(stage_kernel_line<T, N>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
+    {
       // all of the unified L1/shared capacity as shared memory: 7 CTAs of the FP32 N = 7 kernel
-      e = cudaFuncSetAttribute(stage_kernel_line<T, N>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               (int)cudaSharedmemCarveoutMaxShared);
+      cudaError_t e = configure_kernel((const void*)stage_kernel_line<T, N>, smem, true);
       if (e != cudaSuccess) return e;
-      configured = true;
     }
     if (!A.E) return cudaSuccess;
     if (!A.after_mortar) {
@@ -112,19 +123,17 @@ cudaError_t run_stage_batched(int layout, const StageArgs* tab, const int2* map,
                               cudaStream_t s) {
   if (layout == 1) {
     constexpr int EPB = epb_node(D, N);
+    constexpr size_t smem = node_smem_bytes<T, D, N, EPB>();
     if (nblocks <= 0) return cudaSuccess;
-    stage_kernel_batched<T, D, N, EPB><<<nblocks, EPB * ipow(N + 1, D), 0, s>>>(tab, map);
+    stage_kernel_batched<T, D, N, EPB><<<nblocks, EPB * ipow(N + 1, D), smem, s>>>(tab, map);
     return cudaGetLastError();
   }
   constexpr int NF = ipow(N + 1, D - 1);
   constexpr int EPB = epb_col(D, N);
   constexpr size_t smem = async_smem_bytes<T, D, N, EPB>();
-  static bool configured = false;
-  if (!configured) {   // done on the first call, also with nblocks == 0 (before a capture)
-    cudaError_t e = cudaFuncSetAttribute(stage_kernel_async_batched<T, D, N, EPB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {   // done on the first call, also with nblocks == 0 (before a capture)
+    cudaError_t e = configure_kernel((const void*)stage_kernel_async_batched<T, D, N, EPB>, smem, false);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   if (nblocks <= 0) return cudaSuccess;
   stage_kernel_async_batched<T, D, N, EPB><<<nblocks, EPB * NF, smem, s>>>(tab, map);

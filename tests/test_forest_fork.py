@@ -53,3 +53,45 @@ def test_forked_child_runs_its_own_pool():
         pytest.fail("forked child did not finish")
     assert p.exitcode == 0 and got is not None
     assert got == _digests(want)
+
+
+def _regrid_loop(pkg, stop):
+    k = 0
+    while not stop.is_set():
+        _sequence(pkg, 20 + (k % 5), rounds=2)
+        k += 1
+
+
+@pytest.mark.timeout(600)
+def test_fork_while_another_thread_regrids():
+    """Children forked while a parent thread is in the middle of regrids (inside the pool, its
+    job loops or the pool's lookup) must still run their own pool to the end."""
+    import threading
+    from paper_2404_16648_gb300 import build as b
+    b.build()
+    import paper_2404_16648_gb300 as pkg
+    want = _digests(_sequence(pkg, 7))
+    stop = threading.Event()
+    t = threading.Thread(target=_regrid_loop, args=(pkg, stop), daemon=True)
+    t.start()
+    ctx = mp.get_context("fork")
+    try:
+        for _ in range(6):
+            q = ctx.Queue()
+            with warnings.catch_warnings():
+                warnings.simplefilter("ignore", DeprecationWarning)
+                p = ctx.Process(target=_child, args=(q,))
+                p.start()
+            try:
+                got = q.get(timeout=120)
+            except Exception:
+                got = None
+            p.join(30)
+            if p.is_alive():
+                p.kill()
+                p.join()
+                pytest.fail("child forked during a regrid did not finish")
+            assert p.exitcode == 0 and got == want
+    finally:
+        stop.set()
+        t.join(120)

@@ -12,9 +12,6 @@ import pytest
 
 import workloads
 
-pytestmark = pytest.mark.gpu
-
-
 @pytest.fixture(scope="module")
 def pkg():
     import torch
@@ -25,6 +22,7 @@ def pkg():
     return p
 
 
+@pytest.mark.gpu
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_noalloc_integrals_match_dg_integrals_twice(pkg, precision):
     import torch
@@ -50,10 +48,39 @@ def test_noalloc_integrals_match_dg_integrals_twice(pkg, precision):
         np.testing.assert_allclose(got[[2, 4]], want[[2, 4]], rtol=1e-11)
 
 
+@pytest.mark.gpu
 def test_noalloc_rejects_sizes_beyond_the_scratch(pkg):
     lib = pkg.load_library()
     m = pkg.Mesh(3, 8, (1, 1, 1), (1000.0, 1000.0, 1000.0))
     # 729 nodes per element: 100,000 elements exceed the 67,108,864-node limit
     st = lib.dg_integrals_noalloc(ctypes.byref(m.desc), ctypes.c_void_p(16), 100000,
+                                  ctypes.c_void_p(16), ctypes.c_void_p(16), None)
+    assert st == 1
+
+
+# The argument checks below return before any device call, so they run without a GPU.
+
+@pytest.fixture(scope="module")
+def hostlib():
+    from paper_2404_16648_gb300 import build as b
+    b.build()
+    import paper_2404_16648_gb300 as p
+    return p
+
+
+def test_noalloc_rejects_an_element_count_whose_node_count_wraps(hostlib):
+    lib = hostlib.load_library()
+    d = hostlib.make_desc(3, 7, (1, 1, 1), (1000.0, 1000.0, 1000.0))
+    # 512 nodes per element: 2^55 elements give 2^64 nodes, which wraps to 0 in int64
+    st = lib.dg_integrals_noalloc(ctypes.byref(d), ctypes.c_void_p(16), 1 << 55,
+                                  ctypes.c_void_p(16), ctypes.c_void_p(16), None)
+    assert st == 1
+
+
+def test_noalloc_rejects_a_box_above_the_neutral_atmosphere(hostlib):
+    lib = hostlib.load_library()
+    # cp theta0 / g = 1004.5 * 300 / 9.81 = 30,718 m: a 40 km column has no background at its top
+    d = hostlib.make_desc(2, 3, (2, 2), (1000.0, 40000.0))
+    st = lib.dg_integrals_noalloc(ctypes.byref(d), ctypes.c_void_p(16), 4,
                                   ctypes.c_void_p(16), ctypes.c_void_p(16), None)
     assert st == 1
