@@ -223,7 +223,41 @@ def fp32_accuracy(pkg, cfg, steps):
     return out
 
 
-def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, world=1):
+def _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D, per_node=None):
+    """Runs `steps` SSP-RK3 steps (regrid every `regrid_every` inside) between two CUDA events on
+    the mesh stream; returns the elapsed ms and the work counters of the region."""
+    import torch
+    dt = cfg["dt"]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    c = dict(dof_stage=0, alg_bytes=0, alg_flops=0, launches=0, traffic=0.0, regrid_s=[])
+    ev0.record()
+    for i in range(steps):
+        E = m.num_elements
+        m.step(dt, 1)
+        c["dof_stage"] += 3 * E * NP
+        c["alg_bytes"] += stage_bytes(E, NP, NV, b, n1, D)
+        c["alg_flops"] += stage_flops(E, NP, NV, n1, D)
+        if per_node:
+            c["traffic"] += E * NP * sum(per_node)
+        c["launches"] += 3 * (1 + (m.num_mortars > 0))   # stage (+ mortar) launches per step
+        if regrid_every and (i + 1) % regrid_every == 0:
+            torch.cuda.synchronize()     # dg_adapt starts with this wait anyway
+            tr = time.perf_counter()
+            m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
+            c["regrid_s"].append(time.perf_counter() - tr)
+            c["launches"] += 3   # indicator, transfer, background
+    ev1.record()
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), c
+
+
+def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, world=1, repeats=5):
+    """The production path timed `repeats` times over `steps` steps each (the stage kernels run
+    as in any dg_step call: after their mortar kernels as programmatic dependent launches); the
+    median repeat is the result.  A further region of `steps` steps with per-stage CUDA events
+    (dg_enable_timing, which needs an event between the mortar and the stage launch and so runs
+    them without the dependent launch) gives the stage kernel's own time per launch."""
     import torch
     m = build_mesh(pkg, cfg, precision)
     dt = cfg["dt"]
@@ -234,51 +268,40 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
         m.step(dt, 1)
     torch.cuda.synchronize()
     m.integrals()
-    m.enable_timing(True)
-    m.stage_timing(reset=True)
+    default_layout = 4 if (precision == "fp32" and D == 3) else 2
+    per_node = measured_traffic(D, N, precision, default_layout if STAGE_KERNEL is None else STAGE_KERNEL)
     _barrier(world)
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    dof_stage = 0
-    alg_bytes = 0
-    alg_flops = 0
-    launches = 0
-    default_layout = 4 if (precision == "fp32" and D == 3) else 2
-    per_node = measured_traffic(D, N, precision, default_layout if STAGE_KERNEL is None else STAGE_KERNEL)
-    traffic = 0.0
-    regrid_s = []
-    ev0.record()
-    for i in range(steps):
-        E = m.num_elements
-        m.step(dt, 1)
-        dof_stage += 3 * E * NP
-        alg_bytes += stage_bytes(E, NP, NV, b, n1, D)
-        alg_flops += stage_flops(E, NP, NV, n1, D)
-        if per_node:
-            traffic += E * NP * sum(per_node)
-        launches += 3 * (1 + (m.num_mortars > 0))   # stage (+ mortar) launches per step
-        if regrid_every and (i + 1) % regrid_every == 0:
-            torch.cuda.synchronize()     # dg_adapt starts with this wait anyway
-            tr = time.perf_counter()
-            m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
-            regrid_s.append(time.perf_counter() - tr)
-            launches += 3   # indicator, transfer, background
-    ev1.record()
-    torch.cuda.synchronize()
+    reps = []
+    for r in range(repeats):
+        _barrier(world)
+        torch.cuda.synchronize()
+        ms, c = _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D)
+        ms = _barrier_max(ms, world)
+        reps.append((c["dof_stage"] / (ms / 1e3), ms, c))
     clocks = sampler.stop() if sampler else None
-    ms = ev0.elapsed_time(ev1)
-    ms = _barrier_max(ms, world)
+    rates = sorted(x[0] for x in reps)
+    med = rates[len(rates) // 2]
+    rate, ms, c = next(x for x in reps if x[0] == med)
+    # stage-kernel time per launch, from a region with per-stage events
+    m.enable_timing(True)
+    m.stage_timing(reset=True)
+    _barrier(world)
+    torch.cuda.synchronize()
+    ms_t, ct = _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D, per_node)
     stage_ms, stage_launches = m.stage_timing(reset=True)
     m.enable_timing(False)
     integ = m.integrals()
-    out = dict(ms=ms, dof_stage=dof_stage, stage_ms=stage_ms, stage_launches=stage_launches,
-               alg_bytes=alg_bytes, alg_flops=alg_flops, launches=launches, clocks=clocks,
+    regrid_s = [t for x in reps for t in x[2]["regrid_s"]]
+    out = dict(ms=ms, rate=rate, rates=[x[0] for x in reps], dof_stage=c["dof_stage"],
+               launches=c["launches"], clocks=clocks,
+               stage_ms=stage_ms, stage_launches=stage_launches, ms_timed_region=ms_t,
+               alg_bytes=ct["alg_bytes"], alg_flops=ct["alg_flops"],
                elements=m.num_elements, nodes=m.num_nodes, integrals=integ.tolist(),
                state_bytes=NV * m.num_nodes * b, mortars=m.num_mortars,
-               traffic_per_launch=(traffic / (3 * steps)) if per_node else None,
+               traffic_per_launch=(ct["traffic"] / (3 * steps)) if per_node else None,
                regrid_ms=(1e3 * sum(regrid_s) / len(regrid_s)) if regrid_s else None,
                regrids=len(regrid_s))
     return m, out
@@ -526,26 +549,110 @@ def run_batch(pkg, steps=500, compare_steps=50):
             "layouts": {"node": int(np.sum(layouts == 1)), "column_async": int(np.sum(layouts == 2))}}
 
 
-def oracle_sample(cfg, n_elem=1024, reps=1, warmup=0):
-    """Times the oracle on a bounded sample: per repetition, three RHS evaluations (one RK3
-    step's worth) restricted to a contiguous block of elements of the adapted mesh."""
+_ORACLE = {}
+
+
+def _oracle_setup(cfg_name):
+    """The oracle mesh of a workload and its initial state (built once per process)."""
     from oracle import dg as odg, forest as ofo
-    b = cfg["bubble"]
-    om = odg.adapt_initial(ofo.Forest(cfg["base"], cfg["max_level"]), cfg["N"], cfg["length"],
-                           lambda mm: odg.bubble_theta(mm, b["center"], b["radius"], b["amp"]),
-                           cfg["threshold"], cfg["buffer"])
-    q = odg.state_from_theta(om, odg.bubble_theta(om, b["center"], b["radius"], b["amp"]))
-    start = max(0, om.E // 2 - n_elem // 2)
-    elems = np.arange(start, min(om.E, start + n_elem))
-    for _ in range(warmup):
-        odg.rhs(om, q, elems=elems)
+    if cfg_name not in _ORACLE:
+        cfg = workloads.CONFIGS[cfg_name]
+        b = cfg["bubble"]
+        om = odg.adapt_initial(ofo.Forest(cfg["base"], cfg["max_level"]), cfg["N"], cfg["length"],
+                               lambda mm: odg.bubble_theta(mm, b["center"], b["radius"], b["amp"]),
+                               cfg["threshold"], cfg["buffer"])
+        q = odg.state_from_theta(om, odg.bubble_theta(om, b["center"], b["radius"], b["amp"]))
+        _ORACLE[cfg_name] = (om, q)
+    return _ORACLE[cfg_name]
+
+
+def _oracle_block_step(args):
+    """One SSP-RK3 step of the oracle (mortars included) for a block of consecutive elements;
+    its stages are evaluated on the block's two- and one-hop neighbourhoods as the step needs."""
+    cfg_name, start, n = args
+    from oracle import dg as odg
+    om, q = _oracle_setup(cfg_name)
+    elems = np.arange(start, min(om.E, start + n))
     t0 = time.perf_counter()
-    for _ in range(reps):
-        for _s in range(3):
-            odg.rhs(om, q, elems=elems)
+    odg.step_on(om, q, workloads.CONFIGS[cfg_name]["dt"], elems)
     sec = time.perf_counter() - t0
-    units = reps * 3 * len(elems) * om.np_
-    return units / sec, len(elems), om.E, sec
+    # node-stage updates the oracle performed: stage 1 on the two-hop neighbourhood, stage 2 on
+    # the one-hop neighbourhood, stage 3 on the block
+    hop1 = set(elems.tolist())
+    for e in elems:
+        hop1 |= set(om.forest.face_neighbors(int(e)))
+    hop2 = set(hop1)
+    for e in list(hop1):
+        hop2 |= set(om.forest.face_neighbors(int(e)))
+    return len(hop2) + len(hop1) + len(elems), sec
+
+
+def host_description():
+    """CPU model and core count of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+class OraclePool:
+    """The oracle stepped on blocks of consecutive elements by a pool of host processes (spawned,
+    so the pool is safe to start after the GPU is in use).  A timed map is one SSP-RK3 step of
+    `procs` blocks of `block` elements taken from the middle of the leaf order."""
+
+    def __init__(self, cfg, procs, block):
+        import multiprocessing as mp
+        self.cfg, self.procs, self.block = cfg, procs, block
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_setup, initargs=(cfg["name"],))
+        om, _ = _oracle_setup(cfg["name"])   # for the sizes (and the single-core leg)
+        self.E, self.NP = om.E, om.np_
+        first = max(0, om.E // 2 - procs * block // 2)
+        self.tasks = [(cfg["name"], first + k * block, block) for k in range(procs)]
+        self.pool.map(_oracle_block_step, self.tasks, chunksize=1)   # warm-up: every worker ready
+
+    def step(self):
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_block_step, self.tasks, chunksize=1)
+        sec = time.perf_counter() - t0
+        return sum(r[0] for r in res) * self.NP, sec
+
+    def single(self):
+        n, sec = _oracle_block_step(self.tasks[0])
+        return n * self.NP, sec
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(cfg, procs=None, block=96, maps=2):
+    """The oracle timed on the host cores on a bounded sample of the workload: one SSP-RK3 step
+    (three RHS evaluations with mortars, Shu-Osher combination) on blocks of consecutive
+    elements, single-threaded and on all cores."""
+    procs = procs or os.cpu_count() or 1
+    pool = OraclePool(cfg, procs, block)
+    units = sec = 0.0
+    for _ in range(maps):
+        u, t = pool.step()
+        units += u
+        sec += t
+    u1, t1 = pool.single()
+    pool.close()
+    host = host_description()
+    return {"value": units / sec, "unit": METRIC, "cores": procs, "kind": "oracle",
+            "sample": "one SSP-RK3 step (mortars included) of %d blocks of %d consecutive elements "
+                      "of %d, %d times (%.1f s); single core: one block (%.1f s).  Counted: every "
+                      "node-stage update performed (stage 1 on a block's two-hop face "
+                      "neighbourhood, stage 2 on its one-hop neighbourhood, stage 3 on the block)"
+                      % (procs, block, pool.E, maps, sec, t1),
+            "single_core": {"value": u1 / t1, "cores": 1},
+            "cpu_model": host["cpu_model"], "nproc": host["nproc"]}
 
 
 def main():
@@ -553,6 +660,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed repeats of --steps steps each; the median is reported (at least 5)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=workloads.BUBBLE_3D["name"])
     ap.add_argument("--no-fp64", action="store_true")
@@ -587,15 +696,29 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        rate, nel, E, sec = oracle_sample(cfg, n_elem=256, reps=max(1, args.steps),
-                                          warmup=args.warmup)
+        procs = os.cpu_count() or 1
+        pool = OraclePool(cfg, procs, block=48)
+        for _ in range(args.warmup):
+            pool.step()
+        units = sec = 0.0
+        for _ in range(max(1, args.steps)):
+            u, t = pool.step()
+            units += u
+            sec += t
+        pool.close()
+        rate = units / sec
+        host = host_description()
         line = {"metric": METRIC, "value": rate, "unit": METRIC, "impl": "reference",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * sec / max(1, args.steps), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config,
-                "cpu_baseline": {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-                                 "sample": "3 RHS evaluations per step on %d of %d elements" % (nel, E)},
+                "cpu_baseline": {"value": rate, "unit": METRIC, "cores": procs, "kind": "oracle",
+                                 "sample": "per step: one SSP-RK3 step (mortars included) of %d blocks of "
+                                           "48 consecutive elements of %d; every node-stage update "
+                                           "performed is counted (stages 1 and 2 on the blocks' two- "
+                                           "and one-hop face neighbourhoods)" % (procs, pool.E),
+                                 "cpu_model": host["cpu_model"], "nproc": host["nproc"]},
                 "e2e": {"value": rate, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -609,19 +732,24 @@ def main():
     pkg.load_library()
     peaks, peak_kind = _peaks()
     sampler = ClockSampler(local, args.clock_log)
-    m32, r32 = run_path(pkg, cfg, "fp32", args.steps, args.warmup, regrid_every, sampler, world)
+    R = max(5, args.repeats)
+    m32, r32 = run_path(pkg, cfg, "fp32", args.steps, args.warmup, regrid_every, sampler, world, R)
     e2e = run_e2e(pkg, m32, cfg, max(4, min(args.steps, 20)), regrid_every, world)
     m32.close()
     r64 = None
     if not args.no_fp64:
-        m64, r64 = run_path(pkg, cfg, "fp64", args.steps, args.warmup, regrid_every, None, world)
+        m64, r64 = run_path(pkg, cfg, "fp64", args.steps, args.warmup, regrid_every, None, world, R)
         m64.close()
-    value = world * r32["dof_stage"] / (r32["ms"] / 1e3)
+    value = world * r32["rate"]
     achieved = r32["alg_bytes"] / (r32["stage_ms"] / 1e3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config,
+            "timing": {"repeats": R, "statistic": "median repeat of %d steps each" % args.steps,
+                       "repeat_values": [world * v for v in r32["rates"]],
+                       "path": "production dg_step (stage kernels as programmatic dependent launches "
+                               "after their mortar kernels)"},
             "precision_path": "FP32 state/flux arithmetic; FP64 background and integrals; P' to FP64 accuracy before its FP32 rounding",
             "stage_kernel": {None: "default", 0: "column", 1: "node", 2: "column-async", 3: "half-column-async", 4: "line"}[STAGE_KERNEL],
             "elements": r32["elements"], "nodes_per_variable": r32["nodes"],
@@ -634,19 +762,25 @@ def main():
                                          "(profiles/stage_traffic_bubble3d_N7.json) scaled to this run's "
                                          "nodes; null when the kernel sources changed",
                          "algorithmic_bytes_per_launch": r32["alg_bytes"] / (3 * args.steps),
-                         "stage_ms_per_launch": r32["stage_ms"] / max(1, r32["stage_launches"])},
+                         "stage_ms_per_launch": r32["stage_ms"] / max(1, r32["stage_launches"]),
+                         "stage_timing": "CUDA events around each stage launch over a further "
+                                         "%d-step region (%.3f ms per step there)"
+                                         % (args.steps, r32["ms_timed_region"] / args.steps)},
             "clocks": r32["clocks"], "e2e": e2e,
             "regrid": {"count": r32["regrids"], "ms_avg_host_wall": r32["regrid_ms"],
                        "note": "dg_adapt inside the timed region: indicator, host tree work, "
                                "topology tables, conservative transfer"}}
     if r64 is not None:
-        v64 = world * r64["dof_stage"] / (r64["ms"] / 1e3)
-        fp64_peak = 152 * peaks.get("sm_max_mhz", 2070.0) * 1e6 * 4 / 1e12
+        v64 = world * r64["rate"]
+        fp64_peak = pkg.probe_fma_rate("fp64") / 1e12
         ach64 = r64["alg_flops"] / (r64["stage_ms"] / 1e3) / 1e12
         line["fp64"] = {"value": v64, "ms_per_step": r64["ms"] / args.steps, "dtype": "f64",
+                        "repeat_values": [world * v for v in r64["rates"]],
                         "roofline": {"bound": "alu", "kernel": "stage_kernel", "achieved": ach64,
                                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach64 / fp64_peak,
-                                     "peak_kind": "derived: 152 SMs x max SM clock x 4 FP64 flop/clk"},
+                                     "peak_kind": "measured: dg_probe_fma_rate (independent FP64 "
+                                                  "multiply-adds on every SM, CUDA events)",
+                                     "stage_ms_per_launch": r64["stage_ms"] / max(1, r64["stage_launches"])},
                         "integrals": r64["integrals"]}
         line["fp32_over_fp64"] = value / v64
     if not args.no_accuracy and cfg.get("threshold") is not None:
@@ -662,9 +796,7 @@ def main():
     if not args.no_vortex:
         line["vortex"] = run_vortex(pkg)
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, nel, E, sec = oracle_sample(cfg, n_elem=1024, reps=1)
-        line["cpu_baseline"] = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-                                "sample": "3 RHS evaluations on %d of %d elements (%.1f s)" % (nel, E, sec)}
+        line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -39,7 +39,8 @@ typedef enum {
   DG_ERR_ARG = 1,          /* invalid argument (null pointer, size, range, layout) */
   DG_ERR_CUDA = 2,         /* a CUDA runtime call failed; detail in dg_last_error */
   DG_ERR_OOM = 3,          /* device or host allocation failed */
-  DG_ERR_STATE = 4,        /* non-finite value detected in the state */
+  DG_ERR_STATE = 4,        /* non-finite value detected in the state, inconsistent tables,
+                              or a mesh left unusable by a failed regrid (see dg_adapt) */
   DG_ERR_TIMEOUT = 5,      /* a bounded device wait ran out */
   DG_ERR_UNSUPPORTED = 6   /* combination not compiled in (dimension, degree, precision) */
 } dg_status;
@@ -179,7 +180,10 @@ dg_status dg_step(dg_mesh* mesh, double dt, int32_t nsteps, void* stream);
 /* One regrid pass with conservative transfer of the state (Sec. 3.3).  Synchronous: the
  * criterion is evaluated on the device, the tree work runs on the host, the transfer on the
  * device.  Element order and count change; state pointers obtained earlier stay valid only as
- * copies.  `report` may be NULL. */
+ * copies.  `report` may be NULL.  Errors: a failure while the new tree and its tables are built
+ * and checked leaves the mesh as it was; a failure after the new tree is committed (an
+ * allocation or copy of the new tables) leaves the mesh unusable, and every later call on it
+ * returns DG_ERR_STATE. */
 dg_status dg_adapt(dg_mesh* mesh, const dg_adapt_params* params, dg_adapt_report* report);
 
 /* Per-element refinement indicator max_n |theta'| (FP64), written to host `out` (E doubles). */
@@ -303,7 +307,13 @@ const char* dg_batch_last_error(const dg_batch* batch);
  * registers (3 and 4: 3D with odd N; other shapes run layout 2).  Default: 4 for FP32 3D
  * meshes, 2 otherwise.  All compute the same operator; the option exists for tuning and
  * cross-checking. */
-enum { DG_OPT_STAGE_KERNEL = 1 };
+enum { DG_OPT_STAGE_KERNEL = 1, DG_OPT_FAIL_NEXT_ADAPT = 2 };
+/* DG_OPT_FAIL_NEXT_ADAPT is a host-side failure injection for tests of the regrid's error path
+ * (no device fault is involved): value 1 makes the next dg_adapt fail where it checks the new
+ * tables, before anything of the mesh changes, so the mesh stays usable; value 2 makes it fail
+ * after it has committed the new tree, as a failed allocation there would.  A mesh in the
+ * second state is unusable: every later call on it returns DG_ERR_STATE (dg_last_error says
+ * why) and only dg_mesh_destroy remains.  The flag is cleared by the dg_adapt it affects. */
 dg_status dg_set_option(dg_mesh* mesh, int32_t option, int64_t value);
 
 /* Kernel timing: when enabled, the fused stage launches of dg_step are bracketed by CUDA
@@ -373,6 +383,14 @@ dg_status dg_forest_partition(const dg_forest* forest, int32_t nparts, int64_t* 
  * per fine neighbour.  *count receives the row count; rows (capacity `cap` rows) may be NULL. */
 dg_status dg_forest_halo(const dg_forest* forest, int32_t nparts, int32_t part, int32_t* rows,
                          size_t cap, int64_t* count);
+
+/* Measurement utility (the paper has no counterpart): the rate of independent fused
+ * multiply-adds the current device sustains in FP64 (precision DG_FP64) or FP32
+ * (DG_FP32_PERT), in FLOP/s counting 2 per multiply-add.  8 chains per thread, 8 CTAs of 256
+ * threads per SM, timed with CUDA events on `stream` (NULL: legacy default stream) after one
+ * warm-up launch; synchronous; allocates and frees a small device buffer.  It is the measured
+ * peak against which the FP64 stage kernel's pipe-bound roofline is reported. */
+dg_status dg_probe_fma_rate(int32_t precision, double* flop_per_s, void* stream);
 
 /* Detail of the last error on this mesh (never NULL). */
 const char* dg_last_error(const dg_mesh* mesh);

@@ -328,6 +328,28 @@ def step(mesh, q, dt, nsteps=1, nu=0.0):
     return q
 
 
+def step_on(mesh, q, dt, elems):
+    """One SSP-RK3 step (Shu-Osher form, as ssprk3_step) evaluated only where it is needed for
+    the elements ``elems``: the tendency of stage s at an element reads its face neighbours'
+    stage-s state, so stage 1 is taken on the elements within two face hops of ``elems``,
+    stage 2 within one hop and stage 3 on ``elems`` alone.  Returns the new state there (other
+    elements are NaN).  The same arithmetic as step(); for sampled checks on large meshes."""
+    hop1 = set(int(e) for e in elems)
+    for e in list(hop1):
+        hop1 |= set(mesh.forest.face_neighbors(e))
+    hop2 = set(hop1)
+    for e in list(hop1):
+        hop2 |= set(mesh.forest.face_neighbors(e))
+    s0, s1, s2 = (np.array(sorted(x), dtype=np.int64) for x in (elems, hop1, hop2))
+    q1 = q.copy()
+    q1[:, s2] = q[:, s2] + dt * rhs(mesh, q, elems=s2)[:, s2]
+    q2 = q.copy()
+    q2[:, s1] = 0.75 * q[:, s1] + 0.25 * (q1[:, s1] + dt * rhs(mesh, q1, elems=s1)[:, s1])
+    out = np.full_like(q, np.nan)
+    out[:, s0] = (1.0 / 3.0) * q[:, s0] + (2.0 / 3.0) * (q2[:, s0] + dt * rhs(mesh, q2, elems=s0)[:, s0])
+    return out
+
+
 def transfer(q_old, mesh_old, mesh_new, tmap):
     """Conservative L2 solution transfer after a regrid (Sec. 3.3).
 

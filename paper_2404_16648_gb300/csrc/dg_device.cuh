@@ -295,20 +295,30 @@ __device__ __forceinline__ int face_node(int a, int side, int t) {
   return idx[0] + n1 * (idx[1] + n1 * idx[2]);
 }
 
+// Dynamic shared memory of the node-per-thread layout: D, then the flux tile [EPB][NV][NP].
+template <class T, int D, int N, int EPB>
+__host__ __device__ constexpr size_t node_smem_bytes() {
+  return sizeof(T) * ((size_t)(N + 1) * (N + 1) + (size_t)EPB * (D + 2) * ipow(N + 1, D));
+}
+
 // Body of the node-per-thread stage kernel for the EPB elements e0, e0 + 1, ... of mesh A.
+// Threads beyond EPB (N+1)^d (a persistent block of a fixed size) only take part in the
+// barriers.
 template <class T, int D, int N, int EPB>
 __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
   constexpr int NSUB = 1 << (D - 1);
-  __shared__ T sD[n1 * n1];
-  __shared__ T sF[EPB][NV][NP];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sD = reinterpret_cast<T*>(smem_raw);             // [n1 * n1]
+  T* sF = sD + n1 * n1;                                // [EPB][NV][NP]
   const int tid = threadIdx.x;
   const T* ops = (const T*)A.ops;
   for (int i = tid; i < n1 * n1; i += blockDim.x) sD[i] = ops[i];
   const T gamma = gamma_of<T>(A.ph, A.gammaf);
   const int le = tid / NP, n = tid - le * NP;
+  const bool inblk = le < EPB;
   const int64_t e = e0 + le;
-  const bool valid = e < A.E;
+  const bool valid = inblk && e < A.E;
   int idx[3];
   idx[0] = n % n1;
   idx[1] = (n / n1) % n1;
@@ -341,8 +351,10 @@ __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) 
   for (int a = 0; a < D; ++a) {
     T F[NV];
     flux_axis<T, D>(q, nd, pp, a, F);
+    if (inblk) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sF[le][v][n] = F[v];
+      for (int v = 0; v < NV; ++v) sF[(le * NV + v) * NP + n] = F[v];
+    }
     __syncthreads();
     if (valid) {
       const int stride = ipow(n1, a);
@@ -352,7 +364,7 @@ __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) 
       for (int v = 0; v < NV; ++v) {
         T s = (T)0;
 #pragma unroll
-        for (int m = 0; m < n1; ++m) s = fma(sD[ia * n1 + m], sF[le][v][b0 + m * stride], s);
+        for (int m = 0; m < n1; ++m) s = fma(sD[ia * n1 + m], sF[(le * NV + v) * NP + b0 + m * stride], s);
         acc[v] = fma(-inv2h[a], s, acc[v]);
       }
     }

@@ -88,7 +88,10 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
   double* sBc = reinterpret_cast<double*>(sBg + n1 * 4);   // [n1] (FP32 path)
   T* sDh = reinterpret_cast<T*>(smem_raw) + EPB * EW;
   const int64_t e = e0 + le;
-  const bool valid = e < A.E;
+  // threads beyond EPB columns (a persistent block of a fixed size) only take part in the
+  // barriers and write no shared memory
+  const bool inblk = le < EPB;
+  const bool valid = inblk && e < A.E;
   const int ci = t % n1, cj = (D == 3) ? t / n1 : 0;
   const int P = A.plane32;
   const T* qe = (const T*)A.qs + (valid ? e : 0) * NP;
@@ -154,8 +157,10 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
     const NodeDer<T> nd = node_der<T, D>(q, bg);
     T F[NV];
     flux_axis<T, D>(q, nd, pp, 0, F);
+    if (inblk) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) sA[v * NP + n] = F[v];
+      for (int v = 0; v < NV; ++v) sA[v * NP + n] = F[v];
+    }
     flux_axis<T, D>(q, nd, pp, D - 1, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) Fz[v][k] = F[v];
@@ -211,8 +216,10 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
                                  : NodeBg<T>{(T)1, (T)1, (T)1};
       T F[NV];
       flux_axis<T, D>(q, node_der<T, D>(q, bg), pp, 1, F);
+      if (inblk) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) sA[v * NP + NF * k + n1 * ci + cj] = F[v];
+        for (int v = 0; v < NV; ++v) sA[v * NP + NF * k + n1 * ci + cj] = F[v];
+      }
     }
     __syncthreads();
     if (valid) {

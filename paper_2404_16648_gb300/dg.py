@@ -29,7 +29,7 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_step_state", "dg_step_vjp", "dg_step_record", "dg_step_vjp_record", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
             "dg_bubble_theta", "dg_forest_partition", "dg_forest_halo", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
             "dg_batch_run", "dg_batch_sync", "dg_batch_autotune", "dg_batch_last_error",
-            "dg_last_error", "dg_version"]
+            "dg_probe_fma_rate", "dg_last_error", "dg_version"]
 
 
 class MeshDesc(ctypes.Structure):
@@ -134,6 +134,7 @@ def load_library(path=None):
         "dg_batch_sync": (i32, [vp]),
         "dg_batch_autotune": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int32)]),
         "dg_batch_last_error": (ctypes.c_char_p, [vp]),
+        "dg_probe_fma_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double), vp]),
         "dg_last_error": (ctypes.c_char_p, [vp]),
         "dg_version": (ctypes.c_char_p, []),
     }
@@ -162,6 +163,38 @@ def _ptr(x):
     return x.data_ptr(), (DG_DEVICE if x.is_cuda else DG_HOST)
 
 
+def make_desc(dim, N, base, length, max_level=0, precision="fp64", theta0=300.0, p0=1.0e5, g=9.81,
+              R=287.0, cp=1004.5, nu=0.0, equations="euler", face_mode="mortar", wind_period=0.0,
+              periodic=(False, False, False)):
+    """The dg_mesh_desc of a mesh (no device call)."""
+    d = MeshDesc()
+    d.dim, d.N = dim, N
+    for a in range(3):
+        d.base[a] = int(base[a]) if a < len(base) else 1
+        d.length[a] = float(length[a]) if a < len(length) else 1.0
+    d.max_level = max_level
+    d.precision = DG_FP64 if precision == "fp64" else DG_FP32_PERT
+    d.theta0, d.p0, d.g, d.R, d.cp, d.nu = theta0, p0, g, R, cp, nu
+    if equations not in ("euler", "tracer") or face_mode not in ("mortar", "interp"):
+        raise ValueError("equations must be 'euler' or 'tracer', face_mode 'mortar' or 'interp'")
+    d.equations = 1 if equations == "tracer" else 0
+    d.face_mode = 1 if face_mode == "interp" else 0
+    d.wind_period = wind_period
+    for a in range(3):
+        d.periodic[a] = 1 if a < len(periodic) and periodic[a] else 0
+    return d
+
+
+def probe_fma_rate(precision="fp64"):
+    """Measured FMA throughput of the current device in FLOP/s (dg_probe_fma_rate)."""
+    lib = load_library()
+    out = ctypes.c_double()
+    st = lib.dg_probe_fma_rate(DG_FP64 if precision == "fp64" else DG_FP32_PERT, ctypes.byref(out), None)
+    if st != DG_OK:
+        raise DGError(st, "dg_probe_fma_rate failed")
+    return out.value
+
+
 class Mesh:
     """A forest-of-trees dGSEM mesh with its state on the GPU (one dg_mesh handle)."""
 
@@ -169,21 +202,8 @@ class Mesh:
                  p0=1.0e5, g=9.81, R=287.0, cp=1004.5, nu=0.0, stream=None, equations="euler",
                  face_mode="mortar", wind_period=0.0, periodic=(False, False, False)):
         self.lib = load_library()
-        d = MeshDesc()
-        d.dim, d.N = dim, N
-        for a in range(3):
-            d.base[a] = int(base[a]) if a < len(base) else 1
-            d.length[a] = float(length[a]) if a < len(length) else 1.0
-        d.max_level = max_level
-        d.precision = DG_FP64 if precision == "fp64" else DG_FP32_PERT
-        d.theta0, d.p0, d.g, d.R, d.cp, d.nu = theta0, p0, g, R, cp, nu
-        if equations not in ("euler", "tracer") or face_mode not in ("mortar", "interp"):
-            raise ValueError("equations must be 'euler' or 'tracer', face_mode 'mortar' or 'interp'")
-        d.equations = 1 if equations == "tracer" else 0
-        d.face_mode = 1 if face_mode == "interp" else 0
-        d.wind_period = wind_period
-        for a in range(3):
-            d.periodic[a] = 1 if a < len(periodic) and periodic[a] else 0
+        d = make_desc(dim, N, base, length, max_level, precision, theta0, p0, g, R, cp, nu,
+                      equations, face_mode, wind_period, periodic)
         self.desc = d
         self.equations = equations
         self.dim, self.N, self.nv = dim, N, (1 if equations == "tracer" else dim + 2)
@@ -460,6 +480,11 @@ class Mesh:
         column (3D, odd N); 4: one pass per axis, two threads per node line, fluxes in registers
         (3D, odd N).  Default: 4 for FP32 3D meshes, 2 otherwise."""
         self._check(self.lib.dg_set_option(self.h, 1, int(layout)))
+
+    def fail_next_adapt(self, where):
+        """Host-side failure injection for the next adapt (DG_OPT_FAIL_NEXT_ADAPT): 1 fails
+        before the new tree is committed, 2 after it (the mesh is then unusable)."""
+        self._check(self.lib.dg_set_option(self.h, 2, int(where)))
 
     def enable_timing(self, on=True):
         self._check(self.lib.dg_enable_timing(self.h, 1 if on else 0))

@@ -76,3 +76,43 @@ def test_batch_rejects_a_regridded_member(pkg):
     ms[1].adapt(flags=np.ones(ms[1].num_elements, np.uint8), buffer=0)
     with pytest.raises(DGError):
         batch.run(1)
+
+
+@pytest.mark.parametrize("refine", [False, True])
+def test_batch_members_against_the_oracle(pkg, refine):
+    """Batch members checked against the oracle itself, not only against single-mesh runs: two
+    FP64 and two FP32 members of different degree, each stepped three times in the batch and
+    compared with oracle.dg.step on its own (independently built) forest.  Bounds on the state
+    change per variable: FP64 1e-11, FP32 1e-4 (three steps of FP32 tendencies, each stage
+    within 2e-5 of max|rhs|)."""
+    from oracle import dg as odg, forest as ofo
+    pool = workloads.batch_instances(64, seed=15, meshes=((4, 4), (6, 3), (5, 5)))
+    picked, seen = [], set()
+    for d in pool:
+        key = (d["precision"], d["N"])
+        if key not in seen and sum(p["precision"] == d["precision"] for p in picked) < 2:
+            picked.append(d)
+            seen.add(key)
+    assert len(picked) == 4
+    ms = _make(pkg, picked, refine)
+    dts = [d["dt"] * (0.5 if refine else 1.0) for d in picked]
+    q0s, oms = [], []
+    for k, (m, d) in enumerate(zip(ms, picked)):
+        of = ofo.Forest(d["base"], 1)
+        if refine:
+            of, _ = of.regrid(workloads.random_flags(len(of), 0.2, seed=300 + k).astype(bool), 0)
+        om = odg.Mesh(of, d["N"], (1000.0, 1000.0))
+        assert om.E == m.num_elements
+        dtype = np.float64 if d["precision"] == "fp64" else np.float32
+        q0 = workloads.random_state(om.nv, om.E, om.np_, seed=400 + k, rho_scale=1e-4, u_scale=0.2,
+                                    theta_scale=0.02, dtype=dtype)
+        m.set_state(q0)
+        q0s.append(q0.astype(np.float64))
+        oms.append(om)
+    batch = pkg.Batch(ms, dts)
+    batch.run(3, graph=True)
+    for m, om, q0, dt, d in zip(ms, oms, q0s, dts, picked):
+        got = m.get_state().astype(np.float64) - q0
+        want = odg.step(om, q0, dt, 3) - q0
+        err = max(np.abs(got[v] - want[v]).max() / np.abs(want[v]).max() for v in range(om.nv))
+        assert err <= (1e-11 if d["precision"] == "fp64" else 1e-4), (d["precision"], d["N"], err)

@@ -207,6 +207,73 @@ def test_full_size_octree_sampled_parity(pkg):
     assert _rel_err(got[:, sample], want[:, sample]) <= 1e-12
 
 
+_FULL = {}
+
+
+def _full_size_pair(pkg, precision):
+    """The 3D octree workload at full size (16^3 roots, N = 7, two levels where |theta'| > 0.05 K):
+    a library mesh in the given precision and the oracle mesh, built independently."""
+    if precision not in _FULL:
+        cfg = workloads.BUBBLE_3D
+        b = cfg["bubble"]
+        lm = pkg.Mesh(3, cfg["N"], cfg["base"], cfg["length"], max_level=cfg["max_level"],
+                      precision=precision)
+        pkg.adapt_initial(lm, b, cfg["threshold"], cfg["buffer"])
+        if "oracle" not in _FULL:
+            _FULL["oracle"] = odg.adapt_initial(
+                ofo.Forest(cfg["base"], cfg["max_level"]), cfg["N"], cfg["length"],
+                lambda m: odg.bubble_theta(m, b["center"], b["radius"], b["amp"]),
+                cfg["threshold"], cfg["buffer"])
+        om = _FULL["oracle"]
+        np.testing.assert_array_equal(lm.leaves()[:, 1], [l for l, _ in om.forest.leaves])
+        _FULL[precision] = lm
+    return _FULL[precision], _FULL["oracle"]
+
+
+def _full_size_sample(om, count, seed):
+    """Seeded sample of elements plus coarse mortar elements, and elements from the far end of
+    the leaf order (the last resident wave: no element ahead of them for the L2 lookahead)."""
+    sample = workloads.sample_elements(om.E, count, seed=seed)
+    _, mort, _ = om.forest.face_lists()
+    coarse = sorted({m[0] for m in mort})[:8]
+    return np.unique(np.concatenate([sample, coarse, [om.E - 1, om.E - 7 * 152 - 1]]))
+
+
+def test_full_size_octree_sampled_parity_fp32(pkg):
+    """The benchmarked FP32 path at full size: the default line layout (4) with its programmatic
+    dependent launch after the mortar kernel and its L2 lookahead one resident wave ahead, GPU
+    RHS of every element against the oracle on the FP32-rounded input at a seeded sample.
+    Bound: 2e-5 of max|rhs| per variable, as for the small FP32 meshes."""
+    lm, om = _full_size_pair(pkg, "fp32")
+    assert om.E > 7 * 152 * 10 and len(om.forest.face_lists()[1]) > 0
+    q32 = workloads.random_state(om.nv, om.E, om.np_, seed=23, rho_scale=1e-3, u_scale=1.0,
+                                 theta_scale=0.2, dtype=np.float32)
+    got = _gpu_rhs(lm, q32).astype(np.float64)
+    sample = _full_size_sample(om, 48, seed=24)
+    want = odg.rhs(om, q32.astype(np.float64), elems=sample)
+    assert _rel_err(got[:, sample], want[:, sample]) <= 2e-5
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 4e-5)])
+def test_full_size_octree_step_sampled(pkg, precision, tol):
+    """One SSP-RK3 step of the full-size octree through dg_step (three fused stage launches,
+    each after its mortar kernel) against the oracle's step restricted to a seeded sample
+    (odg.step_on).  Compared on the state change per variable: FP64 1e-11 as for the small
+    meshes; FP32 4e-5, twice the per-RHS bound (three FP32 tendencies combined, each within
+    2e-5, plus the FP32 rounding of the stage states)."""
+    lm, om = _full_size_pair(pkg, precision)
+    dt = np.float64 if precision == "fp64" else np.float32
+    q0 = workloads.random_state(om.nv, om.E, om.np_, seed=25, rho_scale=1e-4, u_scale=0.2,
+                                theta_scale=0.02, dtype=dt)
+    lm.set_state(q0)
+    lm.step(workloads.BUBBLE_3D["dt"], 1)
+    got = lm.get_state().astype(np.float64)
+    sample = _full_size_sample(om, 12, seed=26)
+    q64 = q0.astype(np.float64)
+    want = odg.step_on(om, q64, workloads.BUBBLE_3D["dt"], sample)
+    assert _rel_err(got[:, sample] - q64[:, sample], want[:, sample] - q64[:, sample]) <= tol
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 def test_rhs_parity_large_theta_uses_fallback_branch(pkg, precision, tol):
     # |Theta'| ~ 20 makes |Theta'/Theta_bar| exceed 2^-5 at many nodes, so the pressure

@@ -278,3 +278,30 @@ def test_rhs_subset_equals_full():
     sub = np.array([0, 3, mesh.E - 1])
     part = dg.rhs(mesh, q, elems=sub)
     np.testing.assert_array_equal(part[:, sub], full[:, sub])
+
+
+@pytest.mark.parametrize("base,N,L", [((4, 4), 3, (1200.0, 1200.0)), ((3, 2, 3), 2, (900.0, 600.0, 900.0))])
+def test_step_on_sampled_elements_equals_the_full_step(base, N, L):
+    """step_on restricts one SSP-RK3 step to the elements a sample needs (two face hops for
+    stage 1, one for stage 2): on the sample it gives the full step's values bit for bit, also
+    for elements whose neighbourhood crosses hanging faces."""
+    mesh = dg.Mesh(_hanging_forest(base, seed=8), N, L, K)
+    q = 1e-2 * _random_state(mesh, 9)
+    full = dg.step(mesh, q, 0.01, 1)
+    _, mort, _ = mesh.forest.face_lists()
+    sample = np.unique([0, mesh.E // 2, mesh.E - 1] + [int(mort[0][0])])
+    part = dg.step_on(mesh, q, 0.01, sample)
+    np.testing.assert_array_equal(part[:, sample], full[:, sample])
+    others = np.setdiff1d(np.arange(mesh.E), sample)
+    assert np.all(np.isnan(part[:, others]))
+    # a stage short of the two-hop neighbourhood would not be exact: drop the second hop
+    hop1 = set(sample.tolist())
+    for e in sample:
+        hop1 |= set(mesh.forest.face_neighbors(int(e)))
+    s1 = np.array(sorted(hop1))
+    q1 = q.copy()
+    q1[:, s1] = q[:, s1] + 0.01 * dg.rhs(mesh, q, elems=s1)[:, s1]
+    q2 = q.copy()
+    q2[:, s1] = 0.75 * q[:, s1] + 0.25 * (q1[:, s1] + 0.01 * dg.rhs(mesh, q1, elems=s1)[:, s1])
+    short = (1.0 / 3.0) * q + (2.0 / 3.0) * (q2 + 0.01 * dg.rhs(mesh, q2, elems=sample))
+    assert not np.array_equal(short[:, sample], full[:, sample])
