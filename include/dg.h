@@ -274,13 +274,20 @@ dg_status dg_theta_vjp(dg_mesh* mesh, const double* theta, const void* lam_q, do
  * dg_integrals) at the caller's state q (device). */
 dg_status dg_ke_grad(dg_mesh* mesh, const void* q, void* out, void* stream);
 
-/* ---- Batched solves: many independent meshes advanced together.  The batch groups its
- * meshes by (precision, dimension, N); per SSP-RK3 stage it makes one stage launch per group that
- * covers every element of every member (per-member arguments in a device table, a block ->
- * (member, first element) map), plus each member's own mortar launches.  A step is captured
- * once into a CUDA graph and replayed.  The members keep their state in their own buffers
- * (dg_get_state etc. work as usual); a member must not be regridded while in a batch
- * (DG_ERR_STATE).  Members may have different sizes, degrees and precisions. */
+/* ---- Batched solves: many independent meshes advanced together (the batched instances of the
+ * study's benchmark set; Sec. 3.5 names throughput on accelerators as the aim).  The 2D members
+ * run through ONE persistent launch per SSP-RK3 stage: a device array of work items -- first
+ * every member's mortar groups (Sec. 3.3), then tiles of elements of every member, whatever its
+ * degree and precision -- taken in order from an atomic counter by a grid of 128-thread CTAs
+ * sized to what stays resident.  A stage item waits, thread 0 with an iteration limit of about a
+ * second, until its member's mortar items are done; if the limit ever runs out the kernel
+ * records it and dg_batch_sync returns DG_ERR_TIMEOUT (the states are then not valid).  3D
+ * members are grouped by (precision, N): one stage launch per group over all of its members'
+ * elements after the members' mortar launches.  A step is captured once into a CUDA graph and
+ * replayed.  The members keep their state in their own buffers (dg_get_state etc. work as
+ * usual); a member must not be regridded while in a batch (DG_ERR_STATE).  Members may have
+ * different sizes, degrees and precisions.  A member advanced in the batch gets the bits that
+ * dg_step gives it with the same stage layout. */
 typedef struct dg_batch dg_batch;
 
 /* `meshes`: `count` distinct meshes (not owned). */
@@ -292,12 +299,22 @@ dg_status dg_batch_set_dt(dg_batch* batch, const double* dt);
  * already queued on each member's stream and before later work there.  use_graph != 0 replays a
  * captured step graph; 0 launches directly (same kernels, same results). */
 dg_status dg_batch_run(dg_batch* batch, int32_t nsteps, int32_t use_graph);
+/* Waits for the batch's stream; DG_ERR_TIMEOUT if a wait inside the persistent launch ran out. */
 dg_status dg_batch_sync(dg_batch* batch);
-/* Autotuner: times the node-per-thread and the asynchronous-column stage layouts of each group
- * on its members (reps launches each, state untouched) and keeps the faster one; the choice is
- * also applied to each member's own launches.  `layouts` (count int32, may be NULL) receives
- * the chosen layout per member (1 or 2, see DG_OPT_STAGE_KERNEL). */
+/* Autotuner, timed on the members themselves with stage-1 launches (reps each; they read q^n and
+ * write only scratch buffers, so the states are untouched).  For the persistent launch of the 2D
+ * members it chooses, greedily and groups with the most work first: the register budget (the
+ * kernel compiled for 2 or for 4 resident CTAs per SM), per (precision, N) group the element
+ * tile -- node layout, (N+1)^2 threads per element and 128 / (N+1)^2 elements per CTA pass, or
+ * column layout, N+1 threads per element and 128 / (N+1) elements per pass -- and the tiles per
+ * work item (1, 2, 4 or 8).  For 3D groups it keeps the faster of the two grouped layouts.  The
+ * layout choice is also applied to each member's own launches.  `layouts` (count int32, may be
+ * NULL) receives the chosen layout per member (1 node or 2 column, see DG_OPT_STAGE_KERNEL). */
 dg_status dg_batch_autotune(dg_batch* batch, int32_t reps, int32_t* layouts);
+/* The persistent launch's shapes: out[0] resident CTAs per SM its register budget is compiled
+ * for, out[1] element tiles per stage item, out[2] grid (CTAs), out[3] work items per stage,
+ * out[4] dynamic shared memory per CTA in bytes; all zero without 2D members. */
+dg_status dg_batch_shape(dg_batch* batch, int64_t out[5]);
 const char* dg_batch_last_error(const dg_batch* batch);
 
 /* Tuning options.  DG_OPT_STAGE_KERNEL selects the fused stage kernel's thread layout:

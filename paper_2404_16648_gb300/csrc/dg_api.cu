@@ -258,10 +258,15 @@ dg_status set_error(dg_mesh* m, dg_status st, const char* msg) {
   return st;
 }
 
+void fill_mortar_args(const dg_mesh* m, const void* qs, const void* pp_in, dgk::MortarArgs* M) {
+  *M = dgk::MortarArgs{qs, pp_in, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, bgt(m),
+                       m->d_bgc, m->d_ops, (float)m->ph.gamma, m->ph};
+}
+
 dg_status launch_mortars(dg_mesh* m, const void* qs, const void* pp_in, cudaStream_t s) {
   if (m->G == 0) return DG_OK;
-  dgk::MortarArgs M{qs, pp_in, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, bgt(m),
-                    m->d_bgc, m->d_ops, (float)m->ph.gamma, m->ph};
+  dgk::MortarArgs M;
+  fill_mortar_args(m, qs, pp_in, &M);
   bool ok = m->prec == DG_FP64
                 ? (m->D == 2 ? dgk::launch_mortar_f64_2d(m->N, M, s) : dgk::launch_mortar_f64_3d(m->N, M, s))
                 : (m->D == 2 ? dgk::launch_mortar_f32_2d(m->N, M, s) : dgk::launch_mortar_f32_3d(m->N, M, s));
@@ -384,6 +389,8 @@ dg_status init_device_tables(dg_mesh* m) {
   CU(dgk::init_stage_f64_3d(all.data()));
   CU(dgk::init_stage_f32_2d(all.data()));
   CU(dgk::init_stage_f32_3d(all.data()));
+  CU(dgk::init_stage_batch_w(all.data()));
+  CU(dgk::init_stage_batch_d(all.data()));
   done.insert(dev);
   return DG_OK;
 }

@@ -1,6 +1,10 @@
 // Internal launch interface between the C ABI (dg_api.cu) and the kernel translation units.
 #pragma once
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include <cuda_runtime.h>
 
 #include "dg_adjoint.cuh"
@@ -11,6 +15,27 @@
 namespace dgk {
 
 constexpr int NUM_INTEGRALS = 5;
+
+// Function attributes (dynamic shared-memory limit, carveout) belong to a device's context: a
+// kernel is configured once per (kernel, device), under a mutex, so concurrent host threads and
+// a second GPU in the same process each see a configured kernel.  Shared by every stage unit
+// (an inline function's statics are one object across translation units).
+inline cudaError_t configure_kernel(const void* fn, size_t smem, bool max_carveout) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({fn, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && max_carveout)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  done.insert({fn, dev});
+  return cudaSuccess;
+}
 
 // Tracer meshes (tracer_f64.cu): stage, hanging faces (mortar or point interpolation), initial
 // bell, indicator max |C| and the compensated totals {int C, volume} into out[0..1].
@@ -40,6 +65,19 @@ cudaError_t init_stage_f64_2d(const double* dtab_all);
 cudaError_t init_stage_f64_3d(const double* dtab_all);
 cudaError_t init_stage_f32_2d(const double* dtab_all);
 cudaError_t init_stage_f32_3d(const double* dtab_all);
+// Persistent batched stage kernel over the 2D members of a batch (dg_batch_persist.cuh), in two
+// register budgets: "w" for 2 resident CTAs of 128 threads per SM, "d" for 4.
+struct BatchArgs;
+cudaError_t init_stage_batch_w(const double* dtab_all);
+cudaError_t init_stage_batch_d(const double* dtab_all);
+cudaError_t launch_batch_w(const BatchArgs& B, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_batch_d(const BatchArgs& B, int grid, size_t smem, cudaStream_t s);
+cudaError_t occupancy_batch_w(size_t smem, int* ctas_per_sm);
+cudaError_t occupancy_batch_d(size_t smem, int* ctas_per_sm);
+// Largest dynamic shared memory of the persistent kernel's bodies for one (precision, N, layout)
+// (layout 0 node, 1 column-async, 2 mortar).
+size_t batch_body_smem_bytes(int prec32, int N, int layout);
+
 // Stage kernels over many meshes at once (tab: per-mesh arguments on the device, map: per block
 // the mesh index and its first element); layout 1 node-per-thread, 2 column with async staging.
 cudaError_t launch_stage_batched_f64_2d(int N, int layout, const StageArgs* tab, const int2* map, int nblocks, cudaStream_t s);

@@ -80,6 +80,8 @@ void* pp_plane(const dg_mesh* m, void* q);
 // Arguments of one fused stage launch on mesh m (mode 1: Shu-Osher combination).
 void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const void* qn, void* out,
                      void* pp_out, int mode, double dt, double ca, double cb, dgk::StageArgs* A);
+// Arguments of the mortar work of mesh m for stage input qs.
+void fill_mortar_args(const dg_mesh* m, const void* qs, const void* pp_in, dgk::MortarArgs* M);
 // Launches the mortar kernel of mesh m for stage input qs (no-op without hanging faces).
 dg_status launch_mortars(dg_mesh* m, const void* qs, const void* pp_in, cudaStream_t s);
 // Makes the P' plane of m->q[0] current.

@@ -1,35 +1,10 @@
 // Instantiates the stage and mortar kernels of one (precision, dimension) for N = 1..8.
 // Included by stage_<prec>_<dim>.cu with DG_T and DG_D defined.
-#include <mutex>
-#include <set>
-#include <utility>
-
 #include "dg_launch.hpp"
 #include "dg_stage_half.cuh"
 #include "dg_stage_line.cuh"
 
 namespace dgk {
-// Function attributes (dynamic shared-memory limit, carveout) belong to a device's context: a
-// kernel is configured once per (kernel, device), under a mutex, so concurrent host threads and
-// a second GPU in the same process each see a configured kernel.  Shared by every stage unit
-// (an inline function's statics are one object across translation units).
-inline cudaError_t configure_kernel(const void* fn, size_t smem, bool max_carveout) {
-  static std::mutex mu;
-  static std::set<std::pair<const void*, int>> done;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  std::lock_guard<std::mutex> lk(mu);
-  if (done.count({fn, dev})) return cudaSuccess;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess && max_carveout)
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
-  done.insert({fn, dev});
-  return cudaSuccess;
-}
-
 namespace {
 
 template <class T, int D, int N>

@@ -28,7 +28,7 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
             "dg_step_state", "dg_step_vjp", "dg_step_record", "dg_step_vjp_record", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
             "dg_bubble_theta", "dg_forest_partition", "dg_forest_halo", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
-            "dg_batch_run", "dg_batch_sync", "dg_batch_autotune", "dg_batch_last_error",
+            "dg_batch_run", "dg_batch_sync", "dg_batch_autotune", "dg_batch_shape", "dg_batch_last_error",
             "dg_probe_fma_rate", "dg_last_error", "dg_version"]
 
 
@@ -133,6 +133,7 @@ def load_library(path=None):
         "dg_batch_run": (i32, [vp, i32, i32]),
         "dg_batch_sync": (i32, [vp]),
         "dg_batch_autotune": (i32, [vp, i32, ctypes.POINTER(ctypes.c_int32)]),
+        "dg_batch_shape": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "dg_batch_last_error": (ctypes.c_char_p, [vp]),
         "dg_probe_fma_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double), vp]),
         "dg_last_error": (ctypes.c_char_p, [vp]),
@@ -607,6 +608,13 @@ class Batch:
         out = np.zeros(len(self.meshes), dtype=np.int32)
         self._check(self.lib.dg_batch_autotune(self.h, int(reps), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
         return out
+
+    def shape(self):
+        """The persistent launch's shapes (dg_batch_shape) as a dict."""
+        out = (ctypes.c_int64 * 5)()
+        self._check(self.lib.dg_batch_shape(self.h, out))
+        return {"ctas_per_sm_budget": out[0], "tiles_per_item": out[1], "grid": out[2],
+                "items_per_stage": out[3], "smem_bytes": out[4]}
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

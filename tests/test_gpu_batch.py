@@ -116,3 +116,58 @@ def test_batch_members_against_the_oracle(pkg, refine):
         want = odg.step(om, q0, dt, 3) - q0
         err = max(np.abs(got[v] - want[v]).max() / np.abs(want[v]).max() for v in range(om.nv))
         assert err <= (1e-11 if d["precision"] == "fp64" else 1e-4), (d["precision"], d["N"], err)
+
+
+def test_batch_persistent_launch_shape_and_mixed_dimensions(pkg):
+    """2D members run through the persistent launch (work items of every degree and precision
+    in one kernel); a 3D member in the same batch takes the grouped launch.  Every member still
+    matches its single-mesh run bit for bit with the chosen layout."""
+    inst = _small(8, seed=16)
+    a = _make(pkg, inst, refine=True)
+    b = _make(pkg, inst, refine=True)
+    for ms in (a, b):
+        m3 = pkg.Mesh(3, 3, (2, 2, 2), (1000.0,) * 3, max_level=1)
+        m3.adapt(flags=workloads.random_flags(m3.num_elements, 0.4, seed=17), buffer=0)
+        m3.set_bubble(center=(500.0, 500.0, 350.0), radius=(250.0,) * 3, amp=0.5)
+        ms.append(m3)
+    dts = [d["dt"] * 0.5 for d in inst] + [0.002]
+    batch = pkg.Batch(a, dts)
+    layouts = batch.autotune(reps=2)
+    shape = batch.shape()
+    assert shape["grid"] > 0 and shape["items_per_stage"] > 0
+    assert shape["ctas_per_sm_budget"] in (2, 4) and shape["tiles_per_item"] in (1, 2, 4, 8)
+    for m, layout in zip(b, layouts):
+        m.set_stage_kernel(int(layout))
+    batch.run(4, graph=True)
+    for m, dt in zip(b, dts):
+        m.step(dt, 4)
+    for ma, mb in zip(a, b):
+        x = ma.get_state()
+        assert np.all(np.isfinite(x))
+        assert np.array_equal(x, mb.get_state())
+
+
+@pytest.mark.parametrize("layout", [1, 2])
+def test_batch_every_degree_both_precisions(pkg, layout):
+    """One persistent launch over members of every degree N = 1..8 in both precisions, each with
+    hanging faces, against the same meshes stepped one launch at a time with the same layout."""
+    def make():
+        ms = []
+        for k, (N, prec) in enumerate([(N, p) for N in range(1, 9) for p in ("fp64", "fp32")]):
+            m = pkg.Mesh(2, N, (3, 2), (900.0, 600.0), max_level=1, precision=prec)
+            m.set_stage_kernel(layout)
+            m.adapt(flags=workloads.random_flags(m.num_elements, 0.5, seed=500 + k), buffer=0)
+            q = workloads.random_state(m.nv, m.num_elements, m.np_, seed=600 + k, rho_scale=1e-4,
+                                       u_scale=0.2, theta_scale=0.02,
+                                       dtype=np.float64 if prec == "fp64" else np.float32)
+            m.set_state(q)
+            ms.append(m)
+        return ms
+    a, b = make(), make()
+    batch = pkg.Batch(a, 0.002)
+    batch.run(3, graph=True)
+    for m in b:
+        m.step(0.002, 3)
+    for ma, mb in zip(a, b):
+        assert ma.num_mortars > 0
+        assert np.array_equal(ma.get_state(), mb.get_state())
