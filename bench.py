@@ -497,10 +497,22 @@ def run_vortex(pkg, t_end=3.0, dt=0.0025, regrid_every=40, thr=1e-3):
     return out
 
 
-def run_batch(pkg, steps=500, compare_steps=50):
+def _batch_member_work(m):
+    """Algorithmic HBM bytes and flops of one SSP-RK3 step of a batch member."""
+    D, N = m.dim, m.N
+    b = 8 if m.precision == "fp64" else 4
+    E, NP = m.num_elements, (N + 1) ** D
+    return stage_bytes(E, NP, D + 2, b, N + 1, D), stage_flops(E, NP, D + 2, N + 1, D)
+
+
+def run_batch(pkg, steps=500, compare_steps=50, check_steps=5, peaks=None):
     """Batched workload: 256 seeded 2D bubble instances (mesh 10x10 ... 64x32, N 3..7, FP32/FP64
-    50/50, per-instance dt), autotuned layouts, `steps` graph-replayed SSP-RK3 steps; and the same
-    instances advanced one mesh launch at a time for `compare_steps` steps."""
+    50/50, per-instance dt), autotuned shapes, `steps` graph-replayed SSP-RK3 steps (one
+    persistent launch per stage); the same instances advanced one mesh launch at a time for
+    `compare_steps` steps; bit-identity of the two after `check_steps` steps from the initial
+    state; and per (precision, N) group the time of a batch of that group's members alone,
+    against the group's roofline (its algorithmic bytes at the measured HBM copy rate or its
+    counted flops at the measured FMA rate of its precision, whichever takes longer)."""
     import torch
     cfg = workloads.BATCH_2D
     inst = workloads.batch_instances(cfg["count"])
@@ -518,35 +530,80 @@ def run_batch(pkg, steps=500, compare_steps=50):
     nodes = sum(m.num_nodes for m in meshes)
     batch = pkg.Batch(meshes, dts)
     layouts = batch.autotune(reps=3)
+    shape = batch.shape()
     batch.run(2, graph=True)                      # warm-up (graph capture)
     torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     batch.run(steps, graph=True, sync=False)
     batch.sync()
     t_batch = time.perf_counter() - t0
-    # one mesh launch at a time
+    batch.close()
+    # one mesh launch at a time, and the bit-identity check from the initial state
     singles = make()
     for m, lay in zip(singles, layouts):
         m.set_stage_kernel(int(lay))
+    fresh = make()
+    for m, lay in zip(fresh, layouts):
+        m.set_stage_kernel(int(lay))
+    fb = pkg.Batch(fresh, dts)
+    fb.run(check_steps, graph=True)
     for m, dt in zip(singles, dts):
-        m.step(dt, 1)
+        m.step(dt, check_steps)
     torch.cuda.synchronize()
+    identical = all(np.array_equal(a.get_state(), b.get_state()) for a, b in zip(fresh, singles))
+    fb.close()
     t0 = time.perf_counter()
     for _ in range(compare_steps):
         for m, dt in zip(singles, dts):
             m.step(dt, 1)
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t0
-    batch.close()
-    for m in meshes + singles:
+    # per (precision, N) group: a batch of its members alone
+    groups = {}
+    for k, d in enumerate(inst):
+        groups.setdefault((d["precision"], d["N"]), []).append(k)
+    peaks = peaks or {}
+    hbm = peaks.get("hbm_gbs", 6800.0) * 1e9
+    pipe = {"fp64": peaks.get("fp64_flops"), "fp32": peaks.get("fp32_flops")}
+    per_group, bound_s = [], 0.0
+    for (prec, N), ks in sorted(groups.items()):
+        sub = pkg.Batch([meshes[k] for k in ks], [dts[k] for k in ks])
+        sub.autotune(reps=2)
+        sub.run(2, graph=True)
+        torch.cuda.synchronize()
+        gs = 20
+        t0 = time.perf_counter()
+        sub.run(gs, graph=True, sync=False)
+        sub.sync()
+        ms = 1e3 * (time.perf_counter() - t0) / gs
+        sub.close()
+        byt = sum(_batch_member_work(meshes[k])[0] for k in ks)
+        flo = sum(_batch_member_work(meshes[k])[1] for k in ks)
+        tb = max(byt / hbm, flo / pipe[prec] if pipe[prec] else 0.0)
+        bound_s += tb
+        per_group.append({"precision": prec, "N": N, "members": len(ks),
+                          "nodes_per_variable": sum(meshes[k].num_nodes for k in ks),
+                          "ms_per_step_alone": ms, "roofline_ms": 1e3 * tb,
+                          "bound": "hbm" if byt / hbm >= (flo / pipe[prec] if pipe[prec] else 0.0) else "alu"})
+    for m in meshes + singles + fresh:
         m.close()
     rate_b = 3 * steps * nodes / t_batch
     rate_s = 3 * compare_steps * nodes / t_single
+    ms_step = 1e3 * t_batch / steps
     return {"workload": cfg["name"], "instances": len(inst), "nodes_per_variable": nodes,
-            "steps": steps, "value": rate_b, "unit": METRIC, "ms_per_step": 1e3 * t_batch / steps,
+            "steps": steps, "value": rate_b, "unit": METRIC, "ms_per_step": ms_step,
+            "launch": "one persistent launch per stage over all members (mortar and element-tile "
+                      "work items, graph-replayed)",
+            "shape": shape,
             "one_at_a_time_value": rate_s, "speedup_vs_one_at_a_time": rate_b / rate_s,
-            "layouts": {"node": int(np.sum(layouts == 1)), "column_async": int(np.sum(layouts == 2))}}
+            "bit_identical_to_one_at_a_time": bool(identical), "identity_steps": check_steps,
+            "layouts": {"node": int(np.sum(layouts == 1)), "column_async": int(np.sum(layouts == 2))},
+            "roofline": {"bound": "mixed", "roofline_ms_per_step": 1e3 * bound_s,
+                         "frac": 1e3 * bound_s / ms_step,
+                         "note": "sum over (precision, N) groups of max(algorithmic bytes / measured "
+                                 "HBM copy rate, counted flops / measured FMA rate of the precision), "
+                                 "against the batch's measured step time"},
+            "groups": per_group}
 
 
 _ORACLE = {}
@@ -788,7 +845,10 @@ def main():
     if not args.no_adjoint:
         line["adjoint"] = run_adjoint(pkg)
     if not args.no_batch:
-        line["batch"] = run_batch(pkg)
+        bpeaks = dict(peaks)
+        bpeaks["fp64_flops"] = pkg.probe_fma_rate("fp64")
+        bpeaks["fp32_flops"] = pkg.probe_fma_rate("fp32")
+        line["batch"] = run_batch(pkg, peaks=bpeaks)
     if not args.no_cold2d:
         line["cold2d"] = run_cold2d(pkg)
     if not args.no_leveque:

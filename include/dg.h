@@ -401,6 +401,44 @@ dg_status dg_forest_partition(const dg_forest* forest, int32_t nparts, int64_t* 
 dg_status dg_forest_halo(const dg_forest* forest, int32_t nparts, int32_t part, int32_t* rows,
                          size_t cap, int64_t* count);
 
+/* ---- Sharded meshes (Sec. 3.1: partitioning along the space-filling curve).  Every part keeps
+ * the whole (replicated) tree and full-size state buffers but computes only its own contiguous
+ * range of the leaf order, the SFC partition of dg_forest_partition.  Before each stage the
+ * traces of the faces it shares with other parts -- conforming faces and both sides of mortars,
+ * the rows of dg_forest_halo -- are exchanged: dg_halo_pack gathers, from a state and its P'
+ * plane, the traces other parts need, grouped by destination part in increasing order;
+ * dg_halo_unpack scatters the traces received from other parts, grouped by source part in
+ * increasing order, into the face nodes of the remote elements in the caller's state.  The
+ * transport between parts (NCCL send/recv, host copies, ...) is the caller's.  A slot is one
+ * face trace: (NV + 1) planes x (N+1)^(d-1) face nodes of the state's type, the state planes
+ * first, then P'.  Each part also computes every mortar group that touches one of its
+ * elements, from the traces it owns or received, so both sides of a hanging face see the same
+ * fluxes.  A partitioned mesh evaluates dg_rhs (owned elements of dqdt) and steps with dg_stage;
+ * dg_step, dg_adapt, dg_integrals, the adjoint and batches need the whole mesh (clear the
+ * partition with nparts = 1).  Inviscid Euler meshes only. */
+/* Restricts the mesh's stage launches to SFC part `part` of `nparts` (1 <= nparts <= elements;
+ * nparts = 1 clears the partition) and builds its halo lists. */
+dg_status dg_set_partition(dg_mesh* mesh, int32_t nparts, int32_t part);
+/* range[0] .. range[1]-1: the owned elements; send_slots[q] / recv_slots[q] (nparts entries
+ * each, may be NULL): slots sent to / received from part q; *slot_values (may be NULL): values
+ * per slot.  Unpartitioned: the whole mesh and no slots. */
+dg_status dg_get_partition(const dg_mesh* mesh, int64_t range[2], int64_t* send_slots,
+                           int64_t* recv_slots, int64_t* slot_values);
+/* Gathers the send slots of device state q (full-size layout) and its device P' plane pp (NULL:
+ * that plane is sent as zeros) into the device buffer sendbuf, asynchronously on `stream`. */
+dg_status dg_halo_pack(dg_mesh* mesh, const void* q, const void* pp, void* sendbuf, void* stream);
+/* Scatters the receive slots of device buffer recvbuf into device state q and P' plane pp (NULL:
+ * P' not written; dg_rhs recomputes P' from the state), asynchronously on `stream`. */
+dg_status dg_halo_unpack(dg_mesh* mesh, const void* recvbuf, void* q, void* pp, void* stream);
+/* Device pointers of stage buffer `index` (0 = q^n, 1 and 2 the inputs of stages 2 and 3) and
+ * of its P' plane.  Index 0 first brings the P' plane of q^n up to date (on the mesh stream). */
+dg_status dg_stage_buffer(dg_mesh* mesh, int32_t index, void** q, void** pp);
+/* Stage `stage` (0, 1, 2) of one SSP-RK3 step in Shu-Osher form on the mesh's buffers: reads
+ * stage buffer `stage` and q^n, writes the next buffer (stage 2 writes q^n and advances the
+ * time).  Three calls make one dg_step; a partitioned mesh exchanges the halo of stage buffer
+ * `stage` before each call.  Asynchronous on `stream` (NULL: the mesh stream). */
+dg_status dg_stage(dg_mesh* mesh, int32_t stage, double dt, void* stream);
+
 /* Measurement utility (the paper has no counterpart): the rate of independent fused
  * multiply-adds the current device sustains in FP64 (precision DG_FP64) or FP32
  * (DG_FP32_PERT), in FLOP/s counting 2 per multiply-add.  8 chains per thread, 8 CTAs of 256

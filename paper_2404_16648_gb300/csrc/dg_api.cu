@@ -173,6 +173,8 @@ dg_status build_tables(dg_mesh* m, const dgl::Forest& f, HostTables* t) {
 dg_status upload_tables(dg_mesh* m, HostTables&& t) {
   m->E = t.E;
   m->G = t.G;
+  m->e_begin = 0;
+  m->e_end = t.E;
   m->conf = std::move(t.conf);
   m->mort = std::move(t.mort);
   m->bnd = std::move(t.bnd);
@@ -237,7 +239,7 @@ void* pp_plane(const dg_mesh* m, void* q) {
 void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const void* qn, void* out,
                      void* pp_out, int mode, double dt, double ca, double cb, dgk::StageArgs* A) {
   A->qs = qs; A->pp_in = pp_in; A->qn = qn; A->out = out; A->pp_out = pp_out; A->mbuf = m->d_mbuf;
-  A->plane = plane(m); A->E = (int32_t)m->E;
+  A->plane = plane(m); A->E = (int32_t)m->e_end; A->e_begin = (int32_t)m->e_begin;
   A->elem = m->d_elem; A->conn = m->d_conn; A->bg = m->d_bg; A->bgt = bgt(m); A->bgc = m->d_bgc; A->ops = m->d_ops;
   for (int l = 0; l < dgk::kMaxLevels; ++l)
     for (int a = 0; a < 3; ++a) {
@@ -259,12 +261,14 @@ dg_status set_error(dg_mesh* m, dg_status st, const char* msg) {
 }
 
 void fill_mortar_args(const dg_mesh* m, const void* qs, const void* pp_in, dgk::MortarArgs* M) {
-  *M = dgk::MortarArgs{qs, pp_in, m->d_mbuf, plane(m), (int32_t)m->G, m->d_groups, m->d_bg, bgt(m),
-                       m->d_bgc, m->d_ops, (float)m->ph.gamma, m->ph};
+  const bool part = m->nparts > 1;
+  *M = dgk::MortarArgs{qs, pp_in, m->d_mbuf, plane(m), (int32_t)(part ? m->G_part : m->G), m->d_groups,
+                       m->d_bg, bgt(m), m->d_bgc, m->d_ops, (float)m->ph.gamma, m->ph,
+                       part ? m->d_glist : nullptr};
 }
 
 dg_status launch_mortars(dg_mesh* m, const void* qs, const void* pp_in, cudaStream_t s) {
-  if (m->G == 0) return DG_OK;
+  if ((m->nparts > 1 ? m->G_part : m->G) == 0) return DG_OK;
   dgk::MortarArgs M;
   fill_mortar_args(m, qs, pp_in, &M);
   bool ok = m->prec == DG_FP64
@@ -327,7 +331,8 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
   // layout 4 directly after its mortar kernel: programmatic dependent launch, so the stage
   // kernel stages its own state while the mortar kernel finishes.  A stage timed on its own
   // (dg_enable_timing) needs an event between the two launches, which rules this out.
-  const bool pdl = m->variant == 4 && m->D == 3 && (m->N % 2) == 1 && m->G > 0 && !timed;
+  const bool pdl = m->variant == 4 && m->D == 3 && (m->N % 2) == 1 &&
+                   (m->nparts > 1 ? m->G_part : m->G) > 0 && !timed;
   dg_status st = dgi::launch_mortars(m, qs, pp_in, s);
   if (st != DG_OK) return st;
   dgk::StageArgs A{};
@@ -457,6 +462,77 @@ dg_status vjp_pass(dg_mesh* m, const double* q, const double* pp, const double* 
 
 }  // namespace
 
+namespace {
+
+// The owned range, the halo slot lists and the part's mortar groups of an SFC partition of the
+// mesh's (replicated) tree into nparts parts (Sec. 3.1 names SFC partitioning).  Every part
+// derives the same lists from the same tree: part p sends, per destination part q, the traces
+// of its halo rows toward q in row order; q receives them in that order, as the faces of the
+// remote elements its own elements read.
+dg_status apply_partition(dg_mesh* m) {
+  const int P = m->nparts;
+  m->send_off.assign(P + 1, 0);
+  m->recv_off.assign(P + 1, 0);
+  if (P <= 1) {
+    m->e_begin = 0;
+    m->e_end = m->E;
+    m->G_part = m->G;
+    return DG_OK;
+  }
+  std::vector<int64_t> starts;
+  m->forest.partition(P, &starts);
+  m->e_begin = starts[m->part];
+  m->e_end = starts[m->part + 1];
+  std::vector<int32_t> rows;
+  m->forest.halo(starts, m->part, &rows);
+  std::vector<std::vector<int32_t>> to(P);
+  for (size_t r = 0; r < rows.size(); r += 5) {
+    auto& v = to[rows[r + 4]];
+    v.push_back(rows[r]); v.push_back(rows[r + 1]); v.push_back(rows[r + 2]);
+  }
+  std::vector<int32_t> send, recv;
+  for (int q = 0; q < P; ++q) {
+    m->send_off[q] = (int64_t)send.size() / 3;
+    send.insert(send.end(), to[q].begin(), to[q].end());
+  }
+  m->send_off[P] = (int64_t)send.size() / 3;
+  for (int q = 0; q < P; ++q) {
+    m->recv_off[q] = (int64_t)recv.size() / 3;
+    if (q == m->part) continue;
+    std::vector<int32_t> rq;
+    m->forest.halo(starts, q, &rq);
+    for (size_t r = 0; r < rq.size(); r += 5)
+      if (rq[r + 4] == m->part) { recv.push_back(rq[r]); recv.push_back(rq[r + 1]); recv.push_back(rq[r + 2]); }
+  }
+  m->recv_off[P] = (int64_t)recv.size() / 3;
+  std::vector<int32_t> glist;
+  const int nsub = m->NSUB;
+  for (int64_t g = 0; g < m->G; ++g) {
+    const int32_t* r = m->mort.data() + g * 7;
+    bool mine = r[0] >= m->e_begin && r[0] < m->e_end;
+    for (int k = 0; k < nsub && !mine; ++k) mine = r[3 + k] >= m->e_begin && r[3 + k] < m->e_end;
+    if (mine) glist.push_back((int32_t)g);
+  }
+  m->G_part = (int64_t)glist.size();
+  CU(reserve(m->d_send, m->c_send, send.size() * sizeof(int32_t)));
+  CU(reserve(m->d_recv, m->c_recv, recv.size() * sizeof(int32_t)));
+  CU(reserve(m->d_glist, m->c_glist, glist.size() * sizeof(int32_t)));
+  if (!send.empty()) CU(cudaMemcpy(m->d_send, send.data(), send.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (!recv.empty()) CU(cudaMemcpy(m->d_recv, recv.data(), recv.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (!glist.empty()) CU(cudaMemcpy(m->d_glist, glist.data(), glist.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+// Calls that need the whole mesh on one device refuse a partitioned mesh.
+dg_status whole_mesh_only(dg_mesh* m, const char* what) {
+  if (m->nparts > 1)
+    return fail(m, DG_ERR_UNSUPPORTED, "%s needs the whole mesh: clear the partition first "
+                "(dg_set_partition(mesh, 1, 0))", what);
+  return DG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 // Transpose of one SSP-RK3 step given its three stage inputs b0 = q, b1 = q1, b2 = q2 (each
@@ -479,6 +555,7 @@ dg_status step_transpose(dg_mesh* m, const double* b0, const double* b1, const d
 
 dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void* stream) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m && m->nparts > 1) return whole_mesh_only(m, "the adjoint");
   if (!m || !q || !lam || !out) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
@@ -495,6 +572,7 @@ dg_status dg_rhs_vjp(dg_mesh* m, const void* q, const void* lam, void* out, void
 dg_status dg_step_state(dg_mesh* m, const void* q_in, void* q_out, double dt, int32_t nsteps,
                         void* stream) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m && m->nparts > 1) return whole_mesh_only(m, "dg_step_state");
   if (!m || !q_in || !q_out || nsteps < 0 || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   dg_status st = ensure_adjoint_ws(m);
@@ -510,6 +588,7 @@ dg_status dg_step_state(dg_mesh* m, const void* q_in, void* q_out, double dt, in
 dg_status dg_step_vjp(dg_mesh* m, const void* q_in, double dt, const void* lam_out, void* lam_in,
                       void* stream) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m && m->nparts > 1) return whole_mesh_only(m, "the adjoint");
   if (!m || !q_in || !lam_out || !lam_in || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (lam_out == lam_in) return fail(m, DG_ERR_ARG, "lam_out and lam_in must not alias");
@@ -532,6 +611,7 @@ dg_status dg_step_vjp(dg_mesh* m, const void* q_in, double dt, const void* lam_o
 
 dg_status dg_step_record(dg_mesh* m, const void* q_in, void* q_out, void* record, double dt, void* stream) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m && m->nparts > 1) return whole_mesh_only(m, "dg_step_record");
   if (!m || !q_in || !q_out || !record || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
@@ -554,6 +634,7 @@ dg_status dg_step_record(dg_mesh* m, const void* q_in, void* q_out, void* record
 dg_status dg_step_vjp_record(dg_mesh* m, const void* record, double dt, const void* lam_out, void* lam_in,
                              void* stream) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m && m->nparts > 1) return whole_mesh_only(m, "the adjoint");
   if (!m || !record || !lam_out || !lam_in || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (lam_out == lam_in) return fail(m, DG_ERR_ARG, "lam_out and lam_in must not alias");
@@ -591,6 +672,7 @@ dg_status dg_set_theta(dg_mesh* m, const double* theta, int where) {
 dg_status dg_theta_vjp(dg_mesh* m, const double* theta, const void* lam_q, double* lam_theta,
                        void* stream) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m && m->nparts > 1) return whole_mesh_only(m, "the adjoint");
   if (!m || !theta || !lam_q || !lam_theta) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
@@ -602,6 +684,7 @@ dg_status dg_theta_vjp(dg_mesh* m, const double* theta, const void* lam_q, doubl
 
 dg_status dg_ke_grad(dg_mesh* m, const void* q, void* out, void* stream) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m && m->nparts > 1) return whole_mesh_only(m, "dg_ke_grad");
   if (!m || !q || !out) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
   if (m->prec != DG_FP64) return fail(m, DG_ERR_UNSUPPORTED, "the adjoint is FP64 only");
@@ -727,6 +810,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   for (int i = 0; i < 3; ++i) dfree(m->adj_q[i]);
   for (int i = 0; i < 2; ++i) dfree(m->adj_l[i]);
   dfree(m->d_abuf);
+  dfree(m->d_send); dfree(m->d_recv); dfree(m->d_glist);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   delete m;
 }
@@ -875,6 +959,9 @@ dg_status dg_rhs(dg_mesh* m, const void* q, void* dqdt, void* stream) {
 
 dg_status dg_step(dg_mesh* m, double dt, int32_t nsteps, void* stream) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m && m->nparts > 1)
+    return fail(m, DG_ERR_STATE, "a partitioned mesh steps stage by stage (dg_stage), with the halo "
+                "traces of each stage input exchanged before the stage");
   if (!m || nsteps < 0 || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
   cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
   void* p0 = pp_plane(m, m->q[0]);
@@ -933,6 +1020,7 @@ dg_status dg_primitives(dg_mesh* m, double* out, size_t cap, void* stream) {
 dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   if (!m || !p) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m->nparts > 1) return whole_mesh_only(m, "dg_adapt");
   if (p->buffer < 0) return fail(m, DG_ERR_ARG, "buffer must be >= 0");
   const int maxl = p->max_level < 0 ? m->desc.max_level : p->max_level;
   if (maxl > m->desc.max_level) return fail(m, DG_ERR_ARG, "max_level above the mesh limit");
@@ -1028,6 +1116,7 @@ static double two_sum(double a, double b, double* err) {
 // adds the two compensated results with their rounding errors.
 dg_status dg_integrals(dg_mesh* m, double out[DG_NUM_INTEGRALS]) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m && m->nparts > 1) return whole_mesh_only(m, "dg_integrals");
   if (!m || !out) return fail(m, DG_ERR_ARG, "bad argument");
   if (m->tracer) {
     double r[2] = {0.0, 0.0};
@@ -1090,6 +1179,93 @@ dg_status dg_stage_timing(dg_mesh* m, double* total_ms, int64_t* launches, int32
   *launches = (int64_t)(m->ev_used / 2);
   if (reset) m->ev_used = 0;
   return DG_OK;
+}
+
+dg_status dg_set_partition(dg_mesh* m, int32_t nparts, int32_t part) {
+  if (!m) return DG_ERR_ARG;
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (nparts < 1 || part < 0 || part >= nparts || nparts > m->E)
+    return fail(m, DG_ERR_ARG, "need 1 <= nparts <= elements and 0 <= part < nparts");
+  if (nparts > 1 && (m->tracer || m->desc.nu > 0.0))
+    return fail(m, DG_ERR_UNSUPPORTED, "partitioned meshes: inviscid Euler equations only");
+  m->nparts = nparts;
+  m->part = part;
+  dg_status st = apply_partition(m);
+  if (st != DG_OK) {
+    m->nparts = 1;
+    m->part = 0;
+    apply_partition(m);
+  }
+  return st;
+}
+
+dg_status dg_get_partition(const dg_mesh* mc, int64_t range[2], int64_t* send_slots, int64_t* recv_slots,
+                           int64_t* slot_values) {
+  dg_mesh* m = const_cast<dg_mesh*>(mc);
+  if (!m || !range) return DG_ERR_ARG;
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  range[0] = m->e_begin;
+  range[1] = m->e_end;
+  for (int q = 0; q < m->nparts; ++q) {
+    if (send_slots) send_slots[q] = m->nparts > 1 ? m->send_off[q + 1] - m->send_off[q] : 0;
+    if (recv_slots) recv_slots[q] = m->nparts > 1 ? m->recv_off[q + 1] - m->recv_off[q] : 0;
+  }
+  if (slot_values) *slot_values = (int64_t)(m->NV + 1) * m->NF;
+  return DG_OK;
+}
+
+dg_status dg_halo_pack(dg_mesh* m, const void* q, const void* pp, void* sendbuf, void* stream) {
+  if (!m || !q) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m->nparts <= 1) return DG_OK;
+  const int64_t n = m->send_off[m->nparts];
+  if (n > 0 && !sendbuf) return fail(m, DG_ERR_ARG, "send buffer missing");
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  CU(dgk::launch_halo(m->prec == DG_FP64 ? 0 : 1, 0, n, m->n1, m->D, m->NV, m->d_send, const_cast<void*>(q),
+                      const_cast<void*>(pp), plane(m), sendbuf, s));
+  return DG_OK;
+}
+
+dg_status dg_halo_unpack(dg_mesh* m, const void* recvbuf, void* q, void* pp, void* stream) {
+  if (!m || !q) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m->nparts <= 1) return DG_OK;
+  const int64_t n = m->recv_off[m->nparts];
+  if (n > 0 && !recvbuf) return fail(m, DG_ERR_ARG, "receive buffer missing");
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  CU(dgk::launch_halo(m->prec == DG_FP64 ? 0 : 1, 1, n, m->n1, m->D, m->NV, m->d_recv, q, pp, plane(m),
+                      const_cast<void*>(recvbuf), s));
+  return DG_OK;
+}
+
+dg_status dg_stage_buffer(dg_mesh* m, int32_t index, void** q, void** pp) {
+  if (!m || index < 0 || index > 2 || !q || !pp) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "not available for tracer meshes");
+  if (index == 0) {
+    dg_status st = dgi::ensure_pp(m, m->stream);
+    if (st != DG_OK) return st;
+  }
+  *q = m->q[index];
+  *pp = pp_plane(m, m->q[index]);
+  return DG_OK;
+}
+
+dg_status dg_stage(dg_mesh* m, int32_t stage, double dt, void* stream) {
+  if (!m || stage < 0 || stage > 2 || !(dt > 0.0)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m->tracer || m->desc.nu > 0.0) return fail(m, DG_ERR_UNSUPPORTED, "dg_stage: inviscid Euler equations only");
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  void* p[3] = {pp_plane(m, m->q[0]), pp_plane(m, m->q[1]), pp_plane(m, m->q[2])};
+  if (stage == 0) {
+    dg_status st = dgi::ensure_pp(m, s);
+    if (st != DG_OK) return st;
+    return launch_rhs_pass(m, m->q[0], p[0], m->q[0], m->q[1], p[1], 1, dt, 0.0, 1.0, s);
+  }
+  if (stage == 1) return launch_rhs_pass(m, m->q[1], p[1], m->q[0], m->q[2], p[2], 1, dt, 0.75, 0.25, s);
+  dg_status st = launch_rhs_pass(m, m->q[2], p[2], m->q[0], m->q[0], p[0], 1, dt, 1.0 / 3.0, 2.0 / 3.0, s);
+  if (st == DG_OK) m->time += dt;
+  return st;
 }
 
 }  // extern "C"

@@ -297,6 +297,7 @@ dg_status dg_batch_create(dg_mesh* const* meshes, int32_t count, dg_batch** out)
     dg_mesh* m = meshes[i];
     if (!m) { delete b; return DG_ERR_ARG; }
     if (m->broken) { delete b; return DG_ERR_STATE; }   // a regrid of this mesh failed after its commit
+    if (m->nparts > 1) { delete b; return DG_ERR_UNSUPPORTED; }   // a batch member is a whole mesh
     if (m->desc.nu > 0.0 || m->tracer) { delete b; return DG_ERR_UNSUPPORTED; }   // inviscid Euler only
     for (int32_t j = 0; j < i; ++j)
       if (meshes[j] == m) { delete b; return DG_ERR_ARG; }   // each mesh once

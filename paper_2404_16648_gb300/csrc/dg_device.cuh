@@ -244,6 +244,8 @@ struct StageArgs {
   // layout 4: the launch directly follows the mortar kernel of the same stage and may begin
   // before it ends (programmatic dependent launch); the kernel waits for it before reading mbuf
   int32_t after_mortar;
+  // the launch covers elements e_begin .. E - 1 (a part of an SFC partition; 0 otherwise)
+  int32_t e_begin;
 };
 
 struct MortarArgs {
@@ -259,6 +261,7 @@ struct MortarArgs {
   const void* ops;
   float gammaf;
   PhysC ph;
+  const int32_t* glist;  // the launch's mortar groups (a part of an SFC partition); null: 0 .. G-1
 };
 
 template <class T> __device__ __forceinline__ T gamma_of(const PhysC& ph, float gf) {
@@ -447,7 +450,7 @@ __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) 
 template <class T, int D, int N, int EPB>
 __global__ void __launch_bounds__(EPB * ipow(N + 1, D))
 stage_kernel(const __grid_constant__ StageArgs A) {
-  stage_body_node<T, D, N, EPB>(A, (int64_t)blockIdx.x * EPB);
+  stage_body_node<T, D, N, EPB>(A, (int64_t)A.e_begin + (int64_t)blockIdx.x * EPB);
 }
 
 // Batched form: block b works on mesh tab[map[b].x], elements from map[b].y.
@@ -493,7 +496,7 @@ mortar_kernel(const __grid_constant__ MortarArgs A) {
     sC[0][i] = ops[3 * n1 * n1 + i];
     sC[1][i] = ops[4 * n1 * n1 + i];
   }
-  const int g = blockIdx.x;
+  const int g = A.glist ? A.glist[blockIdx.x] : (int)blockIdx.x;
   const int32_t* row = A.groups + (size_t)g * 7;
   const int64_t ec = row[0];
   const int a = row[1], side = row[2];

@@ -112,6 +112,10 @@ cudaError_t launch_integrals(int prec, bool background, int32_t E, int n1, int D
                              const double* xi, const double* w, const double* root_h,
                              const double* bg, const void* q, int64_t plane, const PhysC& ph,
                              double* partial, int* bad, double* out, cudaStream_t s);
+// Halo traces of a sharded mesh (dg_halo_pack / dg_halo_unpack): slot rows {element, axis,
+// side}; pp may be null (its plane is then packed as zeros and not unpacked).
+cudaError_t launch_halo(int prec, int unpack, int64_t slots, int n1, int D, int NV, const int32_t* rows,
+                        void* q, void* pp, int64_t plane, void* buf, cudaStream_t s);
 cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, int nv, const int32_t* tmap,
                             const double* ops, const void* qold, int64_t plane_old, void* qnew,
                             int64_t plane_new, cudaStream_t s);

@@ -46,6 +46,18 @@ struct dg_mesh {
   int variant = 2;             // stage kernel layout (DG_OPT_STAGE_KERNEL); set at creation
   int fail_next_adapt = 0;     // DG_OPT_FAIL_NEXT_ADAPT: host-side failure injection for tests
   bool broken = false;         // a regrid failed after its commit: every later call is refused
+  // SFC partition (dg_set_partition): stage launches cover elements e_begin .. e_end - 1 of the
+  // replicated tree; the face traces of the other elements arrive through the halo functions.
+  // Slot lists are rows {element, axis, side}; send slots grouped by destination part, receive
+  // slots by source part (offsets per part, nparts + 1 entries each).
+  int nparts = 1, part = 0;
+  int64_t e_begin = 0, e_end = 0;
+  std::vector<int64_t> send_off, recv_off;
+  int32_t* d_send = nullptr;
+  int32_t* d_recv = nullptr;
+  int32_t* d_glist = nullptr;  // mortar groups touching the part's elements
+  size_t c_send = 0, c_recv = 0, c_glist = 0;
+  int64_t G_part = 0;
   bool tracer = false;         // DG_EQ_TRACER: one passive tracer plane, prescribed wind
   double time = 0.0;           // model time of the state (dg_set_time, advanced by dg_step)
   double stage_g = 1.0;        // tracer wind factor cos(pi t / T) of the stage being launched

@@ -624,4 +624,53 @@ cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, int nv, const
   return cudaGetLastError();
 }
 
+// ---- halo exchange of a sharded mesh: the face traces (NV state planes and the P' plane) of
+// listed element faces, packed into or unpacked from a contiguous buffer.  Slot i holds face
+// (rows[3i + 1], rows[3i + 2]) of element rows[3i] as [NV + 1][face nodes], the face nodes in
+// the order of the kernels' face_node (axis a at 0 or N, the other axes lowest first).
+__device__ __forceinline__ int halo_face_node(int n1, int D, int a, int side, int t) {
+  int idx[3] = {0, 0, 0};
+  idx[a] = side ? n1 - 1 : 0;
+  int r = t;
+  for (int b = 0; b < D; ++b)
+    if (b != a) { idx[b] = r % n1; r /= n1; }
+  return idx[0] + n1 * (idx[1] + n1 * idx[2]);
+}
+
+template <class T>
+__global__ void halo_kernel(int unpack, int64_t slots, int n1, int D, int NV, const int32_t* rows,
+                            T* q, T* pp, int64_t plane, T* buf) {
+  const int NF = D == 3 ? n1 * n1 : n1, NP = NF * n1;
+  const int64_t per = (int64_t)(NV + 1) * NF;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= slots * per) return;
+  const int64_t sl = i / per;
+  const int r = (int)(i - sl * per);
+  const int v = r / NF, t = r - v * NF;
+  const int64_t e = rows[sl * 3];
+  const int n = halo_face_node(n1, D, rows[sl * 3 + 1], rows[sl * 3 + 2], t);
+  T* dst = v < NV ? q + (size_t)v * plane + (size_t)e * NP + n : (pp ? pp + (size_t)e * NP + n : nullptr);
+  if (unpack) {
+    if (dst) *dst = buf[i];
+  } else {
+    buf[i] = dst ? *dst : (T)0;
+  }
+}
+
+cudaError_t launch_halo(int prec, int unpack, int64_t slots, int n1, int D, int NV, const int32_t* rows,
+                        void* q, void* pp, int64_t plane, void* buf, cudaStream_t s) {
+  const int NF = D == 3 ? n1 * n1 : n1;
+  const int64_t total = slots * (NV + 1) * NF;
+  if (total == 0) return cudaSuccess;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((total + threads - 1) / threads);
+  if (prec == 0)
+    halo_kernel<double><<<blocks, threads, 0, s>>>(unpack, slots, n1, D, NV, rows, (double*)q, (double*)pp,
+                                                   plane, (double*)buf);
+  else
+    halo_kernel<float><<<blocks, threads, 0, s>>>(unpack, slots, n1, D, NV, rows, (float*)q, (float*)pp,
+                                                  plane, (float*)buf);
+  return cudaGetLastError();
+}
+
 }  // namespace dgk

@@ -353,7 +353,7 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
 template <class T, int D, int N, int EPB>
 __global__ void __launch_bounds__(EPB * ipow(N + 1, D - 1))
 stage_kernel_async(const __grid_constant__ StageArgs A) {
-  stage_body_async<T, D, N, EPB>(A, (int64_t)blockIdx.x * EPB);
+  stage_body_async<T, D, N, EPB>(A, (int64_t)A.e_begin + (int64_t)blockIdx.x * EPB);
 }
 
 // Batched form: block b works on mesh tab[map[b].x], elements from map[b].y.

@@ -115,7 +115,7 @@ stage_kernel_col(const __grid_constant__ StageArgs A) {
   T* sDh = reinterpret_cast<T*>(smem_raw + sizeof(T) * (EPB * NT * NV * NP + EPB * (NV + 1) * QT + EPB * n1 * 3));
   const int tid = threadIdx.x;
   const int le = tid / NF, t = tid - le * NF;
-  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const int64_t e = (int64_t)A.e_begin + (int64_t)blockIdx.x * EPB + le;
   const bool valid = e < A.E;
   const int ci = t % n1, cj = (D == 3) ? t / n1 : 0;
   const T* ops = (const T*)A.ops;

@@ -484,7 +484,7 @@ constexpr int line_min_blocks() { return (sizeof(T) == 4 && N == 7) ? 7 : 1; }
 template <class T, int N>
 __global__ void __launch_bounds__(LineCfg<N>::THREADS, line_min_blocks<T, N>())
 stage_kernel_line(const __grid_constant__ StageArgs A) {
-  stage_body_line<T, N>(A, (int64_t)blockIdx.x);
+  stage_body_line<T, N>(A, (int64_t)A.e_begin + (int64_t)blockIdx.x);
 }
 
 }  // namespace dgk

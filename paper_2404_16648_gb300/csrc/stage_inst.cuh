@@ -12,7 +12,7 @@ void run_stage_node(const StageArgs& A, cudaStream_t s) {
   constexpr int NP = ipow(N + 1, D);
   constexpr int EPB = epb_node(D, N);
   constexpr size_t smem = node_smem_bytes<T, D, N, EPB>();
-  const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
+  const unsigned blocks = (unsigned)((A.E - A.e_begin + EPB - 1) / EPB);
   if (blocks) stage_kernel<T, D, N, EPB><<<blocks, EPB * NP, smem, s>>>(A);
 }
 
@@ -25,7 +25,7 @@ cudaError_t run_stage_col(const StageArgs& A, cudaStream_t s) {
     cudaError_t e = configure_kernel((const void*)stage_kernel_col<T, D, N, EPB>, smem, false);
     if (e != cudaSuccess) return e;
   }
-  const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
+  const unsigned blocks = (unsigned)((A.E - A.e_begin + EPB - 1) / EPB);
   if (blocks) stage_kernel_col<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
   return cudaSuccess;
 }
@@ -39,7 +39,7 @@ cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
     cudaError_t e = configure_kernel((const void*)stage_kernel_async<T, D, N, EPB>, smem, false);
     if (e != cudaSuccess) return e;
   }
-  const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
+  const unsigned blocks = (unsigned)((A.E - A.e_begin + EPB - 1) / EPB);
   if (blocks) stage_kernel_async<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
   return cudaSuccess;
 }
@@ -53,7 +53,8 @@ cudaError_t run_stage_half(const StageArgs& A, cudaStream_t s) {
       cudaError_t e = configure_kernel((const void*)stage_kernel_half<T, N>, smem, false);
       if (e != cudaSuccess) return e;
     }
-    if (A.E) stage_kernel_half<T, N><<<(unsigned)A.E, HalfCfg<N>::THREADS, smem, s>>>(A);
+    if (A.E > A.e_begin)
+      stage_kernel_half<T, N><<<(unsigned)(A.E - A.e_begin), HalfCfg<N>::THREADS, smem, s>>>(A);
     return cudaSuccess;
   } else {
     return run_stage_async<T, D, N>(A, s);
@@ -70,14 +71,14 @@ cudaError_t run_stage_line(const StageArgs& A, cudaStream_t s) {
       cudaError_t e = configure_kernel((const void*)stage_kernel_line<T, N>, smem, true);
       if (e != cudaSuccess) return e;
     }
-    if (!A.E) return cudaSuccess;
+    if (A.E <= A.e_begin) return cudaSuccess;
     if (!A.after_mortar) {
-      stage_kernel_line<T, N><<<(unsigned)A.E, LineCfg<N>::THREADS, smem, s>>>(A);
+      stage_kernel_line<T, N><<<(unsigned)(A.E - A.e_begin), LineCfg<N>::THREADS, smem, s>>>(A);
       return cudaSuccess;
     }
     // programmatic dependent launch after the mortar kernel (see stage_body_line)
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)A.E);
+    cfg.gridDim = dim3((unsigned)(A.E - A.e_begin));
     cfg.blockDim = dim3(LineCfg<N>::THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;

@@ -29,7 +29,8 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_step_state", "dg_step_vjp", "dg_step_record", "dg_step_vjp_record", "dg_set_theta", "dg_theta_vjp", "dg_ke_grad",
             "dg_bubble_theta", "dg_forest_partition", "dg_forest_halo", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
             "dg_batch_run", "dg_batch_sync", "dg_batch_autotune", "dg_batch_shape", "dg_batch_last_error",
-            "dg_probe_fma_rate", "dg_last_error", "dg_version"]
+            "dg_set_partition", "dg_get_partition", "dg_halo_pack", "dg_halo_unpack", "dg_stage_buffer",
+            "dg_stage", "dg_probe_fma_rate", "dg_last_error", "dg_version"]
 
 
 class MeshDesc(ctypes.Structure):
@@ -136,6 +137,13 @@ def load_library(path=None):
         "dg_batch_shape": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "dg_batch_last_error": (ctypes.c_char_p, [vp]),
         "dg_probe_fma_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double), vp]),
+        "dg_set_partition": (i32, [vp, i32, i32]),
+        "dg_get_partition": (i32, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "dg_halo_pack": (i32, [vp, vp, vp, vp, vp]),
+        "dg_halo_unpack": (i32, [vp, vp, vp, vp, vp]),
+        "dg_stage_buffer": (i32, [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "dg_stage": (i32, [vp, i32, dbl, vp]),
         "dg_last_error": (ctypes.c_char_p, [vp]),
         "dg_version": (ctypes.c_char_p, []),
     }
@@ -481,6 +489,38 @@ class Mesh:
         column (3D, odd N); 4: one pass per axis, two threads per node line, fluxes in registers
         (3D, odd N).  Default: 4 for FP32 3D meshes, 2 otherwise."""
         self._check(self.lib.dg_set_option(self.h, 1, int(layout)))
+
+    # ------------------------------------------------------------------ sharded meshes
+    def set_partition(self, nparts, part):
+        self._check(self.lib.dg_set_partition(self.h, int(nparts), int(part)))
+        self.nparts = int(nparts)
+
+    def partition(self):
+        """(owned range, send slots per part, receive slots per part, values per slot)."""
+        n = getattr(self, "nparts", 1)
+        rng = (ctypes.c_int64 * 2)()
+        snd = (ctypes.c_int64 * n)()
+        rcv = (ctypes.c_int64 * n)()
+        sv = ctypes.c_int64()
+        self._check(self.lib.dg_get_partition(self.h, rng, snd, rcv, ctypes.byref(sv)))
+        return (rng[0], rng[1]), list(snd), list(rcv), sv.value
+
+    def halo_pack(self, q, pp, sendbuf, stream=None):
+        self._check(self.lib.dg_halo_pack(self.h, ctypes.c_void_p(q), ctypes.c_void_p(pp) if pp else None,
+                                          ctypes.c_void_p(sendbuf.data_ptr()), self._stream_ptr(stream)))
+
+    def halo_unpack(self, recvbuf, q, pp, stream=None):
+        self._check(self.lib.dg_halo_unpack(self.h, ctypes.c_void_p(recvbuf.data_ptr()), ctypes.c_void_p(q),
+                                            ctypes.c_void_p(pp) if pp else None, self._stream_ptr(stream)))
+
+    def stage_buffer(self, index):
+        """Device addresses (q, P') of stage buffer `index` (0 = q^n)."""
+        q, pp = ctypes.c_void_p(), ctypes.c_void_p()
+        self._check(self.lib.dg_stage_buffer(self.h, int(index), ctypes.byref(q), ctypes.byref(pp)))
+        return q.value, pp.value
+
+    def stage(self, stage, dt, stream=None):
+        self._check(self.lib.dg_stage(self.h, int(stage), float(dt), self._stream_ptr(stream)))
 
     def fail_next_adapt(self, where):
         """Host-side failure injection for the next adapt (DG_OPT_FAIL_NEXT_ADAPT): 1 fails
