@@ -439,6 +439,30 @@ dg_status dg_stage_buffer(dg_mesh* mesh, int32_t index, void** q, void** pp);
  * `stage` before each call.  Asynchronous on `stream` (NULL: the mesh stream). */
 dg_status dg_stage(dg_mesh* mesh, int32_t stage, double dt, void* stream);
 
+/* ---- Cubed-sphere solution transfer (Sec. 3.4 "Considerations for spherical geometry",
+ * App. B).  The sphere of radius r is six equiangular gnomonic tiles laid side by side in one
+ * 2D forest of 6n x n roots (tile t = root column / n; dg_forest_* give the leaves and the
+ * regrid map); every element is an isoparametric quadrilateral of degree N.  The layout's 2:1
+ * closure acts across its seams, not the sphere's edges; the transfer needs no neighbours.  All
+ * arrays are device memory and FP64; fields are [nv][E][(N+1)^2] as the mesh states. */
+/* Per element: nodal weights W[e][n] = w_i w_j J, J = |x_xi x x_eta| of the degree-N
+ * interpolated surface (the tangent vectors by the collocation derivative), and area[e], the
+ * spherical excess r^2 (A + B + C - pi) of the two spherical triangles of the element's corners.
+ * leaves: [E][5] rows of dg_forest_leaves (device copy).  Asynchronous on `stream`. */
+dg_status dg_sphere_geometry(int32_t N, int32_t n, double radius, const int32_t* leaves, int64_t E,
+                             double* W, double* area, void* stream);
+/* Fields q_old (E_old elements) to q_new (E_new) after a regrid whose map `tmap` (host, [E_new][9]
+ * rows of dg_forest_regrid) leads from the old to the new leaves: kept elements are copied; the
+ * four children of a refined parent take the reference interpolation and then, per field, one
+ * factor uniform over the four that makes sum W q equal the parent's; a coarsened parent takes
+ * the reference restriction of its children weighted by their areas (4 V_c / sum V) and the same
+ * integral-matching factor (applied when |I_new| > 1e-8 sum W |q|, else 1).  W and area from
+ * dg_sphere_geometry of the old and new leaves.  1 <= nv <= 8.  DG_ERR_ARG for a map row out of
+ * range or a family whose four children are not consecutive.  Synchronous. */
+dg_status dg_sphere_transfer(int32_t N, int32_t n, int32_t nv, const int32_t* tmap, int64_t E_new,
+                             const double* W_old, const double* area_old, const double* q_old,
+                             int64_t E_old, const double* W_new, double* q_new, void* stream);
+
 /* Measurement utility (the paper has no counterpart): the rate of independent fused
  * multiply-adds the current device sustains in FP64 (precision DG_FP64) or FP32
  * (DG_FP32_PERT), in FLOP/s counting 2 per multiply-add.  8 chains per thread, 8 CTAs of 256

@@ -30,7 +30,8 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_bubble_theta", "dg_forest_partition", "dg_forest_halo", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
             "dg_batch_run", "dg_batch_sync", "dg_batch_autotune", "dg_batch_shape", "dg_batch_last_error",
             "dg_set_partition", "dg_get_partition", "dg_halo_pack", "dg_halo_unpack", "dg_stage_buffer",
-            "dg_stage", "dg_probe_fma_rate", "dg_last_error", "dg_version"]
+            "dg_stage", "dg_sphere_geometry", "dg_sphere_transfer", "dg_probe_fma_rate", "dg_last_error",
+            "dg_version"]
 
 
 class MeshDesc(ctypes.Structure):
@@ -137,6 +138,9 @@ def load_library(path=None):
         "dg_batch_shape": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "dg_batch_last_error": (ctypes.c_char_p, [vp]),
         "dg_probe_fma_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double), vp]),
+        "dg_sphere_geometry": (i32, [i32, i32, dbl, vp, i64, vp, vp, vp]),
+        "dg_sphere_transfer": (i32, [i32, i32, i32, ctypes.POINTER(ctypes.c_int32), i64, vp, vp, vp, i64, vp,
+                                     vp, vp]),
         "dg_set_partition": (i32, [vp, i32, i32]),
         "dg_get_partition": (i32, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
@@ -612,6 +616,41 @@ class Forest:
             self.close()
         except Exception:
             pass
+
+
+def sphere_geometry(N, n, radius, leaves):
+    """(W [E, (N+1)^2], area [E]) device tensors of the cubed-sphere elements whose leaf rows
+    (Forest.leaves of a 6n x n forest) are given (dg_sphere_geometry)."""
+    torch = _torch()
+    lib = load_library()
+    lv = torch.from_numpy(np.ascontiguousarray(leaves, dtype=np.int32)).cuda()
+    E = lv.shape[0]
+    W = torch.empty((E, (N + 1) ** 2), dtype=torch.float64, device="cuda")
+    area = torch.empty(E, dtype=torch.float64, device="cuda")
+    st = lib.dg_sphere_geometry(int(N), int(n), float(radius), ctypes.c_void_p(lv.data_ptr()), E,
+                                ctypes.c_void_p(W.data_ptr()), ctypes.c_void_p(area.data_ptr()), None)
+    if st != DG_OK:
+        raise DGError(st, "dg_sphere_geometry failed")
+    torch.cuda.synchronize()
+    return W, area
+
+
+def sphere_transfer(N, n, q_old, tmap, W_old, area_old, W_new):
+    """Cubed-sphere transfer of the device fields q_old [nv, E_old, (N+1)^2] along the regrid map
+    tmap (rows of Forest.regrid) into a new device tensor (dg_sphere_transfer)."""
+    torch = _torch()
+    lib = load_library()
+    tm = np.ascontiguousarray(tmap, dtype=np.int32)
+    nv, E_old = q_old.shape[0], q_old.shape[1]
+    E_new = tm.shape[0]
+    q_new = torch.empty((nv, E_new, q_old.shape[2]), dtype=torch.float64, device="cuda")
+    st = lib.dg_sphere_transfer(int(N), int(n), int(nv), tm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), E_new,
+                                ctypes.c_void_p(W_old.data_ptr()), ctypes.c_void_p(area_old.data_ptr()),
+                                ctypes.c_void_p(q_old.data_ptr()), E_old, ctypes.c_void_p(W_new.data_ptr()),
+                                ctypes.c_void_p(q_new.data_ptr()), None)
+    if st != DG_OK:
+        raise DGError(st, "dg_sphere_transfer failed")
+    return q_new
 
 
 class Batch:
