@@ -153,6 +153,19 @@ dg_status dg_get_faces(const dg_mesh* mesh, int64_t counts[3], int32_t* conformi
 /* Copies a state in (out) in the layout above; where = DG_HOST or DG_DEVICE.  Synchronous. */
 dg_status dg_set_state(dg_mesh* mesh, const void* q, int where);
 dg_status dg_get_state(dg_mesh* mesh, void* q, int where);
+/* Asynchronous forms for pipelines that must not wait on the host.  dg_set_state_async and
+ * dg_get_state_async copy the state in or out on `stream` (NULL: the mesh stream) after the work
+ * already queued on the mesh stream, with no host wait; host buffers should be pinned, must stay
+ * untouched until the copy is done (synchronise the stream), and later mesh work must be ordered
+ * after a copy on another stream by the caller.  dg_integrals_async computes the integrals of
+ * dg_integrals on `stream` and writes 6 doubles to `out` (host pinned or device memory): mass,
+ * total energy, kinetic energy, volume, perturbation mass, and 1.0 if a non-finite value was seen
+ * in the state (0.0 otherwise); the values are those dg_integrals returns, bit for bit.  The first
+ * call after a regrid first takes the background sums synchronously.  Integrals on one mesh share
+ * one scratch buffer: calls that overlap on the GPU race.  Euler meshes, unpartitioned. */
+dg_status dg_set_state_async(dg_mesh* mesh, const void* q, int where, void* stream);
+dg_status dg_get_state_async(dg_mesh* mesh, void* q, int where, void* stream);
+dg_status dg_integrals_async(dg_mesh* mesh, double* out, void* stream);
 
 /* Copies the pressure perturbation P' = P(Theta_bar + Theta') - P(Theta_bar) of the current state
  * (Sec. 2.1, perturbation form; one plane of E (N+1)^dim values in the state precision) into
@@ -470,6 +483,11 @@ dg_status dg_sphere_transfer(int32_t N, int32_t n, int32_t nv, const int32_t* tm
  * warm-up launch; synchronous; allocates and frees a small device buffer.  It is the measured
  * peak against which the FP64 stage kernel's pipe-bound roofline is reported. */
 dg_status dg_probe_fma_rate(int32_t precision, double* flop_per_s, void* stream);
+
+/* Check utility: the FP64 reciprocal and square root the flux kernels use, applied to the n
+ * device values x (positive, normal) into the device arrays rcp and sqrt_out, asynchronously on
+ * `stream`.  Each is within about one ulp of the exact value. */
+dg_status dg_probe_recip_sqrt(int64_t n, const double* x, double* rcp, double* sqrt_out, void* stream);
 
 /* Detail of the last error on this mesh (never NULL). */
 const char* dg_last_error(const dg_mesh* mesh);

@@ -785,6 +785,7 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   if (st == DG_OK) {
     if (cudaMalloc(&m->d_partial, dgk::integrals_scratch_doubles() * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&m->d_out, 8 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&m->d_bgint, 12 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&m->d_bad, sizeof(int)) != cudaSuccess)
       st = fail(m, DG_ERR_OOM, "scratch allocation failed");
   }
@@ -806,12 +807,13 @@ void dg_mesh_destroy(dg_mesh* m) {
   dfree(m->d_elem); dfree(m->d_conn); dfree(m->d_groups); dfree(m->d_bg); dfree(m->d_mbuf);
   dfree(m->d_bgf); dfree(m->d_bgc); dfree(m->d_ppscratch);
   dfree(m->d_sigma); dfree(m->d_V); dfree(m->d_vbuf);
-  dfree(m->d_ops); dfree(m->d_opsd); dfree(m->d_partial); dfree(m->d_out); dfree(m->d_bad);
+  dfree(m->d_ops); dfree(m->d_opsd); dfree(m->d_partial); dfree(m->d_out); dfree(m->d_bad); dfree(m->d_bgint);
   for (int i = 0; i < 3; ++i) dfree(m->adj_q[i]);
   for (int i = 0; i < 2; ++i) dfree(m->adj_l[i]);
   dfree(m->d_abuf);
   dfree(m->d_send); dfree(m->d_recv); dfree(m->d_glist);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
+  if (m->ev_order) cudaEventDestroy(m->ev_order);
   delete m;
 }
 
@@ -1135,6 +1137,7 @@ dg_status dg_integrals(dg_mesh* m, double out[DG_NUM_INTEGRALS]) {
     CU(dgk::launch_integrals(m->prec, true, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), d_w(m), m->root_h,
                              m->d_bg, nullptr, plane(m), m->ph, m->d_partial, m->d_bad, m->d_out, m->stream));
     CU(cudaMemcpyAsync(m->bgint, m->d_out, 6 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaMemcpyAsync(m->d_bgint, m->d_out, 6 * sizeof(double), cudaMemcpyDeviceToDevice, m->stream));
     CU(cudaStreamSynchronize(m->stream));
     m->bgint_valid = true;
   }
@@ -1266,6 +1269,59 @@ dg_status dg_stage(dg_mesh* m, int32_t stage, double dt, void* stream) {
   dg_status st = launch_rhs_pass(m, m->q[2], p[2], m->q[0], m->q[0], p[0], 1, dt, 1.0 / 3.0, 2.0 / 3.0, s);
   if (st == DG_OK) m->time += dt;
   return st;
+}
+
+// Work already queued on the mesh stream comes before later work on stream s.
+static dg_status order_after_mesh(dg_mesh* m, cudaStream_t s) {
+  if (s == m->stream) return DG_OK;
+  if (!m->ev_order) CU(cudaEventCreateWithFlags(&m->ev_order, cudaEventDisableTiming));
+  CU(cudaEventRecord(m->ev_order, m->stream));
+  CU(cudaStreamWaitEvent(s, m->ev_order, 0));
+  return DG_OK;
+}
+
+dg_status dg_set_state_async(dg_mesh* m, const void* q, int where, void* stream) {
+  if (!m || !q || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  dg_status st = order_after_mesh(m, s);
+  if (st != DG_OK) return st;
+  m->pp_valid = false;
+  CU(cudaMemcpyAsync(m->q[0], q, (size_t)m->NV * plane(m) * m->tsize,
+                     where == DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  return DG_OK;
+}
+
+dg_status dg_get_state_async(dg_mesh* m, void* q, int where, void* stream) {
+  if (!m || !q || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  dg_status st = order_after_mesh(m, s);
+  if (st != DG_OK) return st;
+  CU(cudaMemcpyAsync(q, m->q[0], (size_t)m->NV * plane(m) * m->tsize,
+                     where == DG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  return DG_OK;
+}
+
+dg_status dg_integrals_async(dg_mesh* m, double* out, void* stream) {
+  if (!m || !out) return fail(m, DG_ERR_ARG, "bad argument");
+  if (m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
+  if (m->nparts > 1) return whole_mesh_only(m, "dg_integrals_async");
+  if (m->tracer) return fail(m, DG_ERR_UNSUPPORTED, "tracer meshes: use dg_integrals");
+  if (!m->bgint_valid) {   // the background sums, once per topology (synchronous)
+    double tmp[DG_NUM_INTEGRALS];
+    dg_status st = dg_integrals(m, tmp);
+    if (st != DG_OK && st != DG_ERR_STATE) return st;
+  }
+  cudaStream_t s = stream ? (cudaStream_t)stream : m->stream;
+  dg_status st = order_after_mesh(m, s);
+  if (st != DG_OK) return st;
+  CU(cudaMemsetAsync(m->d_bad, 0, sizeof(int), s));
+  CU(dgk::launch_integrals(m->prec, false, (int32_t)m->E, m->n1, m->D, m->d_elem, d_x(m), d_w(m), m->root_h,
+                           m->d_bg, m->q[0], plane(m), m->ph, m->d_partial, m->d_bad, m->d_out, s));
+  CU(dgk::launch_integrals_combine(m->d_out, m->d_bgint, m->d_bad, m->d_bgint + 6, s));
+  CU(cudaMemcpyAsync(out, m->d_bgint + 6, 6 * sizeof(double), cudaMemcpyDefault, s));
+  return DG_OK;
 }
 
 }  // extern "C"

@@ -148,15 +148,40 @@ struct NodeBg {
 
 // Reciprocal and square root used by the fluxes.  Deterministic (the same inputs give the same
 // bits wherever they are evaluated), so the two elements of a face agree bit for bit.  FP64:
-// correctly rounded.  FP32: the hardware approximations (about 1 ulp; rho is never subnormal),
-// far below the FP32 path's stated error bound.
-__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+// Newton-Raphson from the hardware approximation, within about one ulp (not always correctly
+// rounded: the 1e-12 FP64 parity bound is far above that, and the FP64 pipe, which bounds the
+// FP64 kernels, does less work than for the correctly rounded forms).  FP32: the hardware
+// approximations (about 1 ulp; rho is never subnormal), far below the FP32 path's stated error
+// bound.
+//
+// 1/x: Newton's iteration for f(r) = 1/r - x, r <- r + r (1 - x r), the residual by one fma.
+// Each step squares the relative error of r, so two steps from the hardware seed (relative error
+// below 2^-20) reach the rounding of the last one.
+__device__ __forceinline__ double recip(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
 __device__ __forceinline__ float recip(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ double sqrt_fast(double x) { return __dsqrt_rn(x); }
+// sqrt(a) for a > 0: Newton's iteration for the inverse square root, y <- y (3/2 - (a/2) y^2),
+// twice from the hardware seed, then s = a y corrected once by Newton's step for s^2 = a,
+// s <- s + (y/2) (a - s^2), the residual by one fma.
+__device__ __forceinline__ double sqrt_fast(double a) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
+  const double h = 0.5 * a;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  const double s = a * y;
+  return fma(0.5 * y, fma(-s, s, a), s);
+}
 __device__ __forceinline__ float sqrt_fast(float x) { return __fmul_rn(x, rsqrtf(x)); }
 
 // Quantities of one node's state that every flux component needs, computed once.

@@ -116,6 +116,9 @@ cudaError_t launch_integrals(int prec, bool background, int32_t E, int n1, int D
 // side}; pp may be null (its plane is then packed as zeros and not unpacked).
 cudaError_t launch_halo(int prec, int unpack, int64_t slots, int n1, int D, int NV, const int32_t* rows,
                         void* q, void* pp, int64_t plane, void* buf, cudaStream_t s);
+// res[0..5] = {mass, energy, kinetic energy, volume, perturbation mass, non-finite flag} from the
+// state sums S[6] and background sums B[6] (the combination of dg_integrals, on the device).
+cudaError_t launch_integrals_combine(const double* S, const double* B, const int* bad, double* res, cudaStream_t s);
 cudaError_t launch_transfer(int prec, int32_t Enew, int n1, int D, int nv, const int32_t* tmap,
                             const double* ops, const void* qold, int64_t plane_old, void* qnew,
                             int64_t plane_new, cudaStream_t s);

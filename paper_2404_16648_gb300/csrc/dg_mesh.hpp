@@ -75,12 +75,14 @@ struct dg_mesh {
   double* d_partial = nullptr;
   double* d_out = nullptr;
   double bgint[6] = {0, 0, 0, 0, 0, 0};   // background sums of the integrals (see dg_integrals)
+  double* d_bgint = nullptr;   // the same on the device, and the combined results (12 doubles)
   bool bgint_valid = false;
   int* d_bad = nullptr;
   // timing
   bool timing = false;
   std::vector<cudaEvent_t> ev;
   size_t ev_used = 0;
+  cudaEvent_t ev_order = nullptr;   // orders a caller's stream after the mesh stream
   std::string err;
 };
 

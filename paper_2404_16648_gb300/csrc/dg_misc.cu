@@ -406,6 +406,31 @@ __global__ void __launch_bounds__(kIntThreads) integrals_final(int nblocks, cons
   }
 }
 
+// The integrals' last step on the device (dg_integrals_async): the state sums S (three sums and
+// their rounding errors) added to the background sums B with their rounding errors (TwoSum,
+// explicitly rounded, so the bits are those of the host combination in dg_integrals):
+//   res = {mass, total energy, kinetic energy, volume, perturbation mass, non-finite flag}.
+__device__ __forceinline__ double two_sum_rn(double a, double b, double* err) {
+  const double t = __dadd_rn(a, b);
+  const double bb = __dsub_rn(t, a);
+  *err = __dadd_rn(__dsub_rn(a, __dsub_rn(t, bb)), __dsub_rn(b, bb));
+  return t;
+}
+
+__global__ void integrals_combine(const double* S, const double* B, const int* bad, double* res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double e0, e1;
+  const double t0 = two_sum_rn(B[0], S[0], &e0);
+  const double t1 = two_sum_rn(B[1], S[1], &e1);
+  res[0] = __dadd_rn(t0, __dadd_rn(e0, __dadd_rn(B[3], S[3])));
+  res[1] = __dadd_rn(t1, __dadd_rn(e1, __dadd_rn(B[4], S[4])));
+  res[2] = S[2];
+  res[3] = B[2];
+  res[4] = S[0];
+  res[5] = *bad ? 1.0 : 0.0;
+}
+
+
 // Conservative transfer after a regrid (Sec. 3.3), one CTA per new element, FP64 arithmetic:
 //   keep:   copy;
 //   child:  (P_{c_2} x P_{c_1} x P_{c_0}) parent, P_c the half-interval interpolation;
@@ -586,6 +611,11 @@ cudaError_t launch_primitives(int prec, int32_t E, int n1, int D, const double* 
 }
 
 size_t integrals_scratch_doubles() { return (size_t)kIntBlocks * 3 * 2; }
+
+cudaError_t launch_integrals_combine(const double* S, const double* B, const int* bad, double* res, cudaStream_t s) {
+  integrals_combine<<<1, 32, 0, s>>>(S, B, bad, res);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_integrals(int prec, bool background, int32_t E, int n1, int D, const int32_t* elem,
                              const double* xi, const double* w, const double* root_h,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/dg.h"
+#include "dg_device.cuh"
 
 namespace {
 
@@ -50,7 +51,22 @@ cudaError_t time_probe(int blocks, int iters, cudaStream_t s, float* ms) {
   return e;
 }
 
+__global__ void recip_sqrt_probe_kernel(int64_t n, const double* x, double* r, double* s) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  r[i] = dgk::recip(x[i]);
+  s[i] = dgk::sqrt_fast(x[i]);
+}
+
 }  // namespace
+
+extern "C" dg_status dg_probe_recip_sqrt(int64_t n, const double* x, double* rcp, double* sqrt_out,
+                                         void* stream) {
+  if (n < 0 || (n > 0 && (!x || !rcp || !sqrt_out))) return DG_ERR_ARG;
+  if (n == 0) return DG_OK;
+  recip_sqrt_probe_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, x, rcp, sqrt_out);
+  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+}
 
 extern "C" dg_status dg_probe_fma_rate(int32_t precision, double* flop_per_s, void* stream) {
   if (!flop_per_s || (precision != DG_FP64 && precision != DG_FP32_PERT)) return DG_ERR_ARG;

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 
 
 # every symbol include/dg.h declares
 EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_nodes", "dg_get_leaves",
-            "dg_get_faces", "dg_set_state", "dg_get_state", "dg_get_pprime", "dg_set_vortex", "dg_set_bubble", "dg_rhs", "dg_step",
+            "dg_get_faces", "dg_set_state", "dg_get_state", "dg_set_state_async", "dg_get_state_async",
+            "dg_integrals_async", "dg_get_pprime", "dg_set_vortex", "dg_set_bubble", "dg_rhs", "dg_step",
             "dg_adapt", "dg_indicator", "dg_primitives", "dg_integrals", "dg_set_time", "dg_get_time", "dg_set_option", "dg_enable_timing", "dg_stage_timing",
             "dg_forest_create_periodic", "dg_forest_create", "dg_forest_destroy", "dg_forest_size", "dg_forest_leaves",
             "dg_forest_faces", "dg_forest_regrid", "dg_integrals_noalloc", "dg_rhs_vjp",
@@ -30,7 +31,7 @@ EXPORTED = ["dg_mesh_create", "dg_mesh_destroy", "dg_num_elements", "dg_num_node
             "dg_bubble_theta", "dg_forest_partition", "dg_forest_halo", "dg_batch_create", "dg_batch_destroy", "dg_batch_set_dt",
             "dg_batch_run", "dg_batch_sync", "dg_batch_autotune", "dg_batch_shape", "dg_batch_last_error",
             "dg_set_partition", "dg_get_partition", "dg_halo_pack", "dg_halo_unpack", "dg_stage_buffer",
-            "dg_stage", "dg_sphere_geometry", "dg_sphere_transfer", "dg_probe_fma_rate", "dg_last_error",
+            "dg_stage", "dg_sphere_geometry", "dg_sphere_transfer", "dg_probe_recip_sqrt", "dg_probe_fma_rate", "dg_last_error",
             "dg_version"]
 
 
@@ -94,6 +95,9 @@ def load_library(path=None):
         "dg_get_faces": (i32, [vp, ctypes.POINTER(ctypes.c_int64), vp, sz, vp, sz, vp, sz]),
         "dg_set_state": (i32, [vp, vp, ctypes.c_int]),
         "dg_get_state": (i32, [vp, vp, ctypes.c_int]),
+        "dg_set_state_async": (i32, [vp, vp, ctypes.c_int, vp]),
+        "dg_get_state_async": (i32, [vp, vp, ctypes.c_int, vp]),
+        "dg_integrals_async": (i32, [vp, vp, vp]),
         "dg_get_pprime": (i32, [vp, vp, ctypes.c_int]),
         "dg_set_bubble": (i32, [vp, ctypes.POINTER(BubbleDesc)]),
         "dg_set_vortex": (i32, [vp, ctypes.POINTER(VortexDesc)]),
@@ -138,6 +142,7 @@ def load_library(path=None):
         "dg_batch_shape": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "dg_batch_last_error": (ctypes.c_char_p, [vp]),
         "dg_probe_fma_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double), vp]),
+        "dg_probe_recip_sqrt": (i32, [i64, vp, vp, vp, vp]),
         "dg_sphere_geometry": (i32, [i32, i32, dbl, vp, i64, vp, vp, vp]),
         "dg_sphere_transfer": (i32, [i32, i32, i32, ctypes.POINTER(ctypes.c_int32), i64, vp, vp, vp, i64, vp,
                                      vp, vp]),
@@ -300,6 +305,25 @@ class Mesh:
             out = np.empty(self.state_shape, dtype=self.np_dtype)
         p, where = _ptr(out)
         self._check(self.lib.dg_get_state(self.h, ctypes.c_void_p(p), where))
+        return out
+
+    def set_state_async(self, q, stream=None):
+        """Copy in on `stream` without a host wait (q: contiguous tensor; host tensors pinned)."""
+        if tuple(q.shape) != self.state_shape:
+            raise ValueError("state shape %s != %s" % (tuple(q.shape), self.state_shape))
+        p, where = _ptr(q)
+        self._check(self.lib.dg_set_state_async(self.h, ctypes.c_void_p(p), where, self._stream_ptr(stream)))
+
+    def get_state_async(self, out, stream=None):
+        """Copy out on `stream` after the mesh stream's queued work, without a host wait."""
+        p, where = _ptr(out)
+        self._check(self.lib.dg_get_state_async(self.h, ctypes.c_void_p(p), where, self._stream_ptr(stream)))
+        return out
+
+    def integrals_async(self, out, stream=None):
+        """The integrals into `out` (6 float64: 5 integrals and a non-finite flag; a pinned host
+        or a device tensor), without a host wait."""
+        self._check(self.lib.dg_integrals_async(self.h, ctypes.c_void_p(out.data_ptr()), self._stream_ptr(stream)))
         return out
 
     def pprime(self, out=None):
