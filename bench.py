@@ -616,11 +616,11 @@ def run_batch(pkg, steps=500, compare_steps=50, check_steps=5, peaks=None):
 _ORACLE = {}
 
 
-def _oracle_setup(cfg_name):
+def _oracle_setup(cfg):
     """The oracle mesh of a workload and its initial state (built once per process)."""
     from oracle import dg as odg, forest as ofo
+    cfg_name = cfg["name"]
     if cfg_name not in _ORACLE:
-        cfg = workloads.CONFIGS[cfg_name]
         b = cfg["bubble"]
         om = odg.adapt_initial(ofo.Forest(cfg["base"], cfg["max_level"]), cfg["N"], cfg["length"],
                                lambda mm: odg.bubble_theta(mm, b["center"], b["radius"], b["amp"]),
@@ -633,12 +633,12 @@ def _oracle_setup(cfg_name):
 def _oracle_block_step(args):
     """One SSP-RK3 step of the oracle (mortars included) for a block of consecutive elements;
     its stages are evaluated on the block's two- and one-hop neighbourhoods as the step needs."""
-    cfg_name, start, n = args
+    cfg, start, n = args
     from oracle import dg as odg
-    om, q = _oracle_setup(cfg_name)
+    om, q = _oracle_setup(cfg)
     elems = np.arange(start, min(om.E, start + n))
     t0 = time.perf_counter()
-    odg.step_on(om, q, workloads.CONFIGS[cfg_name]["dt"], elems)
+    odg.step_on(om, q, cfg["dt"], elems)
     sec = time.perf_counter() - t0
     # node-stage updates the oracle performed: stage 1 on the two-hop neighbourhood, stage 2 on
     # the one-hop neighbourhood, stage 3 on the block
@@ -673,11 +673,11 @@ class OraclePool:
     def __init__(self, cfg, procs, block):
         import multiprocessing as mp
         self.cfg, self.procs, self.block = cfg, procs, block
-        self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_setup, initargs=(cfg["name"],))
-        om, _ = _oracle_setup(cfg["name"])   # for the sizes (and the single-core leg)
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_oracle_setup, initargs=(cfg,))
+        om, _ = _oracle_setup(cfg)   # for the sizes (and the single-core leg)
         self.E, self.NP = om.E, om.np_
         first = max(0, om.E // 2 - procs * block // 2)
-        self.tasks = [(cfg["name"], first + k * block, block) for k in range(procs)]
+        self.tasks = [(cfg, first + k * block, block) for k in range(procs)]
         self.pool.map(_oracle_block_step, self.tasks, chunksize=1)   # warm-up: every worker ready
 
     def step(self):
@@ -724,6 +724,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--base-div", type=int, default=1,
+                    help="divide the workload's root grid by this factor (a smaller copy of the same "
+                         "workload, for profiler captures; the default is the full workload)")
     ap.add_argument("--repeats", type=int, default=5,
                     help="timed repeats of --steps steps each; the median is reported (at least 5)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -750,6 +753,8 @@ def main():
     global STAGE_KERNEL
     STAGE_KERNEL = args.stage_kernel
     cfg = workloads.CONFIGS[args.config]
+    if args.base_div > 1:
+        cfg = workloads.scaled(cfg, base_div=args.base_div)
     world, rank, local = _dist()
     regrid_every = cfg.get("regrid_every")
     config = {"workload": cfg["name"], "dim": cfg["dim"], "N": cfg["N"], "base": list(cfg["base"]),
