@@ -230,7 +230,7 @@ __device__ __forceinline__ void rusanov(const T* qm, const T* Fm, T sm, const T*
   const T hl = mul_rn((T)0.5, sm > sp ? sm : sp);
 #pragma unroll
   for (int v = 0; v < NV; ++v)
-    Fs[v] = sub_rn(mul_rn((T)0.5, add_rn(Fm[v], Fp[v])), mul_rn(hl, sub_rn(qp[v], qm[v])));
+    Fs[v] = fma(-hl, sub_rn(qp[v], qm[v]), mul_rn((T)0.5, add_rn(Fm[v], Fp[v])));
 }
 
 // Flux and wave speed of a face state in one call.

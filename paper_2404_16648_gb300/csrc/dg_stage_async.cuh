@@ -165,15 +165,41 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
 #pragma unroll
     for (int v = 0; v < NV; ++v) Fz[v][k] = F[v];
   }
+  if constexpr (n1 % 2 == 0) {
+    // the whole vertical line is this thread's: the even/odd split of the antisymmetric
+    // derivative, 2 K2^2 multiply-adds and 2 n1 adds per line instead of n1^2 multiply-adds
+    constexpr int K2 = n1 / 2;
 #pragma unroll
-  for (int v = 0; v < NV; ++v)
+    for (int v = 0; v < NV; ++v) {
+      T Ev[K2], Ov[K2];
 #pragma unroll
-    for (int k = 0; k < n1; ++k) {
-      T s = (T)0;
+      for (int m = 0; m < K2; ++m) {
+        Ev[m] = add_rn(Fz[v][m], Fz[v][N - m]);
+        Ov[m] = sub_rn(Fz[v][m], Fz[v][N - m]);
+      }
 #pragma unroll
-      for (int m = 0; m < n1; ++m) s = fma(dtab<T>(dtab_offset(N) + k * n1 + m), Fz[v][m], s);
-      acc[v][k] = fma(-inv2h[D - 1], s, acc[v][k]);
+      for (int i = 0; i < K2; ++i) {
+        T se = (T)0, so = (T)0;
+#pragma unroll
+        for (int m = 0; m < K2; ++m) {
+          se = fma(dtab_eo<T>(dtab_offset(N) + i * K2 + m), Ev[m], se);
+          so = fma(dtab_eo<T>(dtab_offset(N) + K2 * K2 + i * K2 + m), Ov[m], so);
+        }
+        acc[v][i] = fma(-inv2h[D - 1], add_rn(se, so), acc[v][i]);
+        acc[v][N - i] = fma(-inv2h[D - 1], sub_rn(so, se), acc[v][N - i]);
+      }
     }
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int k = 0; k < n1; ++k) {
+        T s = (T)0;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) s = fma(dtab<T>(dtab_offset(N) + k * n1 + m), Fz[v][m], s);
+        acc[v][k] = fma(-inv2h[D - 1], s, acc[v][k]);
+      }
+  }
   __syncthreads();
   auto line_dot = [&](const T* row, const T* Dr) {
     T s = (T)0;
@@ -278,9 +304,9 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
 #pragma unroll
       for (int v = 0; v < NV; ++v) Fs[v] = nb[v * NF + fn];
     }
-    const T coef = s ? -lift_of<T>(A, level, a) : lift_of<T>(A, level, a);
+    // the flux jump; its lift factor (2/h)/w0, signed by the side, is applied by the caller
 #pragma unroll
-    for (int v = 0; v < NV; ++v) L[v] = coef * (Fs[v] - Fo[v]);
+    for (int v = 0; v < NV; ++v) L[v] = sub_rn(Fs[v], Fo[v]);
   };
   if (valid) {
 #pragma unroll
@@ -302,8 +328,9 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
       const int k = s ? N : 0;
       T L[NV];
       face_lift(D - 1, s, t, t + NF * k, k, L);
+      const T coef = s ? -lift_of<T>(A, level, D - 1) : lift_of<T>(A, level, D - 1);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v][k] += L[v];
+      for (int v = 0; v < NV; ++v) acc[v][k] = fma(coef, L[v], acc[v][k]);
     }
   }
   __syncthreads();
@@ -315,11 +342,13 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       if (own != (s ? N : 0)) continue;
+      const T coef = s ? -lift_of<T>(A, level, a) : lift_of<T>(A, level, a);
 #pragma unroll
       for (int v = 0; v < NV; ++v)
 #pragma unroll
         for (int k = 0; k < n1; ++k)
-          acc[v][k] += sLift[((2 * a + s) * NV + v) * NF + (D == 3 ? u : 0) + (D == 3 ? n1 : 1) * k];
+          acc[v][k] = fma(coef, sLift[((2 * a + s) * NV + v) * NF + (D == 3 ? u : 0) + (D == 3 ? n1 : 1) * k],
+                          acc[v][k]);
     }
   }
   // ---- output
@@ -339,10 +368,10 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
     T qnew[NV];
     if (first) {   // uniform over the grid
 #pragma unroll
-      for (int v = 0; v < NV; ++v) qnew[v] = sQ[v * NP + n] + dt * acc[v][k];
+      for (int v = 0; v < NV; ++v) qnew[v] = fma(dt, acc[v][k], sQ[v * NP + n]);
     } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) qnew[v] = ca * qn_col[v][k] + cb * (sQ[v * NP + n] + dt * acc[v][k]);
+      for (int v = 0; v < NV; ++v) qnew[v] = fma(ca, qn_col[v][k], cb * fma(dt, acc[v][k], sQ[v * NP + n]));
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];

@@ -39,6 +39,12 @@ static __constant__ double c_dtab_ad[kDTabSize];
 // both halves; c_dtab_afr[m][i] for even m holds entries (m, i) and (m + 1, i).
 static __constant__ unsigned long long c_dtab_af2[kDTabSize];
 static __constant__ unsigned long long c_dtab_afr[kDTabSize];
+// Even/odd split of the antisymmetric matrix A (odd N, K2 = (N+1)/2): with E_m = F_m + F_{N-m} and
+// O_m = F_m - F_{N-m} (m < K2), (A F)_i = SE_i + SO_i and (A F)_{N-i} = SO_i - SE_i for i < K2,
+// SE_i = sum_m Ae[i][m] E_m, SO_i = sum_m Ao[i][m] O_m, Ae = (A[i][m] + A[i][N-m]) / 2,
+// Ao = (A[i][m] - A[i][N-m]) / 2.  Ae at the degree's offset, Ao K2^2 entries after it.
+static __constant__ float c_dtab_eo_f[kDTabSize];
+static __constant__ double c_dtab_eo_d[kDTabSize];
 
 static inline cudaError_t upload_dtab(const double* all) {
   float f[kDTabSize];
@@ -57,6 +63,24 @@ static inline cudaError_t upload_dtab(const double* all) {
   for (int i = 0; i < kDTabSize; ++i) f[i] = (float)a[i];
   e = cudaMemcpyToSymbol(c_dtab_af, f, sizeof(f));
   if (e != cudaSuccess) return e;
+  {
+    double eo[kDTabSize];
+    float eof[kDTabSize];
+    for (int i = 0; i < kDTabSize; ++i) eo[i] = 0.0;
+    for (int N = 1; N <= 8; N += 2) {
+      const int o = dtab_offset(N), n1 = N + 1, K2 = n1 / 2;
+      for (int i = 0; i < K2; ++i)
+        for (int m = 0; m < K2; ++m) {
+          eo[o + i * K2 + m] = 0.5 * (a[o + i * n1 + m] + a[o + i * n1 + (N - m)]);
+          eo[o + K2 * K2 + i * K2 + m] = 0.5 * (a[o + i * n1 + m] - a[o + i * n1 + (N - m)]);
+        }
+    }
+    for (int i = 0; i < kDTabSize; ++i) eof[i] = (float)eo[i];
+    e = cudaMemcpyToSymbol(c_dtab_eo_d, eo, sizeof(eo));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyToSymbol(c_dtab_eo_f, eof, sizeof(eof));
+    if (e != cudaSuccess) return e;
+  }
   unsigned long long f2[kDTabSize];
   for (int i = 0; i < kDTabSize; ++i) {
     uint32_t b;
@@ -83,6 +107,9 @@ static inline cudaError_t upload_dtab(const double* all) {
 template <class T> __device__ __forceinline__ T dtab(int i);
 template <> __device__ __forceinline__ float dtab<float>(int i) { return c_dtab_f[i]; }
 template <> __device__ __forceinline__ double dtab<double>(int i) { return c_dtab_d[i]; }
+template <class T> __device__ __forceinline__ T dtab_eo(int i);
+template <> __device__ __forceinline__ float dtab_eo<float>(int i) { return c_dtab_eo_f[i]; }
+template <> __device__ __forceinline__ double dtab_eo<double>(int i) { return c_dtab_eo_d[i]; }
 template <class T> __device__ __forceinline__ T dtab_anti(int i);
 template <> __device__ __forceinline__ float dtab_anti<float>(int i) { return c_dtab_af[i]; }
 template <> __device__ __forceinline__ double dtab_anti<double>(int i) { return c_dtab_ad[i]; }
