@@ -171,14 +171,12 @@ __device__ __forceinline__ float recip(float x) {
   return r;
 }
 // sqrt(a) for a > 0: Newton's iteration for the inverse square root, y <- y (3/2 - (a/2) y^2),
-// twice from the hardware seed, then s = a y corrected once by Newton's step for s^2 = a,
-// s <- s + (y/2) (a - s^2), the residual by one fma.
+// once from the hardware seed, then s = a y corrected once by Newton's step for s^2 = a,
+// s <- s + (y/2) (a - s^2), the residual by one fma: each step squares the relative error.
 __device__ __forceinline__ double sqrt_fast(double a) {
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-  const double h = 0.5 * a;
-  y = y * fma(-h * y, y, 1.5);
-  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-(0.5 * a) * y, y, 1.5);
   const double s = a * y;
   return fma(0.5 * y, fma(-s, s, a), s);
 }

@@ -201,8 +201,8 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
       }
   }
   __syncthreads();
-  auto line_dot = [&](const T* row, const T* Dr) {
-    T s = (T)0;
+  // acc + sum_m Dr[m] row[m], the rows Dr already scaled by -2/h
+  auto line_dot = [&](const T* row, const T* Dr, T s) {
     if constexpr (VEC) {
 #pragma unroll
       for (int m = 0; m < n1; m += 4) {
@@ -221,11 +221,11 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
   if (valid) {
     T Dr[n1];
 #pragma unroll
-    for (int m = 0; m < n1; ++m) Dr[m] = sDh[ci * n1 + m];
+    for (int m = 0; m < n1; ++m) Dr[m] = mul_rn(-inv2h[0], sDh[ci * n1 + m]);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int k = 0; k < n1; ++k) acc[v][k] = fma(-inv2h[0], line_dot(&sA[v * NP + NF * k + n1 * cj], Dr), acc[v][k]);
+      for (int k = 0; k < n1; ++k) acc[v][k] = line_dot(&sA[v * NP + NF * k + n1 * cj], Dr, acc[v][k]);
   }
   if (D == 3) {
     // y fluxes recomputed from the staged state into the same tile, transposed so that the
@@ -251,12 +251,11 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
     if (valid) {
       T Dr[n1];
 #pragma unroll
-      for (int m = 0; m < n1; ++m) Dr[m] = sDh[cj * n1 + m];
+      for (int m = 0; m < n1; ++m) Dr[m] = mul_rn(-inv2h[1], sDh[cj * n1 + m]);
 #pragma unroll
       for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int k = 0; k < n1; ++k)
-          acc[v][k] = fma(-inv2h[1], line_dot(&sA[v * NP + NF * k + n1 * ci], Dr), acc[v][k]);
+        for (int k = 0; k < n1; ++k) acc[v][k] = line_dot(&sA[v * NP + NF * k + n1 * ci], Dr, acc[v][k]);
     }
   }
   __syncthreads();
