@@ -5,6 +5,8 @@
 // FP64 background, the mortar flux buffer, and the integral reduction scratch.  Regrids
 // rebuild the tables and transfer q^n; the stage states are reallocated with it.
 #include <atomic>
+#include <initializer_list>
+#include <utility>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -64,6 +66,45 @@ cudaError_t reserve(P*& p, size_t& cap, size_t bytes) {
   if (e != cudaSuccess) return e;
   p = (P*)v;
   cap = want;
+  return cudaSuccess;
+}
+
+// Grow-only pinned host buffer `slot` of the mesh; the caller's stream work that reads the old
+// buffer must be complete before it is replaced (the mesh stream is synchronised first).
+cudaError_t pin_reserve(dg_mesh* m, int slot, size_t bytes) {
+  if (m->h_pin[slot] && m->c_pin[slot] >= bytes) return cudaSuccess;
+  if (m->h_pin[slot]) {
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return e;
+    cudaFreeHost(m->h_pin[slot]);
+  }
+  m->h_pin[slot] = nullptr;
+  m->c_pin[slot] = 0;
+  const size_t want = bytes + bytes / 4 + 256;
+  void* p = nullptr;
+  cudaError_t e = cudaMallocHost(&p, want);
+  if (e != cudaSuccess) return e;
+  m->h_pin[slot] = (unsigned char*)p;
+  m->c_pin[slot] = want;
+  return cudaSuccess;
+}
+
+// Host arrays to device buffers through pinned staging buffer `slot`, asynchronously on the mesh
+// stream; the staging buffer stays untouched until the mesh stream is next synchronised.
+cudaError_t upload_pinned(dg_mesh* m, int slot, std::initializer_list<std::pair<void*, std::pair<const void*, size_t>>> items) {
+  size_t total = 0;
+  for (const auto& it : items) total += (it.second.second + 255) / 256 * 256;
+  cudaError_t e = pin_reserve(m, slot, total);
+  if (e != cudaSuccess) return e;
+  size_t off = 0;
+  for (const auto& it : items) {
+    const size_t bytes = it.second.second;
+    if (bytes == 0) continue;
+    std::memcpy(m->h_pin[slot] + off, it.second.first, bytes);
+    e = cudaMemcpyAsync(it.first, m->h_pin[slot] + off, bytes, cudaMemcpyHostToDevice, m->stream);
+    if (e != cudaSuccess) return e;
+    off += (bytes + 255) / 256 * 256;
+  }
   return cudaSuccess;
 }
 
@@ -181,14 +222,14 @@ dg_status upload_tables(dg_mesh* m, HostTables&& t) {
   const std::vector<int32_t>& conn = t.conn;
   const std::vector<int32_t>& elem = t.elem;
   CU(reserve(m->d_elem, m->c_elem, elem.size() * sizeof(int32_t)));
-  CU(cudaMemcpy(m->d_elem, elem.data(), elem.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   CU(reserve(m->d_conn, m->c_conn, conn.size() * sizeof(int32_t)));
-  CU(cudaMemcpy(m->d_conn, conn.data(), conn.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   if (m->G > 0) {
     CU(reserve(m->d_groups, m->c_groups, m->mort.size() * sizeof(int32_t)));
-    CU(cudaMemcpy(m->d_groups, m->mort.data(), m->mort.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CU(reserve(m->d_mbuf, m->c_mbuf, (size_t)m->G * (1 + m->NSUB) * m->NV * m->NF * m->tsize));
   }
+  CU(upload_pinned(m, 1, {{m->d_elem, {elem.data(), elem.size() * sizeof(int32_t)}},
+                          {m->d_conn, {conn.data(), conn.size() * sizeof(int32_t)}},
+                          {m->d_groups, {m->mort.data(), m->G > 0 ? m->mort.size() * sizeof(int32_t) : 0}}}));
   CU(reserve(m->d_bg, m->c_bg, (size_t)m->E * m->n1 * 4 * sizeof(double)));
   if (m->prec == DG_FP32_PERT) {
     CU(reserve(m->d_bgf, m->c_bgf, (size_t)m->E * m->n1 * 4 * sizeof(float)));
@@ -812,6 +853,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   for (int i = 0; i < 2; ++i) dfree(m->adj_l[i]);
   dfree(m->d_abuf);
   dfree(m->d_send); dfree(m->d_recv); dfree(m->d_glist);
+  for (int i = 0; i < 3; ++i) if (m->h_pin[i]) cudaFreeHost(m->h_pin[i]);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   if (m->ev_order) cudaEventDestroy(m->ev_order);
   delete m;
@@ -1033,8 +1075,9 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
     if (!p->flags) return fail(m, DG_ERR_ARG, "flags missing");
     for (int64_t e = 0; e < m->E; ++e) tag[e] = p->flags[e] ? 1 : 0;
   } else if (p->criterion == DG_CRIT_THETA) {
-    std::vector<double> ind((size_t)m->E);
-    dg_status st = dg_indicator(m, ind.data(), ind.size());
+    CU(pin_reserve(m, 2, (size_t)(m->E > 0 ? m->E : 1) * sizeof(double)));
+    double* ind = reinterpret_cast<double*>(m->h_pin[2]);
+    dg_status st = dg_indicator(m, ind, (size_t)m->E);
     if (st != DG_OK) return st;
     for (int64_t e = 0; e < m->E; ++e) tag[e] = ind[e] > p->threshold ? 1 : 0;
   } else {
@@ -1060,7 +1103,7 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   static_assert(sizeof(dgl::TransferEntry) == 9 * sizeof(int32_t), "transfer rows are 9 int32");
   const size_t tm_bytes = tmap.size() * sizeof(dgl::TransferEntry);
   CU(reserve(m->d_tm, m->c_tm, tm_bytes + 4));
-  CU(cudaMemcpy(m->d_tm, tmap.data(), tm_bytes, cudaMemcpyHostToDevice));
+  CU(upload_pinned(m, 0, {{m->d_tm, {tmap.data(), tm_bytes}}}));
   CU(reserve(m->q_spare, m->q_spare_cap, (size_t)(m->NV + 1) * plane_new * m->tsize));
   const size_t sb_new = (size_t)(m->NV + 1) * plane_new * m->tsize;
   for (int i = 1; i < 3; ++i) CU(reserve(m->q[i], m->q_cap[i], sb_new));

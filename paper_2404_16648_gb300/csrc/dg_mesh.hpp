@@ -33,6 +33,10 @@ struct dg_mesh {
   size_t c_elem = 0, c_conn = 0, c_groups = 0, c_bg = 0, c_mbuf = 0, c_bgf = 0, c_bgc = 0, c_pps = 0;
   size_t c_sigma = 0, c_V = 0, c_vbuf = 0, c_tm = 0, c_ind = 0;
   int32_t* d_tm = nullptr;     // transfer map of the last regrid
+  // pinned host staging of a regrid's uploads (transfer map; tables) and of its indicator
+  // read-back: asynchronous copies at the link's rate instead of pageable synchronous ones
+  unsigned char* h_pin[3] = {nullptr, nullptr, nullptr};
+  size_t c_pin[3] = {0, 0, 0};
   double* d_ind = nullptr;     // refinement indicator
   int32_t* d_elem = nullptr;
   int32_t* d_conn = nullptr;
