@@ -369,11 +369,11 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
                           void* pp_out, int mode, double dt, double ca, double cb, cudaStream_t s) {
   if (m->tracer) return tracer_pass(m, qs, qn, out, mode, dt, ca, cb, s);
   const bool timed = m->timing && mode == 1;
-  // layout 4 directly after its mortar kernel: programmatic dependent launch, so the stage
-  // kernel stages its own state while the mortar kernel finishes.  A stage timed on its own
-  // (dg_enable_timing) needs an event between the two launches, which rules this out.
-  const bool pdl = m->variant == 4 && m->D == 3 && (m->N % 2) == 1 &&
-                   (m->nparts > 1 ? m->G_part : m->G) > 0 && !timed;
+  // layouts 4 and 2 directly after their mortar kernel: programmatic dependent launch, so the
+  // stage kernel runs its elements without hanging faces while the mortar kernel finishes and
+  // only the others wait for it.  A stage timed on its own (dg_enable_timing) needs an event
+  // between the two launches, which rules this out.
+  const bool pdl = (m->variant == 4 || m->variant == 2) && (m->nparts > 1 ? m->G_part : m->G) > 0 && !timed;
   dg_status st = dgi::launch_mortars(m, qs, pp_in, s);
   if (st != DG_OK) return st;
   dgk::StageArgs A{};

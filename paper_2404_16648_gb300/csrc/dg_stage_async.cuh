@@ -122,6 +122,9 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
         for (int v = 0; v < NV; ++v) cp_async_bytes(dst + v * NF + t, qb + v * P + no, (int)sizeof(T));
         cp_async_bytes(dst + NV * NF + t, (const T*)A.pp_in + (int64_t)c[1] * NP + no, (int)sizeof(T));
       } else if (kind == FACE_FINE || kind == FACE_COARSE) {
+        // launched as the programmatic dependent of this stage's mortar kernel: only the
+        // elements with a hanging face wait for it, before they read its fluxes
+        if (A.after_mortar) asm volatile("griddepcontrol.wait;\n" ::: "memory");
         const int64_t gg = (kind == FACE_FINE) ? c[2] : c[1];
         const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
         const T* src = (const T*)A.mbuf + (((size_t)gg * (1 + NSUB) + slot) * NV) * NF;

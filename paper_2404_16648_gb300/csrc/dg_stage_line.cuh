@@ -334,9 +334,6 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
   stage_run<T>(sBg, (const T*)A.bgt + e * n1 * 4, n1 * 4, tid, THREADS);
   if (sizeof(T) == 4) stage_run<double>(sBc, A.bgc + e * n1, n1, tid, THREADS);
   cp_async_commit();
-  // the mortar fluxes are written by the mortar kernel of this stage, which may still run when
-  // this grid was launched as its programmatic dependent (no-op otherwise)
-  if (A.after_mortar) asm volatile("griddepcontrol.wait;\n" ::: "memory");
   // ---- the faces this thread lifts: (a, h) at face node L of each axis a; only this thread
   // reads them, so they form a group of their own that it waits for before its first lift
   auto stage_face = [&](int a, int s, int fn) -> int {
@@ -351,6 +348,11 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
       for (int v = 0; v < NV; ++v) cp_async_bytes(dst + v * NF + fn, qb + v * P + no, (int)sizeof(T));
       cp_async_bytes(dst + NV * NF + fn, (const T*)A.pp_in + (int64_t)c[1] * NP + no, (int)sizeof(T));
     } else if (kind == FACE_FINE || kind == FACE_COARSE) {
+      // the mortar fluxes are written by the mortar kernel of this stage, which may still run
+      // when this grid was launched as its programmatic dependent: only a thread that reads
+      // them waits for it (everything else this kernel reads comes from the previous stage,
+      // complete before the mortar kernel began)
+      if (A.after_mortar) asm volatile("griddepcontrol.wait;\n" ::: "memory");
       const int64_t gg = (kind == FACE_FINE) ? c[2] : c[1];
       const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
       const T* src = (const T*)A.mbuf + (((size_t)gg * (1 + NSUB) + slot) * NV) * NF;

@@ -40,8 +40,24 @@ cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   const unsigned blocks = (unsigned)((A.E - A.e_begin + EPB - 1) / EPB);
-  if (blocks) stage_kernel_async<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
-  return cudaSuccess;
+  if (!blocks) return cudaSuccess;
+  if (!A.after_mortar) {
+    stage_kernel_async<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
+    return cudaSuccess;
+  }
+  // programmatic dependent launch after the mortar kernel (see the hanging-face staging of
+  // stage_body_async)
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(EPB * NF);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, stage_kernel_async<T, D, N, EPB>, A);
 }
 
 // Layout 3 (3D, odd N); other shapes take layout 2.
