@@ -161,10 +161,26 @@ dg_status build_tables(dg_mesh* m, const dgl::Forest& f, HostTables* t) {
   f.face_lists(&t->conf, &t->mort, &t->bnd);
   t->G = (int64_t)(t->mort.size() / 7);
   f.connectivity(t->mort, &t->conn);
-  // every index a kernel will follow must be in range before anything is uploaded; the error
-  // names the first bad row
   const int nf = 2 * m->D;
   const int64_t E = t->E, G = t->G;
+  // face-flux slots of stage layout 5 in the third field of the conforming and wall rows:
+  // conforming faces 0 .. C-1 (list order), boundary faces C .. C+B-1
+  const int64_t C = (int64_t)t->conf.size() / 3, Bn = (int64_t)t->bnd.size() / 3;
+  for (int64_t c = 0; c < C; ++c) {
+    const int32_t* r = t->conf.data() + c * 3;
+    if (r[0] < 0 || r[0] >= E || r[1] < 0 || r[1] >= E || r[2] < 0 || r[2] >= m->D)
+      return fail(m, DG_ERR_STATE, "inconsistent conforming face %lld", (long long)c);
+    t->conn[((size_t)r[0] * nf + 2 * r[2] + 1) * 5 + 2] = (int32_t)c;
+    t->conn[((size_t)r[1] * nf + 2 * r[2]) * 5 + 2] = (int32_t)c;
+  }
+  for (int64_t b = 0; b < Bn; ++b) {
+    const int32_t* r = t->bnd.data() + b * 3;
+    if (r[0] < 0 || r[0] >= E || r[1] < 0 || r[1] >= m->D || r[2] < 0 || r[2] > 1)
+      return fail(m, DG_ERR_STATE, "inconsistent boundary face %lld", (long long)b);
+    t->conn[((size_t)r[0] * nf + 2 * r[1] + r[2]) * 5 + 2] = (int32_t)(C + b);
+  }
+  // every index a kernel will follow must be in range before anything is uploaded; the error
+  // names the first bad row
   const int NSUB = m->NSUB, D = m->D;
   const std::vector<int32_t>& conn = t->conn;
   const std::vector<int32_t>& mort = t->mort;
@@ -178,8 +194,8 @@ dg_status build_tables(dg_mesh* m, const dgl::Forest& f, HostTables* t) {
       const int32_t* c = conn.data() + r * 5;
       bool ok = true;
       switch (c[0]) {
-        case dgl::FACE_WALL: break;
-        case dgl::FACE_CONF: ok = c[1] >= 0 && c[1] < E; break;
+        case dgl::FACE_WALL: ok = c[2] >= C && c[2] < C + Bn; break;
+        case dgl::FACE_CONF: ok = c[1] >= 0 && c[1] < E && c[2] >= 0 && c[2] < C; break;
         case dgl::FACE_FINE: ok = c[1] >= 0 && c[1] < E && c[2] >= 0 && c[2] < G && c[3] >= 0 && c[3] < NSUB; break;
         case dgl::FACE_COARSE: ok = c[1] >= 0 && c[1] < G; break;
         default: ok = false;
@@ -227,9 +243,13 @@ dg_status upload_tables(dg_mesh* m, HostTables&& t) {
     CU(reserve(m->d_groups, m->c_groups, m->mort.size() * sizeof(int32_t)));
     CU(reserve(m->d_mbuf, m->c_mbuf, (size_t)m->G * (1 + m->NSUB) * m->NV * m->NF * m->tsize));
   }
+  CU(reserve(m->d_fconf, m->c_fconf, m->conf.size() * sizeof(int32_t)));
+  CU(reserve(m->d_fbnd, m->c_fbnd, m->bnd.size() * sizeof(int32_t)));
   CU(upload_pinned(m, 1, {{m->d_elem, {elem.data(), elem.size() * sizeof(int32_t)}},
                           {m->d_conn, {conn.data(), conn.size() * sizeof(int32_t)}},
-                          {m->d_groups, {m->mort.data(), m->G > 0 ? m->mort.size() * sizeof(int32_t) : 0}}}));
+                          {m->d_groups, {m->mort.data(), m->G > 0 ? m->mort.size() * sizeof(int32_t) : 0}},
+                          {m->d_fconf, {m->conf.data(), m->conf.size() * sizeof(int32_t)}},
+                          {m->d_fbnd, {m->bnd.data(), m->bnd.size() * sizeof(int32_t)}}}));
   CU(reserve(m->d_bg, m->c_bg, (size_t)m->E * m->n1 * 4 * sizeof(double)));
   if (m->prec == DG_FP32_PERT) {
     CU(reserve(m->d_bgf, m->c_bgf, (size_t)m->E * m->n1 * 4 * sizeof(float)));
@@ -281,6 +301,7 @@ void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const 
                      void* pp_out, int mode, double dt, double ca, double cb, dgk::StageArgs* A) {
   A->qs = qs; A->pp_in = pp_in; A->qn = qn; A->out = out; A->pp_out = pp_out; A->mbuf = m->d_mbuf;
   A->plane = plane(m); A->E = (int32_t)m->e_end; A->e_begin = (int32_t)m->e_begin;
+  A->fbuf = m->d_fbuf;
   A->elem = m->d_elem; A->conn = m->d_conn; A->bg = m->d_bg; A->bgt = bgt(m); A->bgc = m->d_bgc; A->ops = m->d_ops;
   for (int l = 0; l < dgk::kMaxLevels; ++l)
     for (int a = 0; a < 3; ++a) {
@@ -373,11 +394,27 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
   // stage kernel runs its elements without hanging faces while the mortar kernel finishes and
   // only the others wait for it.  A stage timed on its own (dg_enable_timing) needs an event
   // between the two launches, which rules this out.
-  const bool pdl = (m->variant == 4 || m->variant == 2) && (m->nparts > 1 ? m->G_part : m->G) > 0 && !timed;
+  // layout 5 (face fluxes once per face, then the column-async stage) needs the whole mesh's
+  // face lists; a partitioned mesh runs layout 2
+  const int variant = (m->variant == 5 && m->nparts > 1) ? 2 : m->variant;
+  const bool mortars = (m->nparts > 1 ? m->G_part : m->G) > 0;
+  bool pdl = (variant == 4 || variant == 2) && mortars && !timed;
   dg_status st = dgi::launch_mortars(m, qs, pp_in, s);
   if (st != DG_OK) return st;
+  if (variant == 5) {
+    const int64_t C = (int64_t)m->conf.size() / 3, Bn = (int64_t)m->bnd.size() / 3;
+    CU(reserve(m->d_fbuf, m->c_fbuf, (size_t)(C + Bn > 0 ? C + Bn : 1) * m->NV * m->NF * m->tsize));
+    dgk::FaceArgs F{qs, pp_in, m->d_fbuf, plane(m), (int32_t)C, (int32_t)Bn, m->d_fconf, m->d_fbnd, bgt(m),
+                    (float)m->ph.gamma, m->ph};
+    const bool fpdl = mortars;   // the face kernel follows the mortar kernel directly
+    CU(m->prec == DG_FP64
+           ? (m->D == 2 ? dgk::launch_face_f64_2d(m->N, F, fpdl, s) : dgk::launch_face_f64_3d(m->N, F, fpdl, s))
+           : (m->D == 2 ? dgk::launch_face_f32_2d(m->N, F, fpdl, s) : dgk::launch_face_f32_3d(m->N, F, fpdl, s)));
+    pdl = !timed;                // the stage kernel follows the face kernel directly
+  }
   dgk::StageArgs A{};
   dgi::fill_stage_args(m, qs, pp_in, qn, out, pp_out, mode, dt, ca, cb, &A);
+  A.variant = variant;
   A.after_mortar = pdl ? 1 : 0;
   if (timed) {
     while (m->ev.size() < m->ev_used + 2) {
@@ -738,7 +775,7 @@ dg_status dg_ke_grad(dg_mesh* m, const void* q, void* out, void* stream) {
 dg_status dg_set_option(dg_mesh* m, int32_t option, int64_t value) {
   if (!m) return DG_ERR_ARG;
   if (option == DG_OPT_STAGE_KERNEL) {
-    if (value < 0 || value > 4) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0 .. 4");
+    if (value < 0 || value > 5) return fail(m, DG_ERR_ARG, "stage kernel layout must be 0 .. 5");
     m->variant = (int)value;
     return DG_OK;
   }
@@ -800,7 +837,8 @@ dg_status dg_mesh_create(const dg_mesh_desc* desc, void* stream, dg_mesh** out) 
   m->NV = m->tracer ? 1 : m->D + 2; m->NSUB = 1 << (m->D - 1);
   m->prec = desc->precision;
   m->tsize = m->prec == DG_FP64 ? sizeof(double) : sizeof(float);
-  m->variant = (m->prec == DG_FP32_PERT && m->D == 3) ? 4 : 2;   // fastest measured layouts
+  // fastest measured layouts: the line layout for FP32 in 3D, face fluxes once per face for FP64
+  m->variant = (m->prec == DG_FP32_PERT && m->D == 3) ? 4 : (m->prec == DG_FP64 && !m->tracer ? 5 : 2);
   m->stream = (cudaStream_t)stream;
   m->ph.theta0 = desc->theta0; m->ph.p0 = desc->p0; m->ph.g = desc->g; m->ph.R = desc->R;
   m->ph.cp = desc->cp; m->ph.cv = desc->cp - desc->R; m->ph.gamma = desc->cp / (desc->cp - desc->R);
@@ -853,6 +891,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   for (int i = 0; i < 2; ++i) dfree(m->adj_l[i]);
   dfree(m->d_abuf);
   dfree(m->d_send); dfree(m->d_recv); dfree(m->d_glist);
+  dfree(m->d_fbuf); dfree(m->d_fconf); dfree(m->d_fbnd);
   for (int i = 0; i < 3; ++i) if (m->h_pin[i]) cudaFreeHost(m->h_pin[i]);
   for (cudaEvent_t e : m->ev) cudaEventDestroy(e);
   if (m->ev_order) cudaEventDestroy(m->ev_order);

@@ -269,6 +269,9 @@ struct StageArgs {
   int32_t after_mortar;
   // the launch covers elements e_begin .. E - 1 (a part of an SFC partition; 0 otherwise)
   int32_t e_begin;
+  // layout 5: F* of conforming and wall faces, one slot per face (dg_face.cuh); the slot of a
+  // face is the third field of its connectivity row
+  const void* fbuf;
 };
 
 struct MortarArgs {

@@ -9,6 +9,7 @@
 
 #include "dg_adjoint.cuh"
 #include "dg_device.cuh"
+#include "dg_face.cuh"
 #include "dg_tracer.cuh"
 #include "dg_viscous.cuh"
 
@@ -59,6 +60,12 @@ bool launch_mortar_f64_2d(int N, const MortarArgs& A, cudaStream_t s);
 bool launch_mortar_f64_3d(int N, const MortarArgs& A, cudaStream_t s);
 bool launch_mortar_f32_2d(int N, const MortarArgs& A, cudaStream_t s);
 bool launch_mortar_f32_3d(int N, const MortarArgs& A, cudaStream_t s);
+// Face kernel of stage layout 5 (conforming and wall fluxes into the face buffer); pdl: as the
+// programmatic dependent of the mortar kernel launched just before.
+cudaError_t launch_face_f64_2d(int N, const FaceArgs& F, bool pdl, cudaStream_t s);
+cudaError_t launch_face_f64_3d(int N, const FaceArgs& F, bool pdl, cudaStream_t s);
+cudaError_t launch_face_f32_2d(int N, const FaceArgs& F, bool pdl, cudaStream_t s);
+cudaError_t launch_face_f32_3d(int N, const FaceArgs& F, bool pdl, cudaStream_t s);
 // Upload the derivative matrices of every degree (concatenated, N = 1..8) to each unit's
 // constant memory; called once before the first stage launch.
 cudaError_t init_stage_f64_2d(const double* dtab_all);

@@ -45,6 +45,10 @@ struct dg_mesh {
   float* d_bgf = nullptr;      // FP32 copy of the background (FP32 path)
   double* d_bgc = nullptr;     // gamma p_bar / Theta_bar per z-level (FP32 path's P')
   void* d_mbuf = nullptr;
+  void* d_fbuf = nullptr;      // layout 5: conforming and wall face fluxes (dg_face.cuh)
+  int32_t* d_fconf = nullptr;  // the conforming and boundary face lists on the device
+  int32_t* d_fbnd = nullptr;
+  size_t c_fbuf = 0, c_fconf = 0, c_fbnd = 0;
   void* d_ppscratch = nullptr; // P' plane of a caller's state in dg_rhs
   bool pp_valid = false;       // P' plane of q[0] matches q[0]
   int variant = 2;             // stage kernel layout (DG_OPT_STAGE_KERNEL); set at creation

@@ -13,4 +13,7 @@ cudaError_t launch_stage_batched_f32_3d(int N, int layout, const StageArgs* tab,
                                         int nblocks, cudaStream_t s) {
   return batched_dispatch<float, 3>(N, layout, tab, map, nblocks, s);
 }
+cudaError_t launch_face_f32_3d(int N, const FaceArgs& F, bool pdl, cudaStream_t s) {
+  return face_dispatch<float, 3>(N, F, pdl, s);
+}
 }  // namespace dgk

@@ -1,5 +1,6 @@
 // Instantiates the stage and mortar kernels of one (precision, dimension) for N = 1..8.
 // Included by stage_<prec>_<dim>.cu with DG_T and DG_D defined.
+#include "dg_face.cuh"
 #include "dg_launch.hpp"
 #include "dg_stage_half.cuh"
 #include "dg_stage_line.cuh"
@@ -30,19 +31,19 @@ cudaError_t run_stage_col(const StageArgs& A, cudaStream_t s) {
   return cudaSuccess;
 }
 
-template <class T, int D, int N>
+template <class T, int D, int N, bool FB = false>
 cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
   constexpr int NF = ipow(N + 1, D - 1);
   constexpr int EPB = epb_col(D, N);
   constexpr size_t smem = async_smem_bytes<T, D, N, EPB>();
   {
-    cudaError_t e = configure_kernel((const void*)stage_kernel_async<T, D, N, EPB>, smem, false);
+    cudaError_t e = configure_kernel((const void*)stage_kernel_async<T, D, N, EPB, FB>, smem, false);
     if (e != cudaSuccess) return e;
   }
   const unsigned blocks = (unsigned)((A.E - A.e_begin + EPB - 1) / EPB);
   if (!blocks) return cudaSuccess;
   if (!A.after_mortar) {
-    stage_kernel_async<T, D, N, EPB><<<blocks, EPB * NF, smem, s>>>(A);
+    stage_kernel_async<T, D, N, EPB, FB><<<blocks, EPB * NF, smem, s>>>(A);
     return cudaSuccess;
   }
   // programmatic dependent launch after the mortar kernel (see the hanging-face staging of
@@ -57,7 +58,7 @@ cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, stage_kernel_async<T, D, N, EPB>, A);
+  return cudaLaunchKernelEx(&cfg, stage_kernel_async<T, D, N, EPB, FB>, A);
 }
 
 // Layout 3 (3D, odd N); other shapes take layout 2.
@@ -154,7 +155,48 @@ void run_stage(const StageArgs& A, cudaStream_t s) {
   else if (A.variant == 2) run_stage_async<T, D, N>(A, s);
   else if (A.variant == 3) run_stage_half<T, D, N>(A, s);
   else if (A.variant == 4) run_stage_line<T, D, N>(A, s);
+  else if (A.variant == 5) run_stage_async<T, D, N, true>(A, s);
   else run_stage_col<T, D, N>(A, s);
+}
+
+// Face kernel of layout 5 (dg_face.cuh); pdl: launched as the programmatic dependent of the
+// mortar kernel just before it.
+template <class T, int D, int N>
+cudaError_t run_face(const FaceArgs& F, bool pdl, cudaStream_t s) {
+  constexpr int FPB = face_per_block<D, N>();
+  constexpr int NF = ipow(N + 1, D - 1);
+  const int64_t n = (int64_t)F.C + F.B;
+  if (n == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + FPB - 1) / FPB);
+  if (!pdl) {
+    face_kernel<T, D, N><<<blocks, FPB * NF, 0, s>>>(F);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(FPB * NF);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, face_kernel<T, D, N>, F);
+}
+
+template <class T, int D>
+cudaError_t face_dispatch(int N, const FaceArgs& F, bool pdl, cudaStream_t s) {
+  switch (N) {
+    case 1: return run_face<T, D, 1>(F, pdl, s);
+    case 2: return run_face<T, D, 2>(F, pdl, s);
+    case 3: return run_face<T, D, 3>(F, pdl, s);
+    case 4: return run_face<T, D, 4>(F, pdl, s);
+    case 5: return run_face<T, D, 5>(F, pdl, s);
+    case 6: return run_face<T, D, 6>(F, pdl, s);
+    case 7: return run_face<T, D, 7>(F, pdl, s);
+    case 8: return run_face<T, D, 8>(F, pdl, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class T, int D, int N>

@@ -69,7 +69,7 @@ MESHES = [
 ]
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dim,N,base,length,rounds", MESHES)
 def test_rhs_parity_fp64(pkg, dim, N, base, length, rounds, layout):
     lm, om = _pair(pkg, dim, N, base, length, flags_rounds=rounds)
@@ -91,7 +91,7 @@ def test_rest_state_exactly_zero(pkg, precision):
     assert torch.count_nonzero(out).item() == 0
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("dim,N,base,length,rounds", MESHES)
 def test_rhs_parity_fp32_perturbation(pkg, dim, N, base, length, rounds, layout):
     # FP32 state and flux arithmetic, FP64 background and pressure perturbation.  Bound: the
@@ -128,7 +128,7 @@ def test_step_parity_rising_bubble(pkg):
     assert _rel_err(got - q0, want - q0) <= 1e-11
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5])
 def test_step_parity_hanging_3d(pkg, layout):
     lm, om = _pair(pkg, 3, 3, (2, 2, 2), (2000.0,) * 3, flags_rounds=((0.3, 11),))
     lm.set_stage_kernel(layout)
@@ -290,7 +290,7 @@ def test_rhs_parity_large_theta_uses_fallback_branch(pkg, precision, tol):
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
 @pytest.mark.parametrize("dim,N,base", [(2, 3, (1, 1)), (3, 3, (1, 1, 1)), (3, 7, (1, 1, 1))])
-@pytest.mark.parametrize("layout", [1, 2, 3, 4])
+@pytest.mark.parametrize("layout", [1, 2, 3, 4, 5])
 def test_single_element_mesh(pkg, precision, tol, dim, N, base, layout):
     """One element with walls on every face: the smallest mesh the method has."""
     import torch
