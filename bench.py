@@ -223,7 +223,7 @@ def fp32_accuracy(pkg, cfg, steps):
     return out
 
 
-def _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D, per_node=None):
+def _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D, per_node=None, face_kernel=False):
     """Runs `steps` SSP-RK3 steps (regrid every `regrid_every` inside) between two CUDA events on
     the mesh stream; returns the elapsed ms and the work counters of the region."""
     import torch
@@ -240,7 +240,8 @@ def _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D, per_node=None):
         c["alg_flops"] += stage_flops(E, NP, NV, n1, D)
         if per_node:
             c["traffic"] += E * NP * sum(per_node)
-        c["launches"] += 3 * (1 + (m.num_mortars > 0))   # stage (+ mortar) launches per step
+        # stage (+ mortar, + face kernel in layout 5) launches per step
+        c["launches"] += 3 * (1 + (m.num_mortars > 0) + face_kernel)
         if regrid_every and (i + 1) % regrid_every == 0:
             torch.cuda.synchronize()     # dg_adapt starts with this wait anyway
             tr = time.perf_counter()
@@ -268,8 +269,9 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
         m.step(dt, 1)
     torch.cuda.synchronize()
     m.integrals()
-    default_layout = 4 if (precision == "fp32" and D == 3) else 2
-    per_node = measured_traffic(D, N, precision, default_layout if STAGE_KERNEL is None else STAGE_KERNEL)
+    default_layout = 4 if (precision == "fp32" and D == 3) else (5 if precision == "fp64" else 2)
+    layout = default_layout if STAGE_KERNEL is None else STAGE_KERNEL
+    per_node = measured_traffic(D, N, precision, layout)
     _barrier(world)
     torch.cuda.synchronize()
     if sampler:
@@ -278,7 +280,7 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
     for r in range(repeats):
         _barrier(world)
         torch.cuda.synchronize()
-        ms, c = _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D)
+        ms, c = _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D, face_kernel=layout == 5)
         ms = _barrier_max(ms, world)
         reps.append((c["dof_stage"] / (ms / 1e3), ms, c))
     clocks = sampler.stop() if sampler else None
@@ -290,7 +292,7 @@ def run_path(pkg, cfg, precision, steps, warmup, regrid_every, sampler=None, wor
     m.stage_timing(reset=True)
     _barrier(world)
     torch.cuda.synchronize()
-    ms_t, ct = _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D, per_node)
+    ms_t, ct = _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D, per_node, face_kernel=layout == 5)
     stage_ms, stage_launches = m.stage_timing(reset=True)
     m.enable_timing(False)
     integ = m.integrals()
@@ -745,10 +747,10 @@ def main():
                     help="directory for the raw nvidia-smi clock samples (default: a temporary one)")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the FP32-vs-FP64 field comparison over the workload's full step count")
-    ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--stage-kernel", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="stage kernel layout: 0 column, 1 node-per-thread, 2 column with "
-                         "asynchronous staging, 3 as 2 with two threads per column "
-                         "(default: the library's)")
+                         "asynchronous staging, 3 as 2 with two threads per column, 4 line, "
+                         "5 as 2 with the face fluxes once per face (default: the library's)")
     args = ap.parse_args()
     global STAGE_KERNEL
     STAGE_KERNEL = args.stage_kernel
@@ -820,7 +822,8 @@ def main():
                        "path": "production dg_step (stage kernels as programmatic dependent launches "
                                "after their mortar kernels)"},
             "precision_path": "FP32 state/flux arithmetic; FP64 background and integrals; P' to FP64 accuracy before its FP32 rounding",
-            "stage_kernel": {None: "default", 0: "column", 1: "node", 2: "column-async", 3: "half-column-async", 4: "line"}[STAGE_KERNEL],
+            "stage_kernel": {None: "default", 0: "column", 1: "node", 2: "column-async", 3: "half-column-async", 4: "line",
+                             5: "column-async with face kernel"}[STAGE_KERNEL],
             "elements": r32["elements"], "nodes_per_variable": r32["nodes"],
             "gpu_launches": r32["launches"], "mortar_groups": r32["mortars"],
             "roofline": {"bound": "hbm", "kernel": "stage_kernel", "achieved": achieved,
@@ -845,11 +848,14 @@ def main():
         ach64 = r64["alg_flops"] / (r64["stage_ms"] / 1e3) / 1e12
         line["fp64"] = {"value": v64, "ms_per_step": r64["ms"] / args.steps, "dtype": "f64",
                         "repeat_values": [world * v for v in r64["rates"]],
-                        "roofline": {"bound": "alu", "kernel": "stage_kernel", "achieved": ach64,
+                        "roofline": {"bound": "alu", "kernel": "stage_kernel (+ face_kernel in layout 5)",
+                                     "achieved": ach64,
                                      "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach64 / fp64_peak,
                                      "peak_kind": "measured: dg_probe_fma_rate (independent FP64 "
                                                   "multiply-adds on every SM, CUDA events)",
-                                     "stage_ms_per_launch": r64["stage_ms"] / max(1, r64["stage_launches"])},
+                                     "stage_ms_per_launch": r64["stage_ms"] / max(1, r64["stage_launches"]),
+                                     "stage_timing": "CUDA events around each stage's face kernel "
+                                                     "(layout 5) and stage kernel"},
                         "integrals": r64["integrals"]}
         line["fp32_over_fp64"] = value / v64
     if not args.no_accuracy and cfg.get("threshold") is not None:

@@ -350,9 +350,10 @@ dg_status dg_set_option(dg_mesh* mesh, int32_t option, int64_t value);
 
 /* Kernel timing: when enabled, the fused stage launches of dg_step are bracketed by CUDA
  * events on the mesh stream; dg_stage_timing returns the summed milliseconds and launch count
- * since the last reset (synchronises the stream).  Untimed, a layout-4 stage launch may begin
- * while its mortar kernel finishes (programmatic dependent launch); timed, it starts after it,
- * so that the events bracket the stage kernel alone. */
+ * since the last reset (synchronises the stream).  Untimed, a stage launch of layouts 2, 4 and 5
+ * may begin while the kernel before it finishes (programmatic dependent launch); timed, it
+ * starts after it, so that the events bracket the stage kernel alone (in layout 5, the face
+ * kernel and the stage kernel). */
 dg_status dg_enable_timing(dg_mesh* mesh, int32_t enable);
 dg_status dg_stage_timing(dg_mesh* mesh, double* total_ms, int64_t* launches, int32_t reset);
 

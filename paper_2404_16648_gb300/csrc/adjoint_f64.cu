@@ -7,11 +7,14 @@ namespace dgk {
 namespace {
 
 template <int D, int N>
-void run_vjp(const AdjArgs& A, cudaStream_t s) {
+void run_vjp(const AdjArgs& A, cudaStream_t s, cudaError_t& err) {
   constexpr int NP = ipow(N + 1, D);
   constexpr int EPB = NP >= 128 ? 1 : 256 / NP;
+  constexpr size_t smem = VjpSmem<D, N, EPB>::bytes;
   const unsigned blocks = (unsigned)((A.E + EPB - 1) / EPB);
-  if (blocks) vjp_kernel<D, N, EPB><<<blocks, EPB * NP, 0, s>>>(A);
+  if (!blocks) return;
+  err = configure_kernel((const void*)vjp_kernel<D, N, EPB>, smem, false);
+  if (err == cudaSuccess) vjp_kernel<D, N, EPB><<<blocks, EPB * NP, smem, s>>>(A);
 }
 
 template <int D, int N>
@@ -20,16 +23,16 @@ void run_mortar_vjp(const MortarAdjArgs& A, cudaStream_t s) {
 }
 
 template <int D>
-bool vjp_dispatch(int N, const AdjArgs& A, cudaStream_t s) {
+bool vjp_dispatch(int N, const AdjArgs& A, cudaStream_t s, cudaError_t& err) {
   switch (N) {
-    case 1: run_vjp<D, 1>(A, s); return true;
-    case 2: run_vjp<D, 2>(A, s); return true;
-    case 3: run_vjp<D, 3>(A, s); return true;
-    case 4: run_vjp<D, 4>(A, s); return true;
-    case 5: run_vjp<D, 5>(A, s); return true;
-    case 6: run_vjp<D, 6>(A, s); return true;
-    case 7: run_vjp<D, 7>(A, s); return true;
-    case 8: run_vjp<D, 8>(A, s); return true;
+    case 1: run_vjp<D, 1>(A, s, err); return true;
+    case 2: run_vjp<D, 2>(A, s, err); return true;
+    case 3: run_vjp<D, 3>(A, s, err); return true;
+    case 4: run_vjp<D, 4>(A, s, err); return true;
+    case 5: run_vjp<D, 5>(A, s, err); return true;
+    case 6: run_vjp<D, 6>(A, s, err); return true;
+    case 7: run_vjp<D, 7>(A, s, err); return true;
+    case 8: run_vjp<D, 8>(A, s, err); return true;
     default: return false;
   }
 }
@@ -110,8 +113,9 @@ __global__ void ke_grad_kernel(int64_t total, int NP, int n1, int D, const int32
 
 }  // namespace
 
-bool launch_vjp(int D, int N, const AdjArgs& A, cudaStream_t s) {
-  return D == 2 ? vjp_dispatch<2>(N, A, s) : vjp_dispatch<3>(N, A, s);
+bool launch_vjp(int D, int N, const AdjArgs& A, cudaStream_t s, cudaError_t& err) {
+  err = cudaSuccess;
+  return D == 2 ? vjp_dispatch<2>(N, A, s, err) : vjp_dispatch<3>(N, A, s, err);
 }
 
 bool launch_mortar_vjp(int D, int N, const MortarAdjArgs& A, cudaStream_t s) {

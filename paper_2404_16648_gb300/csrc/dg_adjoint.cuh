@@ -56,7 +56,9 @@ struct MortarAdjArgs {
 };
 
 // Everything about one node's state that the Jacobians need (the sound speed c is formed only
-// where a face needs it, see sound_speed).
+// where a face needs it, see sound_speed).  Reciprocals and square roots are the forward
+// kernels' Newton forms (recip, sqrt_fast: within one ulp of the rounded results), which take
+// fewer FP64 operations than IEEE division and square root.
 template <int D>
 struct NodeLin {
   double rinv, u[D], Theta, iTheta, P, dPdT;
@@ -68,11 +70,11 @@ template <int D>
 __device__ __forceinline__ NodeLin<D> node_lin(const double* q, double rb, double Tb, double pb,
                                                double pp, const PhysC& ph) {
   NodeLin<D> L;
-  L.rinv = 1.0 / (rb + q[0]);
+  L.rinv = recip(rb + q[0]);
 #pragma unroll
   for (int b = 0; b < D; ++b) L.u[b] = q[1 + b] * L.rinv;
   L.Theta = Tb + q[D + 1];
-  L.iTheta = 1.0 / L.Theta;
+  L.iTheta = recip(L.Theta);
   L.P = pb + pp;
   L.dPdT = ph.gamma * L.P * L.iTheta;                // dP/dTheta of the EOS of Sec. 2.1
   return L;
@@ -80,7 +82,7 @@ __device__ __forceinline__ NodeLin<D> node_lin(const double* q, double rb, doubl
 
 template <int D>
 __device__ __forceinline__ double sound_speed(const NodeLin<D>& L, double gamma) {
-  return sqrt(gamma * L.P * L.rinv);
+  return sqrt_fast(gamma * L.P * L.rinv);
 }
 
 // out += J_a(q)^T mu with J_a = dF_a/dq (perturbation variables).
@@ -178,34 +180,144 @@ __device__ __forceinline__ void rusanov_vjp_own(const double* q, const NodeLin<D
 template <int D>
 __device__ __forceinline__ double neighbour_speed(const double* q, double rb, double pb, double pp, int a,
                                                   double gamma) {
-  const double rinv = 1.0 / (rb + q[0]);
-  return fabs(q[1 + a] * rinv) + sqrt(gamma * (pb + pp) * rinv);
+  const double rinv = recip(rb + q[0]);
+  return fabs(q[1 + a] * rinv) + sqrt_fast(gamma * (pb + pp) * rinv);
 }
 
+// Shared memory of vjp_kernel (doubles): D, then per element of the block Lambda [NV][NP], the
+// node reciprocals 1/rho and 1/Theta [2][NP], and the face contributions: the cotangent each face
+// node adds to its node's J_a^T input [2D][NV][NF] and the part it adds to the node's result
+// [2D][NV][NF].
+template <int D, int N, int EPB>
+struct VjpSmem {
+  static constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  static constexpr int oL = n1 * n1;
+  static constexpr int oR = oL + EPB * NV * NP;
+  static constexpr int oC = oR + EPB * 2 * NP;
+  static constexpr int oA = oC + EPB * 2 * D * NV * NF;
+  static constexpr int total = oA + EPB * 2 * D * NV * NF;
+  static constexpr size_t bytes = sizeof(double) * (size_t)total;
+};
+
+// Phase 2 of vjp_kernel at tangential node t of face (AX, s) of element e: the cotangent the
+// face adds to the node's J_AX^T input (the lift's own-flux part and the Rusanov flux part) and
+// the part it adds to the node's result (dissipation, wave-speed gradient, mirror state or
+// mortar contribution), to sC and sA at [2 AX + s][v][t].
+template <int D, int N, int AX>
+__device__ __forceinline__ void vjp_face(const AdjArgs& A, int64_t e, int level, int s, int t,
+                                         const double* sL, const double* sR, double* sC, double* sA) {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  constexpr int NSUB = 1 << (D - 1);
+  constexpr int a = AX;
+  const int f = 2 * a + s;
+  const size_t ebase = (size_t)e * NP;
+  const int nn = face_node<D, N>(a, s, t);
+  const int32_t* c = A.conn + ((size_t)e * 2 * D + f) * 5;
+  const int kind = c[0];
+  const double coef = A.lift[level][a];
+  const double sign = s ? -1.0 : 1.0;
+  double lo[NV], cotf[NV], accf[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    lo[v] = sL[v * NP + nn];
+    cotf[v] = -sign * coef * lo[v];        // own flux in the lift: L += sign coef (F* - F(q))
+    accf[v] = 0.0;
+  }
+  if (kind == FACE_CONF || kind == FACE_WALL) {
+    double qn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) qn[v] = A.q[(size_t)v * A.plane + ebase + nn];
+    const int kz = (D == 3) ? nn / (n1 * n1) : nn / n1;
+    const double* bz = A.bg + ((size_t)e * n1 + kz) * 4;
+    const double zrb = bz[0], zpb = bz[2];
+    const double zpp = A.pp[ebase + nn];
+    // the node's linearisation from its stored reciprocals (node_lin's values bit for bit)
+    NodeLin<D> Ln;
+    Ln.rinv = sR[nn];
+    Ln.iTheta = sR[NP + nn];
+#pragma unroll
+    for (int b = 0; b < D; ++b) Ln.u[b] = qn[1 + b] * Ln.rinv;
+    Ln.Theta = bz[1] + qn[D + 1];
+    Ln.P = zpb + zpp;
+    Ln.dPdT = A.ph.gamma * Ln.P * Ln.iTheta;
+    if (kind == FACE_CONF) {
+      constexpr int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
+      const size_t no = (size_t)c[1] * NP + nn + (s ? -N : N) * stride_a;
+      double qo[NV], mu[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        qo[v] = A.q[(size_t)v * A.plane + no];
+        mu[v] = sign * coef * (lo[v] - A.lam[(size_t)v * A.plane + no]);
+      }
+      const double c_own = sound_speed<D>(Ln, A.ph.gamma);
+      const double so = neighbour_speed<D>(qo, zrb, zpb, A.pp[no], a, A.ph.gamma);
+      rusanov_vjp_own<D>(qn, Ln, c_own, qo, so, a, s == 1, A.ph.gamma, mu, cotf, accf);
+    } else {
+      // mirror state: momentum along a negated, so its linearisation differs from the node's
+      // only in u_a (an exact negation)
+      double gq[NV], mu[NV], gacc[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) { gq[v] = qn[v]; mu[v] = sign * coef * lo[v]; gacc[v] = 0.0; }
+      gq[1 + a] = -qn[1 + a];
+      NodeLin<D> Lg = Ln;
+      Lg.u[a] = -Ln.u[a];
+      if (s) rusanov_vjp<D>(qn, Ln, gq, Lg, a, A.ph.gamma, mu, accf, gacc);
+      else   rusanov_vjp<D>(gq, Lg, qn, Ln, a, A.ph.gamma, mu, gacc, accf);
+      gacc[1 + a] = -gacc[1 + a];                        // mirror map is its own transpose
+#pragma unroll
+      for (int v = 0; v < NV; ++v) accf[v] += gacc[v];
+    }
+  } else {
+    const int64_t g = (kind == FACE_FINE) ? c[2] : c[1];
+    const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
+    const double* src = A.abuf + (((size_t)g * (1 + NSUB) + slot) * NV) * NF + t;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) accf[v] = src[(size_t)v * NF];
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    sC[(f * NV + v) * NF + t] = cotf[v];
+    sA[(f * NV + v) * NF + t] = accf[v];
+  }
+}
+
+// J(q)^T Lambda for EPB elements per block, in three phases.  (1) One thread per node: Lambda
+// and the node's reciprocals to shared memory.  (2) One thread per face node (the element's
+// 2D (N+1)^(D-1) face nodes spread over its threads): the face's contributions at that node,
+// from its own and its neighbour's state and Lambda; then one thread per node again: the
+// volume cotangents -(2/h_a) D_a^T Lambda.  (3) One thread per node: the contributions of the
+// faces the node lies on, the flux-Jacobian transposes and the epilogue.  The face work of
+// phase 2 runs with every lane of a warp on a face node; done by the node's own thread, only
+// the lanes of face nodes would do it while the FP64 pipe is held for the whole warp.
 template <int D, int N, int EPB>
 __global__ void __launch_bounds__(EPB * ipow(N + 1, D))
 vjp_kernel(const AdjArgs A) {
+  using S = VjpSmem<D, N, EPB>;
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
   constexpr int NSUB = 1 << (D - 1);
-  __shared__ double sD[n1 * n1];
-  __shared__ double sL[EPB][NV][NP];
+  extern __shared__ __align__(16) double vjp_smem[];
+  double* sD = vjp_smem;
   const int tid = threadIdx.x;
   for (int i = tid; i < n1 * n1; i += blockDim.x) sD[i] = A.ops[i];
   const int le = tid / NP, n = tid - le * NP;
+  double* sL = vjp_smem + S::oL + le * NV * NP;
+  double* sR = vjp_smem + S::oR + le * 2 * NP;
+  double* sC = vjp_smem + S::oC + le * 2 * D * NV * NF;
+  double* sA = vjp_smem + S::oA + le * 2 * D * NV * NF;
   const int64_t e = (int64_t)blockIdx.x * EPB + le;
   const bool valid = e < A.E;
   int idx[3];
   idx[0] = n % n1;
   idx[1] = (n / n1) % n1;
   idx[2] = (D == 3) ? n / (n1 * n1) : 0;
-  const size_t base = (size_t)(valid ? e : 0) * NP + n;
-  double q[NV], lam[NV], acc[NV];
+  const size_t ebase = (size_t)(valid ? e : 0) * NP;
+  const size_t base = ebase + n;
+  double q[NV], lam[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     q[v] = valid ? A.q[(size_t)v * A.plane + base] : 0.0;
     lam[v] = valid ? A.lam[(size_t)v * A.plane + base] : 0.0;
-    acc[v] = 0.0;
-    sL[le][v][n] = lam[v];
+    sL[v * NP + n] = lam[v];
   }
   const int level = valid ? A.elem[e * 4] : 0;
   const double* bgp = A.bg + ((size_t)(valid ? e : 0) * n1 + idx[D - 1]) * 4;
@@ -213,14 +325,24 @@ vjp_kernel(const AdjArgs A) {
   const double pb = valid ? bgp[2] : 1.0;
   const double ppn = valid ? A.pp[base] : 0.0;
   const NodeLin<D> L = node_lin<D>(q, rb, Tb, pb, ppn, A.ph);
+  sR[n] = L.rinv;
+  sR[NP + n] = L.iTheta;
   __syncthreads();
-  if (!valid) return;
-  // buoyancy source -rho' g on the vertical momentum
-  acc[0] += -A.ph.g * lam[D];
-  // Every own-node term along axis a goes through J_a(q)^T: the volume cotangent
-  // mu_a = -(2/h_a) D_a^T Lambda, the face lift's -n (2/h)/w0 Lambda and the Rusanov flux part
-  // are summed in cot[a] first and transposed once per axis.
-  double cot[D][NV];
+  // ---- phase 2: face contributions, one face node per thread
+  if (valid) {
+    for (int fi = n; fi < 2 * D * NF; fi += NP) {
+      const int f = fi / NF, t = fi - f * NF;
+      // the axis as a template argument keeps every per-axis index of the face arithmetic
+      // constant, so its arrays stay in registers
+      if (f < 2) vjp_face<D, N, 0>(A, e, level, f & 1, t, sL, sR, sC, sA);
+      else if (D == 2 || f < 4) vjp_face<D, N, 1>(A, e, level, f & 1, t, sL, sR, sC, sA);
+      else vjp_face<D, N, (D == 3 ? 2 : 1)>(A, e, level, f & 1, t, sL, sR, sC, sA);
+    }
+  }
+  // ---- volume cotangents: every own-node term along axis a goes through J_a(q)^T, so the
+  // volume cotangent mu_a = -(2/h_a) D_a^T Lambda, the face lift's own-flux part and the
+  // Rusanov flux part are summed in cot[a] and transposed once per axis
+  double acc[NV], cot[D][NV];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     const int stride = ipow(n1, a);
@@ -231,58 +353,29 @@ vjp_kernel(const AdjArgs A) {
     for (int v = 0; v < NV; ++v) {
       double s = 0.0;
 #pragma unroll
-      for (int i = 0; i < n1; ++i) s += sD[i * n1 + ia] * sL[le][v][b0 + i * stride];
+      for (int i = 0; i < n1; ++i) s += sD[i * n1 + ia] * sL[v * NP + b0 + i * stride];
       cot[a][v] = -s2h * s;
     }
   }
-  // faces
-  double c_own = -1.0;                         // sound speed of this node, formed on first use
+  // buoyancy source -rho' g on the vertical momentum
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  acc[0] = -A.ph.g * lam[D];
+  __syncthreads();
+  if (!valid) return;
+  // ---- phase 3: the contributions of the faces this node lies on
 #pragma unroll
   for (int a = 0; a < D; ++a) {
+    if (idx[a] != 0 && idx[a] != N) continue;
+    const int f = 2 * a + (idx[a] == N ? 1 : 0);
+    int t = 0, mul = 1;
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      if (idx[a] != (s ? N : 0)) continue;
-      const int32_t* c = A.conn + ((size_t)e * 2 * D + 2 * a + s) * 5;
-      const int kind = c[0];
-      const double coef = A.lift[level][a];
-      const double sign = s ? -1.0 : 1.0;
-      // own flux in the lift: L += sign coef (F* - F(q))
+    for (int b = 0; b < D; ++b)
+      if (b != a) { t += idx[b] * mul; mul *= n1; }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) cot[a][v] += -sign * coef * lam[v];
-      if (kind == FACE_CONF) {
-        const int stride_a = (a == 0) ? 1 : (a == 1 ? n1 : n1 * n1);
-        const size_t no = (size_t)c[1] * NP + n + ((s ? 0 : N) - idx[a]) * stride_a;
-        double qo[NV], mu[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          qo[v] = A.q[(size_t)v * A.plane + no];
-          mu[v] = sign * coef * (lam[v] - A.lam[(size_t)v * A.plane + no]);
-        }
-        if (c_own < 0.0) c_own = sound_speed<D>(L, A.ph.gamma);
-        const double so = neighbour_speed<D>(qo, rb, pb, A.pp[no], a, A.ph.gamma);
-        rusanov_vjp_own<D>(q, L, c_own, qo, so, a, s == 1, A.ph.gamma, mu, cot[a], acc);
-      } else if (kind == FACE_WALL) {
-        double gq[NV], mu[NV], gacc[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) { gq[v] = q[v]; mu[v] = sign * coef * lam[v]; gacc[v] = 0.0; }
-        gq[1 + a] = -q[1 + a];
-        const NodeLin<D> Lg = node_lin<D>(gq, rb, Tb, pb, ppn, A.ph);
-        if (s) rusanov_vjp<D>(q, L, gq, Lg, a, A.ph.gamma, mu, acc, gacc);
-        else   rusanov_vjp<D>(gq, Lg, q, L, a, A.ph.gamma, mu, gacc, acc);
-        gacc[1 + a] = -gacc[1 + a];                      // mirror map is its own transpose
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] += gacc[v];
-      } else {
-        int t = 0, mul = 1;
-#pragma unroll
-        for (int b = 0; b < D; ++b)
-          if (b != a) { t += idx[b] * mul; mul *= n1; }
-        const int64_t g = (kind == FACE_FINE) ? c[2] : c[1];
-        const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
-        const double* src = A.abuf + (((size_t)g * (1 + NSUB) + slot) * NV) * NF + t;
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] += src[(size_t)v * NF];
-      }
+    for (int v = 0; v < NV; ++v) {
+      cot[a][v] += sC[(f * NV + v) * NF + t];
+      acc[v] += sA[(f * NV + v) * NF + t];
     }
   }
 #pragma unroll

@@ -401,12 +401,21 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
   bool pdl = (variant == 4 || variant == 2) && mortars && !timed;
   dg_status st = dgi::launch_mortars(m, qs, pp_in, s);
   if (st != DG_OK) return st;
+  // a timed stage spans the stage kernel and, in layout 5, the face kernel before it
+  if (timed) {
+    while (m->ev.size() < m->ev_used + 2) {
+      cudaEvent_t e;
+      CU(cudaEventCreate(&e));
+      m->ev.push_back(e);
+    }
+    CU(cudaEventRecord(m->ev[m->ev_used], s));
+  }
   if (variant == 5) {
     const int64_t C = (int64_t)m->conf.size() / 3, Bn = (int64_t)m->bnd.size() / 3;
     CU(reserve(m->d_fbuf, m->c_fbuf, (size_t)(C + Bn > 0 ? C + Bn : 1) * m->NV * m->NF * m->tsize));
     dgk::FaceArgs F{qs, pp_in, m->d_fbuf, plane(m), (int32_t)C, (int32_t)Bn, m->d_fconf, m->d_fbnd, bgt(m),
                     (float)m->ph.gamma, m->ph};
-    const bool fpdl = mortars;   // the face kernel follows the mortar kernel directly
+    const bool fpdl = mortars && !timed;   // the face kernel follows the mortar kernel directly
     CU(m->prec == DG_FP64
            ? (m->D == 2 ? dgk::launch_face_f64_2d(m->N, F, fpdl, s) : dgk::launch_face_f64_3d(m->N, F, fpdl, s))
            : (m->D == 2 ? dgk::launch_face_f32_2d(m->N, F, fpdl, s) : dgk::launch_face_f32_3d(m->N, F, fpdl, s)));
@@ -416,14 +425,6 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
   dgi::fill_stage_args(m, qs, pp_in, qn, out, pp_out, mode, dt, ca, cb, &A);
   A.variant = variant;
   A.after_mortar = pdl ? 1 : 0;
-  if (timed) {
-    while (m->ev.size() < m->ev_used + 2) {
-      cudaEvent_t e;
-      CU(cudaEventCreate(&e));
-      m->ev.push_back(e);
-    }
-    CU(cudaEventRecord(m->ev[m->ev_used], s));
-  }
   bool ok = m->prec == DG_FP64
                 ? (m->D == 2 ? dgk::launch_stage_f64_2d(m->N, A, s) : dgk::launch_stage_f64_3d(m->N, A, s))
                 : (m->D == 2 ? dgk::launch_stage_f32_2d(m->N, A, s) : dgk::launch_stage_f32_3d(m->N, A, s));
@@ -533,7 +534,9 @@ dg_status vjp_pass(dg_mesh* m, const double* q, const double* pp, const double* 
       A.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
       A.lift[l][a] = A.inv2h[l][a] / m->basis.w[0];
     }
-  if (!dgk::launch_vjp(m->D, m->N, A, s)) return fail(m, DG_ERR_UNSUPPORTED, "adjoint kernel not compiled");
+  cudaError_t cfg = cudaSuccess;
+  if (!dgk::launch_vjp(m->D, m->N, A, s, cfg)) return fail(m, DG_ERR_UNSUPPORTED, "adjoint kernel not compiled");
+  CU(cfg);
   CU(cudaGetLastError());
   return DG_OK;
 }

@@ -137,7 +137,8 @@ cudaError_t launch_visc_add(int32_t E, int n1, int D, const double* V, double co
                             cudaStream_t s);
 
 // Adjoint (FP64): right-hand-side vector-Jacobian products and their helpers.
-bool launch_vjp(int D, int N, const AdjArgs& A, cudaStream_t s);
+// false: (D, N) not compiled; err: the kernel configuration's error, if any
+bool launch_vjp(int D, int N, const AdjArgs& A, cudaStream_t s, cudaError_t& err);
 bool launch_mortar_vjp(int D, int N, const MortarAdjArgs& A, cudaStream_t s);
 cudaError_t launch_theta_state(int prec, int32_t E, int n1, int D, const double* bg,
                                const double* theta, double theta0, void* q, int64_t plane,

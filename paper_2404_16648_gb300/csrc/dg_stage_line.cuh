@@ -243,7 +243,7 @@ __device__ __forceinline__ void line_pass(const LineCtx<T>& C, T (&out)[(N + 1) 
   const NodeDer<T> ndf{rinvf, thf};
   const T* nb = C.sNb + (2 * a + h) * NBS;
   const int kd = C.kind[a];
-  T Fs[NV];
+  const T coef = h ? -C.lc[a] : C.lc[a];
   if (kd == FACE_WALL || kd == FACE_CONF) {
     const T so = wave_speed<T>(qf, ndf, bgf, ppf, a, C.gamma);
     T qo[NV], Fn[NV], sn;
@@ -258,22 +258,19 @@ __device__ __forceinline__ void line_pass(const LineCtx<T>& C, T (&out)[(N + 1) 
       for (int v = 0; v < NV; ++v) qo[v] = nb[v * NF + L];
       sn = face_side<T, D>(qo, bgf, nb[NV * NF + L], a, C.gamma, Fn);
     }
-    // Rusanov flux with the thread's side as the low one (h = 1) or the high one (h = 0): the
-    // average is symmetric and the jump changes sign (an exact negation), so one code path for
-    // both halves of the warp gives the bits of the two oriented calls
-    const T hl = mul_rn((T)0.5, so > sn ? so : sn);
+    // Rusanov flux F* = (Ff + Fn)/2 - (lambda/2) s (qo - qf), s = +1 with the thread's side as
+    // the low one (h = 1), -1 as the high one (h = 0); its lift coef (F* - Ff), coef = -s lc,
+    // is (coef/2) (Fn - Ff) + lc (lambda/2) (qo - qf): two differences and two fma per
+    // variable, the same expression for both halves of the warp
+    const T cA = mul_rn((T)0.5, coef);
+    const T cB = mul_rn(C.lc[a], mul_rn((T)0.5, so > sn ? so : sn));
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      const T d = sub_rn(qo[v], qf[v]);
-      Fs[v] = sub_rn(mul_rn((T)0.5, add_rn(Ff[v], Fn[v])), mul_rn(hl, h ? d : -d));
-    }
+    for (int v = 0; v < NV; ++v)
+      out[0][v] = fma(cB, sub_rn(qo[v], qf[v]), fma(cA, sub_rn(Fn[v], Ff[v]), out[0][v]));
   } else {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fs[v] = nb[v * NF + L];
+    for (int v = 0; v < NV; ++v) out[0][v] = fma(coef, nb[v * NF + L] - Ff[v], out[0][v]);
   }
-  const T coef = h ? -C.lc[a] : C.lc[a];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) out[0][v] = fma(coef, Fs[v] - Ff[v], out[0][v]);
 }
 
 template <class T, int N>
