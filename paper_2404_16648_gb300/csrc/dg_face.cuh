@@ -38,9 +38,6 @@ template <class T, int D, int N>
 __global__ void __launch_bounds__(256) face_kernel(const __grid_constant__ FaceArgs A) {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
   constexpr int FPB = face_per_block<D, N>();
-  // the stage kernel launched after this grid may start now; it waits for this grid's
-  // completion before it reads the face buffer
-  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   const int lf = threadIdx.x / NF, t = threadIdx.x - lf * NF;
   const int64_t slot = (int64_t)blockIdx.x * FPB + lf;
   if (lf < FPB && slot < (int64_t)A.C + A.B) {
@@ -92,6 +89,11 @@ __global__ void __launch_bounds__(256) face_kernel(const __grid_constant__ FaceA
 #pragma unroll
     for (int v = 0; v < NV; ++v) dst[v * NF + t] = Fs[v];
   }
+  // the stage kernel launched after this grid may start once every CTA of this grid has got
+  // here (its prologue then overlaps this grid's last wave); it waits for this grid's
+  // completion before it reads the face buffer.  Signalled at the start instead, the stage
+  // kernel's CTAs would fill the SMs while most of this grid still had to run.
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   // launched as the programmatic dependent of this stage's mortar kernel, this grid completes
   // only after it, so the stage kernel's wait for this grid covers the mortar fluxes too
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
