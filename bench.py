@@ -606,7 +606,8 @@ def run_batch(pkg, steps=500, compare_steps=50, check_steps=5, peaks=None):
             "shape": shape,
             "one_at_a_time_value": rate_s, "speedup_vs_one_at_a_time": rate_b / rate_s,
             "bit_identical_to_one_at_a_time": bool(identical), "identity_steps": check_steps,
-            "layouts": {"node": int(np.sum(layouts == 1)), "column_async": int(np.sum(layouts == 2))},
+            "layouts": {"node": int(np.sum(layouts == 1)), "column_async": int(np.sum(layouts == 2)),
+                        "column_async_face_items": int(np.sum(layouts == 5))},
             "roofline": {"bound": "mixed", "roofline_ms_per_step": 1e3 * bound_s,
                          "frac": 1e3 * bound_s / ms_step,
                          "note": "sum over (precision, N) groups of max(algorithmic bytes / measured "

@@ -300,7 +300,8 @@ dg_status dg_ke_grad(dg_mesh* mesh, const void* q, void* out, void* stream);
  * replayed.  The members keep their state in their own buffers (dg_get_state etc. work as
  * usual); a member must not be regridded while in a batch (DG_ERR_STATE).  Members may have
  * different sizes, degrees and precisions.  A member advanced in the batch gets the bits that
- * dg_step gives it with the same stage layout. */
+ * dg_step gives it with the same stage layout (an FP32 2D member set to layout 5 is switched to
+ * layout 2 by dg_batch_create: the persistent launch has layout 5 for FP64 members only). */
 typedef struct dg_batch dg_batch;
 
 /* `meshes`: `count` distinct meshes (not owned). */
@@ -318,11 +319,13 @@ dg_status dg_batch_sync(dg_batch* batch);
  * write only scratch buffers, so the states are untouched).  For the persistent launch of the 2D
  * members it chooses, greedily and groups with the most work first: the register budget (the
  * kernel compiled for 2 or for 4 resident CTAs per SM), per (precision, N) group the element
- * tile -- node layout, (N+1)^2 threads per element and 128 / (N+1)^2 elements per CTA pass, or
- * column layout, N+1 threads per element and 128 / (N+1) elements per pass -- and the tiles per
- * work item (1, 2, 4 or 8).  For 3D groups it keeps the faster of the two grouped layouts.  The
- * layout choice is also applied to each member's own launches.  `layouts` (count int32, may be
- * NULL) receives the chosen layout per member (1 node or 2 column, see DG_OPT_STAGE_KERNEL). */
+ * tile -- node layout, (N+1)^2 threads per element and 128 / (N+1)^2 elements per CTA pass,
+ * column layout, N+1 threads per element and 128 / (N+1) elements per pass, or (FP64 groups)
+ * the column layout that reads the Rusanov fluxes of conforming and wall faces from face work
+ * items of the same launch -- and the tiles per work item (1, 2, 4 or 8).  For 3D groups it
+ * keeps the faster of the two grouped layouts.  The layout choice is also applied to each
+ * member's own launches.  `layouts` (count int32, may be NULL) receives the chosen layout per
+ * member (1 node, 2 column or 5 column with face fluxes, see DG_OPT_STAGE_KERNEL). */
 dg_status dg_batch_autotune(dg_batch* batch, int32_t reps, int32_t* layouts);
 /* The persistent launch's shapes: out[0] resident CTAs per SM its register budget is compiled
  * for, out[1] element tiles per stage item, out[2] grid (CTAs), out[3] work items per stage,

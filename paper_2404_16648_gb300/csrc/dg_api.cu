@@ -322,6 +322,18 @@ dg_status set_error(dg_mesh* m, dg_status st, const char* msg) {
   return st;
 }
 
+void fill_face_args(const dg_mesh* m, const void* qs, const void* pp_in, dgk::FaceArgs* F) {
+  const int64_t C = (int64_t)m->conf.size() / 3, Bn = (int64_t)m->bnd.size() / 3;
+  *F = dgk::FaceArgs{qs, pp_in, m->d_fbuf, plane(m), (int32_t)C, (int32_t)Bn, m->d_fconf, m->d_fbnd, bgt(m),
+                     (float)m->ph.gamma, m->ph};
+}
+
+dg_status ensure_face_buffer(dg_mesh* m) {
+  const int64_t C = (int64_t)m->conf.size() / 3, Bn = (int64_t)m->bnd.size() / 3;
+  CU(reserve(m->d_fbuf, m->c_fbuf, (size_t)(C + Bn > 0 ? C + Bn : 1) * m->NV * m->NF * m->tsize));
+  return DG_OK;
+}
+
 void fill_mortar_args(const dg_mesh* m, const void* qs, const void* pp_in, dgk::MortarArgs* M) {
   const bool part = m->nparts > 1;
   *M = dgk::MortarArgs{qs, pp_in, m->d_mbuf, plane(m), (int32_t)(part ? m->G_part : m->G), m->d_groups,
@@ -411,10 +423,10 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
     CU(cudaEventRecord(m->ev[m->ev_used], s));
   }
   if (variant == 5) {
-    const int64_t C = (int64_t)m->conf.size() / 3, Bn = (int64_t)m->bnd.size() / 3;
-    CU(reserve(m->d_fbuf, m->c_fbuf, (size_t)(C + Bn > 0 ? C + Bn : 1) * m->NV * m->NF * m->tsize));
-    dgk::FaceArgs F{qs, pp_in, m->d_fbuf, plane(m), (int32_t)C, (int32_t)Bn, m->d_fconf, m->d_fbnd, bgt(m),
-                    (float)m->ph.gamma, m->ph};
+    st = dgi::ensure_face_buffer(m);
+    if (st != DG_OK) return st;
+    dgk::FaceArgs F;
+    dgi::fill_face_args(m, qs, pp_in, &F);
     const bool fpdl = mortars && !timed;   // the face kernel follows the mortar kernel directly
     CU(m->prec == DG_FP64
            ? (m->D == 2 ? dgk::launch_face_f64_2d(m->N, F, fpdl, s) : dgk::launch_face_f64_3d(m->N, F, fpdl, s))

@@ -11,8 +11,9 @@
 // stage 1, which reads q^n and writes only scratch): the register budget (2 or 4 resident CTAs
 // of 128 threads per SM), per (precision, N) group the element tile (node layout: (N+1)^2
 // threads per element, 128 / (N+1)^2 elements per CTA pass; column layout: N+1 threads per
-// element, 128 / (N+1) elements per pass) and the tiles per work item; for 3D groups the faster
-// of the two grouped layouts.
+// element, 128 / (N+1) elements per pass; for FP64 groups also the column layout that reads the
+// conforming and wall fluxes from face items of the same launch, stage layout 5) and the tiles
+// per work item; for 3D groups the faster of the two grouped layouts.
 #include <algorithm>
 #include <cstdio>
 #include <map>
@@ -32,7 +33,8 @@ struct dg_batch {
     int2* d_map[3] = {nullptr, nullptr, nullptr};
     dgk::StageArgs* d_tab[3] = {nullptr, nullptr, nullptr};   // per stage
   };
-  // 2D members: the persistent launch; layout 0 node, 1 column-async
+  // 2D members: the persistent launch; layout 0 node, 1 column-async, 2 column-async with the
+  // face buffer (stage layout 5, FP64 only)
   struct PGroup {
     int prec32 = 0, N = 1, layout = 1;
     std::vector<int> members;
@@ -51,7 +53,8 @@ struct dg_batch {
   size_t items_cap = 0;
   dgk::StageArgs* d_ptab[3] = {nullptr, nullptr, nullptr};   // per stage, per member
   dgk::MortarArgs* d_mtab[3] = {nullptr, nullptr, nullptr};
-  int32_t* d_need = nullptr;             // per member: mortar groups
+  dgk::FaceArgs* d_ftab[3] = {nullptr, nullptr, nullptr};
+  int32_t* d_need = nullptr;             // per member: mortar groups, plus face slots in layout 5
   int32_t* d_counters = nullptr;         // [3][1 + members]: item counter, mortar groups done
   int32_t* d_status = nullptr;           // 1 after a wait for mortar fluxes ran out
   cudaStream_t stream = nullptr;
@@ -105,6 +108,12 @@ int tile_elems(const dg_batch::PGroup& g) {
   return g.layout == 0 ? dgk::batch_epb_node(g.N) : dgk::batch_epb_col(g.N);
 }
 
+// Face slots (conforming, then boundary faces) of a layout-5 member.
+int64_t face_slots(const dg_mesh* m) { return (int64_t)(m->conf.size() / 3 + m->bnd.size() / 3); }
+
+// The single-mesh stage layout of a 2D group's layout.
+int stage_layout(int glayout) { return glayout == 0 ? 1 : (glayout == 1 ? 2 : 5); }
+
 // The work items of the persistent launch for the current shapes (the same list serves the
 // three stages), the launch's shared memory and its grid.
 dg_status build_items(dg_batch* b) {
@@ -122,6 +131,19 @@ dg_status build_items(dg_batch* b) {
     }
     if (any) smem = std::max(smem, dgk::batch_body_smem_bytes(g.prec32, g.N, 2));
   }
+  // then the face items of layout-5 members: four passes of slots each
+  std::vector<int32_t> need(b->meshes.size(), 0);
+  for (size_t i = 0; i < b->meshes.size(); ++i) need[i] = b->meshes[i]->D == 2 ? (int32_t)b->meshes[i]->G : 0;
+  for (const auto& g : b->pgroups) {
+    if (g.layout != 2) continue;
+    const int per = 4 * dgk::batch_fpb(g.N);
+    for (int idx : g.members) {
+      const int64_t F = face_slots(b->meshes[idx]);
+      for (int64_t f = 0; f < F; f += per)
+        items.push_back(make_int4(dgk::batch_code(2, 2, 0, g.N), idx, (int)f, (int)std::min<int64_t>(per, F - f)));
+      need[idx] += (int32_t)F;
+    }
+  }
   // stage items, the groups with the most work per element first
   std::vector<const dg_batch::PGroup*> order;
   for (const auto& g : b->pgroups) order.push_back(&g);
@@ -137,7 +159,7 @@ dg_status build_items(dg_batch* b) {
         items.push_back(make_int4(dgk::batch_code(1, g->layout, g->prec32, g->N), idx, (int)e,
                                   (int)std::min<int64_t>(per, E - e)));
     }
-    smem = std::max(smem, dgk::batch_body_smem_bytes(g->prec32, g->N, g->layout));
+    smem = std::max(smem, dgk::batch_body_smem_bytes(g->prec32, g->N, g->layout == 2 ? 3 : g->layout));
   }
   if (items.size() > b->items_cap) {
     if (b->d_items) cudaFree(b->d_items);
@@ -148,6 +170,7 @@ dg_status build_items(dg_batch* b) {
   }
   if (!items.empty())
     BCU(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  BCU(cudaMemcpy(b->d_need, need.data(), need.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
   b->nitems = (int)items.size();
   b->smem = smem;
   int per_sm = 0, dev = 0, sms = 0;
@@ -179,22 +202,28 @@ dg_status build_tables(dg_batch* b) {
     for (int s = 0; s < 3; ++s) {
       std::vector<dgk::StageArgs> tab(M);
       std::vector<dgk::MortarArgs> mt(M);
+      std::vector<dgk::FaceArgs> ft(M);
       for (size_t i = 0; i < M; ++i) {
         dg_mesh* m = b->meshes[i];
         if (m->D != 2) continue;
+        // every FP64 member gets its face buffer, so that the autotuner may pick layout 5
+        if (m->prec == DG_FP64) {
+          dg_status st = dgi::ensure_face_buffer(m);
+          if (st != DG_OK) return bfail(b, st, m->err);
+        }
         const void* qs; void* pp_in; void* out; void* pp_out; double ca, cb;
         stage_buffers(m, s, &qs, &pp_in, &out, &pp_out, &ca, &cb);
         dgi::fill_stage_args(m, qs, pp_in, m->q[0], out, pp_out, 1, b->dt[i], ca, cb, &tab[i]);
         dgi::fill_mortar_args(m, qs, pp_in, &mt[i]);
+        dgi::fill_face_args(m, qs, pp_in, &ft[i]);
       }
       if (!b->d_ptab[s]) BCU(cudaMalloc(&b->d_ptab[s], M * sizeof(dgk::StageArgs)));
       if (!b->d_mtab[s]) BCU(cudaMalloc(&b->d_mtab[s], M * sizeof(dgk::MortarArgs)));
+      if (!b->d_ftab[s]) BCU(cudaMalloc(&b->d_ftab[s], M * sizeof(dgk::FaceArgs)));
       BCU(cudaMemcpy(b->d_ptab[s], tab.data(), M * sizeof(dgk::StageArgs), cudaMemcpyHostToDevice));
       BCU(cudaMemcpy(b->d_mtab[s], mt.data(), M * sizeof(dgk::MortarArgs), cudaMemcpyHostToDevice));
+      BCU(cudaMemcpy(b->d_ftab[s], ft.data(), M * sizeof(dgk::FaceArgs), cudaMemcpyHostToDevice));
     }
-    std::vector<int32_t> need(M, 0);
-    for (size_t i = 0; i < M; ++i) need[i] = b->meshes[i]->D == 2 ? (int32_t)b->meshes[i]->G : 0;
-    BCU(cudaMemcpy(b->d_need, need.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice));
   }
   b->tables_dirty = false;
   return DG_OK;
@@ -209,6 +238,7 @@ dg_status launch_persistent(dg_batch* b, int st, cudaStream_t s) {
   B.nitems = b->nitems;
   B.stage = b->d_ptab[st];
   B.mortar = b->d_mtab[st];
+  B.face = b->d_ftab[st];
   B.need = b->d_need;
   B.fetch = b->d_counters + (size_t)st * (1 + M);
   B.done = B.fetch + 1;
@@ -306,12 +336,15 @@ dg_status dg_batch_create(dg_mesh* const* meshes, int32_t count, dg_batch** out)
     b->generations.push_back(m->generation);
     b->dt.push_back(0.0);
     auto key = std::make_tuple(m->prec, m->D, m->N);
+    // the persistent launch has the face-buffer layout for FP64 members only: an FP32 member set
+    // to it runs the column layout, in the batch and in its own launches alike
+    if (m->D == 2 && m->prec != DG_FP64 && m->variant == 5) m->variant = 2;
     if (m->D == 2) {
       auto it = pid.find(key);
       if (it == pid.end()) {
         dg_batch::PGroup g;
         g.prec32 = m->prec == DG_FP32_PERT ? 1 : 0; g.N = m->N;
-        g.layout = m->variant == 1 ? 0 : 1;
+        g.layout = m->variant == 1 ? 0 : (m->variant == 5 && g.prec32 == 0 ? 2 : 1);
         pid[key] = (int)b->pgroups.size();
         b->pgroups.push_back(g);
         it = pid.find(key);
@@ -371,6 +404,7 @@ void dg_batch_destroy(dg_batch* b) {
   for (int s = 0; s < 3; ++s) {
     if (b->d_ptab[s]) cudaFree(b->d_ptab[s]);
     if (b->d_mtab[s]) cudaFree(b->d_mtab[s]);
+    if (b->d_ftab[s]) cudaFree(b->d_ftab[s]);
   }
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_need) cudaFree(b->d_need);
@@ -523,11 +557,17 @@ dg_status dg_batch_autotune(dg_batch* b, int32_t reps, int32_t* layouts) {
       if (st != DG_OK) return finish(st);
       for (size_t oi : order) {
         auto& g = b->pgroups[oi];
-        g.layout ^= 1;
-        float t = 0.f;
-        st = time_persistent(b, reps, e0, e1, &t);
-        if (st != DG_OK) return finish(st);
-        if (t < cur) cur = t; else g.layout ^= 1;
+        const int keep = g.layout;
+        int bestl = keep;
+        for (int cand : {0, 1, 2}) {
+          if (cand == keep || (cand == 2 && g.prec32)) continue;
+          g.layout = cand;
+          float t = 0.f;
+          st = time_persistent(b, reps, e0, e1, &t);
+          if (st != DG_OK) return finish(st);
+          if (t < cur) { cur = t; bestl = cand; }
+        }
+        g.layout = bestl;
       }
       int kbest = b->tiles_per_item;
       for (int k : {1, 4, 8}) {
@@ -548,7 +588,7 @@ dg_status dg_batch_autotune(dg_batch* b, int32_t reps, int32_t* layouts) {
     b->tiles_per_item = best_k;
     for (size_t i = 0; i < b->pgroups.size(); ++i) {
       b->pgroups[i].layout = best_layouts[i];
-      for (int idx : b->pgroups[i].members) b->meshes[idx]->variant = best_layouts[i] == 0 ? 1 : 2;
+      for (int idx : b->pgroups[i].members) b->meshes[idx]->variant = stage_layout(best_layouts[i]);
     }
     b->items_dirty = true;
   }
@@ -557,7 +597,7 @@ dg_status dg_batch_autotune(dg_batch* b, int32_t reps, int32_t* layouts) {
     for (auto& g : b->groups)
       for (int idx : g.members) layouts[idx] = g.layout;
     for (auto& g : b->pgroups)
-      for (int idx : g.members) layouts[idx] = g.layout == 0 ? 1 : 2;
+      for (int idx : g.members) layouts[idx] = stage_layout(g.layout);
   }
   return finish(DG_OK);
 }

@@ -6,14 +6,18 @@
 // tile of elements of one member: volume term, face lifts, Shu-Osher combination, P').  A fixed
 // grid of 128-thread CTAs, sized to what stays resident, takes items in order from an atomic
 // counter until the array is exhausted.  Item codes select the body: the node-per-thread
-// layout (layout 1 of the single-mesh kernels) or the column layout with asynchronous staging
-// (layout 2), instantiated for both precisions and N = 1..8; a tile is the elements one pass of
-// that body covers, and an item holds `count` elements (a multiple of the tile).
+// layout (layout 1 of the single-mesh kernels), the column layout with asynchronous staging
+// (layout 2) or, for FP64 members, that layout reading the Rusanov fluxes of conforming and
+// wall faces from a face buffer (layout 5), instantiated for N = 1..8; a tile is the elements
+// one pass of that body covers, and an item holds `count` elements (a multiple of the tile).
+// A layout-5 member also has face items, queued with the mortar items: `count` face slots, one
+// thread per face node, the arithmetic of face_kernel.
 //
-// A stage item reads the mortar fluxes of its member, which the member's mortar items write in
-// the same launch.  Each member has a counter of mortar groups done: a mortar item adds its
-// groups after its writes are fenced, and a CTA that takes a stage item waits (thread 0, with
-// an iteration limit) until its member's count is complete.  This cannot deadlock: items are
+// A stage item reads the mortar fluxes (and, in layout 5, the face fluxes) of its member, which
+// the member's mortar and face items write in the same launch.  Each member has a counter of
+// mortar groups and face slots done: a mortar or face item adds its count after its writes are
+// fenced, and a CTA that takes a stage item waits (thread 0, with an iteration limit) until its
+// member's count is complete.  This cannot deadlock: items are
 // taken in array order, so every mortar item of the member was taken earlier by a CTA that is
 // running and that waits for nothing.  If the limit runs out the kernel records it in
 // `status` and goes on (the host reports DG_ERR_TIMEOUT); the results are then not valid.
@@ -22,6 +26,9 @@
 // the unit compiled without implicit contraction), so a member advanced in the batch gets the
 // bits it gets from dg_step with the same layout.
 #pragma once
+#include <type_traits>
+
+#include "dg_face.cuh"
 #include "dg_launch.hpp"
 #include "dg_stage_async.cuh"
 
@@ -31,10 +38,10 @@ constexpr int kBatchThreads = 128;
 // spins of __nanosleep(64) before a wait for mortar fluxes gives up (of the order of a second)
 constexpr int kBatchSpinLimit = 1 << 23;
 
-// Item code: bit 0 kind (0 mortar, 1 stage), bit 1 layout (0 node, 1 column-async),
-// bit 2 precision (0 FP64, 1 FP32), bits 3.. N.
+// Item code: bits 0-1 kind (0 mortar, 1 stage, 2 face), bits 2-3 layout (0 node, 1 column-async,
+// 2 column-async with the face buffer, FP64 only), bit 4 precision (0 FP64, 1 FP32), bits 5.. N.
 __host__ __device__ constexpr int batch_code(int kind, int layout, int prec32, int N) {
-  return kind | (layout << 1) | (prec32 << 2) | (N << 3);
+  return kind | (layout << 2) | (prec32 << 4) | (N << 5);
 }
 
 // Elements per pass of the node layout in a 128-thread CTA (NP = (N+1)^2 threads each).
@@ -45,13 +52,16 @@ __host__ __device__ constexpr int batch_epb_node(int N) {
 __host__ __device__ constexpr int batch_epb_col(int N) { return kBatchThreads / (N + 1); }
 // Mortar groups per pass (2 (N + 1) threads each).
 __host__ __device__ constexpr int batch_gpb(int N) { return kBatchThreads / (2 * (N + 1)); }
+// Face slots per pass of a face item (N + 1 threads each).
+__host__ __device__ constexpr int batch_fpb(int N) { return kBatchThreads / (N + 1); }
 
 struct BatchArgs {
   const int4* items;         // {code, member, first element / group, count}
   int32_t nitems;
   const StageArgs* stage;    // per member: the stage's arguments
   const MortarArgs* mortar;  // per member: the stage's mortar arguments
-  const int32_t* need;       // per member: mortar groups (0: no hanging faces)
+  const FaceArgs* face;      // per member: the stage's face-kernel arguments (layout 5)
+  const int32_t* need;       // per member: mortar groups, plus face slots in layout 5
   int32_t* fetch;            // item counter of this stage (zero before the launch)
   int32_t* done;             // per member: mortar groups finished in this stage (zero before)
   int32_t* status;           // set to 1 when a wait for mortar fluxes ran out
@@ -191,6 +201,23 @@ __device__ __noinline__ void batch_mortar_item(const BatchArgs& B, int member, i
   if (threadIdx.x == 0) atomicAdd(B.done + member, count);
 }
 
+// A face item: F* of face slots first .. first + count - 1 of a 2D FP64 member, one thread per
+// face node, then the member's counter is advanced once every thread's stores are fenced.
+template <int N>
+__device__ __noinline__ void batch_face_item(const BatchArgs& B, int member, int64_t first, int count) {
+  constexpr int NF = N + 1, FPB = batch_fpb(N);
+  const FaceArgs& A = B.face[member];
+  const int lf = threadIdx.x / NF, t = threadIdx.x - lf * NF;
+  const int64_t end = first + count;
+  for (int64_t s0 = first; s0 < end; s0 += FPB) {
+    const int64_t slot = s0 + lf;
+    if (lf < FPB && slot < end) face_flux_node<double, 2, N>(A, slot, t);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(B.done + member, count);
+}
+
 __device__ __forceinline__ int ld_acquire_gpu(const int32_t* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
@@ -221,10 +248,12 @@ __device__ __forceinline__ void batch_wait_mortars(const BatchArgs& B, int membe
 template <class T, int N, int LAYOUT>
 __device__ __noinline__ void batch_stage_item(const StageArgs& A, int64_t first, int count) {
   constexpr int EPB = LAYOUT == 0 ? batch_epb_node(N) : batch_epb_col(N);
+  static_assert(LAYOUT != 2 || std::is_same<T, double>::value, "the face-buffer layout is FP64 only");
   const int64_t end = first + count;
   for (int64_t e0 = first; e0 < end; e0 += EPB) {
     if constexpr (LAYOUT == 0) stage_body_node<T, 2, N, EPB>(A, e0);
-    else                       stage_body_async<T, 2, N, EPB>(A, e0);
+    else if constexpr (LAYOUT == 1) stage_body_async<T, 2, N, EPB>(A, e0);
+    else                       stage_body_async<T, 2, N, EPB, true>(A, e0);
     __syncthreads();   // the next pass rewrites the shared tiles
   }
 }
@@ -234,10 +263,13 @@ __device__ __forceinline__ void batch_dispatch_n(const BatchArgs& B, int kind, i
                                                  int64_t first, int count) {
   if (kind == 0) {
     batch_mortar_item<T, N>(B, member, first, count);
+  } else if (kind == 2) {
+    if constexpr (std::is_same<T, double>::value) batch_face_item<N>(B, member, first, count);
   } else {
     batch_wait_mortars(B, member);
     if (layout == 0) batch_stage_item<T, N, 0>(B.stage[member], first, count);
-    else             batch_stage_item<T, N, 1>(B.stage[member], first, count);
+    else if (layout == 1) batch_stage_item<T, N, 1>(B.stage[member], first, count);
+    else if constexpr (std::is_same<T, double>::value) batch_stage_item<T, N, 2>(B.stage[member], first, count);
   }
 }
 
@@ -269,19 +301,20 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_stage_kernel(const 
     const int it = s_item;
     if (it >= B.nitems) return;
     const int4 w = B.items[it];
-    const int kind = w.x & 1, layout = (w.x >> 1) & 1, prec32 = (w.x >> 2) & 1, N = w.x >> 3;
+    const int kind = w.x & 3, layout = (w.x >> 2) & 3, prec32 = (w.x >> 4) & 1, N = w.x >> 5;
     if (prec32) batch_dispatch<float>(B, kind, layout, N, w.y, (int64_t)w.z, w.w);
     else        batch_dispatch<double>(B, kind, layout, N, w.y, (int64_t)w.z, w.w);
   }
 }
 
-// Dynamic shared memory of the bodies per (precision, N, layout 0 node / 1 column / 2 mortar);
-// a launch takes the largest over the bodies its items use.
+// Dynamic shared memory of the bodies per (precision, N, layout 0 node / 1 column / 2 mortar /
+// 3 column with the face buffer); a launch takes the largest over the bodies its items use
+// (face items use none).
 template <class T, int N>
 constexpr size_t batch_body_smem(int layout) {
   return layout == 0 ? node_smem_bytes<T, 2, N, batch_epb_node(N)>()
-         : layout == 1 ? async_smem_bytes<T, 2, N, batch_epb_col(N)>()
-                       : batch_mortar_smem_bytes<T, N>();
+         : (layout == 1 || layout == 3) ? async_smem_bytes<T, 2, N, batch_epb_col(N)>()
+                                        : batch_mortar_smem_bytes<T, N>();
 }
 
 inline size_t batch_body_smem_any(int prec32, int N, int layout) {

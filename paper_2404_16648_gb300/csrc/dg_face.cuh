@@ -34,61 +34,66 @@ __host__ __device__ constexpr int face_per_block() {
   return ipow(N + 1, D - 1) >= 256 ? 1 : 256 / ipow(N + 1, D - 1);
 }
 
+// F* of face slot `slot` at its tangential node t, to the face buffer.
+template <class T, int D, int N>
+__device__ __forceinline__ void face_flux_node(const FaceArgs& A, int64_t slot, int t) {
+  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  const T* qs = (const T*)A.qs;
+  const T* ppl = (const T*)A.pp_in;
+  const T gamma = gamma_of<T>(A.ph, A.gammaf);
+  T Fs[NV];
+  if (slot < A.C) {
+    const int32_t* r = A.conf + slot * 3;
+    const int64_t el = r[0], eh = r[1];
+    const int a = r[2];
+    const int nm = face_node<D, N>(a, 1, t), np = face_node<D, N>(a, 0, t);
+    const int k = (D == 3) ? nm / (n1 * n1) : nm / n1;
+    const T* b = (const T*)A.bgt + ((size_t)el * n1 + k) * 4;
+    const NodeBg<T> bg{b[0], b[1], b[2]};
+    T qm[NV], qp[NV], Fm[NV], Fp[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      qm[v] = qs[(size_t)v * A.plane + (size_t)el * NP + nm];
+      qp[v] = qs[(size_t)v * A.plane + (size_t)eh * NP + np];
+    }
+    const T sm = face_side<T, D>(qm, bg, ppl[(size_t)el * NP + nm], a, gamma, Fm);
+    const T sp = face_side<T, D>(qp, bg, ppl[(size_t)eh * NP + np], a, gamma, Fp);
+    rusanov<T, D>(qm, Fm, sm, qp, Fp, sp, Fs);
+  } else {
+    const int32_t* r = A.bnd + (slot - A.C) * 3;
+    const int64_t e = r[0];
+    const int a = r[1], s = r[2];
+    const int n = face_node<D, N>(a, s, t);
+    const int k = (D == 3) ? n / (n1 * n1) : n / n1;
+    const T* b = (const T*)A.bgt + ((size_t)e * n1 + k) * 4;
+    const NodeBg<T> bg{b[0], b[1], b[2]};
+    T q[NV], qo[NV], Fo[NV], Fn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = qs[(size_t)v * A.plane + (size_t)e * NP + n];
+    const T pp = ppl[(size_t)e * NP + n];
+    const NodeDer<T> nd = node_der<T, D>(q, bg);
+    flux_axis<T, D>(q, nd, pp, a, Fo);
+    const T so = wave_speed<T>(q, nd, bg, pp, a, gamma);
+    // mirror state: same Theta, rho and P', normal momentum negated (reading R5)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) qo[v] = q[v];
+    qo[1 + a] = -q[1 + a];
+    flux_axis<T, D>(qo, nd, pp, a, Fn);
+    if (s) rusanov<T, D>(q, Fo, so, qo, Fn, so, Fs);
+    else   rusanov<T, D>(qo, Fn, so, q, Fo, so, Fs);
+  }
+  T* dst = (T*)A.fbuf + (size_t)slot * NV * NF;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) dst[v * NF + t] = Fs[v];
+}
+
 template <class T, int D, int N>
 __global__ void __launch_bounds__(256) face_kernel(const __grid_constant__ FaceArgs A) {
-  constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
+  constexpr int NF = ipow(N + 1, D - 1);
   constexpr int FPB = face_per_block<D, N>();
   const int lf = threadIdx.x / NF, t = threadIdx.x - lf * NF;
   const int64_t slot = (int64_t)blockIdx.x * FPB + lf;
-  if (lf < FPB && slot < (int64_t)A.C + A.B) {
-    const T* qs = (const T*)A.qs;
-    const T* ppl = (const T*)A.pp_in;
-    const T gamma = gamma_of<T>(A.ph, A.gammaf);
-    T Fs[NV];
-    if (slot < A.C) {
-      const int32_t* r = A.conf + slot * 3;
-      const int64_t el = r[0], eh = r[1];
-      const int a = r[2];
-      const int nm = face_node<D, N>(a, 1, t), np = face_node<D, N>(a, 0, t);
-      const int k = (D == 3) ? nm / (n1 * n1) : nm / n1;
-      const T* b = (const T*)A.bgt + ((size_t)el * n1 + k) * 4;
-      const NodeBg<T> bg{b[0], b[1], b[2]};
-      T qm[NV], qp[NV], Fm[NV], Fp[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        qm[v] = qs[(size_t)v * A.plane + (size_t)el * NP + nm];
-        qp[v] = qs[(size_t)v * A.plane + (size_t)eh * NP + np];
-      }
-      const T sm = face_side<T, D>(qm, bg, ppl[(size_t)el * NP + nm], a, gamma, Fm);
-      const T sp = face_side<T, D>(qp, bg, ppl[(size_t)eh * NP + np], a, gamma, Fp);
-      rusanov<T, D>(qm, Fm, sm, qp, Fp, sp, Fs);
-    } else {
-      const int32_t* r = A.bnd + (slot - A.C) * 3;
-      const int64_t e = r[0];
-      const int a = r[1], s = r[2];
-      const int n = face_node<D, N>(a, s, t);
-      const int k = (D == 3) ? n / (n1 * n1) : n / n1;
-      const T* b = (const T*)A.bgt + ((size_t)e * n1 + k) * 4;
-      const NodeBg<T> bg{b[0], b[1], b[2]};
-      T q[NV], qo[NV], Fo[NV], Fn[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) q[v] = qs[(size_t)v * A.plane + (size_t)e * NP + n];
-      const T pp = ppl[(size_t)e * NP + n];
-      const NodeDer<T> nd = node_der<T, D>(q, bg);
-      flux_axis<T, D>(q, nd, pp, a, Fo);
-      const T so = wave_speed<T>(q, nd, bg, pp, a, gamma);
-      // mirror state: same Theta, rho and P', normal momentum negated (reading R5)
-#pragma unroll
-      for (int v = 0; v < NV; ++v) qo[v] = q[v];
-      qo[1 + a] = -q[1 + a];
-      flux_axis<T, D>(qo, nd, pp, a, Fn);
-      if (s) rusanov<T, D>(q, Fo, so, qo, Fn, so, Fs);
-      else   rusanov<T, D>(qo, Fn, so, q, Fo, so, Fs);
-    }
-    T* dst = (T*)A.fbuf + (size_t)slot * NV * NF;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) dst[v * NF + t] = Fs[v];
-  }
+  if (lf < FPB && slot < (int64_t)A.C + A.B) face_flux_node<T, D, N>(A, slot, t);
   // the stage kernel launched after this grid may start once every CTA of this grid has got
   // here (its prologue then overlaps this grid's last wave); it waits for this grid's
   // completion before it reads the face buffer.  Signalled at the start instead, the stage

@@ -104,6 +104,10 @@ void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const 
                      void* pp_out, int mode, double dt, double ca, double cb, dgk::StageArgs* A);
 // Arguments of the mortar work of mesh m for stage input qs.
 void fill_mortar_args(const dg_mesh* m, const void* qs, const void* pp_in, dgk::MortarArgs* M);
+// Arguments of the face kernel of mesh m (stage layout 5) for stage input qs.
+void fill_face_args(const dg_mesh* m, const void* qs, const void* pp_in, dgk::FaceArgs* F);
+// Sizes the face buffer of layout 5 for the mesh's conforming and boundary faces.
+dg_status ensure_face_buffer(dg_mesh* m);
 // Launches the mortar kernel of mesh m for stage input qs (no-op without hanging faces).
 dg_status launch_mortars(dg_mesh* m, const void* qs, const void* pp_in, cudaStream_t s);
 // Makes the P' plane of m->q[0] current.
