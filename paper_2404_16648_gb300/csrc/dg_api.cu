@@ -312,6 +312,8 @@ void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const 
       A->liftd[l][a] = A->inv2hd[l][a] / m->basis.w[0];
       A->liftf[l][a] = A->inv2hf[l][a] / (float)m->basis.w[0];
     }
+  A->rw0d = 1.0 / m->basis.w[0];
+  A->rw0f = (float)A->rw0d;
   A->dt = dt; A->ca = ca; A->cb = cb; A->mode = mode; A->variant = m->variant; A->ph = m->ph;
   A->plane32 = (int32_t)plane(m);
   A->gammaf = (float)m->ph.gamma; A->gf = (float)m->ph.g;

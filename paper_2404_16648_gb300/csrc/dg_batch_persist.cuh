@@ -31,6 +31,7 @@
 #include "dg_face.cuh"
 #include "dg_launch.hpp"
 #include "dg_stage_async.cuh"
+#include "dg_stage_fb.cuh"
 
 namespace dgk {
 
@@ -253,7 +254,7 @@ __device__ __noinline__ void batch_stage_item(const StageArgs& A, int64_t first,
   for (int64_t e0 = first; e0 < end; e0 += EPB) {
     if constexpr (LAYOUT == 0) stage_body_node<T, 2, N, EPB>(A, e0);
     else if constexpr (LAYOUT == 1) stage_body_async<T, 2, N, EPB>(A, e0);
-    else                       stage_body_async<T, 2, N, EPB, true>(A, e0);
+    else                       stage_body_fb<T, 2, N, EPB>(A, e0);
     __syncthreads();   // the next pass rewrites the shared tiles
   }
 }
@@ -313,8 +314,9 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_stage_kernel(const 
 template <class T, int N>
 constexpr size_t batch_body_smem(int layout) {
   return layout == 0 ? node_smem_bytes<T, 2, N, batch_epb_node(N)>()
-         : (layout == 1 || layout == 3) ? async_smem_bytes<T, 2, N, batch_epb_col(N)>()
-                                        : batch_mortar_smem_bytes<T, N>();
+         : layout == 1 ? async_smem_bytes<T, 2, N, batch_epb_col(N)>()
+         : layout == 3 ? fb_smem_bytes<T, 2, N, batch_epb_col(N)>()
+                       : batch_mortar_smem_bytes<T, N>();
 }
 
 inline size_t batch_body_smem_any(int prec32, int N, int layout) {
@@ -334,7 +336,7 @@ inline size_t batch_smem_limit() {
   size_t mx = 0;
   for (int p = 0; p < 2; ++p)
     for (int N = 1; N <= 8; ++N)
-      for (int l = 0; l < 3; ++l) {
+      for (int l = 0; l < 4; ++l) {
         const size_t b = batch_body_smem_any(p, N, l);
         if (b > mx) mx = b;
       }

@@ -272,6 +272,10 @@ struct StageArgs {
   // layout 5: F* of conforming and wall faces, one slot per face (dg_face.cuh); the slot of a
   // face is the third field of its connectivity row
   const void* fbuf;
+  // 1 / w0 (w0 the LGL weight of an end node): layout 5 adds the lifts to the unscaled
+  // derivative of a line, which is then scaled by -2/h, so the lift enters as (1/w0)(F* - F)
+  double rw0d;
+  float rw0f;
 };
 
 struct MortarArgs {

@@ -66,9 +66,8 @@ __host__ __device__ constexpr size_t async_smem_bytes() {
   return sizeof(T) * ((size_t)EPB * async_elem_words<T, D, N>() + (size_t)(N + 1) * (N + 1));
 }
 
-// Body for the EPB elements e0, e0 + 1, ... of mesh A.  FB (layout 5): the fluxes of conforming
-// and wall faces come from the face buffer written by face_kernel, like those of hanging faces.
-template <class T, int D, int N, int EPB, bool FB = false>
+// Body for the EPB elements e0, e0 + 1, ... of mesh A.
+template <class T, int D, int N, int EPB>
 __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0) {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
   constexpr int NSUB = 1 << (D - 1);
@@ -116,24 +115,19 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
       kinds[f] = kind;
       const int a = f >> 1, s = f & 1;
       T* dst = sNb + f * (NV + 1) * NF;
-      if (kind == FACE_CONF && !FB) {
+      if (kind == FACE_CONF) {
         const int no = face_node<D, N>(a, 1 - s, t);
         const T* qb = (const T*)A.qs + (int64_t)c[1] * NP;
 #pragma unroll
         for (int v = 0; v < NV; ++v) cp_async_bytes(dst + v * NF + t, qb + v * P + no, (int)sizeof(T));
         cp_async_bytes(dst + NV * NF + t, (const T*)A.pp_in + (int64_t)c[1] * NP + no, (int)sizeof(T));
-      } else if (kind == FACE_FINE || kind == FACE_COARSE || FB) {
-        // launched as the programmatic dependent of this stage's mortar (or face) kernel: only
-        // the elements that read its fluxes wait for it, before they read them
+      } else if (kind == FACE_FINE || kind == FACE_COARSE) {
+        // launched as the programmatic dependent of this stage's mortar kernel: only the
+        // elements that read its fluxes wait for it, before they read them
         if (A.after_mortar) asm volatile("griddepcontrol.wait;\n" ::: "memory");
-        const T* src;
-        if (kind == FACE_FINE || kind == FACE_COARSE) {
-          const int64_t gg = (kind == FACE_FINE) ? c[2] : c[1];
-          const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
-          src = (const T*)A.mbuf + (((size_t)gg * (1 + NSUB) + slot) * NV) * NF;
-        } else {
-          src = (const T*)A.fbuf + (size_t)c[2] * NV * NF;
-        }
+        const int64_t gg = (kind == FACE_FINE) ? c[2] : c[1];
+        const int slot = (kind == FACE_FINE) ? 1 + c[3] : 0;
+        const T* src = (const T*)A.mbuf + (((size_t)gg * (1 + NSUB) + slot) * NV) * NF;
 #pragma unroll
         for (int v = 0; v < NV; ++v) cp_async_bytes(dst + v * NF + t, src + v * NF + t, (int)sizeof(T));
       }
@@ -292,7 +286,7 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
     const T* nb = sNb + f * (NV + 1) * NF;
     T Fo[NV], Fs[NV];
     flux_axis<T, D>(q, nd, pp, a, Fo);
-    if (!FB && (kind == FACE_WALL || kind == FACE_CONF)) {
+    if (kind == FACE_WALL || kind == FACE_CONF) {
       const T so = wave_speed<T>(q, nd, bg, pp, a, gamma);
       T qo[NV], Fn[NV], sn;
       if (kind == FACE_WALL) {
@@ -387,10 +381,10 @@ __device__ __forceinline__ void stage_body_async(const StageArgs& A, int64_t e0)
   }
 }
 
-template <class T, int D, int N, int EPB, bool FB = false>
+template <class T, int D, int N, int EPB>
 __global__ void __launch_bounds__(EPB * ipow(N + 1, D - 1))
 stage_kernel_async(const __grid_constant__ StageArgs A) {
-  stage_body_async<T, D, N, EPB, FB>(A, (int64_t)A.e_begin + (int64_t)blockIdx.x * EPB);
+  stage_body_async<T, D, N, EPB>(A, (int64_t)A.e_begin + (int64_t)blockIdx.x * EPB);
 }
 
 // Batched form: block b works on mesh tab[map[b].x], elements from map[b].y.

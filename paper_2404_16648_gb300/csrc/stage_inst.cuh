@@ -2,6 +2,7 @@
 // Included by stage_<prec>_<dim>.cu with DG_T and DG_D defined.
 #include "dg_face.cuh"
 #include "dg_launch.hpp"
+#include "dg_stage_fb.cuh"
 #include "dg_stage_half.cuh"
 #include "dg_stage_line.cuh"
 
@@ -31,23 +32,21 @@ cudaError_t run_stage_col(const StageArgs& A, cudaStream_t s) {
   return cudaSuccess;
 }
 
-template <class T, int D, int N, bool FB = false>
-cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
+// A column-mapped stage kernel (EPB elements per CTA, one thread per column), as the
+// programmatic dependent of the kernel before it when A.after_mortar is set.
+template <int D, int N, int EPB>
+cudaError_t launch_col_kernel(void (*kernel)(StageArgs), size_t smem, const StageArgs& A, cudaStream_t s) {
   constexpr int NF = ipow(N + 1, D - 1);
-  constexpr int EPB = epb_col(D, N);
-  constexpr size_t smem = async_smem_bytes<T, D, N, EPB>();
   {
-    cudaError_t e = configure_kernel((const void*)stage_kernel_async<T, D, N, EPB, FB>, smem, false);
+    cudaError_t e = configure_kernel((const void*)kernel, smem, false);
     if (e != cudaSuccess) return e;
   }
   const unsigned blocks = (unsigned)((A.E - A.e_begin + EPB - 1) / EPB);
   if (!blocks) return cudaSuccess;
   if (!A.after_mortar) {
-    stage_kernel_async<T, D, N, EPB, FB><<<blocks, EPB * NF, smem, s>>>(A);
+    kernel<<<blocks, EPB * NF, smem, s>>>(A);
     return cudaSuccess;
   }
-  // programmatic dependent launch after the mortar kernel (see the hanging-face staging of
-  // stage_body_async)
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(EPB * NF);
@@ -58,7 +57,21 @@ cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, stage_kernel_async<T, D, N, EPB, FB>, A);
+  return cudaLaunchKernelEx(&cfg, kernel, A);
+}
+
+// Layout 2 (after the mortar kernel: see the hanging-face staging of stage_body_async).
+template <class T, int D, int N>
+cudaError_t run_stage_async(const StageArgs& A, cudaStream_t s) {
+  constexpr int EPB = epb_col(D, N);
+  return launch_col_kernel<D, N, EPB>(stage_kernel_async<T, D, N, EPB>, async_smem_bytes<T, D, N, EPB>(), A, s);
+}
+
+// Layout 5 (after the face kernel: see the staging of stage_body_fb).
+template <class T, int D, int N>
+cudaError_t run_stage_fb(const StageArgs& A, cudaStream_t s) {
+  constexpr int EPB = epb_col(D, N);
+  return launch_col_kernel<D, N, EPB>(stage_kernel_fb<T, D, N, EPB>, fb_smem_bytes<T, D, N, EPB>(), A, s);
 }
 
 // Layout 3 (3D, odd N); other shapes take layout 2.
@@ -155,7 +168,7 @@ void run_stage(const StageArgs& A, cudaStream_t s) {
   else if (A.variant == 2) run_stage_async<T, D, N>(A, s);
   else if (A.variant == 3) run_stage_half<T, D, N>(A, s);
   else if (A.variant == 4) run_stage_line<T, D, N>(A, s);
-  else if (A.variant == 5) run_stage_async<T, D, N, true>(A, s);
+  else if (A.variant == 5) run_stage_fb<T, D, N>(A, s);
   else run_stage_col<T, D, N>(A, s);
 }
 
