@@ -4,8 +4,10 @@
 //
 // The operator is the one of the other layouts (volume term of the strong form, Sec. 2.2; face
 // lifts (2/h)/w0 (F* - F) with the Rusanov flux or the mortar flux, Sec. 3.3; the Shu-Osher
-// combination and P' of the new state).  The CTA stages the element's state and P', its
-// background and the F* of its 2d faces into shared memory, then:
+// combination and P' of the new state).  The CTA stages the element's state, its background
+// and the F* of its horizontal faces into shared memory (each column thread keeps its P' and
+// the F* of its two vertical faces in registers, which holds the FP64 N = 7 CTA to 52.8 KB, 4
+// per SM), then:
 //   column pass  - one thread per vertical node line (column): the fluxes of its nodes along
 //                  x to a shared tile and along the vertical axis in registers; the vertical
 //                  derivative by the even/odd split of the antisymmetric LGL matrix, and the
@@ -35,11 +37,12 @@ __host__ __device__ constexpr int fb_tile_words() {
   constexpr int n1 = N + 1, NV = D + 2;
   return ((D == 3 ? n1 * n1 : n1) * (n1 + 1) * NV + 3) / 4 * 4;
 }
-// Words of T per element: tile, state and P', face fluxes [2d][NV][NF], background, FP64 c.
+// Words of T per element: tile, state, fluxes of the 2(d-1) horizontal faces [NV][NF] each,
+// background, FP64 c.  P' and the vertical faces' fluxes go to registers.
 template <class T, int D, int N>
 __host__ __device__ constexpr int fb_elem_words() {
   constexpr int n1 = N + 1, NP = ipow(n1, D), NF = ipow(n1, D - 1), NV = D + 2;
-  return fb_tile_words<T, D, N>() + ((NV + 1) * NP + 3) / 4 * 4 + (2 * D * NV * NF + 3) / 4 * 4 + n1 * 4 +
+  return fb_tile_words<T, D, N>() + (NV * NP + 3) / 4 * 4 + (2 * (D - 1) * NV * NF + 3) / 4 * 4 + n1 * 4 +
          ((n1 * (int)(8 / sizeof(T))) + 3) / 4 * 4;
 }
 template <class T, int D, int N, int EPB>
@@ -95,16 +98,16 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
   constexpr int RS = n1 + 1;                       // tile stride of an x line
   constexpr int TV = (D == 3 ? n1 * n1 : n1) * RS; // tile words per variable
   constexpr int RA = fb_tile_words<T, D, N>();
-  constexpr int RQ = ((NV + 1) * NP + 3) / 4 * 4;
-  constexpr int RN = (2 * D * NV * NF + 3) / 4 * 4;
+  constexpr int RQ = (NV * NP + 3) / 4 * 4;
+  constexpr int RN = (2 * (D - 1) * NV * NF + 3) / 4 * 4;
   constexpr int EW = fb_elem_words<T, D, N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x;
   const int le = tid / NF, t = tid - le * NF;
   T* base = reinterpret_cast<T*>(smem_raw) + (le < EPB ? le : 0) * EW;
   T* sA = base;                       // [NV][TV] flux tile, then line derivatives
-  T* sQ = base + RA;                  // [NV + 1][NP] state and P'
-  T* sF = base + RA + RQ;             // [2D][NV][NF] F* of every face
+  T* sQ = base + RA;                  // [NV][NP] state
+  T* sF = base + RA + RQ;             // [2 (D - 1)][NV][NF] F* of the horizontal faces
   T* sBg = base + RA + RQ + RN;       // [n1][4]
   double* sBc = reinterpret_cast<double*>(sBg + n1 * 4);   // [n1] (FP32 path)
   const int64_t e = e0 + le;
@@ -119,13 +122,17 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
   auto tix = [&](int i, int j, int k) { return (D == 3 ? (k * n1 + j) : k) * RS + i; };
   const int P = A.plane32;
   const T* qe = (const T*)A.qs + (valid ? e : 0) * NP;
-  // ---- staging: own state, P', background column, the face fluxes of all 2d faces
+  // ---- staging: own state and background column to shared memory, the fluxes of the
+  // horizontal faces too; this column's P' and the vertical faces' fluxes to registers
+  T ppc[n1], Fv[2][NV];
   if (valid) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) stage_run<T>(sQ + v * NP, qe + v * P, NP, t, NF);
-    stage_run<T>(sQ + NV * NP, (const T*)A.pp_in + e * NP, NP, t, NF);
     stage_run<T>(sBg, (const T*)A.bgt + e * n1 * 4, n1 * 4, t, NF);
     if (sizeof(T) == 4) stage_run<double>(sBc, A.bgc + e * n1, n1, t, NF);
+    const T* ppe = (const T*)A.pp_in + e * NP;
+#pragma unroll
+    for (int k = 0; k < n1; ++k) ppc[k] = ppe[t + NF * k];
     // launched as the programmatic dependent of this stage's face kernel, which completes only
     // after the mortar kernel: wait for it before reading either buffer
     if (A.after_mortar) asm volatile("griddepcontrol.wait;\n" ::: "memory");
@@ -141,9 +148,19 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
       } else {
         src = (const T*)A.fbuf + (size_t)c[2] * NV * NF;
       }
+      if (f < 2 * (D - 1)) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) cp_async_bytes(sF + (f * NV + v) * NF + t, src + v * NF + t, (int)sizeof(T));
+        for (int v = 0; v < NV; ++v) cp_async_bytes(sF + (f * NV + v) * NF + t, src + v * NF + t, (int)sizeof(T));
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Fv[f - 2 * (D - 1)][v] = src[v * NF + t];
+      }
     }
+  } else {
+#pragma unroll
+    for (int k = 0; k < n1; ++k) ppc[k] = (T)0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { Fv[0][v] = (T)0; Fv[1][v] = (T)0; }
   }
   cp_async_commit();
   const T g = sizeof(T) == 4 ? (T)A.gf : (T)A.ph.g;
@@ -164,7 +181,7 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
       T q[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) q[v] = valid ? sQ[v * NP + n] : (T)0;
-      const T pp = valid ? sQ[NV * NP + n] : (T)0;
+      const T pp = ppc[k];
       const NodeBg<T> bg = valid ? NodeBg<T>{sBg[k * 4], sBg[k * 4 + 1], sBg[k * 4 + 2]}
                                  : NodeBg<T>{(T)1, (T)1, (T)1};
 #pragma unroll
@@ -185,8 +202,7 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       T dz[n1];
-      fb_line<T, N>(Fz[v], valid ? sF[(2 * (D - 1) * NV + v) * NF + t] : (T)0,
-                    valid ? sF[((2 * (D - 1) + 1) * NV + v) * NF + t] : (T)0, rw0, dz);
+      fb_line<T, N>(Fz[v], Fv[0][v], Fv[1][v], rw0, dz);
 #pragma unroll
       for (int k = 0; k < n1; ++k) acc[v][k] = fma(-inv2h[D - 1], dz[k], acc[v][k]);
     }
@@ -230,11 +246,10 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
       T q[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) q[v] = valid ? sQ[v * NP + n] : (T)0;
-      const T pp = valid ? sQ[NV * NP + n] : (T)0;
       const NodeBg<T> bg = valid ? NodeBg<T>{sBg[k * 4], sBg[k * 4 + 1], sBg[k * 4 + 2]}
                                  : NodeBg<T>{(T)1, (T)1, (T)1};
       T F[NV];
-      flux_axis<T, D>(q, node_der<T, D>(q, bg), pp, 1, F);
+      flux_axis<T, D>(q, node_der<T, D>(q, bg), ppc[k], 1, F);
       if (inblk) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) sA[v * TV + tix(ci, cj, k)] = F[v];
