@@ -173,6 +173,7 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
   __syncthreads();
   // ---- column pass: x fluxes to the tile, the vertical derivative and the vertical lifts
   T acc[NV][n1];
+  T rinvc[n1];   // 1/rho of the column's nodes, kept for the y fluxes
   {
     T Fz[NV][n1];
 #pragma unroll
@@ -188,6 +189,7 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
       for (int v = 0; v < NV; ++v) acc[v][k] = (T)0;
       acc[D][k] = -(q[0] * g);               // buoyancy -rho' g on the vertical momentum
       const NodeDer<T> nd = node_der<T, D>(q, bg);
+      rinvc[k] = nd.rinv;
       T F[NV];
       flux_axis<T, D>(q, nd, pp, 0, F);
       if (inblk) {
@@ -249,7 +251,7 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
       const NodeBg<T> bg = valid ? NodeBg<T>{sBg[k * 4], sBg[k * 4 + 1], sBg[k * 4 + 2]}
                                  : NodeBg<T>{(T)1, (T)1, (T)1};
       T F[NV];
-      flux_axis<T, D>(q, node_der<T, D>(q, bg), ppc[k], 1, F);
+      flux_axis<T, D>(q, NodeDer<T>{rinvc[k], add_rn(bg.Tb, q[D + 1])}, ppc[k], 1, F);
       if (inblk) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) sA[v * TV + tix(ci, cj, k)] = F[v];
