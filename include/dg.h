@@ -337,9 +337,10 @@ const char* dg_batch_last_error(const dg_batch* batch);
  * 0 = one thread per vertical node column, 1 = one thread per node, 2 = one thread per column
  * with all operands staged into shared memory by asynchronous copies, 3 = as 2 with two
  * threads per column, 4 = one pass per axis with two threads per node line, fluxes kept in
- * registers (3 and 4: 3D with odd N; other shapes run layout 2), 5 = layout 2 with the Rusanov
- * flux of every conforming and wall face computed once per face by a face kernel before the
- * stage kernel (a partitioned mesh runs layout 2 instead).  Default: 4 for FP32 3D meshes, 5 for
+ * registers (3 and 4: 3D with odd N; other shapes run layout 2), 5 = the Rusanov flux of every
+ * conforming and wall face computed once per face by a face kernel before the stage kernel,
+ * whose volume term runs as a column pass and one line pass per horizontal axis, each line
+ * thread lifting the two faces at its ends (a partitioned mesh runs layout 2 instead).  Default: 4 for FP32 3D meshes, 5 for
  * FP64 Euler meshes, 2 otherwise.  All compute the same operator; the option exists for tuning
  * and cross-checking. */
 enum { DG_OPT_STAGE_KERNEL = 1, DG_OPT_FAIL_NEXT_ADAPT = 2 };

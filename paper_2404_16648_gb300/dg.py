@@ -515,7 +515,8 @@ class Mesh:
         """0: one thread per vertical node column; 1: one thread per node; 2: column layout with
         asynchronous staging of every operand in shared memory; 3: as 2 with two threads per
         column (3D, odd N); 4: one pass per axis, two threads per node line, fluxes in registers
-        (3D, odd N); 5: layout 2 with the conforming and wall face fluxes computed once per face.
+        (3D, odd N); 5: conforming and wall face fluxes computed once per face by a face kernel,
+        then a column pass and one line pass per horizontal axis.
         Default: 4 for FP32 3D meshes, 5 for FP64 Euler meshes, 2 otherwise."""
         self._check(self.lib.dg_set_option(self.h, 1, int(layout)))
 
