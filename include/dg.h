@@ -193,7 +193,9 @@ dg_status dg_step(dg_mesh* mesh, double dt, int32_t nsteps, void* stream);
 /* One regrid pass with conservative transfer of the state (Sec. 3.3).  Synchronous: the
  * criterion is evaluated on the device, the tree work runs on the host, the transfer on the
  * device.  Element order and count change; state pointers obtained earlier stay valid only as
- * copies.  `report` may be NULL.  Errors: a failure while the new tree and its tables are built
+ * copies.  A pass that refines and coarsens nothing leaves the mesh, its state and its tables as
+ * they are (no transfer, no table rebuild).  `report` may be NULL.  Errors: a failure while the
+ * new tree and its tables are built
  * and checked leaves the mesh as it was; a failure after the new tree is committed (an
  * allocation or copy of the new tables) leaves the mesh unusable, and every later call on it
  * returns DG_ERR_STATE. */

@@ -1146,6 +1146,17 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   if (!m->forest.regrid(tag, p->buffer, maxl, &nf, &tmap, &nref, &ncoarse, &why))
     return fail(m, DG_ERR_STATE, "regrid failed: %s", why.c_str());
   const int64_t E_old = m->E;
+  if (nref == 0 && ncoarse == 0 && inject == 0) {
+    // nothing refined or coarsened: the new forest is the old one, the transfer would copy
+    // every element and the tables would come out the same, so the mesh is left as it is
+    if (rep) {
+      rep->elements_before = E_old;
+      rep->elements_after = E_old;
+      rep->refined = 0;
+      rep->coarsened = 0;
+    }
+    return DG_OK;
+  }
   const int64_t plane_old = plane(m);
   const int64_t E_new = nf.size();
   if ((int64_t)(m->NV + 1) * E_new * m->NP >= ((int64_t)1 << 31))

@@ -159,6 +159,27 @@ def test_adapt_transfer_parity(pkg, dim, N, base):
     np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * np.abs(q).max())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_noop_adapt_keeps_mesh_and_state(pkg, precision):
+    """A regrid pass that refines and coarsens nothing (level-0 roots, no flags) leaves the
+    leaves and the state as they were, bit for bit, and the next steps equal those of a twin
+    mesh that never adapted; the oracle's regrid agrees that nothing changes."""
+    base, length = (3, 2, 2), (1500.0, 1000.0, 1000.0)
+    a = pkg.Mesh(3, 3, base, length, max_level=2, precision=precision)
+    b = pkg.Mesh(3, 3, base, length, max_level=2, precision=precision)
+    for m in (a, b):
+        m.set_bubble(center=(700.0, 500.0, 400.0), radius=(300.0,) * 3, amp=0.5)
+    leaves0, q0 = a.leaves().copy(), a.get_state().copy()
+    rep = a.adapt(flags=np.zeros(a.num_elements, np.uint8), buffer=1)
+    of2, _ = ofo.Forest(base, 2).regrid(np.zeros(len(q0[0]), bool), 1)
+    assert rep["before"] == rep["after"] == len(of2.leaves) == a.num_elements
+    np.testing.assert_array_equal(a.leaves(), leaves0)
+    assert np.array_equal(a.get_state(), q0)
+    a.step(0.004, 3)
+    b.step(0.004, 3)
+    assert np.array_equal(a.get_state(), b.get_state())
+
+
 def test_integrals_parity(pkg):
     lm, om = _pair(pkg, 3, 4, (2, 2, 3), (2000.0, 2000.0, 3000.0), flags_rounds=((0.3, 15),))
     q = workloads.random_state(om.nv, om.E, om.np_, seed=16)
