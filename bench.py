@@ -245,9 +245,10 @@ def _timed_steps(m, cfg, steps, regrid_every, NP, NV, b, n1, D, per_node=None, f
         if regrid_every and (i + 1) % regrid_every == 0:
             torch.cuda.synchronize()     # dg_adapt starts with this wait anyway
             tr = time.perf_counter()
-            m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
+            rep = m.adapt(threshold=cfg["threshold"], buffer=cfg["buffer"])
             c["regrid_s"].append(time.perf_counter() - tr)
-            c["launches"] += 3   # indicator, transfer, background
+            # indicator; transfer and background only when the pass changes the mesh
+            c["launches"] += 1 + (2 if rep["refined"] or rep["coarsened"] else 0)
     ev1.record()
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1), c
