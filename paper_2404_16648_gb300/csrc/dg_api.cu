@@ -1130,12 +1130,23 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   if (p->criterion == DG_CRIT_FLAGS) {
     if (!p->flags) return fail(m, DG_ERR_ARG, "flags missing");
     for (int64_t e = 0; e < m->E; ++e) tag[e] = p->flags[e] ? 1 : 0;
-  } else if (p->criterion == DG_CRIT_THETA) {
+  } else if (p->criterion == DG_CRIT_THETA && m->tracer) {
     CU(pin_reserve(m, 2, (size_t)(m->E > 0 ? m->E : 1) * sizeof(double)));
     double* ind = reinterpret_cast<double*>(m->h_pin[2]);
     dg_status st = dg_indicator(m, ind, (size_t)m->E);
     if (st != DG_OK) return st;
     for (int64_t e = 0; e < m->E; ++e) tag[e] = ind[e] > p->threshold ? 1 : 0;
+  } else if (p->criterion == DG_CRIT_THETA) {
+    // the comparison with the threshold decided on the device (launch_tags: the decisions of
+    // dg_indicator > threshold, mostly without its divisions), one byte per element back
+    CU(pin_reserve(m, 2, (size_t)(m->E > 0 ? m->E : 1)));
+    CU(reserve(m->d_ind, m->c_ind, (size_t)(m->E > 0 ? m->E : 1) * sizeof(double)));
+    uint8_t* d_tag = reinterpret_cast<uint8_t*>(m->d_ind);
+    CU(dgk::launch_tags(m->prec, (int32_t)m->E, m->n1, m->D, m->d_bg, m->q[0], plane(m), m->ph.theta0,
+                        p->threshold, d_tag, m->stream));
+    if (m->E > 0) CU(cudaMemcpyAsync(m->h_pin[2], d_tag, (size_t)m->E, cudaMemcpyDeviceToHost, m->stream));
+    CU(cudaStreamSynchronize(m->stream));
+    std::memcpy(tag.data(), m->h_pin[2], (size_t)m->E);
   } else {
     return fail(m, DG_ERR_ARG, "unknown criterion");
   }
@@ -1143,12 +1154,13 @@ dg_status dg_adapt(dg_mesh* m, const dg_adapt_params* p, dg_adapt_report* rep) {
   std::vector<dgl::TransferEntry> tmap;
   int64_t nref = 0, ncoarse = 0;
   std::string why;
-  if (!m->forest.regrid(tag, p->buffer, maxl, &nf, &tmap, &nref, &ncoarse, &why))
+  if (!m->forest.regrid(tag, p->buffer, maxl, &nf, &tmap, &nref, &ncoarse, &why, inject == 0))
     return fail(m, DG_ERR_STATE, "regrid failed: %s", why.c_str());
   const int64_t E_old = m->E;
   if (nref == 0 && ncoarse == 0 && inject == 0) {
-    // nothing refined or coarsened: the new forest is the old one, the transfer would copy
-    // every element and the tables would come out the same, so the mesh is left as it is
+    // nothing refined or coarsened: the new forest is the old one (the host pass skipped
+    // building it), the transfer would copy every element and the tables would come out the
+    // same, so the mesh is left as it is
     if (rep) {
       rep->elements_before = E_old;
       rep->elements_after = E_old;

@@ -109,6 +109,9 @@ cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* ele
                           cudaStream_t s);
 cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
                              int64_t plane, double theta0, double* out, cudaStream_t s);
+// tag[e] = (the theta' indicator of element e > thr), as 0 / 1 bytes.
+cudaError_t launch_tags(int prec, int32_t E, int n1, int D, const double* bg, const void* q, int64_t plane,
+                        double theta0, double thr, uint8_t* tag, cudaStream_t s);
 cudaError_t launch_primitives(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
                               int64_t plane, double theta0, double* out, cudaStream_t s);
 size_t integrals_scratch_doubles();

@@ -244,6 +244,73 @@ __global__ void indicator_kernel(int32_t E, int n1, int D, const double* bg, con
   if (lane == 0) out[e] = m;
 }
 
+// Refinement tags of the theta' criterion: tag[e] = (the indicator of element e > thr), with
+// the indicator as indicator_kernel returns it, decided without forming it where the FP32
+// intervals of indicator_screen settle the comparison.  |fl(fl(A/B) - theta0)| differs from
+// |D/B| by the two FP64 roundings, below 2^-52 (|A/B| + |theta0|), which the margin `del`
+// (host: 2^-30 (|theta0| + |thr|)) covers many times over: a node is certainly above the
+// threshold when its interval lies beyond +-fh >= thr + del, certainly below when it lies
+// within +-fl <= thr - del.  Only an element with no node certainly above and some node that
+// is neither takes FP64 divisions, at those nodes; an element outside the bounds' range, or a
+// threshold too small for the margins (screen == 0), takes them at every node.  Non-finite
+// values compare false, as the indicator's fmax leaves them out.
+template <class T>
+__global__ void tag_kernel(int32_t E, int n1, int D, const double* bg, const T* q, int64_t plane,
+                           double theta0, float thf, float dth, double thr, float fh, float fl, int screen,
+                           uint8_t* tag) {
+  __shared__ float lay[kIndWarps][DG_MAX_N + 1][3];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * kIndWarps + w;
+  if (e >= E) return;   // whole warps leave together; no block-wide barrier below
+  const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;
+  const int layer = D == 3 ? n1 * n1 : n1;
+  const uint32_t M = ((1u << 20) + (uint32_t)layer - 1) / (uint32_t)layer;
+  const T* q0 = q + e * NP;
+  const T* q3 = q + (int64_t)(D + 1) * plane + e * NP;
+  const double* be = bg + e * n1 * 4;
+  if (lane < n1) {
+    const double b0 = be[lane * 4], b1 = be[lane * 4 + 1];
+    lay[w][lane][0] = (float)fma(-theta0, b0, b1);
+    lay[w][lane][1] = (float)b0;
+    lay[w][lane][2] = (float)b1;
+  }
+  __syncwarp();
+  auto exceeds = [&](int n) {
+    const int k = (int)(((uint32_t)n * M) >> 20);
+    return fabs((be[k * 4 + 1] + (double)q3[n]) / (be[k * 4] + (double)q0[n]) - theta0) > thr;
+  };
+  bool above = false, unsure = false;
+  if (screen) {
+    bool ok = true;
+    for (int n = lane; n < NP; n += 32) {
+      const int k = (int)(((uint32_t)n * M) >> 20);
+      const IndScreen s = indicator_screen<T>(lay[w][k][0], lay[w][k][1], lay[w][k][2], q0[n], q3[n], thf, dth);
+      ok = ok && s.ok;
+      above = above || s.lo > fh || s.hi < -fh;
+      unsure = unsure || !(s.hi < fl && s.lo > -fl);
+    }
+    if (__all_sync(0xffffffffu, ok)) {
+      above = __any_sync(0xffffffffu, above);
+      unsure = __any_sync(0xffffffffu, unsure);
+      if (!above && unsure) {
+        bool hit = false;
+        for (int n = lane; n < NP; n += 32) {
+          const int k = (int)(((uint32_t)n * M) >> 20);
+          const IndScreen s = indicator_screen<T>(lay[w][k][0], lay[w][k][1], lay[w][k][2], q0[n], q3[n], thf, dth);
+          if (!(s.hi < fl && s.lo > -fl)) hit = hit || exceeds(n);
+        }
+        above = __any_sync(0xffffffffu, hit);
+      }
+      if (lane == 0) tag[e] = above ? 1 : 0;
+      return;
+    }
+  }
+  bool hit = false;
+  for (int n = lane; n < NP; n += 32) hit = hit || exceeds(n);
+  hit = __any_sync(0xffffffffu, hit);
+  if (lane == 0) tag[e] = hit ? 1 : 0;
+}
+
 // Primitive diagnostics per node in FP64: out[a] = U_a / rho (a < D), out[D] = theta'
 // = (Theta_bar + Theta') / (rho_bar + rho') - theta0; planes of length E * NP.
 template <class T>
@@ -596,6 +663,27 @@ cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* b
     indicator_kernel<double><<<grid, 32 * kIndWarps, 0, s>>>(E, n1, D, bg, (const double*)q, plane, theta0, thf, dth, out);
   else
     indicator_kernel<float><<<grid, 32 * kIndWarps, 0, s>>>(E, n1, D, bg, (const float*)q, plane, theta0, thf, dth, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tags(int prec, int32_t E, int n1, int D, const double* bg, const void* q, int64_t plane,
+                        double theta0, double thr, uint8_t* tag, cudaStream_t s) {
+  if (E == 0) return cudaSuccess;
+  const int grid = (int)((E + kIndWarps - 1) / kIndWarps);
+  const float thf = (float)theta0;
+  const float dth = (float)(std::fabs((double)thf - theta0) * (1.0 + 0x1p-20));
+  const double del = std::ldexp(std::fabs(theta0) + std::fabs(thr), -30);
+  // FP32 bounds on the FP64 thresholds: fh >= thr + del, fl <= thr - del
+  float fh = (float)(thr + del), fl = (float)(thr - del);
+  if ((double)fh < thr + del) fh = std::nextafter(fh, INFINITY);
+  if ((double)fl > thr - del) fl = std::nextafter(fl, -INFINITY);
+  const int screen = std::isfinite(thr) && thr - del > 0.0 && std::isfinite(fh) ? 1 : 0;
+  if (prec == 0)
+    tag_kernel<double><<<grid, 32 * kIndWarps, 0, s>>>(E, n1, D, bg, (const double*)q, plane, theta0, thf, dth, thr,
+                                                       fh, fl, screen, tag);
+  else
+    tag_kernel<float><<<grid, 32 * kIndWarps, 0, s>>>(E, n1, D, bg, (const float*)q, plane, theta0, thf, dth, thr,
+                                                      fh, fl, screen, tag);
   return cudaGetLastError();
 }
 

@@ -120,7 +120,7 @@ FaceInfo Forest::classify(int32_t e, int axis, int side) const {
 
 bool Forest::regrid(const std::vector<uint8_t>& tag, int B, int max_level, Forest* out,
                     std::vector<TransferEntry>* tmap, int64_t* n_refined,
-                    int64_t* n_coarsened, std::string* err) const {
+                    int64_t* n_coarsened, std::string* err, bool skip_unchanged) const {
   const int64_t n = size();
   const int nkids = 1 << dim_;
   const int nsub = 1 << (dim_ - 1);
@@ -218,6 +218,11 @@ bool Forest::regrid(const std::vector<uint8_t>& tag, int B, int max_level, Fores
     nref += ref[e];
     ncoarse += coars[e] == 2;
     pos[e] = ref[e] ? nkids : (coars[e] == 1 ? 0 : 1);
+  }
+  if (skip_unchanged && nref == 0 && ncoarse == 0) {
+    *n_refined = 0;
+    *n_coarsened = 0;
+    return true;
   }
   pos[n] = exclusive_scan(pos.data(), n);
   std::vector<Leaf> nl((size_t)pos[n]);

@@ -57,10 +57,12 @@ class Forest {
   // classify() of every face, tabulated once per leaf set: face(e, a, s).
   const FaceInfo& face(int32_t e, int axis, int side) const { return faces_[((size_t)e * dim_ + axis) * 2 + side]; }
 
-  // One regrid pass.  Returns false (with `err`) if the forest is not 2:1 balanced.
+  // One regrid pass.  Returns false (with `err`) if the forest is not 2:1 balanced.  With
+  // skip_unchanged, a pass that refines and coarsens nothing returns with both counts zero and
+  // leaves *out and *tmap untouched (the new forest would equal this one).
   bool regrid(const std::vector<uint8_t>& tag, int B, int max_level, Forest* out,
               std::vector<TransferEntry>* tmap, int64_t* n_refined, int64_t* n_coarsened,
-              std::string* err) const;
+              std::string* err, bool skip_unchanged = false) const;
 
   // Canonical face lists (see dg.h, dg_get_faces).
   void face_lists(std::vector<int32_t>* conf, std::vector<int32_t>* mort,

@@ -74,3 +74,49 @@ def test_indicator_elements_outside_the_fast_range(pkg, precision):
     np.testing.assert_array_equal(got, want)
     assert got[5] == 0.0 and np.isfinite(got[3]) and got[9] > 1e30
     assert np.all(np.isfinite(np.delete(got, [9])))
+
+
+def _twins(pkg, dim, N, precision, theta0):
+    base = (6, 4) if dim == 2 else (3, 3, 2)
+    length = (6000.0, 4000.0) if dim == 2 else (3000.0, 3000.0, 2000.0)
+    return [pkg.Mesh(dim, N, base, length, max_level=1, precision=precision, theta0=theta0) for _ in range(2)]
+
+
+@pytest.mark.parametrize("dim,N,precision,theta0", [(2, 4, "fp64", 300.0), (2, 7, "fp32", 301.7),
+                                                    (3, 3, "fp64", 287.3), (3, 7, "fp32", 300.0)])
+def test_adapt_threshold_tags_equal_indicator_comparison(pkg, dim, N, precision, theta0):
+    """dg_adapt's theta' criterion decides `indicator > threshold` on the device without forming
+    the indicator where FP32 intervals settle it.  Against the same comparison made on the
+    host from dg_indicator: roots at level 0 with one level to go and no buffer, so every tag
+    shows in the leaves.  Thresholds: a typical one, every tenth element's indicator value
+    itself (that element is not tagged) and the next double below it (it is), on random,
+    bubble and below-FP32-resolution states."""
+    a, b = _twins(pkg, dim, N, precision, theta0)
+    E, NP = a.num_elements, (N + 1) ** dim
+    states = [workloads.random_state(dim + 2, E, NP, seed=41, theta_scale=0.05),
+              workloads.random_state(dim + 2, E, NP, seed=42, rho_scale=1e-12, theta_scale=1e-9)]
+    for q in states + [None]:
+        for m in (a, b):
+            if q is None:
+                m.set_bubble(center=(3000.0, 1500.0, 1000.0)[:dim], radius=(1500.0,) * dim, amp=0.05)
+            else:
+                _set(m, q)
+        ind = a.indicator()
+        thrs = [0.05] + [float(ind[e]) for e in range(0, E, 10)] + \
+               [float(np.nextafter(ind[e], -np.inf)) for e in range(0, E, 10)]
+        for thr in thrs:
+            want = (ind > thr).astype(np.uint8)
+            ra = a.adapt(threshold=thr, buffer=0)
+            rb = b.adapt(flags=want, buffer=0)
+            assert ra == rb
+            np.testing.assert_array_equal(a.leaves(), b.leaves())
+            # back to the roots for the next threshold
+            for m in (a, b):
+                m.adapt(flags=np.zeros(m.num_elements, np.uint8), buffer=0)
+            assert a.num_elements == E
+            if q is None:
+                for m in (a, b):
+                    m.set_bubble(center=(3000.0, 1500.0, 1000.0)[:dim], radius=(1500.0,) * dim, amp=0.05)
+            else:
+                for m in (a, b):
+                    _set(m, q)
