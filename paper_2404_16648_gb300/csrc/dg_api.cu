@@ -408,7 +408,7 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
   // stage kernel runs its elements without hanging faces while the mortar kernel finishes and
   // only the others wait for it.  A stage timed on its own (dg_enable_timing) needs an event
   // between the two launches, which rules this out.
-  // layout 5 (face fluxes once per face, then the column-async stage) needs the whole mesh's
+  // layout 5 (face fluxes once per face, then the line-pass stage kernel) needs the whole mesh's
   // face lists; a partitioned mesh runs layout 2
   const int variant = (m->variant == 5 && m->nparts > 1) ? 2 : m->variant;
   const bool mortars = (m->nparts > 1 ? m->G_part : m->G) > 0;
