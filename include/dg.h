@@ -47,6 +47,10 @@ typedef enum {
 
 enum { DG_FP64 = 0, DG_FP32_PERT = 1 };   /* dg_mesh_desc.precision */
 enum { DG_HOST = 0, DG_DEVICE = 1 };      /* where a state pointer lives */
+/* layout_flags of dg_set_state / dg_get_state: the library's state layout q[v][e][n] (planes of
+ * one variable), or the caller's element-major q[e][v][n] (each element's variables together),
+ * converted on the device */
+enum { DG_LAYOUT_PLANES = 0, DG_LAYOUT_ELEMENTS = 1 };
 enum { DG_CRIT_THETA = 0, DG_CRIT_FLAGS = 1 };  /* dg_adapt_params.criterion */
 enum { DG_EQ_EULER = 0, DG_EQ_TRACER = 1 };     /* dg_mesh_desc.equations */
 enum { DG_FACE_MORTAR = 0, DG_FACE_INTERP = 1 };  /* dg_mesh_desc.face_mode */
@@ -150,9 +154,12 @@ dg_status dg_get_leaves(const dg_mesh* mesh, int32_t* out, size_t cap);
 dg_status dg_get_faces(const dg_mesh* mesh, int64_t counts[3], int32_t* conforming, size_t cap_c,
                        int32_t* mortars, size_t cap_m, int32_t* boundary, size_t cap_b);
 
-/* Copies a state in (out) in the layout above; where = DG_HOST or DG_DEVICE.  Synchronous. */
-dg_status dg_set_state(dg_mesh* mesh, const void* q, int where);
-dg_status dg_get_state(dg_mesh* mesh, void* q, int where);
+/* Copies a state in (out): layout_flags = DG_LAYOUT_PLANES for the layout above, or
+ * DG_LAYOUT_ELEMENTS for q[e][v][n] (the permutation runs on the device, through the mesh's
+ * stage buffer for host pointers); where = DG_HOST or DG_DEVICE.  Synchronous.  Any other flag
+ * is DG_ERR_ARG. */
+dg_status dg_set_state(dg_mesh* mesh, const void* q, int layout_flags, int where);
+dg_status dg_get_state(dg_mesh* mesh, void* q, int layout_flags, int where);
 /* Asynchronous forms for pipelines that must not wait on the host.  dg_set_state_async and
  * dg_get_state_async copy the state in or out on `stream` (NULL: the mesh stream) after the work
  * already queued on the mesh stream, with no host wait; host buffers should be pinned, must stay

@@ -946,21 +946,44 @@ dg_status dg_get_faces(const dg_mesh* mc, int64_t counts[3], int32_t* conforming
   return DG_OK;
 }
 
-dg_status dg_set_state(dg_mesh* m, const void* q, int where) {
+dg_status dg_set_state(dg_mesh* m, const void* q, int layout_flags, int where) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
-  if (!m || !q || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (!m || !q || (where != DG_HOST && where != DG_DEVICE) ||
+      (layout_flags != DG_LAYOUT_PLANES && layout_flags != DG_LAYOUT_ELEMENTS))
+    return fail(m, DG_ERR_ARG, "bad argument");
   const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
   m->pp_valid = false;
-  CU(cudaMemcpyAsync(m->q[0], q, bytes, where == DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, m->stream));
+  const cudaMemcpyKind kind = where == DG_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (layout_flags == DG_LAYOUT_PLANES) {
+    CU(cudaMemcpyAsync(m->q[0], q, bytes, kind, m->stream));
+  } else {
+    // element-major in: host data through the stage buffer q[1] (it holds nothing between steps)
+    const void* src = q;
+    if (where == DG_HOST) {
+      CU(cudaMemcpyAsync(m->q[1], q, bytes, kind, m->stream));
+      src = m->q[1];
+    }
+    CU(dgk::launch_state_layout(m->tsize, 1, m->E, m->NP, m->NV, src, m->q[0], plane(m), m->stream));
+  }
   CU(cudaStreamSynchronize(m->stream));
   return DG_OK;
 }
 
-dg_status dg_get_state(dg_mesh* m, void* q, int where) {
+dg_status dg_get_state(dg_mesh* m, void* q, int layout_flags, int where) {
   if (m && m->broken) return fail(m, DG_ERR_STATE, kBrokenMsg);
-  if (!m || !q || (where != DG_HOST && where != DG_DEVICE)) return fail(m, DG_ERR_ARG, "bad argument");
+  if (!m || !q || (where != DG_HOST && where != DG_DEVICE) ||
+      (layout_flags != DG_LAYOUT_PLANES && layout_flags != DG_LAYOUT_ELEMENTS))
+    return fail(m, DG_ERR_ARG, "bad argument");
   const size_t bytes = (size_t)m->NV * plane(m) * m->tsize;
-  CU(cudaMemcpyAsync(q, m->q[0], bytes, where == DG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, m->stream));
+  if (layout_flags == DG_LAYOUT_PLANES) {
+    CU(cudaMemcpyAsync(q, m->q[0], bytes, where == DG_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                       m->stream));
+  } else if (where == DG_DEVICE) {
+    CU(dgk::launch_state_layout(m->tsize, 0, m->E, m->NP, m->NV, m->q[0], q, plane(m), m->stream));
+  } else {
+    CU(dgk::launch_state_layout(m->tsize, 0, m->E, m->NP, m->NV, m->q[0], m->q[1], plane(m), m->stream));
+    CU(cudaMemcpyAsync(q, m->q[1], bytes, cudaMemcpyDeviceToHost, m->stream));
+  }
   CU(cudaStreamSynchronize(m->stream));
   return DG_OK;
 }

@@ -109,6 +109,10 @@ cudaError_t launch_bubble(int prec, int32_t E, int n1, int D, const int32_t* ele
                           cudaStream_t s);
 cudaError_t launch_indicator(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
                              int64_t plane, double theta0, double* out, cudaStream_t s);
+// State layout conversion between element-major [E][NV][NP] and the mesh's planes
+// [NV][plane] (to_planes = 1: into planes); tsize 4 or 8 bytes per value.
+cudaError_t launch_state_layout(int tsize, int to_planes, int64_t E, int NP, int NV, const void* src,
+                                void* dst, int64_t plane, cudaStream_t s);
 // tag[e] = (the theta' indicator of element e > thr), as 0 / 1 bytes.
 cudaError_t launch_tags(int prec, int32_t E, int n1, int D, const double* bg, const void* q, int64_t plane,
                         double theta0, double thr, uint8_t* tag, cudaStream_t s);

@@ -687,6 +687,35 @@ cudaError_t launch_tags(int prec, int32_t E, int n1, int D, const double* bg, co
   return cudaGetLastError();
 }
 
+// State layout conversion: element-major s[e][v][n] <-> the planes d[v][plane][...] of the
+// mesh (to_planes = 1: element-major in, planes out; 0: the reverse).  W: the element's word.
+template <class W>
+__global__ void state_layout_kernel(int to_planes, int64_t E, int NP, int NV, const W* src, W* dst,
+                                    int64_t plane) {
+  const int64_t total = E * NV * NP;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const int64_t en = i / NP;               // (e, v) of element-major index i
+  const int n = (int)(i - en * NP);
+  const int64_t e = en / NV;
+  const int v = (int)(en - e * NV);
+  const int64_t p = (int64_t)v * plane + e * NP + n;
+  if (to_planes) dst[p] = src[i];
+  else dst[i] = src[p];
+}
+
+cudaError_t launch_state_layout(int tsize, int to_planes, int64_t E, int NP, int NV, const void* src,
+                                void* dst, int64_t plane, cudaStream_t s) {
+  const int64_t total = E * NV * NP;
+  if (total == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  if (tsize == 8)
+    state_layout_kernel<uint64_t><<<grid, 256, 0, s>>>(to_planes, E, NP, NV, (const uint64_t*)src, (uint64_t*)dst, plane);
+  else
+    state_layout_kernel<uint32_t><<<grid, 256, 0, s>>>(to_planes, E, NP, NV, (const uint32_t*)src, (uint32_t*)dst, plane);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_primitives(int prec, int32_t E, int n1, int D, const double* bg, const void* q,
                               int64_t plane, double theta0, double* out, cudaStream_t s) {
   const int NP = D == 3 ? n1 * n1 * n1 : n1 * n1;

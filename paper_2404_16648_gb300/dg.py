@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libdg.so")
 DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_STATE, DG_ERR_TIMEOUT, DG_ERR_UNSUPPORTED = range(7)
 DG_FP64, DG_FP32_PERT = 0, 1
 DG_HOST, DG_DEVICE = 0, 1
+DG_LAYOUT_PLANES, DG_LAYOUT_ELEMENTS = 0, 1
 DG_CRIT_THETA, DG_CRIT_FLAGS = 0, 1
 NUM_INTEGRALS = 5
 STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_OOM", 4: "DG_ERR_STATE",
@@ -93,8 +94,8 @@ def load_library(path=None):
         "dg_num_nodes": (i64, [vp]),
         "dg_get_leaves": (i32, [vp, ctypes.POINTER(ctypes.c_int32), sz]),
         "dg_get_faces": (i32, [vp, ctypes.POINTER(ctypes.c_int64), vp, sz, vp, sz, vp, sz]),
-        "dg_set_state": (i32, [vp, vp, ctypes.c_int]),
-        "dg_get_state": (i32, [vp, vp, ctypes.c_int]),
+        "dg_set_state": (i32, [vp, vp, ctypes.c_int, ctypes.c_int]),
+        "dg_get_state": (i32, [vp, vp, ctypes.c_int, ctypes.c_int]),
         "dg_set_state_async": (i32, [vp, vp, ctypes.c_int, vp]),
         "dg_get_state_async": (i32, [vp, vp, ctypes.c_int, vp]),
         "dg_integrals_async": (i32, [vp, vp, vp]),
@@ -292,19 +293,33 @@ class Mesh:
         return c, m, b
 
     # ------------------------------------------------------------------ state
-    def set_state(self, q):
-        if tuple(q.shape) != self.state_shape:
-            raise ValueError("state shape %s != %s" % (tuple(q.shape), self.state_shape))
+    def _layout(self, layout):
+        """(layout flag, expected shape): "planes" [nv][E][NP] (the library's), "elements"
+        [E][nv][NP]."""
+        if layout == "planes":
+            return DG_LAYOUT_PLANES, self.state_shape
+        if layout == "elements":
+            nv, E, NP = self.state_shape
+            return DG_LAYOUT_ELEMENTS, (E, nv, NP)
+        raise ValueError("layout must be 'planes' or 'elements'")
+
+    def set_state(self, q, layout="planes"):
+        flag, shape = self._layout(layout)
+        if tuple(q.shape) != shape:
+            raise ValueError("state shape %s != %s" % (tuple(q.shape), shape))
         if isinstance(q, np.ndarray) and q.dtype != self.np_dtype:
             raise ValueError("state dtype must be %s" % self.np_dtype)
         p, where = _ptr(q)
-        self._check(self.lib.dg_set_state(self.h, ctypes.c_void_p(p), where))
+        self._check(self.lib.dg_set_state(self.h, ctypes.c_void_p(p), flag, where))
 
-    def get_state(self, out=None):
+    def get_state(self, out=None, layout="planes"):
+        flag, shape = self._layout(layout)
         if out is None:
-            out = np.empty(self.state_shape, dtype=self.np_dtype)
+            out = np.empty(shape, dtype=self.np_dtype)
+        if tuple(out.shape) != shape:
+            raise ValueError("output shape %s != %s" % (tuple(out.shape), shape))
         p, where = _ptr(out)
-        self._check(self.lib.dg_get_state(self.h, ctypes.c_void_p(p), where))
+        self._check(self.lib.dg_get_state(self.h, ctypes.c_void_p(p), flag, where))
         return out
 
     def set_state_async(self, q, stream=None):

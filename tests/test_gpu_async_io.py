@@ -55,3 +55,29 @@ def test_async_io_equals_sync(pkg, precision):
     b.integrals_async(integ)
     torch.cuda.synchronize()
     assert integ[5].item() == 1.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_state_layout_flags(pkg, precision):
+    """dg_set_state / dg_get_state with DG_LAYOUT_ELEMENTS take and give q[e][v][n]: in from host
+    and device arrays it equals the planes layout of the transposed array, out it is the
+    transpose of the planes, bit for bit; an unknown flag is an argument error."""
+    import ctypes
+    import torch
+    m = pkg.Mesh(3, 3, (2, 2, 1), (1000.0, 1000.0, 1000.0), max_level=1, precision=precision)
+    m.adapt(flags=workloads.random_flags(m.num_elements, 0.5, seed=91), buffer=0)
+    dtype = np.float64 if precision == "fp64" else np.float32
+    q = workloads.random_state(m.nv, m.num_elements, m.np_, seed=92, dtype=dtype)
+    qe = np.ascontiguousarray(q.transpose(1, 0, 2))
+    m.set_state(qe, layout="elements")                           # host, element-major
+    assert np.array_equal(m.get_state(), q)
+    assert np.array_equal(m.get_state(layout="elements"), qe)
+    m.set_state(np.zeros_like(q))
+    m.set_state(torch.from_numpy(qe).cuda(), layout="elements")  # device, element-major
+    assert np.array_equal(m.get_state(), q)
+    out = torch.empty(qe.shape, dtype=torch.float64 if precision == "fp64" else torch.float32, device="cuda")
+    m.get_state(out, layout="elements")
+    assert np.array_equal(out.cpu().numpy(), qe)
+    lib = m.lib
+    assert lib.dg_set_state(m.h, ctypes.c_void_p(qe.ctypes.data), 2, 0) == 1
+    assert lib.dg_get_state(m.h, ctypes.c_void_p(qe.ctypes.data), -1, 0) == 1

@@ -109,8 +109,8 @@ def test_null_mesh_handles_are_rejected_before_any_device_call(pkg):
     lib = pkg.load_library()
     buf = (ctypes.c_double * 8)()
     assert lib.dg_get_pprime(None, buf, 0) == DG_ERR_ARG
-    assert lib.dg_get_state(None, buf, 0) == DG_ERR_ARG
-    assert lib.dg_set_state(None, buf, 0) == DG_ERR_ARG
+    assert lib.dg_get_state(None, buf, 0, 0) == DG_ERR_ARG
+    assert lib.dg_set_state(None, buf, 0, 0) == DG_ERR_ARG
     assert lib.dg_step(None, 0.1, 1, None) == DG_ERR_ARG
     assert lib.dg_indicator(None, buf, 8) == DG_ERR_ARG
     assert lib.dg_integrals(None, buf) == DG_ERR_ARG
