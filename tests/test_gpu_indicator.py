@@ -90,11 +90,17 @@ def test_adapt_threshold_tags_equal_indicator_comparison(pkg, dim, N, precision,
     host from dg_indicator: roots at level 0 with one level to go and no buffer, so every tag
     shows in the leaves.  Thresholds: a typical one, every tenth element's indicator value
     itself (that element is not tagged) and the next double below it (it is), on random,
-    bubble and below-FP32-resolution states."""
+    bubble, below-FP32-resolution and NaN / negative-density states."""
     a, b = _twins(pkg, dim, N, precision, theta0)
     E, NP = a.num_elements, (N + 1) ** dim
     states = [workloads.random_state(dim + 2, E, NP, seed=41, theta_scale=0.05),
               workloads.random_state(dim + 2, E, NP, seed=42, rho_scale=1e-12, theta_scale=1e-9)]
+    # elements outside the intervals' range: a NaN node (left out, as the indicator leaves it
+    # out) and a negative density (every node of that element takes the division)
+    odd = workloads.random_state(dim + 2, E, NP, seed=43, theta_scale=0.05)
+    odd[dim + 1, 3, 0] = np.nan
+    odd[0, 5, :] = -3.0
+    states.append(odd)
     for q in states + [None]:
         for m in (a, b):
             if q is None:
@@ -102,8 +108,8 @@ def test_adapt_threshold_tags_equal_indicator_comparison(pkg, dim, N, precision,
             else:
                 _set(m, q)
         ind = a.indicator()
-        thrs = [0.05] + [float(ind[e]) for e in range(0, E, 10)] + \
-               [float(np.nextafter(ind[e], -np.inf)) for e in range(0, E, 10)]
+        edges = sorted(set(range(0, E, 10)) | {3, 5})
+        thrs = [0.05] + [float(ind[e]) for e in edges] + [float(np.nextafter(ind[e], -np.inf)) for e in edges]
         for thr in thrs:
             want = (ind > thr).astype(np.uint8)
             ra = a.adapt(threshold=thr, buffer=0)
