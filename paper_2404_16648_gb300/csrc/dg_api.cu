@@ -315,6 +315,7 @@ void fill_stage_args(const dg_mesh* m, const void* qs, const void* pp_in, const 
   A->rw0d = 1.0 / m->basis.w[0];
   A->rw0f = (float)A->rw0d;
   A->dt = dt; A->ca = ca; A->cb = cb; A->mode = mode; A->variant = m->variant; A->ph = m->ph;
+  A->dtf = (float)dt; A->caf = (float)ca; A->cbf = (float)cb; A->first = ca == 0.0 ? 1 : 0;
   A->plane32 = (int32_t)plane(m);
   A->gammaf = (float)m->ph.gamma; A->gf = (float)m->ph.g;
 }

@@ -276,7 +276,25 @@ struct StageArgs {
   // derivative of a line, which is then scaled by -2/h, so the lift enters as (1/w0)(F* - F)
   double rw0d;
   float rw0f;
+  // dt, ca, cb rounded to FP32 on the host (the FP32 kernels read them without an FP64
+  // conversion, which the FP64 pipe would carry), and ca == 0 (the first stage)
+  float dtf, caf, cbf;
+  int32_t first;
 };
+
+// The stage's Shu-Osher coefficients in T and whether it is the first stage.
+template <class T>
+struct StageCoef {
+  T dt, ca, cb;
+  bool first;
+};
+template <class T> __device__ __forceinline__ StageCoef<T> stage_coef(const StageArgs& A);
+template <> __device__ __forceinline__ StageCoef<float> stage_coef<float>(const StageArgs& A) {
+  return StageCoef<float>{A.dtf, A.caf, A.cbf, A.first != 0};
+}
+template <> __device__ __forceinline__ StageCoef<double> stage_coef<double>(const StageArgs& A) {
+  return StageCoef<double>{A.dt, A.ca, A.cb, A.first != 0};
+}
 
 struct MortarArgs {
   const void* qs;
@@ -460,12 +478,13 @@ __device__ __forceinline__ void stage_body_node(const StageArgs& A, int64_t e0) 
     return;
   }
   T qnew[NV];
-  const T dt = (T)A.dt;
-  if (A.ca == 0.0) {
+  const StageCoef<T> sc = stage_coef<T>(A);
+  const T dt = sc.dt;
+  if (sc.first) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) qnew[v] = q[v] + dt * acc[v];
   } else {
-    const T ca = (T)A.ca, cb = (T)A.cb;
+    const T ca = sc.ca, cb = sc.cb;
     const T* qne = (const T*)A.qn + e * NP;
 #pragma unroll
     for (int v = 0; v < NV; ++v) qnew[v] = ca * qne[v * P + n] + cb * (q[v] + dt * acc[v]);

@@ -349,8 +349,9 @@ stage_kernel_col(const __grid_constant__ StageArgs A) {
       for (int v = 0; v < NV; ++v) oute[v * P + t + NF * k] = acc[v][k];
     return;
   }
-  const T dt = (T)A.dt, ca = (T)A.ca, cb = (T)A.cb;
-  const bool first = A.ca == 0.0;
+  const StageCoef<T> scf = stage_coef<T>(A);
+  const T dt = scf.dt, ca = scf.ca, cb = scf.cb;
+  const bool first = A.first != 0;
   const T* qne = (const T*)A.qn + e * NP;
   T* ppo = (T*)A.pp_out + e * NP;
 #pragma unroll

@@ -232,7 +232,7 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
       for (int k = 0; k < n1; ++k) acc[v][k] = fma(-inv2h[0], sA[v * TV + tix(ci, cj, k)], acc[v][k]);
   }
   // q^n of this column is requested now and used last
-  const bool first = A.ca == 0.0;
+  const bool first = A.first != 0;
   T qn_col[NV][n1];
   if (valid && A.mode == 1 && !first) {
     const T* qne = (const T*)A.qn + e * NP;
@@ -288,7 +288,8 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
       for (int v = 0; v < NV; ++v) oute[v * P + t + NF * k] = acc[v][k];
     return;
   }
-  const T dt = (T)A.dt, ca = (T)A.ca, cb = (T)A.cb;
+  const StageCoef<T> scf = stage_coef<T>(A);
+  const T dt = scf.dt, ca = scf.ca, cb = scf.cb;
   T* ppo = (T*)A.pp_out + e * NP;
 #pragma unroll
   for (int k = 0; k < n1; ++k) {

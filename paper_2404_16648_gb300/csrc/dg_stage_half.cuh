@@ -116,7 +116,7 @@ __device__ __forceinline__ void stage_body_half(const StageArgs& A, int64_t e) {
   const T* qe = (const T*)A.qs + e * NP;
   // ---- q^n of the Shu-Osher combination is read only in the epilogue: one thread asks the L2
   // for the element's planes now (bulk prefetch, no registers or shared memory held)
-  if (tid == 0 && A.mode == 1 && A.ca != 0.0) {
+  if (tid == 0 && A.mode == 1 && !A.first) {
     const T* qne = (const T*)A.qn + e * NP;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -357,7 +357,7 @@ __device__ __forceinline__ void stage_body_half(const StageArgs& A, int64_t e) {
   __syncthreads();
   // ---- horizontal face terms; the tile now holds their lifts [4][NV][NF]
   T* sLift = sA;
-  const bool first = A.ca == 0.0;
+  const bool first = A.first != 0;
   auto horizontal = [&](auto axis, int own_node, int k) {
     constexpr int a = decltype(axis)::value;
     const int n = half_swz<N>(own_node);
@@ -406,7 +406,8 @@ __device__ __forceinline__ void stage_body_half(const StageArgs& A, int64_t e) {
       for (int v = 0; v < NV; ++v) oute[v * P + t + NF * half_row<N>(h, r)] = acc[v][r];
     return;
   }
-  const T dt = (T)A.dt, ca = (T)A.ca, cb = (T)A.cb;
+  const StageCoef<T> scf = stage_coef<T>(A);
+  const T dt = scf.dt, ca = scf.ca, cb = scf.cb;
   const T* qne = (const T*)A.qn + e * NP;
   T* ppo = (T*)A.pp_out + e * NP;
 #pragma unroll

@@ -304,7 +304,7 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
   };
   if (tid == 0) {
-    if (A.mode == 1 && A.ca != 0.0) {
+    if (A.mode == 1 && !A.first) {
       const T* qne = (const T*)A.qn + e * NP;
 #pragma unroll
       for (int v = 0; v < NV; ++v) prefetch_l2(qne + (int64_t)v * P, (int)(NP * sizeof(T)));
@@ -436,8 +436,9 @@ __device__ __forceinline__ void stage_body_line(const StageArgs& A, int64_t e) {
   line_pass<T, N, 2>(ctx, out);
   if (!lok) return;
   T* oute = (T*)A.out + e * NP;
-  const bool first = A.ca == 0.0;
-  const T dt = (T)A.dt, ca = (T)A.ca, cb = (T)A.cb;
+  const bool first = A.first != 0;
+  const StageCoef<T> scf = stage_coef<T>(A);
+  const T dt = scf.dt, ca = scf.ca, cb = scf.cb;
   const T* qne = (const T*)A.qn + e * NP;
   T* ppo = (T*)A.pp_out + e * NP;
 #pragma unroll
