@@ -457,7 +457,10 @@ dg_status launch_rhs_pass(dg_mesh* m, const void* qs, const void* pp_in, const v
     V.plane = plane(m); V.E = (int32_t)m->E; V.G = (int32_t)m->G; V.elem = m->d_elem;
     V.conn = m->d_conn; V.groups = m->d_groups; V.bg = m->d_bg; V.ops = m->d_opsd;
     for (int l = 0; l < dgk::kMaxLevels; ++l)
-      for (int a = 0; a < 3; ++a) V.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+      for (int a = 0; a < 3; ++a) {
+        V.inv2h[l][a] = std::ldexp(2.0 / m->root_h[a], l);
+        V.lift[l][a] = V.inv2h[l][a] / m->basis.w[0];
+      }
     V.nu = m->desc.nu; V.theta0 = m->ph.theta0;
     for (int pass = 1; pass <= 2; ++pass) {
       if (!dgk::launch_viscous_pass(m->D, m->N, V, pass, s))
