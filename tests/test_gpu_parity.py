@@ -354,3 +354,15 @@ def test_box_above_the_neutral_atmosphere_is_rejected(pkg):
     with pytest.raises(DGError):
         pkg.Mesh(2, 3, (2, 2), (10000.0, 31000.0))
     pkg.Mesh(2, 3, (2, 2), (10000.0, 30000.0)).close()
+
+
+def test_mesh_beyond_32_bit_state_offsets_is_rejected(pkg):
+    """The kernels index a state buffer (NV + 1 planes of E (N+1)^d values) with 32-bit offsets:
+    a mesh whose buffer would reach 2^31 values is refused before anything is allocated (80^3
+    roots at N = 8: 6 x 512,000 x 729 > 2^31), and a mesh of the same degree well inside the
+    limit is accepted."""
+    from paper_2404_16648_gb300.dg import DGError
+    with pytest.raises(DGError) as ex:
+        pkg.Mesh(3, 8, (80, 80, 80), (8000.0, 8000.0, 8000.0), precision="fp32")
+    assert ex.value.status == 6
+    pkg.Mesh(3, 8, (8, 8, 8), (8000.0, 8000.0, 8000.0), precision="fp32").close()
