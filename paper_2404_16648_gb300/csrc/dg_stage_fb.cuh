@@ -21,7 +21,9 @@
 // warp runs a face branch for a few of its lanes, and the lift uses the flux the derivative
 // already read instead of evaluating it again at the face node.  The lifts enter the line's
 // derivative unscaled, as -(1/w0)(F* - F) on the low face and +(1/w0)(F* - F) on the high one,
-// so that the -2/h_a scaling of the line makes them (2/h_a)/w0 (F* - F) with the face's sign.
+// so that the -2/h_a scaling of the line makes them (2/h_a)/w0 (F* - F) with the face's sign;
+// their -F parts sit in the derivative table itself (the summation-by-parts form D - M^-1 B,
+// still centro-antisymmetric), so a line adds only its two F* terms.
 //
 // The tile stores node (i, j, k) at ((k n1 + j) (n1 + 1) + i) (3D) or (k (n1 + 1) + i) (2D):
 // one padding word per x line.  For N = 7 in FP64 that makes the x line pass (each lane reading
@@ -50,12 +52,50 @@ __host__ __device__ constexpr size_t fb_smem_bytes() {
   return sizeof(T) * (size_t)EPB * fb_elem_words<T, D, N>();
 }
 
+// The even/odd split (the layout of c_dtab_eo_*) of A + (1/w0) (e_0 e_0^T - e_N e_N^T), with A
+// the antisymmetric part of the LGL derivative: the derivative with the -(1/w0) F_0 and +(1/w0)
+// F_N parts of the two end-node lifts folded in (the summation-by-parts form D - M^-1 B).  The
+// added diagonal keeps the centro-antisymmetry, so only Ae[0][0] and Ao[0][0] differ from the
+// plain split, each by 1/(2 w0), and a line adds -(1/w0) F*_lo and +(1/w0) F*_hi alone.  Odd N
+// only; per translation unit, filled by upload_dtab_fb() of the unit before its first launch.
+static __constant__ float c_dtab_eob_f[kDTabSize];
+static __constant__ double c_dtab_eob_d[kDTabSize];
+
+static inline cudaError_t upload_dtab_fb(const double* all) {
+  double eo[kDTabSize];
+  float eof[kDTabSize];
+  for (int i = 0; i < kDTabSize; ++i) eo[i] = 0.0;
+  for (int N = 1; N <= 8; N += 2) {
+    const int o = dtab_offset(N), n1 = N + 1, K2 = n1 / 2;
+    auto anti = [&](int m, int i) { return 0.5 * (all[o + m * n1 + i] - all[o + (N - m) * n1 + (N - i)]); };
+    for (int i = 0; i < K2; ++i)
+      for (int m = 0; m < K2; ++m) {
+        eo[o + i * K2 + m] = 0.5 * (anti(i, m) + anti(i, N - m));
+        eo[o + K2 * K2 + i * K2 + m] = 0.5 * (anti(i, m) - anti(i, N - m));
+      }
+    // w0 = 2 / (N (N+1)), rounded as the LGL weights are, so that 1/w0 here is the 1/w0 the
+    // kernels multiply F* by
+    const double half_rw0 = 0.5 * (1.0 / (2.0 / (N * (N + 1.0))));
+    eo[o] += half_rw0;
+    eo[o + K2 * K2] += half_rw0;
+  }
+  for (int i = 0; i < kDTabSize; ++i) eof[i] = (float)eo[i];
+  cudaError_t e = cudaMemcpyToSymbol(c_dtab_eob_d, eo, sizeof(eo));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_dtab_eob_f, eof, sizeof(eof));
+}
+template <class T> __device__ __forceinline__ T dtab_eob(int i);
+template <> __device__ __forceinline__ float dtab_eob<float>(int i) { return c_dtab_eob_f[i]; }
+template <> __device__ __forceinline__ double dtab_eob<double>(int i) { return c_dtab_eob_d[i]; }
+
 template <class T> __device__ __forceinline__ T rw0_of(const StageArgs& A);
 template <> __device__ __forceinline__ float rw0_of<float>(const StageArgs& A) { return A.rw0f; }
 template <> __device__ __forceinline__ double rw0_of<double>(const StageArgs& A) { return A.rw0d; }
 
-// Derivative of one line of n1 values r (unscaled, D r), in place into out; the lifts of its
-// two end nodes added as -rw0 (Flo - r[0]) and +rw0 (Fhi - r[N]).
+// Derivative of one line of n1 values r (unscaled, D r) into out, with the lifts of its two end
+// nodes, -rw0 (Flo - r[0]) and +rw0 (Fhi - r[N]).  For even n1 the -rw0 r[0] and +rw0 r[N] parts
+// come with the derivative from the boundary-folded even/odd table, and only the F* terms are
+// added here.
 template <class T, int N>
 __device__ __forceinline__ void fb_line(const T (&r)[N + 1], T Flo, T Fhi, T rw0, T (&out)[N + 1]) {
   constexpr int n1 = N + 1;
@@ -72,12 +112,14 @@ __device__ __forceinline__ void fb_line(const T (&r)[N + 1], T Flo, T Fhi, T rw0
       T se = (T)0, so = (T)0;
 #pragma unroll
       for (int m = 0; m < K2; ++m) {
-        se = fma(dtab_eo<T>(dtab_offset(N) + i * K2 + m), Ev[m], se);
-        so = fma(dtab_eo<T>(dtab_offset(N) + K2 * K2 + i * K2 + m), Ov[m], so);
+        se = fma(dtab_eob<T>(dtab_offset(N) + i * K2 + m), Ev[m], se);
+        so = fma(dtab_eob<T>(dtab_offset(N) + K2 * K2 + i * K2 + m), Ov[m], so);
       }
       out[i] = add_rn(se, so);
       out[N - i] = sub_rn(so, se);
     }
+    out[0] = fma(-rw0, Flo, out[0]);
+    out[N] = fma(rw0, Fhi, out[N]);
   } else {
 #pragma unroll
     for (int i = 0; i < n1; ++i) {
@@ -86,9 +128,9 @@ __device__ __forceinline__ void fb_line(const T (&r)[N + 1], T Flo, T Fhi, T rw0
       for (int m = 0; m < n1; ++m) s = fma(dtab<T>(dtab_offset(N) + i * n1 + m), r[m], s);
       out[i] = s;
     }
+    out[0] = fma(-rw0, sub_rn(Flo, r[0]), out[0]);
+    out[N] = fma(rw0, sub_rn(Fhi, r[N]), out[N]);
   }
-  out[0] = fma(-rw0, sub_rn(Flo, r[0]), out[0]);
-  out[N] = fma(rw0, sub_rn(Fhi, r[N]), out[N]);
 }
 
 template <class T, int D, int N, int EPB>
@@ -163,12 +205,18 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
     for (int v = 0; v < NV; ++v) { Fv[0][v] = (T)0; Fv[1][v] = (T)0; }
   }
   cp_async_commit();
-  const T g = sizeof(T) == 4 ? (T)A.gf : (T)A.ph.g;
+  // the accumulators hold the right-hand side times sc, the factor the Shu-Osher combination
+  // applies to it (1 for a plain right-hand side, dt in the first stage, cb dt after it): the
+  // scale rides on the -2/h factors and on g, and the combination saves a multiply per value
+  const StageCoef<T> scf = stage_coef<T>(A);
+  const bool first = scf.first;
+  const T sc = A.mode == 0 ? (T)1 : (first ? scf.dt : scf.cb * scf.dt);
+  const T g = (sizeof(T) == 4 ? (T)A.gf : (T)A.ph.g) * sc;
   const T rw0 = rw0_of<T>(A);
   T inv2h[D];
   const int level = valid ? A.elem[e * 4] : 0;
 #pragma unroll
-  for (int a = 0; a < D; ++a) inv2h[a] = valid ? inv2h_of<T>(A, level, a) : (T)0;
+  for (int a = 0; a < D; ++a) inv2h[a] = valid ? inv2h_of<T>(A, level, a) * sc : (T)0;
   cp_async_wait_all();
   __syncthreads();
   // ---- column pass: x fluxes to the tile, the vertical derivative and the vertical lifts
@@ -187,7 +235,7 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
                                  : NodeBg<T>{(T)1, (T)1, (T)1};
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v][k] = (T)0;
-      acc[D][k] = -(q[0] * g);               // buoyancy -rho' g on the vertical momentum
+      acc[D][k] = -(q[0] * g);               // buoyancy -rho' g (times sc) on the vertical momentum
       const NodeDer<T> nd = node_der<T, D>(q, bg);
       rinvc[k] = nd.rinv;
       T F[NV];
@@ -232,7 +280,6 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
       for (int k = 0; k < n1; ++k) acc[v][k] = fma(-inv2h[0], sA[v * TV + tix(ci, cj, k)], acc[v][k]);
   }
   // q^n of this column is requested now and used last
-  const bool first = A.first != 0;
   T qn_col[NV][n1];
   if (valid && A.mode == 1 && !first) {
     const T* qne = (const T*)A.qn + e * NP;
@@ -288,8 +335,7 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
       for (int v = 0; v < NV; ++v) oute[v * P + t + NF * k] = acc[v][k];
     return;
   }
-  const StageCoef<T> scf = stage_coef<T>(A);
-  const T dt = scf.dt, ca = scf.ca, cb = scf.cb;
+  const T ca = scf.ca, cb = scf.cb;
   T* ppo = (T*)A.pp_out + e * NP;
 #pragma unroll
   for (int k = 0; k < n1; ++k) {
@@ -297,10 +343,10 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
     T qnew[NV];
     if (first) {   // uniform over the grid
 #pragma unroll
-      for (int v = 0; v < NV; ++v) qnew[v] = fma(dt, acc[v][k], sQ[v * NP + n]);
+      for (int v = 0; v < NV; ++v) qnew[v] = add_rn(sQ[v * NP + n], acc[v][k]);
     } else {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) qnew[v] = fma(ca, qn_col[v][k], cb * fma(dt, acc[v][k], sQ[v * NP + n]));
+      for (int v = 0; v < NV; ++v) qnew[v] = fma(ca, qn_col[v][k], fma(cb, sQ[v * NP + n], acc[v][k]));
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];

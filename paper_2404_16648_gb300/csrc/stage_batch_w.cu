@@ -4,7 +4,10 @@
 #include "dg_launch.hpp"
 
 namespace dgk {
-cudaError_t init_stage_batch_w(const double* dtab_all) { return upload_dtab(dtab_all); }
+cudaError_t init_stage_batch_w(const double* dtab_all) {
+  const cudaError_t e = upload_dtab(dtab_all);
+  return e != cudaSuccess ? e : upload_dtab_fb(dtab_all);
+}
 cudaError_t launch_batch_w(const BatchArgs& B, int grid, size_t smem, cudaStream_t s) {
   return launch_batch<2>(B, grid, smem, s);
 }
