@@ -67,7 +67,9 @@ static inline cudaError_t upload_dtab_fb(const double* all) {
   for (int i = 0; i < kDTabSize; ++i) eo[i] = 0.0;
   for (int N = 1; N <= 8; N += 2) {
     const int o = dtab_offset(N), n1 = N + 1, K2 = n1 / 2;
-    auto anti = [&](int m, int i) { return 0.5 * (all[o + m * n1 + i] - all[o + (N - m) * n1 + (N - i)]); };
+    auto anti = [&](int m, int i) {
+      return 0.5 * (all[o + m * n1 + i] - all[o + (N - m) * n1 + (N - i)]);
+    };
     for (int i = 0; i < K2; ++i)
       for (int m = 0; m < K2; ++m) {
         eo[o + i * K2 + m] = 0.5 * (anti(i, m) + anti(i, N - m));
@@ -87,6 +89,38 @@ static inline cudaError_t upload_dtab_fb(const double* all) {
 template <class T> __device__ __forceinline__ T dtab_eob(int i);
 template <> __device__ __forceinline__ float dtab_eob<float>(int i) { return c_dtab_eob_f[i]; }
 template <> __device__ __forceinline__ double dtab_eob<double>(int i) { return c_dtab_eob_d[i]; }
+
+// P' of the new state (Sec. 2.1, P' = P_bar ((1 + x)^gamma - 1), x = Theta'/Theta_bar), FP64:
+// the binomial series of pressure_pert with as many terms K as |x| needs instead of six for all
+// |x| < 2^-10 and eleven up to 2^-5.  For 1 < gamma <= 2, |binom(gamma, K+1)| / gamma <=
+// 1 / (K (K+1)), so the first omitted term, relative to the leading one gamma x, stays below
+// 2^-54 / 6 (K = 2, |x| < 2^-27), 2^-54 / 12 (K = 3, < 2^-18), 2^-52 / 20 (K = 4, < 2^-13),
+// 2^-50 / 30 (K = 5, < 2^-10), 2^-54 / 42 (K = 6, < 2^-9), 2^-49 / 56 (K = 7, < 2^-7), all under
+// a third of the result's rounding; |x| >= 2^-7 (and a gamma outside (1, 2], tiers = false)
+// take pressure_pert itself.  The tier is picked from the high word of x by integer compares,
+// which leaves the FP64 pipe to the series.  pb is P_bar at the node's height.
+__device__ __forceinline__ double pprime_tiered(double tp, double invTb, double pb, bool tiers,
+                                                const PhysC& ph) {
+  const double x = __dmul_rn(tp, invTb);
+  const int hx = __double2hiint(x) & 0x7fffffff;   // |x| < 2^-m  <=>  hx < (1023 - m) << 20
+  if (!tiers || hx >= 0x3F800000) return pressure_pert<kSeries>(tp, invTb, pb, ph);   // 2^-7
+  const double* b = ph.binom;                      // b[k - 1] = binom(gamma, k)
+  double p;                                        // sum_{k=1..K} b[k - 1] x^(k - 1)
+  if (hx < 0x3E400000) {                           // 2^-27
+    p = fma(b[1], x, b[0]);
+  } else if (hx < 0x3ED00000) {                    // 2^-18
+    p = fma(fma(b[2], x, b[1]), x, b[0]);
+  } else if (hx < 0x3F200000) {                    // 2^-13
+    p = fma(fma(fma(b[3], x, b[2]), x, b[1]), x, b[0]);
+  } else if (hx < 0x3F500000) {                    // 2^-10
+    p = fma(fma(fma(fma(b[4], x, b[3]), x, b[2]), x, b[1]), x, b[0]);
+  } else if (hx < 0x3F600000) {                    // 2^-9
+    p = fma(fma(fma(fma(fma(b[5], x, b[4]), x, b[3]), x, b[2]), x, b[1]), x, b[0]);
+  } else {
+    p = fma(fma(fma(fma(fma(fma(b[6], x, b[5]), x, b[4]), x, b[3]), x, b[2]), x, b[1]), x, b[0]);
+  }
+  return __dmul_rn(pb, __dmul_rn(p, x));
+}
 
 template <class T> __device__ __forceinline__ T rw0_of(const StageArgs& A);
 template <> __device__ __forceinline__ float rw0_of<float>(const StageArgs& A) { return A.rw0f; }
@@ -336,6 +370,9 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
     return;
   }
   const T ca = scf.ca, cb = scf.cb;
+  // 1 < gamma <= 2 by the bit patterns (positive doubles order as their integers)
+  const long long gbits = __double_as_longlong(A.ph.gamma);
+  const bool tiers = gbits > 0x3FF0000000000000LL && gbits <= 0x4000000000000000LL;
   T* ppo = (T*)A.pp_out + e * NP;
 #pragma unroll
   for (int k = 0; k < n1; ++k) {
@@ -350,7 +387,10 @@ __device__ __forceinline__ void stage_body_fb(const StageArgs& A, int64_t e0) {
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v) oute[v * P + n] = qnew[v];
-    ppo[n] = pprime_of<T>(qnew[D + 1], sBg[k * 4 + 3], A.bg + ((size_t)e * n1 + k) * 4, sBc + k, A.ph);
+    if constexpr (sizeof(T) == 8)
+      ppo[n] = pprime_tiered(qnew[D + 1], sBg[k * 4 + 3], sBg[k * 4 + 2], tiers, A.ph);
+    else
+      ppo[n] = pprime_of<T>(qnew[D + 1], sBg[k * 4 + 3], A.bg + ((size_t)e * n1 + k) * 4, sBc + k, A.ph);
   }
 }
 
