@@ -22,8 +22,8 @@
 // already read instead of evaluating it again at the face node.  The lifts enter the line's
 // derivative unscaled, as -(1/w0)(F* - F) on the low face and +(1/w0)(F* - F) on the high one,
 // so that the -2/h_a scaling of the line makes them (2/h_a)/w0 (F* - F) with the face's sign;
-// their -F parts sit in the derivative table itself (the summation-by-parts form D - M^-1 B,
-// still centro-antisymmetric), so a line adds only its two F* terms.
+// for odd N their -F parts sit in the derivative table itself (the summation-by-parts form
+// D - M^-1 B, still centro-antisymmetric), so a line adds only its two F* terms.
 //
 // The tile stores node (i, j, k) at ((k n1 + j) (n1 + 1) + i) (3D) or (k (n1 + 1) + i) (2D):
 // one padding word per x line.  For N = 7 in FP64 that makes the x line pass (each lane reading
