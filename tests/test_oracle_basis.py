@@ -97,3 +97,66 @@ def test_lumped_restriction_is_not_identity():
     lumped = [0.5 * np.linalg.solve(W, b.P[c].T @ W) for c in (0, 1)]
     err = np.abs(lumped[0] @ b.P[0] + lumped[1] @ b.P[1] - np.eye(5)).max()
     assert err > 0.1
+
+
+def test_legendre_closed_forms():
+    """P_2..P_4 and their derivatives written out; P_n(1) = 1 and P_n'(1) = n (n+1) / 2."""
+    x = np.linspace(-1.0, 1.0, 13)
+    closed = {2: ((3 * x**2 - 1) / 2, 3 * x),
+              3: ((5 * x**3 - 3 * x) / 2, (15 * x**2 - 3) / 2),
+              4: ((35 * x**4 - 30 * x**2 + 3) / 8, (140 * x**3 - 60 * x) / 8)}
+    for n, (p, dp) in closed.items():
+        got_p, got_dp = basis.legendre_and_derivative(n, x)
+        np.testing.assert_allclose(got_p, p, atol=1e-15)
+        np.testing.assert_allclose(got_dp, dp, atol=1e-14)
+    for n in range(0, 10):
+        p1, dp1 = basis.legendre_and_derivative(n, np.array([1.0]))
+        assert abs(p1[0] - 1.0) < 1e-15 and abs(dp1[0] - n * (n + 1) / 2) < 1e-12
+
+
+def test_barycentric_weights_closed_form():
+    """On {-1, 0, 1}: 1 / ((x_j - x_k)(x_j - x_l)) = 1/2, -1, 1/2."""
+    np.testing.assert_allclose(basis.barycentric_weights(np.array([-1.0, 0.0, 1.0])), [0.5, -1.0, 0.5])
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_lagrange_matrix_cardinal_and_exact(N):
+    """l_j(x_i) = delta_ij, and sum_j p(x_j) l_j(x) = p(x) for every polynomial of degree <= N."""
+    x, _ = basis.lgl_nodes_weights(N)
+    np.testing.assert_allclose(basis.lagrange_matrix(x, x), np.eye(N + 1), atol=1e-14)
+    y = np.linspace(-1.0, 1.0, 17)
+    L = basis.lagrange_matrix(x, y)
+    for k in range(N + 1):
+        np.testing.assert_allclose(L @ x**k, y**k, atol=1e-13)
+    # degree N + 1 is not reproduced
+    assert np.abs(L @ x**(N + 1) - y**(N + 1)).max() > 1e-6
+
+
+@pytest.mark.parametrize("n", range(1, 10))
+def test_gauss_legendre_exactness(n):
+    """n points integrate x^k exactly for k <= 2n - 1."""
+    g, gw = basis.gauss_legendre(n)
+    for k in range(2 * n):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        assert abs(np.dot(gw, g**k) - exact) < 1e-13
+
+
+@pytest.mark.parametrize("N", range(1, 9))
+def test_mass_matrices_row_and_column_sums(N):
+    """M 1 = w (the LGL rule is exact on the degree-N l_i), 1^T M 1 = 2, M symmetric positive
+    definite; the mixed matrices S_c 1 = w (the parent basis sums to 1) and
+    sum_c 1^T S_c = 2 w^T (the two children cover the parent, each at half scale); the entries of
+    M against a 30-point Gauss rule."""
+    x, w = basis.lgl_nodes_weights(N)
+    M = basis.exact_mass_matrix(x)
+    np.testing.assert_allclose(M @ np.ones(N + 1), w, atol=1e-14)
+    assert abs(M.sum() - 2.0) < 1e-13
+    np.testing.assert_allclose(M, M.T, atol=1e-15)
+    assert np.linalg.eigvalsh(M).min() > 0.0
+    g, gw = np.polynomial.legendre.leggauss(30)
+    L = basis.lagrange_matrix(x, g)
+    np.testing.assert_allclose(M, L.T @ (gw[:, None] * L), atol=1e-14)
+    S = [basis.mixed_mass_child(x, c) for c in (0, 1)]
+    for Sc in S:
+        np.testing.assert_allclose(Sc @ np.ones(N + 1), w, atol=1e-14)
+    np.testing.assert_allclose(np.ones(N + 1) @ (S[0] + S[1]), 2 * w, atol=1e-13)
