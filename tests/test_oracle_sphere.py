@@ -177,3 +177,25 @@ def test_planted_mistakes_break_conservation():
         sphere._scale = orig
     err = np.abs(m1.integrals(q1) - m0.integrals(q0)) / np.abs(m0.integrals(q0))
     assert err.max() > 1e-6
+
+
+def test_tile_points_lie_on_the_sphere_and_cover_it_once():
+    """Every tile point has norm r; tile t's centre is its axis (+x, +y, -x, -y, +z, -z); inside
+    a tile the axis of the centre is the point's dominant one (the six tiles do not overlap);
+    along the equator belt the edge alpha = pi/4 of tile t is the edge alpha = -pi/4 of tile
+    t + 1 (mod 4) at the same beta."""
+    axes = np.array([[1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float)
+    g = np.random.default_rng(3)
+    a, b = g.uniform(-math.pi / 4, math.pi / 4, (2, 200)) * 0.999
+    for t in range(6):
+        p = sphere.tile_point(t, a, b, R)
+        np.testing.assert_allclose(np.linalg.norm(p, axis=-1), R, rtol=1e-15)
+        np.testing.assert_allclose(sphere.tile_point(t, 0.0, 0.0, R), R * axes[t], atol=1e-9)
+        dom = np.argmax(np.abs(p), axis=-1)
+        sgn = np.sign(p[np.arange(len(dom)), dom])
+        np.testing.assert_array_equal(dom, np.argmax(np.abs(axes[t])))
+        np.testing.assert_array_equal(sgn, axes[t].sum())
+    for t in range(4):
+        edge = np.full_like(b, math.pi / 4)
+        np.testing.assert_allclose(sphere.tile_point(t, edge, b, R),
+                                   sphere.tile_point((t + 1) % 4, -edge, b, R), atol=1e-8)

@@ -70,3 +70,21 @@ def test_convergence_against_exact_operator(N, order):
         errs.append(np.abs(V[1] - exact).max() / np.abs(exact).max())
     rate = math.log2(errs[-2] / errs[-1])
     assert rate >= order - 0.3, (errs, rate)
+
+
+def test_viscous_primitives_against_their_definition():
+    """phi = (U / rho, theta') with rho = rho_bar + rho' and theta' defined as
+    (Theta_bar + Theta') / (rho_bar + rho') - theta0; the oracle's form (Theta' - theta0 rho') / rho
+    is its rewriting for Theta_bar = rho_bar theta0, so both agree to rounding."""
+    m = _hanging((3, 3), 3, (900.0, 900.0), 1)
+    rb, Tb, _ = m.bg
+    g = np.random.default_rng(5)
+    q = np.empty((4, m.E, m.np_))
+    q[0] = 1e-3 * g.standard_normal((m.E, m.np_))
+    q[1:3] = 2.0 * g.standard_normal((2, m.E, m.np_))
+    q[3] = 0.5 * g.standard_normal((m.E, m.np_))
+    phi, rho = dg.viscous_primitives(m, q)
+    np.testing.assert_allclose(rho, rb + q[0], rtol=1e-15)
+    np.testing.assert_allclose(phi[:2], q[1:3] / (rb + q[0]), rtol=1e-14)
+    theta = (Tb + q[3]) / (rb + q[0]) - K.theta0
+    np.testing.assert_allclose(phi[2], theta, rtol=0, atol=1e-11)
