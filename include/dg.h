@@ -349,8 +349,8 @@ const char* dg_batch_last_error(const dg_batch* batch);
  * registers (3 and 4: 3D with odd N; other shapes run layout 2), 5 = the Rusanov flux of every
  * conforming and wall face computed once per face by a face kernel before the stage kernel,
  * whose volume term runs as a column pass and one line pass per horizontal axis, each line
- * thread lifting the two faces at its ends (a partitioned mesh runs layout 2 instead).  Default: 4 for FP32 3D meshes, 5 for
- * FP64 Euler meshes, 2 otherwise.  All compute the same operator; the option exists for tuning
+ * thread lifting the two faces at its ends (a partitioned mesh runs layout 2 instead).
+ * Default: 4 for FP32 3D meshes, 5 for FP64 Euler meshes, 2 otherwise.  All compute the same operator; the option exists for tuning
  * and cross-checking. */
 enum { DG_OPT_STAGE_KERNEL = 1, DG_OPT_FAIL_NEXT_ADAPT = 2 };
 /* DG_OPT_FAIL_NEXT_ADAPT is a host-side failure injection for tests of the regrid's error path
