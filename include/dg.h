@@ -468,7 +468,7 @@ dg_status dg_stage_buffer(dg_mesh* mesh, int32_t index, void** q, void** pp);
  * `stage` before each call.  Asynchronous on `stream` (NULL: the mesh stream). */
 dg_status dg_stage(dg_mesh* mesh, int32_t stage, double dt, void* stream);
 
-/* ---- Cubed-sphere solution transfer (Sec. 3.4 "Considerations for spherical geometry",
+/* ---- Cubed-sphere solution transfer (Sec. 3.4, spherical geometry;
  * App. B).  The sphere of radius r is six equiangular gnomonic tiles laid side by side in one
  * 2D forest of 6n x n roots (tile t = root column / n; dg_forest_* give the leaves and the
  * regrid map); every element is an isoparametric quadrilateral of degree N.  The layout's 2:1

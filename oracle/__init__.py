@@ -7,7 +7,7 @@ no code with the CUDA library in ``paper_2404_16648_gb300`` and never imports it
 Modules (each function cites the passage of arXiv 2404.16648 it restates):
 
 * ``basis``   -- LGL nodes/weights, collocation derivative, L2 projection matrices
-                 (Sec. 3.3, "Solution transfer and non-conformal face flux computations").
+                 (Sec. 3.3: solution transfer and fluxes on non-conforming faces).
 * ``physics`` -- Euler fluxes, equation of state, hydrostatic background, Rusanov flux
                  (Sec. 2.1 Eq. 1 / Eq. "eulervector", Sec. 2.2, Sec. 4.3).
 * ``forest``  -- forest of quad/oct-trees with active-leaf storage, regrid with buffer B,

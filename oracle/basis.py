@@ -1,7 +1,7 @@
 """Reference-element operators of the nodal dGSEM (oracle; test infrastructure only).
 
-Restates, in plain FP64 numpy, the one-dimensional objects that arXiv 2404.16648 builds
-"once for the reference element" and applies "in a tensor-product fashion" (Sec. 3.3):
+Restates, in plain FP64 numpy, the one-dimensional objects that arXiv 2404.16648 builds a
+single time on the reference element and applies axis by axis as tensor products (Sec. 3.3):
 
 * Legendre-Gauss-Lobatto (LGL) nodes and weights of degree N (the collocation points named
   in Sec. 3.3; the diagonal LGL mass matrix of Sec. 2.2);
@@ -12,7 +12,7 @@ Restates, in plain FP64 numpy, the one-dimensional objects that arXiv 2404.16648
   (Sec. 3.3, second mortar projection).  The same matrices serve refinement (parent -> child)
   and coarsening (children -> parent), as Sec. 3.3 states.
 
-Reading (ambiguity): Sec. 3.3 says coarsening is obtained by "integrating over the LGL points"
+Reading (ambiguity): Sec. 3.3 describes coarsening as an integration over the LGL points
 while the mortar formulas use mass matrices M.  The oracle takes M as the *exact* mass matrix
 (Gauss-Legendre with N+2 points), which makes coarsen(refine(q)) = q exactly and conserves the
 LGL-discrete mass.

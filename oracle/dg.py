@@ -19,7 +19,7 @@ Restates arXiv 2404.16648 in plain FP64 numpy:
 Readings: the projected coarse state on a mortar is completed with the fine side's background
 (the background is a function of z, and the mortar points are the fine face's points); the
 initial bubble keeps the pressure hydrostatic (Theta' = 0, rho' = -rho_bar theta'/(theta0 +
-theta')) so "the initial conditions ensure hydrostatic balance" (Sec. 4.3).
+theta')), the reading taken here of the balanced initial conditions of Sec. 4.3.
 
 Node numbering inside an element: i_0 + (N+1) i_1 + (N+1)^2 i_2 (axis 0 fastest); the state is
 an array [nv, E, (N+1)^d].  Pinned by tests/test_oracle_dg.py (rest state, free stream with
@@ -438,7 +438,8 @@ def rff_theta(mesh, sigma, kvec, phase):
 
 def state_from_theta(mesh, th):
     """Hydrostatic-pressure initial state for a theta' field: Theta' = 0, U = 0,
-    rho' = -rho_bar theta' / (theta0 + theta') (reading O-4 of the initial balance)."""
+    rho' = -rho_bar theta' / (theta0 + theta'): the pressure stays hydrostatic, which is how the
+    paper's balanced initial conditions (Sec. 4.3) are read here."""
     rb, _, _ = mesh.bg
     q = np.zeros((mesh.nv, mesh.E, mesh.np_), dtype=np.result_type(th, np.float64))
     q[0] = -rb * th / (mesh.K.theta0 + th)

@@ -2,7 +2,7 @@
 
 Restates the tree-based AMR bookkeeping of arXiv 2404.16648:
 
-* every base (coarse-mesh) cell is the root of a tree ("forest of trees", Sec. 3.1);
+* every base (coarse-mesh) cell is the root of its own tree, so the mesh is a forest (Sec. 3.1);
 * only active leaves are stored; a parent is deleted once its children exist and the
   children are deleted when they are merged back (Sec. 3.1);
 * regrid every T steps with a buffer of B cells between the tagged feature and the

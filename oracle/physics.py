@@ -63,7 +63,8 @@ def eos_pressure(Theta, K):
 
 
 def background(z, K):
-    """(rho_bar, Theta_bar, p_bar) at heights z; p_bar := P(Theta_bar) (reading O-3)."""
+    """(rho_bar, Theta_bar, p_bar) at heights z; p_bar := P(Theta_bar), so that P' is exactly 0
+    at rest (the discrete hydrostatic balance as read here; the paper does not define it)."""
     rb = background_density(z, K)
     Tb = rb * K.theta0
     pb = eos_pressure(Tb, K)

@@ -1,6 +1,6 @@
 """Solution transfer on a cubed sphere (oracle; test infrastructure only).
 
-Restates Sec. 3.4 ("Considerations for spherical geometry") and Appendix B of arXiv 2404.16648
+Restates Sec. 3.4 (spherical geometry) and Appendix B of arXiv 2404.16648
 for the transfer of nodal fields between parent and child elements on a curved surface:
 
 * the cubed sphere: six tiles, each an equiangular gnomonic map of the square

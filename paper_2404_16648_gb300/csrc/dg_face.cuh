@@ -74,7 +74,7 @@ __device__ __forceinline__ void face_flux_node(const FaceArgs& A, int64_t slot, 
     const NodeDer<T> nd = node_der<T, D>(q, bg);
     flux_axis<T, D>(q, nd, pp, a, Fo);
     const T so = wave_speed<T>(q, nd, bg, pp, a, gamma);
-    // mirror state: same Theta, rho and P', normal momentum negated (reading R5)
+    // no-flux wall as a mirror state: same Theta, rho and P', normal momentum negated
 #pragma unroll
     for (int v = 0; v < NV; ++v) qo[v] = q[v];
     qo[1 + a] = -q[1 + a];

@@ -1,4 +1,4 @@
-// Solution transfer on the cubed sphere (Sec. 3.4 "Considerations for spherical geometry",
+// Solution transfer on the cubed sphere (Sec. 3.4, spherical geometry;
 // Appendix B): dg_sphere_geometry and dg_sphere_transfer of include/dg.h.
 //
 // The sphere is six equiangular gnomonic tiles laid side by side in one 2D forest of 6n x n

@@ -1,6 +1,6 @@
 // Host forest of quad/oct-trees for the GB300 dGSEM library.
 //
-// Sec. 3.1 of arXiv 2404.16648: every base cell is the root of a tree ("forest of trees") and
+// Sec. 3.1 of arXiv 2404.16648: every base cell is the root of its own tree (a forest), and
 // only active leaves are stored.  Sec. 3.2.1: regrid every T steps with a buffer of B cells.
 // Sec. 4.3: 2:1 balance across all levels.  Sec. 3.3: conforming faces and hanging faces with
 // 2^(d-1) mortars.  The integer work runs on the host; its outputs (leaf order, face kinds,
