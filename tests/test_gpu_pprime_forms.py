@@ -1,4 +1,4 @@
-"""P' of the FP32 path (reading of "FP64 for the pressure perturbation": P' carried to FP64
+"""P' of the FP32 path (FP64 is kept for the pressure perturbation, read as: P' carried to FP64
 accuracy before its FP32 rounding).  The line stage kernel (layout 4) forms P' of its output by a
 split-FP32 product, the half-column layout and the P' kernel in FP64 arithmetic.  On the same FP32
 state the P' planes must agree bit for bit for layout 3 and within one ulp, on a small fraction of
